@@ -1,0 +1,650 @@
+/*
+ * Oracle for the dust drag-coupling step of Mignone, Flock & Vaidya,
+ * "A Particle Module for the PLUTO Code: III - Dust" (arXiv:1908.10793).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, double-precision
+ * CPU restatement of the method, used by the tests, by the smoke check and
+ * by the CPU-baseline leg of the benchmark.  Nothing on the product path
+ * links, loads or calls it, and it shares no code, header or table with the
+ * CUDA library.
+ *
+ * One call of oracle_step() advances every active grain by one exponential
+ * midpoint (EM) drift-kick-drift step (Sec. 3.2.2, Eq. exp_midpoint; App. B)
+ * and deposits the drag back-reaction on the grid (Eq. dust_feedback_final),
+ * grain by grain, in the order the paper states the algorithm:
+ *
+ *   1. half drift of the coordinates          (Eq. exp_midpoint; Eqs. B.1 drift)
+ *   2. host zone and 1-D weights at x^{n+1/2}  (Sec. 3.4, Eqs. weight, b0, b1,
+ *                                              CIC/TSC_cylindrical, App. C)
+ *   3. gather of gas rho and momentum-like velocity (Eq. Delta_vp)
+ *   4. E = exp(-dt/tau), h1 = tau (1 - exp(-dt/tau))   (Eqs. phi1, h1)
+ *   5. kick, per geometry                      (Eq. kick_modified; App. B.1, B.2)
+ *   6. second half drift with the midpoint metric factors
+ *   7. boundaries (periodic, shear-periodic, outflow)
+ *   8. deposit  -m W (dp - dt a)  and its energy   (Eq. dust_feedback_final)
+ *
+ * The deposit is accumulated densely in double precision; the optional
+ * feedback update of the gas momentum (corrector term of the RK2 step,
+ * Sec. 3.1) is applied after all grains.
+ *
+ * Readings of points the paper leaves open are listed in the design notes and
+ * are repeated where they are used below.
+ *
+ * Parity status: the energy channel of the deposit, the weights on
+ * non-uniform radial grids, the theta-TSC weights and the shear-periodic
+ * y-shift follow stated readings (see the notes at each function); the tests
+ * pin them only by quadrature of the defining integral, by algebraic
+ * identities and by special cases.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OG_CARTESIAN 0
+#define OG_SHEARING_BOX 1
+#define OG_CYLINDRICAL 2
+#define OG_SPHERICAL 3
+
+#define OB_PERIODIC 0
+#define OB_OUTFLOW 1
+
+#define OW_CIC 0
+#define OW_TSC 1
+
+#define OT_CONST 0   /* tau_s given directly                                  */
+#define OT_STOKES 1  /* St given: tau_s = St / Omega_K at the grain           */
+#define OT_EPSTEIN 2 /* tau_s = value / rho_gathered  (Sec. 2, tau_s ~ 1/rho) */
+
+/* 1-D weight kinds (which formula of Sec. 3.4 / App. C is used). */
+#define W1_CART_CIC 0
+#define W1_CART_TSC 1
+#define W1_CYL_R_CIC 2
+#define W1_CYL_R_TSC 3
+#define W1_SPH_R_CIC 4
+#define W1_SPH_R_TSC 5
+#define W1_SPH_TH_CIC 6
+#define W1_SPH_TH_TSC 7
+
+typedef struct {
+    int geom;             /* OG_*                                             */
+    int fargo;            /* shearing box: 1 = orbital-advection residual form */
+    double omega, q;      /* shearing box Omega and shear parameter q         */
+    double gm;            /* point-mass GM (cylindrical / spherical)          */
+    int vertical_gravity; /* SB: -Omega^2 z; cylindrical: z part of GM gravity */
+    int n[3];             /* zones per direction (1 = direction not gridded)  */
+    const double *edges[3]; /* n[d]+1 increasing zone edges per direction     */
+    int bc[3];            /* OB_* per direction                               */
+    int weight;           /* OW_CIC or OW_TSC                                 */
+    int n_species;
+    const double *sp_mass;
+    const int *sp_tau_mode;
+    const double *sp_tau;
+    int feedback_apply;   /* 1: add the deposit to the gas momentum           */
+} oracle_problem;
+
+/* ------------------------------------------------------------------------- */
+/* Grid helpers                                                               */
+/* ------------------------------------------------------------------------- */
+
+/* Zone containing x: largest i with edges[i] <= x (zones are [lo, hi)). */
+int oracle_locate(const double *edges, int n, double x)
+{
+    if (n <= 1) return 0;
+    if (x < edges[0]) return 0;
+    if (x >= edges[n]) return n - 1;
+    int lo = 0, hi = n; /* edges[lo] <= x < edges[hi] */
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (edges[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* Index of stencil node i+o in a direction with n zones.  Periodic
+ * directions wrap; outflow directions fold onto the edge zone (zero-gradient
+ * ghost for the gather, fold-back for the deposit, which keeps the deposit
+ * conservative).  Reading: the paper does not state the non-periodic case. */
+static int node_index(int i, int o, int n, int bc)
+{
+    int k = i + o;
+    if (n <= 1) return 0;
+    if (k < 0) return bc == OB_PERIODIC ? k + n : 0;
+    if (k >= n) return bc == OB_PERIODIC ? k - n : n - 1;
+    return k;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 1-D weights, Sec. 3.4 and App. C.                                          */
+/* w[0], w[1], w[2] are the weights of zones i-1, i, i+1 where i hosts x and  */
+/* [lo, hi) are the edges of zone i.                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Cylindrical radial CIC, Eq. CIC_cylindrical: delta=(R_p-R_i)/dR,
+ * nu = R_i/dR.  On non-uniform grids the host zone's own width and centre
+ * are used (reading: the formula is the defining integral with the three
+ * stencil nodes taking the shape below, inside and above the host zone). */
+static void w_cyl_r_cic(double d, double nu, double w[3])
+{
+    double den = 2.0 * d + 2.0 * nu;
+    w[1] = (d + 2.0 * nu) / den * (1.0 - fabs(d));
+    w[2] = (d + 2.0 * nu + 1.0) / den * (fabs(d) + d) / 2.0;
+    w[0] = (d + 2.0 * nu - 1.0) / den * (fabs(d) - d) / 2.0;
+}
+
+/* Cylindrical radial TSC, Eq. TSC_cylindrical. */
+static void w_cyl_r_tsc(double d, double nu, double w[3])
+{
+    double den = 3.0 * d + 3.0 * nu;
+    w[1] = (d + 3.0 * nu) / den * (0.75 - d * d);
+    w[2] = (d + 3.0 * nu + 2.0) / den * 0.5 * (0.5 + d) * (0.5 + d);
+    w[0] = (d + 3.0 * nu - 2.0) / den * 0.5 * (0.5 - d) * (0.5 - d);
+}
+
+/* Spherical radial CIC, Eq. CIC_spherical_r. */
+static void w_sph_r_cic(double d, double nu, double w[3])
+{
+    double den = 12.0 * (d + nu) * (d + nu) + 1.0;
+    double a = d + 2.0 * nu, b = fabs(d) - 1.0;
+    w[1] = (3.0 * a * a + b * b) / den * (1.0 - fabs(d));
+    double cp = 2.0 * d + 3.0 * nu + 1.5, cm = 2.0 * d + 3.0 * nu - 1.5;
+    w[2] = (cp * cp + 3.0 * (nu + 0.5) * (nu + 0.5)) / den * (fabs(d) + d) / 2.0;
+    w[0] = (cm * cm + 3.0 * (nu - 0.5) * (nu - 0.5)) / den * (fabs(d) - d) / 2.0;
+}
+
+/* Spherical radial TSC, Eq. TSC_spherical_r. */
+static void w_sph_r_tsc(double d, double nu, double w[3])
+{
+    double den = 6.0 * (d + nu) * (d + nu) + 1.0;
+    double a = d + 2.0 * nu;
+    w[1] = ((a * a + 2.0 * nu * nu + 0.75) * (0.75 - d * d) - 0.25) / den;
+    w[2] = (d * d + (4.0 * nu + 3.0) * d + 6.0 * nu * nu + 8.0 * nu + 2.75) / den
+           * 0.5 * (0.5 + d) * (0.5 + d);
+    w[0] = (d * d + (4.0 * nu - 3.0) * d + 6.0 * nu * nu - 8.0 * nu + 2.75) / den
+           * 0.5 * (0.5 - d) * (0.5 - d);
+}
+
+/* Spherical theta CIC, Eq. CIC_spherical_theta with delta = theta_p - theta_i
+ * in radians.  Reading: the printed W_{i-1} has a sign garble; the integral of
+ * sin(theta) over the overlap gives W_{i+-1} = +-[cos x_{i+-1/2} -
+ * cos(x_{i+-1/2} + delta)] / D * H(+-delta). */
+static void w_sph_th_cic(double th, double lo, double hi, double w[3])
+{
+    double tc = 0.5 * (lo + hi);
+    double d = th - tc;
+    double D = cos(lo + d) - cos(hi + d);
+    w[0] = 0.0; w[2] = 0.0;
+    if (d > 0.0) w[2] = (cos(hi) - cos(hi + d)) / D;
+    if (d < 0.0) w[0] = -(cos(lo) - cos(lo + d)) / D;
+    w[1] = 1.0 - w[0] - w[2];
+}
+
+/* Spherical theta TSC.  Not printed in the paper (App. C gives theta-CIC
+ * only).  Reading: the defining integral, Eq. weight with Eq. shape_curv,
+ * b1 of half-width h = dtheta centred on theta_p = t and measure sin(theta).
+ * Integrating (1 - |u|/h) sin(t+u) by parts over the part of the shape that
+ * lies in zone i+1 (an interval of width e = h/2 + delta starting at angle c)
+ * gives  [cos(c) (e - sin e) + 2 sin^2(e/2) sin(c)] / h,  over zone i-1
+ * (width e = h/2 - delta ending at angle c)  [-cos(c) (e - sin e) +
+ * 2 sin^2(e/2) sin(c)] / h, and over the whole shape 4 sin(t) sin^2(h/2) / h.
+ * These are the plain antiderivative differences rearranged so that no O(1)
+ * terms cancel. */
+static void w_sph_th_tsc(double th, double lo, double hi, double w[3])
+{
+    double h = hi - lo;
+    double d = th - 0.5 * (lo + hi);
+    double sh = sin(0.5 * h);
+    double N = 4.0 * sin(th) * sh * sh;
+    double ep = 0.5 * h + d, cp = hi;          /* zone i+1: [hi, th + h]     */
+    double em = 0.5 * h - d, cm = lo;          /* zone i-1: [th - h, lo]     */
+    double sp = sin(0.5 * ep), sm = sin(0.5 * em);
+    w[2] = (cos(cp) * (ep - sin(ep)) + 2.0 * sp * sp * sin(cp)) / N;
+    w[0] = (-cos(cm) * (em - sin(em)) + 2.0 * sm * sm * sin(cm)) / N;
+    w[1] = 1.0 - w[0] - w[2];
+}
+
+void oracle_weights_1d(int kind, double x, double lo, double hi, double w[3])
+{
+    double dx = hi - lo;
+    double xc = 0.5 * (lo + hi);
+    double d = (x - xc) / dx;
+    double nu = xc / dx;
+    switch (kind) {
+    case W1_CART_CIC: /* b0 spline: nu -> infinity limit of Eq. CIC_cylindrical */
+        w[0] = d < 0.0 ? -d : 0.0;
+        w[1] = 1.0 - fabs(d);
+        w[2] = d > 0.0 ? d : 0.0;
+        break;
+    case W1_CART_TSC: /* b1 spline: nu -> infinity limit of Eq. TSC_cylindrical */
+        w[0] = 0.5 * (0.5 - d) * (0.5 - d);
+        w[1] = 0.75 - d * d;
+        w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+        break;
+    case W1_CYL_R_CIC: w_cyl_r_cic(d, nu, w); break;
+    case W1_CYL_R_TSC: w_cyl_r_tsc(d, nu, w); break;
+    case W1_SPH_R_CIC: w_sph_r_cic(d, nu, w); break;
+    case W1_SPH_R_TSC: w_sph_r_tsc(d, nu, w); break;
+    case W1_SPH_TH_CIC: w_sph_th_cic(x, lo, hi, w); break;
+    case W1_SPH_TH_TSC: w_sph_th_tsc(x, lo, hi, w); break;
+    default: w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
+    }
+}
+
+/* Which 1-D weight formula each direction uses (Sec. 3.4: the product of
+ * three 1-D factors, W = W(x1) W(x2) W(x3)). */
+static int weight_kind(const oracle_problem *P, int d)
+{
+    int tsc = P->weight == OW_TSC;
+    if (P->geom == OG_CYLINDRICAL && d == 0) return tsc ? W1_CYL_R_TSC : W1_CYL_R_CIC;
+    if (P->geom == OG_SPHERICAL && d == 0) return tsc ? W1_SPH_R_TSC : W1_SPH_R_CIC;
+    if (P->geom == OG_SPHERICAL && d == 1) return tsc ? W1_SPH_TH_TSC : W1_SPH_TH_CIC;
+    return tsc ? W1_CART_TSC : W1_CART_CIC;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Boundaries                                                                  */
+/* ------------------------------------------------------------------------- */
+
+/* One periodic wrap of x into [lo, hi). */
+static double wrap_once(double x, double lo, double hi)
+{
+    double L = hi - lo;
+    if (x >= hi) { x -= L; if (x < lo) x = lo; }
+    else if (x < lo) { x += L; if (x >= hi) x = lo; }
+    return x;
+}
+
+/* Apply the boundary conditions to a grain at time t.  Returns 0 if the
+ * grain left through an outflow boundary.  Shearing box x-boundaries are
+ * shear-periodic: leaving through +x the grain re-enters at -x with
+ * y += q Omega Lx t (mod Ly); the standard-frame v_y gains q Omega Lx, the
+ * residual velocity of the orbital-advection frame is unchanged (Sec. 2.1). */
+static int apply_bc(const oracle_problem *P, double q[3], double p[3], double t)
+{
+    for (int d = 0; d < 3; d++) {
+        double lo = P->edges[d][0], hi = P->edges[d][P->n[d]];
+        if (q[d] >= lo && q[d] < hi) continue;
+        if (P->bc[d] == OB_OUTFLOW) return 0;
+        if (P->geom == OG_SHEARING_BOX && d == 0) {
+            double Lx = hi - lo;
+            double ylo = P->edges[1][0], yhi = P->edges[1][P->n[1]];
+            double shift = fmod(P->q * P->omega * Lx * t, yhi - ylo);
+            if (q[0] >= hi) {
+                q[1] += shift;
+                if (!P->fargo) p[1] += P->q * P->omega * Lx;
+            } else {
+                q[1] -= shift;
+                if (!P->fargo) p[1] -= P->q * P->omega * Lx;
+            }
+            q[0] = wrap_once(q[0], lo, hi);
+            q[1] = wrap_once(q[1], ylo, yhi);
+        } else {
+            q[d] = wrap_once(q[d], lo, hi);
+        }
+        if (q[d] < lo || q[d] >= hi) return 0; /* moved more than a period */
+    }
+    /* the y-shift above may have pushed y out of range once more */
+    for (int d = 0; d < 3; d++) {
+        double lo = P->edges[d][0], hi = P->edges[d][P->n[d]];
+        if (q[d] < lo || q[d] >= hi) {
+            if (P->bc[d] == OB_OUTFLOW) return 0;
+            q[d] = wrap_once(q[d], lo, hi);
+        }
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Drifts (Eq. exp_midpoint; Eqs. drift1/drift2_cylindrical; App. B.2.2).     */
+/* qm[] receives the metric quantities used by both half drifts.              */
+/* ------------------------------------------------------------------------- */
+
+/* First half drift.  Shearing box with orbital advection: dy/dt includes the
+ * mean shear -q Omega x, evaluated at the drifted x (reading, by analogy with
+ * the midpoint R^2 of the cylindrical drift). */
+static void drift_first(const oracle_problem *P, double q[3], const double p[3], double h)
+{
+    switch (P->geom) {
+    case OG_CYLINDRICAL: {
+        q[0] = q[0] + h * p[0];
+        q[1] = q[1] + h * p[1] / (q[0] * q[0]);
+        q[2] = q[2] + h * p[2];
+        break;
+    }
+    case OG_SPHERICAL: {
+        q[0] = q[0] + h * p[0];
+        q[1] = q[1] + h * p[1] / (q[0] * q[0]);
+        double s = sin(q[1]);
+        q[2] = q[2] + h * p[2] / (q[0] * q[0] * s * s);
+        break;
+    }
+    case OG_SHEARING_BOX:
+        q[0] = q[0] + h * p[0];
+        if (P->fargo) q[1] = q[1] + h * (p[1] - P->q * P->omega * q[0]);
+        else q[1] = q[1] + h * p[1];
+        q[2] = q[2] + h * p[2];
+        break;
+    default:
+        q[0] += h * p[0]; q[1] += h * p[1]; q[2] += h * p[2];
+    }
+}
+
+/* Second half drift: the metric factors (R^2, r^2, r^2 sin^2 theta, and the
+ * shear term's x) stay at their midpoint values qm[]. */
+static void drift_second(const oracle_problem *P, double q[3], const double qm[3],
+                         const double p[3], double h)
+{
+    switch (P->geom) {
+    case OG_CYLINDRICAL:
+        q[0] = q[0] + h * p[0];
+        q[1] = q[1] + h * p[1] / (qm[0] * qm[0]);
+        q[2] = q[2] + h * p[2];
+        break;
+    case OG_SPHERICAL: {
+        double s = sin(qm[1]);
+        q[0] = q[0] + h * p[0];
+        q[1] = q[1] + h * p[1] / (qm[0] * qm[0]);
+        q[2] = q[2] + h * p[2] / (qm[0] * qm[0] * s * s);
+        break;
+    }
+    case OG_SHEARING_BOX:
+        q[0] = q[0] + h * p[0];
+        if (P->fargo) q[1] = q[1] + h * (p[1] - P->q * P->omega * qm[0]);
+        else q[1] = q[1] + h * p[1];
+        q[2] = q[2] + h * p[2];
+        break;
+    default:
+        q[0] += h * p[0]; q[1] += h * p[1]; q[2] += h * p[2];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* External (non-drag) forces                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Point-mass gravity at the midpoint, in the components the kick needs:
+ * cylindrical (g_R, g_phi, g_z), spherical (g_r, g_theta, g_phi). */
+static void gravity(const oracle_problem *P, const double qm[3], double g[3])
+{
+    g[0] = g[1] = g[2] = 0.0;
+    if (P->gm == 0.0) return;
+    if (P->geom == OG_CYLINDRICAL) {
+        double R = qm[0], z = qm[2];
+        if (P->vertical_gravity) {
+            double r2 = R * R + z * z;
+            double r3 = r2 * sqrt(r2);
+            g[0] = -P->gm * R / r3;
+            g[2] = -P->gm * z / r3;
+        } else {
+            g[0] = -P->gm / (R * R);
+        }
+    } else if (P->geom == OG_SPHERICAL) {
+        g[0] = -P->gm / (qm[0] * qm[0]);
+    }
+}
+
+/* Stopping time of a grain (Sec. 2, Epstein regime; constant Stokes number
+ * as in Secs. 4.5-4.6: tau_s = St / Omega_K with Omega_K = sqrt(GM/R^3) at
+ * the cylindrical radius of the midpoint; shearing box: St / Omega). */
+static double stopping_time(const oracle_problem *P, int mode, double value,
+                            const double qm[3], double rho_g)
+{
+    if (mode == OT_CONST) return value;
+    if (mode == OT_EPSTEIN) return value / rho_g;
+    /* OT_STOKES */
+    if (P->geom == OG_CYLINDRICAL || P->geom == OG_SPHERICAL) {
+        double R = P->geom == OG_CYLINDRICAL ? qm[0] : qm[0] * sin(qm[1]);
+        return value * sqrt(R * R * R / P->gm);
+    }
+    return value / P->omega;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The step                                                                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Advance n grains by one step of size dt starting at time t.
+ *   q0..q2, p0..p2 : coordinates and momentum-like variables (updated)
+ *                    Cartesian / shearing box: (x,y,z), (vx,vy,vz) (residual
+ *                    velocity in the orbital-advection frame);
+ *                    cylindrical: (R,phi,z), (v_R, l_phi = R v_phi, v_z);
+ *                    spherical: (r,theta,phi), (v_r, l_theta = r v_theta,
+ *                    l_phi = r sin(theta) v_phi)
+ *   species, param : per-grain species index and stopping-time value
+ *                    (either may be NULL: species 0 / the species value)
+ *   active         : 1 = in the domain; set to 0 when a grain leaves through
+ *                    an outflow boundary
+ *   rho, pg0..pg2  : gas density and momentum-like velocity per zone,
+ *                    zone index i + n0 (j + n1 k); pg updated when
+ *                    feedback_apply is set
+ *   dep            : out, [ncell][4] dense deposit: momentum-like channels
+ *                    0..2 (Eq. dust_feedback_final times the zone volume and
+ *                    dt, i.e. the impulse given to the gas) and energy (3)
+ * Returns the number of grains removed in this step.
+ */
+int64_t oracle_step(const oracle_problem *P,
+                    double *q0, double *q1, double *q2,
+                    double *p0, double *p1, double *p2,
+                    const uint8_t *species, const double *param,
+                    uint8_t *active, int64_t n, double t, double dt,
+                    const double *rho, double *pg0, double *pg1, double *pg2,
+                    double *dep)
+{
+    const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+    const int64_t ncell = (int64_t)n0 * n1 * n2;
+    const double h = 0.5 * dt;
+    int64_t removed = 0;
+    int wk[3];
+    for (int d = 0; d < 3; d++) wk[d] = weight_kind(P, d);
+    memset(dep, 0, sizeof(double) * 4 * ncell);
+
+    for (int64_t g = 0; g < n; g++) {
+        if (!active[g]) continue;
+        int sp = species ? species[g] : 0;
+        double m = P->sp_mass[sp];
+        double q[3] = {q0[g], q1[g], q2[g]};
+        double pn[3] = {p0[g], p1[g], p2[g]};
+
+        /* 1. first half drift and boundaries at t + dt/2 */
+        drift_first(P, q, pn, h);
+        if (!apply_bc(P, q, pn, t + h)) { active[g] = 0; removed++; continue; }
+        double qm[3] = {q[0], q[1], q[2]};
+
+        /* 2. host zone and weights at x^{n+1/2} */
+        int host[3];
+        double w[3][3];
+        for (int d = 0; d < 3; d++) {
+            if (P->n[d] <= 1) {
+                host[d] = 0; w[d][0] = 0.0; w[d][1] = 1.0; w[d][2] = 0.0;
+                continue;
+            }
+            host[d] = oracle_locate(P->edges[d], P->n[d], qm[d]);
+            oracle_weights_1d(wk[d], qm[d], P->edges[d][host[d]],
+                              P->edges[d][host[d] + 1], w[d]);
+        }
+
+        /* 3. gather (Eq. Delta_vp) */
+        double rg = 0.0, vg[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < 3; c++)
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    double W = w[0][a] * w[1][b] * w[2][c];
+                    int64_t idx = node_index(host[0], a - 1, n0, P->bc[0])
+                        + (int64_t)n0 * (node_index(host[1], b - 1, n1, P->bc[1])
+                        + (int64_t)n1 * node_index(host[2], c - 1, n2, P->bc[2]));
+                    rg += W * rho[idx];
+                    vg[0] += W * pg0[idx];
+                    vg[1] += W * pg1[idx];
+                    vg[2] += W * pg2[idx];
+                }
+
+        /* 4. propagators: E = e^{-dt/tau}, cg = h1/tau = 1 - E, h1 = dt phi1 */
+        int mode = P->sp_tau_mode[sp];
+        double value = param ? param[g] : P->sp_tau[sp];
+        double tau = stopping_time(P, mode, value, qm, rg);
+        double x = dt / tau;
+        double E = exp(-x);
+        double cg = -expm1(-x);
+        double h1 = (x == 0.0) ? dt : dt * cg / x;
+
+        /* 5. kick */
+        double pp[3], a[3], dHdp[3];
+        if (P->geom == OG_SHEARING_BOX) {
+            /* App. B.1: R v^{n+1} = E v^n + h1 G(x^{n+1/2}, v^n/2, v_g) */
+            double Om = P->omega, qq = P->q;
+            double zf = P->vertical_gravity ? -Om * Om * qm[2] : 0.0;
+            double Om1 = Om * h1;
+            double r[3];
+            if (!P->fargo) {
+                double G0 = 2.0 * Om * (0.5 * pn[1] + qq * Om * qm[0]);
+                double G1 = -2.0 * (0.5 * pn[0]) * Om;
+                r[0] = E * pn[0] + h1 * G0 + cg * vg[0];
+                r[1] = E * pn[1] + h1 * G1 + cg * vg[1];
+                r[2] = E * pn[2] + h1 * zf + cg * vg[2];
+                double inv = 1.0 / (1.0 + Om1 * Om1);
+                pp[0] = inv * (r[0] + Om1 * r[1]);
+                pp[1] = inv * (-Om1 * r[0] + r[1]);
+                pp[2] = r[2];
+            } else {
+                double Om2 = Om1 * (1.0 - 0.5 * qq);
+                double G0 = 2.0 * Om * (0.5 * pn[1]);
+                double G1 = (0.5 * pn[0]) * Om * (qq - 2.0);
+                r[0] = E * pn[0] + h1 * G0 + cg * vg[0];
+                r[1] = E * pn[1] + h1 * G1 + cg * vg[1];
+                r[2] = E * pn[2] + h1 * zf + cg * vg[2];
+                double inv = 1.0 / (1.0 + Om1 * Om2);
+                pp[0] = inv * (r[0] + Om1 * r[1]);
+                pp[1] = inv * (-Om2 * r[0] + r[1]);
+                pp[2] = r[2];
+            }
+            /* non-frictional acceleration at (x^{n+1/2}, v^{n+1/2}) */
+            double vh[3] = {0.5 * (pn[0] + pp[0]), 0.5 * (pn[1] + pp[1]), 0.5 * (pn[2] + pp[2])};
+            if (!P->fargo) {
+                a[0] = 2.0 * Om * (vh[1] + qq * Om * qm[0]);
+                a[1] = -2.0 * Om * vh[0];
+            } else {
+                a[0] = 2.0 * Om * vh[1];
+                a[1] = (qq - 2.0) * Om * vh[0];
+            }
+            a[2] = zf;
+            dHdp[0] = vh[0]; dHdp[1] = vh[1]; dHdp[2] = vh[2];
+        } else if (P->geom == OG_CYLINDRICAL) {
+            /* App. B.2.1: v_z, then l_phi, then v_R with (l^2)^{n+1/2} */
+            double g[3];
+            gravity(P, qm, g);
+            double R = qm[0];
+            pp[2] = E * pn[2] + h1 * g[2] + cg * vg[2];
+            pp[1] = E * pn[1] + h1 * g[1] * R + cg * vg[1];
+            double l2 = 0.5 * (pn[1] * pn[1] + pp[1] * pp[1]);
+            double aR = l2 / (R * R * R) + g[0];
+            pp[0] = E * pn[0] + h1 * aR + cg * vg[0];
+            a[0] = aR; a[1] = g[1] * R; a[2] = g[2];
+            dHdp[0] = 0.5 * (pn[0] + pp[0]);
+            dHdp[1] = 0.5 * (pn[1] + pp[1]) / (R * R);
+            dHdp[2] = 0.5 * (pn[2] + pp[2]);
+        } else if (P->geom == OG_SPHERICAL) {
+            /* App. B.2.2: l_phi, then l_theta, then v_r; the second averaged
+             * square is (l_theta^2)^{n+1/2} (the printed formula repeats
+             * l_phi, a typo). */
+            double g[3];
+            gravity(P, qm, g);
+            double r = qm[0], st = sin(qm[1]), ct = cos(qm[1]);
+            pp[2] = E * pn[2] + h1 * g[2] * r * st + cg * vg[2];
+            double lp2 = 0.5 * (pn[2] * pn[2] + pp[2] * pp[2]);
+            double ath = lp2 * ct / (r * r * st * st * st) + r * g[1];
+            pp[1] = E * pn[1] + h1 * ath + cg * vg[1];
+            double lt2 = 0.5 * (pn[1] * pn[1] + pp[1] * pp[1]);
+            double ar = lt2 / (r * r * r) + lp2 / (r * r * r * st * st) + g[0];
+            pp[0] = E * pn[0] + h1 * ar + cg * vg[0];
+            a[0] = ar; a[1] = ath; a[2] = g[2] * r * st;
+            dHdp[0] = 0.5 * (pn[0] + pp[0]);
+            dHdp[1] = 0.5 * (pn[1] + pp[1]) / (r * r);
+            dHdp[2] = 0.5 * (pn[2] + pp[2]) / (r * r * st * st);
+        } else {
+            /* Eq. kick_modified: v^{n+1} = E v^n + h1 v_g / tau */
+            for (int d = 0; d < 3; d++) {
+                pp[d] = E * pn[d] + cg * vg[d];
+                a[d] = 0.0;
+                dHdp[d] = 0.5 * (pn[d] + pp[d]);
+            }
+        }
+
+        /* 6. second half drift with the midpoint metric, 7. boundaries */
+        double qn[3] = {qm[0], qm[1], qm[2]};
+        drift_second(P, qn, qm, pp, h);
+        double pnew[3] = {pp[0], pp[1], pp[2]};
+        int alive = apply_bc(P, qn, pnew, t + dt);
+
+        /* 8. deposit at x^{n+1/2}: -m W (dp - dt a), energy = sum dP dH/dp */
+        double D[4];
+        D[3] = 0.0;
+        for (int c = 0; c < 3; c++) {
+            D[c] = -m * ((pp[c] - pn[c]) - dt * a[c]);
+            D[3] += D[c] * dHdp[c];
+        }
+        for (int c = 0; c < 3; c++)
+            for (int b = 0; b < 3; b++)
+                for (int aa = 0; aa < 3; aa++) {
+                    double W = w[0][aa] * w[1][b] * w[2][c];
+                    if (W == 0.0) continue;
+                    int64_t idx = node_index(host[0], aa - 1, n0, P->bc[0])
+                        + (int64_t)n0 * (node_index(host[1], b - 1, n1, P->bc[1])
+                        + (int64_t)n1 * node_index(host[2], c - 1, n2, P->bc[2]));
+                    for (int ch = 0; ch < 4; ch++) dep[4 * idx + ch] += W * D[ch];
+                }
+
+        q0[g] = qn[0]; q1[g] = qn[1]; q2[g] = qn[2];
+        p0[g] = pnew[0]; p1[g] = pnew[1]; p2[g] = pnew[2];
+        if (!alive) { active[g] = 0; removed++; }
+    }
+
+    /* feedback on the gas momentum: rho v_i += dP_i / dV_i */
+    if (P->feedback_apply) {
+        for (int k = 0; k < n2; k++)
+            for (int j = 0; j < n1; j++)
+                for (int i = 0; i < n0; i++) {
+                    int64_t idx = i + (int64_t)n0 * (j + (int64_t)n1 * k);
+                    double a0 = P->edges[0][i], a1 = P->edges[0][i + 1];
+                    double b0 = P->edges[1][j], b1 = P->edges[1][j + 1];
+                    double c0 = P->edges[2][k], c1 = P->edges[2][k + 1];
+                    double dV;
+                    if (P->geom == OG_CYLINDRICAL)
+                        dV = 0.5 * (a1 * a1 - a0 * a0) * (b1 - b0) * (c1 - c0);
+                    else if (P->geom == OG_SPHERICAL)
+                        dV = (a1 * a1 * a1 - a0 * a0 * a0) / 3.0 * (cos(b0) - cos(b1)) * (c1 - c0);
+                    else
+                        dV = (a1 - a0) * (b1 - b0) * (c1 - c0);
+                    double s = 1.0 / (rho[idx] * dV);
+                    pg0[idx] += dep[4 * idx + 0] * s;
+                    pg1[idx] += dep[4 * idx + 1] * s;
+                    pg2[idx] += dep[4 * idx + 2] * s;
+                }
+    }
+    return removed;
+}
+
+/* Gas momentum-like velocity per zone from physical velocity components
+ * (Sec. 2.2: l_phi = R v_phi; spherical l_theta = r v_theta, l_phi = r
+ * sin(theta) v_phi), evaluated at the zone centres (reading: the gathered
+ * angular quantity is the zone's own angular momentum per unit mass). */
+void oracle_gas_momentum(const oracle_problem *P, const double *v0, const double *v1,
+                         const double *v2, double *pg0, double *pg1, double *pg2)
+{
+    const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+    for (int k = 0; k < n2; k++)
+        for (int j = 0; j < n1; j++)
+            for (int i = 0; i < n0; i++) {
+                int64_t idx = i + (int64_t)n0 * (j + (int64_t)n1 * k);
+                double xc = 0.5 * (P->edges[0][i] + P->edges[0][i + 1]);
+                double yc = 0.5 * (P->edges[1][j] + P->edges[1][j + 1]);
+                pg0[idx] = v0[idx];
+                pg1[idx] = v1[idx];
+                pg2[idx] = v2[idx];
+                if (P->geom == OG_CYLINDRICAL) pg1[idx] = xc * v1[idx];
+                if (P->geom == OG_SPHERICAL) {
+                    pg1[idx] = xc * v1[idx];
+                    pg2[idx] = xc * sin(yc) * v2[idx];
+                }
+            }
+}

@@ -1,0 +1,541 @@
+"""Pins of the oracle's exponential-midpoint push and feedback deposit against
+what the paper and the mathematics fix (none of them re-types the oracle):
+
+* exact exponential relaxation toward uniform gas (Eq. kick_modified,
+  "exact solution when G is constant", Sec. 3.2.2);
+* second-order convergence (Sec. 3.2.2, Secs. 4.1, 4.4, 4.5);
+* the stiff limit tau_s -> 0 (Sec. 3.2.2, correct asymptotic solution);
+* time reversibility (Sec. 3.2.2);
+* epicyclic motion: energy exactly conserved with orbital advection,
+  oscillating in the standard frame (Sec. 4.2, Eqs. epicyclic,
+  epicyclic_energy);
+* the circular Kepler orbit is exact; eccentric and inclined orbits converge
+  at second order against the Kepler-equation solution (Sec. 4.4);
+* the NSH equilibrium is a fixed point of the orbital-advection kick
+  (Eq. SI_equil, Sec. 4.3);
+* momentum (and angular momentum) conservation of the feedback (Sec. 3.1,
+  Eq. dust_feedback_final) and the energy identity of the energy channel;
+* the printed stiff-deceleration L1 errors (Sec. 4.1, tests/golden);
+* radial drift against the NSH prediction (Sec. 4.5).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1908_10793_gb300 import inputs as I
+
+INF = float("inf")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def box_problem(n=(4, 4, 4), lo=-100.0, hi=100.0, **kw):
+    edges = [np.linspace(lo, hi, k + 1) if k > 1 else np.array([lo, hi]) for k in n]
+    return O.Problem(edges=edges, **kw)
+
+
+def gas_uniform(prob, rho=1.0, v=(0.0, 0.0, 0.0)):
+    nc = prob.ncell
+    return np.full(nc, float(rho)), [np.full(nc, float(x)) for x in v]
+
+
+def run(prob, q, p, dt, steps, rho, pg, t0=0.0, param=None, species=None, active=None):
+    q = [np.array(x, dtype=np.float64) for x in q]
+    p = [np.array(x, dtype=np.float64) for x in p]
+    n = len(q[0])
+    active = np.ones(n, np.uint8) if active is None else active
+    dep_tot = np.zeros((prob.ncell, 4))
+    for s in range(steps):
+        dep, _ = O.step(prob, q, p, active, t0 + s * dt, dt, rho, pg, species, param)
+        dep_tot += dep
+    return q, p, active, dep_tot
+
+
+# --------------------------------------------------------------------------
+def test_exact_exponential_relaxation_toward_uniform_gas():
+    prob = box_problem(geom=O.OG_CARTESIAN, species_tau=(1.0,))
+    vg = (0.3, -0.2, 0.1)
+    rho, pg = gas_uniform(prob, 1.0, vg)
+    rng = np.random.default_rng(3)
+    n = 8
+    q0 = [rng.uniform(-5, 5, n) for _ in range(3)]
+    v0 = [rng.normal(0, 1, n) for _ in range(3)]
+    dt = 0.1
+    for ratio in (0.01, 0.5, 3.0, 40.0):
+        tau = dt / ratio
+        param = np.full(n, tau)
+        steps = 7
+        _, p, _, _ = run(prob, q0, v0, dt, steps, rho, pg, param=param)
+        for d in range(3):
+            exact = vg[d] + (v0[d] - vg[d]) * np.exp(-steps * dt / tau)
+            assert np.abs(p[d] - exact).max() < 1e-14 * (1 + np.abs(v0[d]).max())
+
+
+def test_position_converges_at_second_order_for_uniform_gas():
+    prob = box_problem(geom=O.OG_CARTESIAN)
+    vg = (0.3, 0.0, 0.0)
+    rho, pg = gas_uniform(prob, 1.0, vg)
+    tau, T, x0, v0 = 0.2, 1.0, 0.1, 2.0
+    exact = x0 + vg[0] * T + tau * (v0 - vg[0]) * (1 - np.exp(-T / tau))
+    errs = []
+    for N in (10, 20, 40, 80):
+        q, _, _, _ = run(prob, [[x0], [0.0], [0.0]], [[v0], [0.0], [0.0]], T / N, N, rho, pg,
+                         param=np.array([tau]))
+        errs.append(abs(q[0][0] - exact))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(slopes - 2.0) < 0.1), slopes
+
+
+def test_second_order_convergence_with_gridded_gas_and_drag():
+    n = 64
+    edges = [np.linspace(0.0, 1.0, n + 1), np.array([0.0, 1.0]), np.array([0.0, 1.0])]
+    prob = O.Problem(geom=O.OG_CARTESIAN, edges=edges, weight=O.OW_TSC)
+    xc = 0.5 * (edges[0][1:] + edges[0][:-1])
+    rho = np.ones(n)
+    pg = [0.4 * np.sin(2 * np.pi * xc), np.zeros(n), np.zeros(n)]
+    tau, T = 0.05, 0.5
+    q0, v0 = [[0.31], [0.5], [0.5]], [[0.7], [0.0], [0.0]]
+
+    def final(N):
+        q, p, _, _ = run(prob, q0, v0, T / N, N, rho, pg, param=np.array([tau]))
+        return q[0][0], p[0][0]
+
+    ref = final(25600)
+    errs = [abs(final(N)[0] - ref[0]) for N in (50, 100, 200, 400)]
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((slopes > 1.75) & (slopes < 2.3)), slopes
+
+
+@pytest.mark.parametrize("tau_over_dt", [1e-8, 1e-300, 0.0])
+def test_stiff_limit_gives_gathered_gas_velocity(tau_over_dt):
+    n = 16
+    edges = [np.linspace(0.0, 1.0, n + 1), np.array([0.0, 1.0]), np.array([0.0, 1.0])]
+    prob = O.Problem(geom=O.OG_CARTESIAN, edges=edges, weight=O.OW_TSC)
+    xc = 0.5 * (edges[0][1:] + edges[0][:-1])
+    rho = np.ones(n)
+    pg = [np.cos(2 * np.pi * xc), np.zeros(n), np.zeros(n)]
+    dt, x0, v0 = 0.01, 0.4, 3.0
+    q, p, _, _ = run(prob, [[x0], [0.5], [0.5]], [[v0], [0.0], [0.0]], dt, 1, rho, pg,
+                     param=np.array([tau_over_dt * dt]))
+    # textbook TSC interpolation at the midpoint x0 + dt/2 v0 (Eq. b1 shape)
+    xm = x0 + 0.5 * dt * v0
+    i = int(xm * n)
+    d = xm * n - (i + 0.5)
+    w = [0.5 * (0.5 - d) ** 2, 0.75 - d * d, 0.5 * (0.5 + d) ** 2]
+    vint = sum(w[k] * pg[0][(i - 1 + k) % n] for k in range(3))
+    assert np.isfinite(p[0][0])
+    assert abs(p[0][0] - vint) < 1e-14
+    assert abs(q[0][0] - (xm + 0.5 * dt * vint)) < 1e-15
+
+
+def test_stiff_limit_shearing_box_tends_to_gas_velocity():
+    prob = box_problem(geom=O.OG_SHEARING_BOX, fargo=0, omega=1.0, q=1.5)
+    vg = (0.02, -0.01, 0.0)
+    rho, pg = gas_uniform(prob, 1.0, vg)
+    dt = 0.1
+    _, p, _, _ = run(prob, [[0.3], [0.1], [0.0]], [[1.0], [2.0], [0.5]], dt, 1, rho, pg,
+                     param=np.array([1e-10 * dt]))
+    # h1 ~ tau: Omega_1 -> 0, R^-1 -> I, E -> 0: v -> v_g + O(tau)
+    assert abs(p[0][0] - vg[0]) < 1e-9 and abs(p[1][0] - vg[1]) < 1e-9 and abs(p[2][0]) < 1e-12
+
+
+# --------------------------------------------------------------------------
+def _reverse(prob, q0, p0, dt, N, rho, pg, param):
+    q, p, _, _ = run(prob, q0, p0, dt, N, rho, pg, param=param)
+    q2, p2, _, _ = run(prob, q, p, -dt, N, rho, pg, t0=N * dt, param=param)
+    return q2, p2
+
+
+def test_time_reversibility_cartesian_gridded_gas():
+    n = 32
+    edges = [np.linspace(0.0, 1.0, n + 1), np.linspace(0.0, 1.0, n + 1), np.array([0.0, 1.0])]
+    prob = O.Problem(geom=O.OG_CARTESIAN, edges=edges, weight=O.OW_TSC)
+    X, Y, _ = I._grid3(edges)
+    rho = np.ones(n * n)
+    pg = [0.2 * np.sin(2 * np.pi * X), 0.1 * np.cos(2 * np.pi * Y), np.zeros(n * n)]
+    q0 = [[0.4, 0.6], [0.45, 0.52], [0.5, 0.5]]
+    p0 = [[0.1, -0.05], [0.05, 0.02], [0.0, 0.0]]
+    dt, N = 0.01, 10
+    q, p = _reverse(prob, q0, p0, dt, N, rho, pg, param=np.array([0.02, 0.02]))  # N dt/tau = 5
+    for d in range(3):
+        assert np.abs(q[d] - np.array(q0[d])).max() < 1e-11
+        assert np.abs(p[d] - np.array(p0[d])).max() < 1e-11
+
+
+@pytest.mark.parametrize("fargo", [0, 1])
+def test_time_reversibility_shearing_box(fargo):
+    prob = box_problem(n=(8, 8, 8), lo=-1.0, hi=1.0, geom=O.OG_SHEARING_BOX, fargo=fargo,
+                       omega=1.0, q=1.5, vertical_gravity=1)
+    X, Y, Z = I._grid3(prob.edges)
+    rho = np.ones(prob.ncell)
+    pg = [0.05 * np.sin(np.pi * Y), 0.03 * np.cos(np.pi * X), 0.02 * np.sin(np.pi * Z)]
+    q0 = [[0.2], [-0.1], [0.05]]
+    p0 = [[0.01], [-0.02], [0.03]]
+    q, p = _reverse(prob, q0, p0, 0.05, 20, rho, pg, param=np.array([0.5]))
+    for d in range(3):
+        assert abs(q[d][0] - q0[d][0]) < 1e-12 and abs(p[d][0] - p0[d][0]) < 1e-12
+
+
+def _cyl_problem(nR=16, nphi=32, nz=8, weight=O.OW_TSC):
+    edges = [np.geomspace(0.5, 2.0, nR + 1), np.linspace(0, 2 * np.pi, nphi + 1),
+             np.linspace(-0.3, 0.3, nz + 1)]
+    return O.Problem(geom=O.OG_CYLINDRICAL, edges=edges, bc=(O.OB_OUTFLOW, 0, 0),
+                     weight=weight, gm=1.0, vertical_gravity=1)
+
+
+def test_time_reversibility_cylindrical_with_drag():
+    prob = _cyl_problem()
+    R, PHI, Z = I._grid3(prob.edges)
+    rho = np.ones(prob.ncell)
+    pg = O.gas_momentum(prob, [0.01 * np.sin(PHI), R ** -0.5 * (1 + 0.01 * np.cos(PHI)),
+                               0.01 * Z])
+    q0 = [[1.1], [0.3], [0.05]]
+    p0 = [[0.02], [1.1 * 0.95], [-0.01]]
+    q, p = _reverse(prob, q0, p0, 0.02, 50, rho, pg, param=np.array([0.3]))
+    for d in range(3):
+        assert abs(q[d][0] - q0[d][0]) < 1e-12 and abs(p[d][0] - p0[d][0]) < 1e-12
+
+
+def _sph_problem(weight=O.OW_TSC, dth=0.6):
+    edges = [np.geomspace(0.5, 1.6, 17), np.linspace(np.pi / 2 - dth, np.pi / 2 + dth, 17),
+             np.linspace(0, 2 * np.pi, 33)]
+    return O.Problem(geom=O.OG_SPHERICAL, edges=edges, bc=(O.OB_OUTFLOW, O.OB_OUTFLOW, 0),
+                     weight=weight, gm=1.0)
+
+
+def test_time_reversibility_spherical_with_drag():
+    prob = _sph_problem()
+    R, TH, PHI = I._grid3(prob.edges)
+    rho = np.ones(prob.ncell)
+    pg = O.gas_momentum(prob, [0.01 * np.cos(PHI), 0.01 * np.sin(PHI),
+                               (R * np.sin(TH)) ** -0.5])
+    q0 = [[1.05], [1.4], [0.7]]
+    p0 = [[0.01], [0.1], [0.9]]
+    q, p = _reverse(prob, q0, p0, 0.02, 50, rho, pg, param=np.array([0.4]))
+    for d in range(3):
+        assert abs(q[d][0] - q0[d][0]) < 1e-12 and abs(p[d][0] - p0[d][0]) < 1e-12
+
+
+# --------------------------------------------------------------------------
+def _epicycle(fargo, dt, T, A=0.4, Om=1.0, qs=1.5):
+    prob = box_problem(n=(4, 4, 4), lo=-1.0, hi=1.0, geom=O.OG_SHEARING_BOX, fargo=fargo,
+                       omega=Om, q=qs)
+    rho, pg = gas_uniform(prob)
+    vy0 = -2.0 * Om * A + (qs * Om * A if fargo else 0.0)
+    q = [np.array([A]), np.array([0.0]), np.array([0.0])]
+    p = [np.array([0.0]), np.array([vy0]), np.array([0.0])]
+    active = np.ones(1, np.uint8)
+    energies, xs = [], []
+    N = int(round(T / dt))
+    for s in range(N):
+        O.step(prob, q, p, active, s * dt, dt, rho, pg, None, np.array([INF]))
+        vy = p[1][0] - (qs * Om * q[0][0] if fargo else 0.0)
+        energies.append(0.5 * (p[0][0] ** 2 + vy ** 2) - qs * Om * Om * q[0][0] ** 2)
+        xs.append((q[0][0], q[1][0]))
+    return np.array(energies), np.array(xs)
+
+
+def test_epicycle_energy_conserved_with_orbital_advection():
+    # Sec. 4.2: A = 0.4, Omega = 1, dt = 0.4, t_f = 40; exact energy omega^2 A^2 / 2
+    E, _ = _epicycle(fargo=1, dt=0.4, T=40.0)
+    E0 = 0.5 * 1.0 * 0.4 ** 2
+    assert np.abs(E / E0 - 1.0).max() < 1e-13
+
+
+def test_epicycle_energy_bounded_in_standard_frame():
+    E, _ = _epicycle(fargo=0, dt=0.4, T=40.0)
+    E0 = 0.5 * 0.4 ** 2
+    dev = E / E0 - 1.0
+    assert np.abs(dev).max() < 0.15          # oscillates around the exact value
+    assert np.abs(dev).max() > 1e-3          # (it does oscillate at this large dt)
+    assert abs(dev[-25:].mean() - dev[:25].mean()) < 0.02   # no secular drift
+
+
+@pytest.mark.parametrize("fargo", [0, 1])
+def test_epicycle_orbit_second_order(fargo):
+    T = 10.0
+    errs = []
+    for N in (100, 200, 400, 800):
+        _, xs = _epicycle(fargo, T / N, T)
+        x_ex = 0.4 * np.cos(T)
+        y_ex = -2.0 * 0.4 * np.sin(T)
+        errs.append(np.hypot(xs[-1][0] - x_ex, xs[-1][1] - y_ex))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(slopes - 2.0) < 0.1), slopes
+
+
+# --------------------------------------------------------------------------
+def _kepler(e, t):
+    M = t % (2 * np.pi)
+    E = M if e < 0.8 else np.pi
+    for _ in range(60):
+        E -= (E - e * np.sin(E) - M) / (1 - e * np.cos(E))
+    R = 1.0 - e * np.cos(E)
+    f = 2.0 * np.arctan2(np.sqrt(1 + e) * np.sin(E / 2), np.sqrt(1 - e) * np.cos(E / 2))
+    return R, f % (2 * np.pi)
+
+
+def test_circular_kepler_orbit_is_exact():
+    # Sec. 4.4: R = 1, l = 1, dt = 0.1, 20 orbits: R and l stay exactly 1
+    prob = _cyl_problem()
+    rho, pg = gas_uniform(prob)
+    dt = 0.1
+    N = int(round(20 * 2 * np.pi / dt))
+    q, p, active, _ = run(prob, [[1.0], [0.0], [0.0]], [[0.0], [1.0], [0.0]], dt, N, rho, pg,
+                          param=np.array([INF]))
+    assert active[0] == 1
+    assert q[0][0] == 1.0 and p[1][0] == 1.0 and p[0][0] == 0.0
+
+
+def test_eccentric_kepler_orbit_second_order():
+    prob = _cyl_problem()
+    rho, pg = gas_uniform(prob)
+    e = 0.3
+    R0 = 1.0 - e
+    l0 = np.sqrt(1.0 * (1.0 - e * e))  # sqrt(GM a (1-e^2)), a = 1
+    T = 2 * np.pi
+    Rex, fex = _kepler(e, T)
+    errs = []
+    for N in (200, 400, 800, 1600):
+        q, p, _, _ = run(prob, [[R0], [0.0], [0.0]], [[0.0], [l0], [0.0]], T / N, N, rho, pg,
+                         param=np.array([INF]))
+        x, y = q[0][0] * np.cos(q[1][0]), q[0][0] * np.sin(q[1][0])
+        errs.append(np.hypot(x - Rex * np.cos(fex), y - Rex * np.sin(fex)))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(slopes - 2.0) < 0.1), slopes
+
+
+def test_inclined_circular_orbit_spherical_second_order():
+    # Sec. 4.4: orbit tilted by 30 degrees, one period, against the exact orbit
+    prob = _sph_problem(dth=0.6)
+    rho, pg = gas_uniform(prob)
+    inc = np.radians(30.0)
+    q0 = [[1.0], [np.pi / 2], [0.0]]
+    p0 = [[0.0], [-np.sin(inc)], [np.cos(inc)]]
+    T = 2 * np.pi
+    errs, lerr = [], []
+    for N in (200, 400, 800, 1600):
+        q, p, active, _ = run(prob, q0, p0, T / N, N, rho, pg, param=np.array([INF]))
+        assert active[0] == 1
+        r, th, ph = q[0][0], q[1][0], q[2][0]
+        xyz = r * np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+        errs.append(np.linalg.norm(xyz - np.array([1.0, 0.0, 0.0])))
+        L = np.sqrt(p[1][0] ** 2 + p[2][0] ** 2 / np.sin(th) ** 2)
+        lerr.append(abs(L - 1.0))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(slopes - 2.0) < 0.15), slopes
+    assert max(lerr) < 1e-3
+
+
+# --------------------------------------------------------------------------
+def _nsh(eps, st, etavk=0.05, printed=False):
+    dl = (1 + eps) ** 2 + st ** 2
+    vg = (2 * eps * st / dl * etavk, -(1 + eps * st ** 2 / dl) / (1 + eps) * etavk, 0.0)
+    vpx = -(2 * eps * st if printed else 2 * st) / dl * etavk
+    vp = (vpx, -(1 - st ** 2 / dl) / (1 + eps) * etavk, 0.0)
+    return vg, vp
+
+
+@pytest.mark.parametrize("st", [0.01, 0.1, 1.0, 10.0])
+def test_nsh_equilibrium_is_fixed_point_of_fargo_kick(st):
+    prob = box_problem(n=(4, 4, 4), lo=-1.0, hi=1.0, geom=O.OG_SHEARING_BOX, fargo=1,
+                       omega=1.0, q=1.5, species_tau_mode=(O.OT_STOKES,), species_tau=(st,))
+    for eps in (0.2, 3.0):
+        vg, vp = _nsh(eps, st)
+        rho, pg = gas_uniform(prob, 1.0, vg)
+        for dt in (1e-3, 0.1, 10.0):
+            _, p, _, _ = run(prob, [[0.1], [0.2], [0.0]], [[vp[0]], [vp[1]], [0.0]], dt, 1,
+                             rho, pg)
+            assert abs(p[0][0] - vp[0]) < 1e-16 and abs(p[1][0] - vp[1]) < 1e-16
+        # the printed dust x-velocity (extra factor eps) is not a steady state
+        _, vpp = _nsh(eps, st, printed=True)
+        _, p, _, _ = run(prob, [[0.1], [0.2], [0.0]], [[vpp[0]], [vpp[1]], [0.0]], 0.1, 1,
+                         rho, pg)
+        assert abs(p[0][0] - vpp[0]) + abs(p[1][0] - vpp[1]) > 1e-6
+
+
+# --------------------------------------------------------------------------
+def _oracle_state(w):
+    """Oracle problem, particle and gas arrays from a workload."""
+    prob = O.Problem(geom=w.geom, edges=w.edges, bc=w.bc, weight=w.weight,
+                     species_mass=w.species_mass, species_tau_mode=w.species_tau_mode,
+                     species_tau=w.species_tau, fargo=w.fargo, omega=w.omega, q=w.qshear,
+                     gm=w.gm, vertical_gravity=w.vertical_gravity, feedback_apply=w.feedback)
+    q = [x.copy() for x in w.q]
+    p = [x.copy() for x in w.v]
+    if w.geom == O.OG_CYLINDRICAL:
+        p[1] = q[0] * w.v[1]
+    if w.geom == O.OG_SPHERICAL:
+        p[1] = q[0] * w.v[1]
+        p[2] = q[0] * np.sin(q[1]) * w.v[2]
+    pg = O.gas_momentum(prob, w.vgas)
+    return prob, q, p, w.rho.copy(), pg
+
+
+def _zone_volumes(prob):
+    e = prob.edges
+    if prob.geom == O.OG_CYLINDRICAL:
+        a = 0.5 * np.diff(e[0] ** 2)
+        b = np.diff(e[1])
+    elif prob.geom == O.OG_SPHERICAL:
+        a = np.diff(e[0] ** 3) / 3.0
+        b = -np.diff(np.cos(e[1]))
+    else:
+        a, b = np.diff(e[0]), np.diff(e[1])
+    c = np.diff(e[2])
+    return (c[:, None, None] * b[None, :, None] * a[None, None, :]).ravel()
+
+
+def test_feedback_conserves_total_momentum_cartesian():
+    w = I.box2d("small")
+    prob, q, p, rho, pg = _oracle_state(w)
+    dV = _zone_volumes(prob)
+    m = w.species_mass[0]
+
+    def total():
+        return np.array([(rho * pg[d] * dV).sum() + m * p[d].sum() for d in range(3)])
+
+    before = total()
+    active = np.ones(w.ngrains, np.uint8)
+    for s in range(5):
+        O.step(prob, q, p, active, s * w.dt, w.dt, rho, pg)
+    after = total()
+    assert np.abs(after - before).max() < 1e-14 * max(1.0, np.abs(before).max())
+    assert np.abs(pg[0] - 0.3).max() > 1e-4   # the gas really was changed
+
+
+def test_feedback_conserves_angular_and_vertical_momentum_cylindrical():
+    w = I.cyldisk("small")
+    prob, q, p, rho, pg = _oracle_state(w)
+    dV = _zone_volumes(prob)
+    ms = np.array(w.species_mass)[w.species]
+
+    def total():
+        return np.array([(rho * pg[d] * dV).sum() + (ms * p[d]).sum() for d in (1, 2)])
+
+    before = total()
+    active = np.ones(w.ngrains, np.uint8)
+    for s in range(3):
+        _, removed = O.step(prob, q, p, active, s * w.dt, w.dt, rho, pg, w.species)
+        assert removed == 0
+    after = total()
+    assert np.abs(after - before).max() < 1e-13 * np.abs(before).max()
+
+
+def test_energy_channel_equals_minus_dust_kinetic_energy_change():
+    # Cartesian, no external force: dE = -m v^{n+1/2} . (v^{n+1} - v^n)
+    #                                  = -m (|v^{n+1}|^2 - |v^n|^2) / 2
+    w = I.box2d("small")
+    w.feedback = 0
+    prob, q, p, rho, pg = _oracle_state(w)
+    m = w.species_mass[0]
+    ke0 = 0.5 * m * sum((x ** 2).sum() for x in p)
+    dep, _ = O.step(prob, q, p, np.ones(w.ngrains, np.uint8), 0.0, w.dt, rho, pg)
+    ke1 = 0.5 * m * sum((x ** 2).sum() for x in p)
+    assert abs(dep[:, 3].sum() + (ke1 - ke0)) < 1e-13 * abs(ke1 - ke0) + 1e-17
+
+
+# --------------------------------------------------------------------------
+def _read_golden():
+    rows = {}
+    with open(os.path.join(GOLDEN, "deceleration_stiff.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                rows[k] = float(v)
+    return rows
+
+
+def _deceleration_stiff(tau):
+    """Sec. 4.1 stiff deceleration with the gas coupled through its half-step
+    drag predictor (Eq. f_D with tau <- max(tau, dt)) and the corrector with
+    the final deposit (Eq. dust_feedback_final).  One grain per zone, eps = 1."""
+    n = 8
+    edges = [np.linspace(0.0, 1.0, n + 1), np.array([0.0, 1.0]), np.array([0.0, 1.0])]
+    dV = 1.0 / n
+    eps = 1.0
+    prob = O.Problem(geom=O.OG_CARTESIAN, edges=edges, weight=O.OW_TSC,
+                     species_mass=(eps * dV,), species_tau=(tau,))
+    q = [(np.arange(n) + 0.5) / n, np.full(n, 0.5), np.full(n, 0.5)]
+    p = [np.ones(n), np.zeros(n), np.zeros(n)]
+    vg = -1.0
+    rho = np.ones(n)
+    active = np.ones(n, np.uint8)
+    dt, tf = 1.0, 10
+    vp_hist = [p[0].mean()]
+    for s in range(tf):
+        vhalf = vg + 0.5 * dt * eps * (p[0].mean() - vg) / max(tau, dt)   # predictor
+        pg = [np.full(n, vhalf), np.zeros(n), np.zeros(n)]
+        dep, _ = O.step(prob, q, p, active, s * dt, dt, rho, pg)
+        vg = vg + dep[:, 0].mean() / (1.0 * dV)                            # corrector
+        vp_hist.append(p[0].mean())
+    t = np.arange(tf + 1) * dt
+    exact = np.exp(-(1 + eps) * t / tau)
+    return np.abs(np.array(vp_hist) - exact).mean(), vp_hist
+
+
+@pytest.mark.parametrize("tau", [0.2, 0.02])
+def test_stiff_deceleration_matches_printed_l1_errors(tau):
+    printed = _read_golden()[str(tau)]
+    l1, hist = _deceleration_stiff(tau)
+    # printed to two significant digits
+    assert abs(l1 - printed) <= 0.5 * 10 ** (np.floor(np.log10(printed)) - 1) + 1e-30, l1
+    if tau == 0.02:
+        single = _read_golden()["single_step_tau0.02"]
+        assert 0.3 * single < abs(hist[1]) < 3 * single
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("st", [0.1, 1.0, 10.0])
+def test_radial_drift_matches_nsh_prediction(st):
+    """Sec. 4.5: fixed gas of Eq. Nelson_equil (p = -1, q = -0.5, H0 = 0.1 at
+    R0 = 1), 64 x 16 zones in R in [0.2, 1.6], z in [-0.2, 0.2]; grains start at
+    R = 1 on Keplerian orbits; time-averaged v_R over 10 orbits against
+    -(3/2)(H0/R0)^2 St / (1 + St^2) v_K (v_K = 1 at R = 1; with p = 2q the
+    predicted drift speed does not depend on R)."""
+    pp, qq, H0 = -1.0, -0.5, 0.1
+    edges = [np.linspace(0.2, 1.6, 65), np.array([0.0, 2 * np.pi]), np.linspace(-0.2, 0.2, 17)]
+    prob = O.Problem(geom=O.OG_CYLINDRICAL, edges=edges, bc=(O.OB_OUTFLOW, 0, 0),
+                     weight=O.OW_TSC, gm=1.0, species_tau_mode=(O.OT_STOKES,),
+                     species_tau=(st,))
+    R, _, Z = I._grid3(edges)
+    r = np.hypot(R, Z)
+    H = H0 * R ** ((qq + 3) / 2)
+    Om = R ** -1.5 * np.sqrt((pp + qq) * (H / R) ** 2 + (1 + qq) - qq * R / r)
+    pg = O.gas_momentum(prob, [np.zeros_like(R), R * Om, np.zeros_like(R)])
+    rho = np.ones_like(R)
+    dt = 0.01
+    N = int(round(20 * np.pi / dt))
+    q = [np.array([1.0]), np.array([0.0]), np.array([0.0])]
+    p = [np.array([0.0]), np.array([1.0]), np.array([0.0])]
+    active = np.ones(1, np.uint8)
+    R0 = q[0][0]
+    for s in range(N):
+        O.step(prob, q, p, active, s * dt, dt, rho, pg)
+    vmean = (q[0][0] - R0) / (N * dt)
+    pred = -1.5 * H0 ** 2 * st / (1 + st * st)
+    assert abs(vmean - pred) < 0.05 * abs(pred), (vmean, pred)
+
+
+@pytest.mark.parametrize("geom", ["sb_std", "sb_fargo", "cyl", "sph"])
+def test_no_drag_means_no_back_reaction(geom):
+    """Eq. dust_feedback_final deducts the non-frictional forces: with
+    tau_s = infinity the velocity change is dt a^{n+1/2} exactly and the
+    deposit must vanish in every geometry."""
+    if geom.startswith("sb"):
+        prob = box_problem(n=(4, 4, 4), lo=-1.0, hi=1.0, geom=O.OG_SHEARING_BOX,
+                           fargo=int(geom == "sb_fargo"), omega=1.0, q=1.5,
+                           vertical_gravity=1)
+        q0, p0 = [[0.3], [0.1], [0.2]], [[0.05], [-0.4], [0.1]]
+    elif geom == "cyl":
+        prob = _cyl_problem()
+        q0, p0 = [[1.2], [0.5], [0.1]], [[0.05], [1.0], [0.02]]
+    else:
+        prob = _sph_problem()
+        q0, p0 = [[1.1], [1.3], [0.5]], [[0.03], [0.2], [0.8]]
+    rho, pg = gas_uniform(prob, 1.0, (0.1, 0.2, 0.3))
+    _, p, _, dep = run(prob, q0, p0, 0.05, 3, rho, pg, param=np.array([INF]))
+    assert np.abs(dep[:, :3]).max() < 1e-15
+    assert np.abs(p[0][0] - p0[0][0]) > 1e-4   # the grain was accelerated
