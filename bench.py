@@ -1,0 +1,355 @@
+"""Benchmark of the dust drag-coupling step (gather + exponential-midpoint push
++ feedback deposit) on the 3-D shearing-box workload: 128^3 zones, 16.8M
+grains (8 per zone), TSC weights, St = 0.1, dust-to-gas ratio 0.02, feedback
+applied, mixed precision (FP32 push and gather, FP64 positions, int64
+fixed-point deposit).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` = grain-updates/s over all ranks (each rank
+steps its own independent instance: weak scaling, no collective on the data
+path); the FP64 GPU path is measured beside it.  `--impl reference` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1908_10793_gb300 import inputs as I  # noqa: E402
+
+METRIC = "grain-updates/s (gather+push+deposit) mixed vs FP64 on 1 GB300; % HBM roofline"
+UNIT = "grain-updates/s"
+WORKLOAD_NAME = ("sbox3d: 3-D shearing box (orbital-advection frame) 128^3 zones, 16,777,216 "
+                 "grains (8/zone), St=0.1, dust/gas 0.02, TSC, feedback on")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sort-interval", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--small", action="store_true", help="16^3 grid (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1908_10793_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, ngrains):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[kernel]
+        if e.get("source_digest") != source_digest():
+            return None
+        return float(e["dram_bytes_per_grain"]) * ngrains
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(w, precision_bytes):
+    """Bytes one step kernel launch must move at minimum: every grain's state
+    read and written once (3 FP64 coordinates + 3 momentum-like values), each
+    zone's gas (rho + 3 velocities) read once and its 4-channel int64 deposit
+    written once."""
+    per_grain = 2 * (3 * 8 + 3 * precision_bytes)
+    per_zone = 4 * precision_bytes + 4 * 8
+    return w.ngrains * per_grain + w.ncell * per_zone, per_grain, per_zone
+
+
+def run_ours(args):
+    import torch
+    from paper_1908_10793_gb300 import dust as D
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = I.sbox3d("small" if args.small else "full")
+    # a real stream (not the legacy default stream) shared by the library and
+    # the timing events
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    def make(precision, timing):
+        ctx = D.Context(w, precision=precision, stream=stream.cuda_stream,
+                        sort_interval=args.sort_interval, timing=timing, device=local)
+        ctx.set_gas(w.rho, w.vgas)
+        ctx.load(w.q, w.v)
+        return ctx
+
+    def timed(ctx, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            ctx.step(w.dt)
+        ctx.sync()
+        ctx.kernel_times(reset=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local) if sample_clocks else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.step(w.dt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ck = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        rc, st = ctx.sync(check=False)
+        kt = ctx.kernel_times(reset=True)
+        return ms, rc, st, kt, ck
+
+    # ---- mixed path, inputs resident in HBM
+    ctx = make(D.DUST_MIXED, 1)
+    ms, rc, st, kt, clocks = timed(ctx, args.steps, args.warmup, sample_clocks=True)
+    ngr = w.ngrains
+    value = world * ngr * args.steps / (ms / 1e3)
+    step_ms_avg = kt.step_ms / max(1, kt.step_launches)
+    ab, per_grain, per_zone = algorithmic_bytes(w, 4)
+    achieved = ab / (step_ms_avg / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    launches = int(kt.step_launches + kt.sort_launches + kt.other_launches)
+    ctx.close()
+
+    # ---- FP64 GPU path beside it
+    fp64 = None
+    if not args.no_fp64:
+        ctx = make(D.DUST_FP64, 1)
+        k64 = max(2, args.steps // 4)
+        ms64, rc64, _, kt64, _ = timed(ctx, k64, min(args.warmup, 3))
+        fp64 = {"value": world * ngr * k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64,
+                "steps": k64, "status": rc64,
+                "step_kernel_ms": kt64.step_ms / max(1, kt64.step_launches)}
+        ctx.close()
+
+    # ---- end to end through the C interface with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ctx = make(D.DUST_MIXED, 0)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hq = [pin(x) for x in w.q]
+        hv = [pin(x) for x in w.v]
+        hrho = pin(w.rho)
+        hg = [pin(x) for x in w.vgas]
+        oq = [pin(np.empty(ngr)) for _ in range(3)]
+        ov = [pin(np.empty(ngr)) for _ in range(3)]
+        oid = torch.empty(ngr, dtype=torch.int64).pin_memory().numpy()
+        odep = torch.empty((w.ncell, 4), dtype=torch.int64).pin_memory().numpy()
+        ke = max(2, min(args.steps, 5))
+
+        def one():
+            D.dust_load_particles(ctx.handle, *hq, *hv)
+            D.dust_set_gas(ctx.handle, hrho, *hg)
+            D.dust_step(ctx.handle, w.dt)
+            D.dust_get_particles(ctx.handle, ngr, *oq, *ov, ids=oid)
+            D.dust_get_deposit(ctx.handle, fixed=odep)
+
+        one()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            one()
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = ngr * 6 * 8 + w.ncell * 4 * 8
+        d2h = ngr * (6 * 8 + 8) + w.ncell * 4 * 8
+        e2e = {"value": world * ngr * ke / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke}
+        ctx.close()
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline(w, steps=2)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Philox; shapes of the paper's shearing-box setup)",
+            "config": {"workload": WORKLOAD_NAME if not args.small else "sbox3d-small 16^3",
+                       "precision": "mixed: f32 push/gather, f64 positions, int64 deposit",
+                       "grains": ngr, "zones": w.ncell, "sort_interval": args.sort_interval or 1,
+                       "l2": "inputs larger than L2 (grain store %d MB)" % (ngr * 36 // 2**20),
+                       "parallelism": "independent instance per GPU"},
+            "status": rc,
+            "kernel_ms_per_step": {"step": kt.step_ms / args.steps, "sort": kt.sort_ms / args.steps,
+                                   "other": kt.other_ms / args.steps},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "kernel": "step (gather+push+deposit)",
+                         "algorithmic_bytes_per_launch": ab,
+                         "bytes_per_grain": per_grain, "bytes_per_zone": per_zone,
+                         "traffic": profiled_traffic("step", ngr)},
+            "gpu_launches": launches,
+            "fp64": fp64,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, steps=2, ngrains=None):
+    """The FP64 oracle as it stands (single thread) on the full grid and a
+    seeded subset (default: all) of the grains, `steps` steps."""
+    import oracle as O
+    O.build()
+    s = w if ngrains is None else I.subsample(w, ngrains)
+    prob = O.Problem(geom=s.geom, edges=s.edges, bc=s.bc, weight=s.weight,
+                     species_mass=s.species_mass, species_tau_mode=s.species_tau_mode,
+                     species_tau=s.species_tau, fargo=s.fargo, omega=s.omega, q=s.qshear,
+                     gm=s.gm, vertical_gravity=s.vertical_gravity, feedback_apply=s.feedback)
+    q = [x.copy() for x in s.q]
+    p = [x.copy() for x in s.v]
+    pg = O.gas_momentum(prob, s.vgas)
+    rho = s.rho.copy()
+    active = np.ones(s.ngrains, np.uint8)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        O.step(prob, q, p, active, k * s.dt, s.dt, rho, pg, s.species, s.param)
+    el = time.perf_counter() - t0
+    return {"value": s.ngrains * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d grains x %d steps of the same workload (full grid), single thread"
+                      % (s.ngrains, steps), "seconds": el}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = I.sbox3d("small" if args.small else "full")
+    n = min(w.ngrains, 1 << 21)
+    cpu_baseline(w, steps=1, ngrains=1024)  # build + warm the library
+    times = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, steps=1, ngrains=n)
+    for _ in range(args.steps):
+        r = cpu_baseline(w, steps=1, ngrains=n)
+        times.append(r["seconds"])
+    tot = sum(times)
+    value = n * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "grains_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d of the %d grains (full grid) per step, single thread"
+                                   % (n, w.ngrains)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

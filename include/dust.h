@@ -1,0 +1,227 @@
+/*
+ * dust.h - C interface of the GB300 dust drag-coupling library.
+ *
+ * One call of dust_step() performs, for every grain, the particle part of
+ * one hybrid time step of Mignone, Flock & Vaidya, "A Particle Module for
+ * the PLUTO Code: III - Dust" (arXiv:1908.10793):
+ *
+ *   - gather of gas density and momentum-like velocity at the grain's
+ *     half-step position with the paper's weights (Eq. Delta_vp; Sec. 3.4
+ *     Eqs. weight, b0, b1, CIC/TSC_cylindrical; App. C);
+ *   - the exponential-midpoint drift-kick-drift push (Eq. exp_midpoint,
+ *     Eqs. phi1, h1, kick_modified; App. B.1 shearing box, App. B.2
+ *     cylindrical and spherical);
+ *   - deposition of the drag back-reaction on the grid (Eq.
+ *     dust_feedback_final), in momentum and energy, into 64-bit fixed-point
+ *     accumulators, and optionally its application to the gas momentum (the
+ *     corrector term of the RK2 step, Sec. 3.1).
+ *
+ * Conventions
+ *   - Zones are indexed i + n[0] * (j + n[1] * k) (Sec. 3.1, cell index
+ *     i = (i,j,k)); a direction with n[d] == 1 is not gridded (2-D runs).
+ *   - Grain coordinates q = (x1, x2, x3): Cartesian (x,y,z); cylindrical
+ *     (R, phi, z); spherical (r, theta, phi).  Velocities passed in and out
+ *     are physical components; internally the library evolves the
+ *     momentum-like variables of Sec. 2.2 (l_phi = R v_phi; l_theta = r
+ *     v_theta, l_phi = r sin(theta) v_phi).  In the shearing box with orbital
+ *     advection (fargo = 1) velocities are the residual v' = v + q Omega x e_y
+ *     (Sec. 2.1).
+ *   - Every call returns an int status: DUST_OK (0) or a negative DUST_E*
+ *     code; dust_last_error() gives a message.
+ *   - Memory: the library owns all device memory of a context.  Inputs are
+ *     copied in; getters copy into caller buffers.  A `mem` argument says
+ *     whether caller pointers are host (DUST_MEM_HOST) or device
+ *     (DUST_MEM_DEVICE) memory; device pointers must be valid on the
+ *     context's device and their contents complete with respect to the
+ *     context's stream.
+ *   - All work is enqueued on the context's stream.  dust_step() does not
+ *     wait for the GPU; dust_sync() waits and returns the device status
+ *     words raised since the previous dust_sync().
+ *   - One context must not be used from two host threads at the same time.
+ */
+#ifndef DUST_H
+#define DUST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DUST_OK 0
+#define DUST_EINVAL (-1)    /* bad argument, NaN/Inf input, size out of range   */
+#define DUST_ENOMEM (-2)    /* device allocation failed                          */
+#define DUST_ECUDA (-3)     /* a CUDA runtime call failed                        */
+#define DUST_ECFL (-4)      /* a grain moved more than 1.8 zones in one step (Eq. particles_dt); results are still correct */
+#define DUST_EOVERFLOW (-5) /* a fixed-point deposit piece exceeded 2^52 quanta */
+#define DUST_ENAN (-6)      /* a NaN/Inf appeared on the device                  */
+#define DUST_ESTATE (-8)    /* call out of order (e.g. dust_step before data)    */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum { DUST_CARTESIAN = 0, DUST_SHEARING_BOX = 1, DUST_CYLINDRICAL = 2, DUST_SPHERICAL = 3 };
+enum { DUST_BC_PERIODIC = 0, DUST_BC_OUTFLOW = 1 };
+enum { DUST_WEIGHT_CIC = 0, DUST_WEIGHT_TSC = 1 };
+/* stopping time: DUST_TAU_CONST tau_s = value; DUST_TAU_STOKES tau_s =
+ * value / Omega_K (Omega_K = sqrt(GM / R^3) at the cylindrical radius of the
+ * half-step position; shearing box: value / Omega); DUST_TAU_EPSTEIN tau_s =
+ * value / rho_gathered (Epstein regime, Sec. 2: tau_s ~ 1/rho). */
+enum { DUST_TAU_CONST = 0, DUST_TAU_STOKES = 1, DUST_TAU_EPSTEIN = 2 };
+/* DUST_FP64: all arithmetic in double precision.  DUST_MIXED: positions in
+ * double precision, momentum-like variables, gas fields, weights, gather and
+ * push in single precision, deposit in 64-bit fixed point. */
+enum { DUST_FP64 = 0, DUST_MIXED = 1 };
+enum { DUST_MEM_HOST = 0, DUST_MEM_DEVICE = 1 };
+/* kernel choice: DUST_KERNEL_AUTO picks the tiled kernel where it applies;
+ * DUST_KERNEL_PER_GRAIN forces the one-thread-per-grain kernel that
+ * deposits through global atomics. */
+enum { DUST_KERNEL_AUTO = 0, DUST_KERNEL_PER_GRAIN = 1, DUST_KERNEL_TILED = 2 };
+
+/* status flag bits returned in dust_stats.flags */
+#define DUST_FLAG_NAN 1
+#define DUST_FLAG_OVERFLOW 2
+#define DUST_FLAG_CFL 4
+#define DUST_FLAG_WRAP 8   /* a grain moved more than one period in one step */
+
+/* ---- descriptors -------------------------------------------------------- */
+typedef struct dust_geometry {
+    int kind;             /* DUST_CARTESIAN .. DUST_SPHERICAL                   */
+    int fargo;            /* shearing box: 1 = orbital-advection (residual)
+                             form, Eq. FARGO_SB_p; 0 = standard, Eq. standard_SB_p */
+    double omega;         /* shearing box angular velocity Omega                */
+    double q;             /* shearing box shear parameter q (3/2: Keplerian)    */
+    double gm;            /* cylindrical / spherical point-mass GM (0 = none)   */
+    int vertical_gravity; /* shearing box: -Omega^2 z term; cylindrical: z
+                             component of the point-mass gravity                */
+} dust_geometry;
+
+typedef struct dust_grid {
+    int n[3];              /* zones per direction, >= 1                         */
+    const double *edges[3];/* host arrays of n[d] + 1 strictly increasing zone
+                              edges; copied by dust_create                      */
+    int bc[3];             /* DUST_BC_PERIODIC or DUST_BC_OUTFLOW per direction;
+                              shearing-box x is shear-periodic when periodic    */
+} dust_grid;
+
+typedef struct dust_species {
+    double mass;           /* grain (macro-particle) mass m_p                   */
+    int tau_mode;          /* DUST_TAU_*                                        */
+    double tau_value;      /* tau_s, St or the Epstein constant (may be +inf)  */
+} dust_species;
+
+typedef struct dust_options {
+    int precision;         /* DUST_FP64 or DUST_MIXED                           */
+    int weight;            /* DUST_WEIGHT_CIC or DUST_WEIGHT_TSC                */
+    int feedback_apply;    /* 1: add the deposit to the gas momentum each step  */
+    double quantum;        /* fixed-point quantum of the deposit (momentum
+                              units); 0 = 2^-50 * (largest species mass), i.e.
+                              velocity changes up to 4 code units per step fit
+                              the 2^52 exact range of one piece                 */
+    void *stream;          /* cudaStream_t to enqueue on; NULL = own stream     */
+    int sort_interval;     /* re-sort grains by zone every k steps (0 = 1)      */
+    int kernel;            /* DUST_KERNEL_*                                     */
+    int device;            /* CUDA device ordinal                               */
+    int timing;            /* 1: record device events around each kernel group
+                              (read with dust_get_kernel_times)                */
+    int tile[3];           /* zones per tile of the tiled kernel and of the
+                              sort order (0 = default: 8x8x8 in 3-D, 16x16 in
+                              2-D; clipped to the grid)                       */
+} dust_options;
+
+typedef struct dust_stats {
+    int64_t n_stored;      /* grains held (active and removed)                  */
+    int64_t n_active;      /* grains inside the domain                          */
+    int64_t n_removed;     /* grains removed through outflow boundaries, total  */
+    double max_cells_moved;/* largest per-step displacement seen, in zones      */
+    int flags;             /* DUST_FLAG_* raised since the previous dust_sync   */
+    int64_t steps;         /* steps taken                                       */
+    double time;           /* simulation time                                   */
+} dust_stats;
+
+/* Device time per kernel group, summed over the steps since the last reset
+ * (needs dust_options.timing = 1; launch counts are always kept). */
+typedef struct dust_kernel_times {
+    double step_ms;        /* gather-push-deposit kernel                        */
+    double sort_ms;        /* zone sort: keys, scan, scatter                    */
+    double other_ms;       /* deposit clear and feedback application            */
+    int64_t step_launches; /* kernels launched by the library, per group        */
+    int64_t sort_launches;
+    int64_t other_launches;
+    int64_t steps;
+} dust_kernel_times;
+
+typedef struct dust_ctx dust_ctx;
+
+/* Create a context for one grid and set of species.  `species` has
+ * n_species (1..16) entries; grains refer to them by index.  The grain
+ * store is described in Sec. 3 (each particle carries x_p, v_p, tau_s,p,
+ * m_p).  Errors: DUST_EINVAL (non-increasing edges, n[d] < 1, bad enums),
+ * DUST_ECUDA, DUST_ENOMEM.  On error *out is NULL. */
+int dust_create(dust_ctx **out, const dust_geometry *geom, const dust_grid *grid,
+                const dust_species *species, int n_species, const dust_options *opt);
+
+/* Set the gas: density rho and the physical velocity components v0, v1, v2
+ * per zone (length = number of zones).  The library stores the density and
+ * the momentum-like velocity p_g of Sec. 2.2, evaluated with the zone
+ * centre radius (cylindrical l_g = R_i v_phi; spherical r_i v_theta,
+ * r_i sin(theta_j) v_phi).  rho must be positive. */
+int dust_set_gas(dust_ctx *ctx, const double *rho, const double *v0, const double *v1,
+                 const double *v2, int mem);
+
+/* Read the gas back (physical velocity components), e.g. after feedback. */
+int dust_get_gas(dust_ctx *ctx, double *rho, double *v0, double *v1, double *v2, int mem);
+
+/* Load n grains (replacing any held): coordinates q0..q2 and physical
+ * velocities v0..v2 (float64, length n).  species: uint8 species index per
+ * grain, or NULL for species 0.  param: per-grain stopping-time value
+ * (overrides the species' tau_value), or NULL.  Grains get ids 0..n-1 in
+ * load order.  Coordinates must lie inside the grid; NaN/Inf rejected. */
+int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, const double *q1,
+                        const double *q2, const double *v0, const double *v1,
+                        const double *v2, const uint8_t *species, const double *param,
+                        int mem);
+
+/* Advance every grain by one step of size dt (dt may be negative: the
+ * scheme is time reversible, Sec. 3.2.2) and deposit the back-reaction of
+ * that step; with feedback_apply the deposit is then added to the gas
+ * momentum.  Asynchronous on the context stream. */
+int dust_step(dust_ctx *ctx, double dt);
+
+/* Wait for the context stream, fill *out (may be NULL) and return
+ * DUST_ENAN / DUST_EOVERFLOW / DUST_ECFL if the matching flag was raised
+ * since the previous dust_sync, else DUST_OK.  Flags are then cleared. */
+int dust_sync(dust_ctx *ctx, dust_stats *out);
+
+/* Deposit of the most recent step, channels (momentum-like 0..2, energy 3)
+ * per zone: fixed ([ncell][4] int64, units of the quantum) and/or as_double
+ * ([ncell][4], fixed * quantum); either may be NULL.  Channel c of zone i is
+ * -sum_p m_p W_ip (dp_c - dt a_c) (Eq. dust_feedback_final times dV dt),
+ * the impulse given to the gas; channel 3 is sum_c of that times dH/dp_c at
+ * the half step (energy given to the gas).  *quantum_out may be NULL. */
+int dust_get_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double,
+                     double *quantum_out, int mem);
+
+/* Copy the stored grains (current storage order, which the zone sort
+ * permutes): coordinates, physical velocities and original ids (int64).
+ * Removed grains are included with NaN coordinates.  cap = capacity of the
+ * caller arrays; *n_out = grains written.  Any pointer but n_out may be
+ * NULL. */
+int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
+                       double *v0, double *v1, double *v2, int64_t *ids, int64_t *n_out,
+                       int mem);
+
+/* Wait for the context stream and return the per-group device times and
+ * launch counts accumulated since the last reset; reset != 0 clears them. */
+int dust_get_kernel_times(dust_ctx *ctx, dust_kernel_times *out, int reset);
+
+/* Message of the last error on this context (static storage of the
+ * context; NULL ctx gives the last dust_create error). */
+const char *dust_last_error(const dust_ctx *ctx);
+
+/* Free the context and all its device memory.  NULL is allowed. */
+void dust_destroy(dust_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DUST_H */

@@ -1,0 +1,1007 @@
+// Host side of the C interface declared in include/dust.h: context
+// management, data movement, unit conversion, step sequencing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dust_internal.h"
+
+using namespace dust;
+
+namespace {
+
+enum { ST_LOAD_BAD = 4 };
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct dust_ctx {
+    int device = 0;
+    dust_geometry geom{};
+    dust_options opt{};
+    int mixed = 1;
+    size_t rsz = 4;
+    int n[3] = {1, 1, 1};
+    int bc[3] = {0, 0, 0};
+    std::vector<double> edges[3];
+    SpeciesDev sp{};
+    int64_t ncell = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    GridDev g{};
+    double *d_edges[3] = {nullptr, nullptr, nullptr};
+    double *d_dvol[3] = {nullptr, nullptr, nullptr};
+    float *d_dvol_f[3] = {nullptr, nullptr, nullptr};
+    double *d_zc[3] = {nullptr, nullptr, nullptr};
+    double *d_ziw[3] = {nullptr, nullptr, nullptr};
+    float *d_ziw_f[3] = {nullptr, nullptr, nullptr};
+    float *d_znu_f[3] = {nullptr, nullptr, nullptr};
+    float *d_zlo_f[3] = {nullptr, nullptr, nullptr};
+    bool need_sort = true;
+    void *d_gas = nullptr;
+    unsigned long long *d_dep = nullptr;
+    unsigned int *d_status = nullptr;
+    unsigned int *h_status = nullptr;
+
+    double *d_q[2][3] = {};
+    void *d_p[2][3] = {};
+    uint8_t *d_species[2] = {nullptr, nullptr};
+    void *d_param[2] = {nullptr, nullptr};
+    int32_t *d_id[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t n_grains = 0, cap = 0;
+    bool has_species = false, has_param = false;
+
+    int32_t *d_key = nullptr, *d_count = nullptr, *d_cursor = nullptr, *d_blocksums = nullptr;
+    double *d_stage = nullptr;
+    size_t stage_bytes = 0;
+
+    double t = 0.0;
+    int64_t steps = 0;
+    int64_t removed_total = 0;
+    float max_moved = 0.f;
+    bool gas_set = false, particles_set = false, have_deposit = false;
+    double quantum = 0.0;
+    int sort_interval = 1;
+    std::string err;
+
+    // per-group device timing (dust_options.timing) and launch counts
+    enum { GROUP_STEP = 0, GROUP_SORT = 1, GROUP_OTHER = 2, N_GROUPS = 3 };
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[N_GROUPS];
+    double group_ms[N_GROUPS] = {0, 0, 0};
+    int64_t launches[N_GROUPS] = {0, 0, 0};
+    int64_t timed_steps = 0;
+};
+
+namespace {
+
+int fail(dust_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? DUST_ENOMEM : DUST_ECUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                    \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+void dfree(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+int edge_kind(const std::vector<double> &e)
+{
+    const int n = (int)e.size() - 1;
+    if (n <= 1) return EDGE_UNIFORM;
+    const double lo = e[0], hi = e[n];
+    bool uni = true, lg = lo > 0.0;
+    for (int i = 0; i <= n && (uni || lg); ++i) {
+        const double u = lo + (hi - lo) * i / n;
+        if (fabs(e[i] - u) > 1e-9 * (hi - lo) / n) uni = false;
+        if (lg) {
+            const double l = lo * pow(hi / lo, (double)i / n);
+            if (fabs(e[i] - l) > 1e-9 * (e[i] * (pow(hi / lo, 1.0 / n) - 1.0))) lg = false;
+        }
+    }
+    return uni ? EDGE_UNIFORM : (lg ? EDGE_LOG : EDGE_GENERAL);
+}
+
+// --------------------------------------------------------- aux kernels ----
+
+__device__ __forceinline__ double centre(const GridDev &g, int d, int i)
+{
+    return 0.5 * (g.edges[d][i] + g.edges[d][i + 1]);
+}
+
+// Physical gas velocity -> stored momentum-like velocity (Sec. 2.2), zone
+// centre factors.
+template <typename Real>
+__global__ void set_gas_kernel(GridDev g, int geom, const double *rho, const double *v0,
+                               const double *v1, const double *v2, Real *gas, unsigned int *st)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    double p0 = v0[c], p1 = v1[c], p2 = v2[c];
+    const double r = rho[c];
+    if (geom == GEOM_CYL) p1 *= centre(g, 0, i);
+    if (geom == GEOM_SPH) {
+        const double rc = centre(g, 0, i);
+        p1 *= rc;
+        p2 *= rc * sin(centre(g, 1, j));
+    }
+    if (!(r > 0.0) || !isfinite(r) || !isfinite(p0) || !isfinite(p1) || !isfinite(p2))
+        atomicOr(&st[ST_LOAD_BAD], 1u);
+    gas[4 * c + 0] = (Real)r;
+    gas[4 * c + 1] = (Real)p0;
+    gas[4 * c + 2] = (Real)p1;
+    gas[4 * c + 3] = (Real)p2;
+}
+
+template <typename Real>
+__global__ void get_gas_kernel(GridDev g, int geom, const Real *gas, double *rho, double *v0,
+                               double *v1, double *v2)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    double p0 = gas[4 * c + 1], p1 = gas[4 * c + 2], p2 = gas[4 * c + 3];
+    if (geom == GEOM_CYL) p1 /= centre(g, 0, i);
+    if (geom == GEOM_SPH) {
+        const double rc = centre(g, 0, i);
+        p1 /= rc;
+        p2 /= rc * sin(centre(g, 1, j));
+    }
+    if (rho) rho[c] = gas[4 * c + 0];
+    if (v0) v0[c] = p0;
+    if (v1) v1[c] = p1;
+    if (v2) v2[c] = p2;
+}
+
+// Physical grain velocity -> momentum-like variables (Sec. 2.2).
+template <typename Real>
+__global__ void load_kernel(GridDev g, int geom, int64_t n, const double *q0, const double *q1,
+                            const double *q2, const double *v0, const double *v1,
+                            const double *v2, const uint8_t *species_in, int n_species,
+                            const double *param_in, StoreDev<Real> s, unsigned int *st)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double x0 = q0[k], x1 = q1[k], x2 = q2[k];
+    double p0 = v0[k], p1 = v1[k], p2 = v2[k];
+    bool bad = !(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(p0) &&
+                 isfinite(p1) && isfinite(p2));
+    bad |= !(x0 >= g.lo[0] && x0 < g.hi[0] && x1 >= g.lo[1] && x1 < g.hi[1] &&
+             x2 >= g.lo[2] && x2 < g.hi[2]);
+    if (geom == GEOM_CYL) p1 *= x0;
+    if (geom == GEOM_SPH) {
+        p1 *= x0;
+        p2 *= x0 * sin(x1);
+    }
+    s.q[0][k] = x0; s.q[1][k] = x1; s.q[2][k] = x2;
+    s.p[0][k] = (Real)p0; s.p[1][k] = (Real)p1; s.p[2][k] = (Real)p2;
+    s.id[k] = (int32_t)k;
+    if (s.species) {
+        const uint8_t sp = species_in[k];
+        if (sp >= n_species) bad = true;
+        s.species[k] = sp;
+    }
+    if (s.param) {
+        const double v = param_in[k];
+        if (!(v >= 0.0) || isnan(v)) bad = true;
+        s.param[k] = (Real)v;
+    }
+    if (bad) atomicOr(&st[ST_LOAD_BAD], 1u);
+}
+
+template <typename Real>
+__global__ void get_particles_kernel(int geom, StoreDev<Real> s, double *q0, double *q1,
+                                     double *q2, double *v0, double *v1, double *v2,
+                                     int64_t *ids)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.n) return;
+    const double x0 = s.q[0][k], x1 = s.q[1][k], x2 = s.q[2][k];
+    double p0 = s.p[0][k], p1 = s.p[1][k], p2 = s.p[2][k];
+    if (geom == GEOM_CYL) p1 /= x0;
+    if (geom == GEOM_SPH) {
+        p1 /= x0;
+        p2 /= x0 * sin(x1);
+    }
+    if (q0) q0[k] = x0;
+    if (q1) q1[k] = x1;
+    if (q2) q2[k] = x2;
+    if (v0) v0[k] = p0;
+    if (v1) v1[k] = p1;
+    if (v2) v2[k] = p2;
+    if (ids) ids[k] = s.id[k];
+}
+
+// Feedback on the gas momentum: rho p_g += dP / dV (corrector term of the
+// RK2 step, Sec. 3.1; the gas is otherwise held fixed).
+template <typename Real>
+__global__ void apply_feedback_kernel(GridDev g, double quantum, Real *gas,
+                                      const unsigned long long *dep)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((int64_t)g.n[0] * g.n[1]));
+    const long long d0 = (long long)dep[4 * c + 0], d1 = (long long)dep[4 * c + 1],
+                    d2 = (long long)dep[4 * c + 2];
+    if ((d0 | d1 | d2) == 0) return;
+    if (sizeof(Real) == 4) {
+        const float s = (float)quantum /
+                        ((float)gas[4 * c] * g.dvol_f[0][i] * g.dvol_f[1][j] * g.dvol_f[2][k]);
+        gas[4 * c + 1] += (Real)((float)d0 * s);
+        gas[4 * c + 2] += (Real)((float)d1 * s);
+        gas[4 * c + 3] += (Real)((float)d2 * s);
+    } else {
+        const double s = quantum / ((double)gas[4 * c] * g.dvol[0][i] * g.dvol[1][j] * g.dvol[2][k]);
+        gas[4 * c + 1] += (Real)((double)d0 * s);
+        gas[4 * c + 2] += (Real)((double)d1 * s);
+        gas[4 * c + 3] += (Real)((double)d2 * s);
+    }
+}
+
+__global__ void dep_to_double_kernel(const unsigned long long *dep, int64_t n, double quantum,
+                                     double *out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = (double)(long long)dep[k] * quantum;
+}
+
+inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <typename Real>
+StoreDev<Real> store_of(dust_ctx *c, int which)
+{
+    StoreDev<Real> s;
+    for (int d = 0; d < 3; ++d) {
+        s.q[d] = c->d_q[which][d];
+        s.p[d] = static_cast<Real *>(c->d_p[which][d]);
+    }
+    s.species = c->has_species ? c->d_species[which] : nullptr;
+    s.param = c->has_param ? static_cast<Real *>(c->d_param[which]) : nullptr;
+    s.id = c->d_id[which];
+    s.n = c->n_grains;
+    return s;
+}
+
+PhysDev phys_of(const dust_ctx *c, double t, double dt)
+{
+    PhysDev ph{};
+    ph.geom = c->geom.kind;
+    ph.fargo = c->geom.fargo;
+    ph.vgrav = c->geom.vertical_gravity;
+    ph.omega = c->geom.omega;
+    ph.qshear = c->geom.q;
+    ph.gm = c->geom.gm;
+    ph.q_om = c->geom.q * c->geom.omega;
+    const double Lx = c->g.hi[0] - c->g.lo[0];
+    const double Ly = c->g.hi[1] - c->g.lo[1];
+    ph.jump_v = c->geom.q * c->geom.omega * Lx;
+    if (c->geom.kind == DUST_SHEARING_BOX) {
+        // same expression order as q Omega Lx t, reduced modulo Ly
+        ph.shift_mid = fmod(c->geom.q * c->geom.omega * Lx * (t + 0.5 * dt), Ly);
+        ph.shift_end = fmod(c->geom.q * c->geom.omega * Lx * (t + dt), Ly);
+    }
+    return ph;
+}
+
+int ensure_stage(dust_ctx *ctx, size_t bytes)
+{
+    if (ctx->stage_bytes >= bytes) return DUST_OK;
+    dfree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->stage_bytes = 0;
+    CU(cudaMalloc(reinterpret_cast<void **>(&ctx->d_stage), bytes));
+    ctx->stage_bytes = bytes;
+    return DUST_OK;
+}
+
+cudaEvent_t take_event(dust_ctx *ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records an event pair around a kernel group when timing is on.
+struct GroupTimer {
+    dust_ctx *ctx;
+    int group;
+    cudaEvent_t a = nullptr;
+    GroupTimer(dust_ctx *c, int g) : ctx(c), group(g)
+    {
+        if (ctx->opt.timing && (a = take_event(ctx))) cudaEventRecord(a, ctx->stream);
+    }
+    ~GroupTimer()
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(ctx);
+        if (!b) { ctx->event_pool.push_back(a); return; }
+        cudaEventRecord(b, ctx->stream);
+        ctx->pending[group].emplace_back(a, b);
+    }
+};
+
+// Copy `count` doubles from caller memory into staging slot `slot` (device).
+const double *stage_in(dust_ctx *ctx, const double *src, int64_t count, int slot, int mem)
+{
+    if (!src) return nullptr;
+    if (mem == DUST_MEM_DEVICE) return src;
+    double *dst = ctx->d_stage + (size_t)slot * count;
+    cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    return dst;
+}
+
+void free_store(dust_ctx *c)
+{
+    for (int w = 0; w < 2; ++w) {
+        for (int d = 0; d < 3; ++d) {
+            dfree(c->d_q[w][d]);
+            dfree(c->d_p[w][d]);
+            c->d_q[w][d] = nullptr;
+            c->d_p[w][d] = nullptr;
+        }
+        dfree(c->d_species[w]);
+        dfree(c->d_param[w]);
+        dfree(c->d_id[w]);
+        c->d_species[w] = nullptr;
+        c->d_param[w] = nullptr;
+        c->d_id[w] = nullptr;
+    }
+    dfree(c->d_key);
+    c->d_key = nullptr;
+    c->cap = 0;
+}
+
+int alloc_store(dust_ctx *ctx, int64_t n)
+{
+    free_store(ctx);
+    for (int w = 0; w < 2; ++w) {
+        for (int d = 0; d < 3; ++d) {
+            CU(dalloc(&ctx->d_q[w][d], n));
+            CU(cudaMalloc(&ctx->d_p[w][d], n * ctx->rsz));
+        }
+        CU(dalloc(&ctx->d_id[w], n));
+        if (ctx->has_species) CU(dalloc(&ctx->d_species[w], n));
+        if (ctx->has_param) CU(cudaMalloc(&ctx->d_param[w], n * ctx->rsz));
+    }
+    CU(dalloc(&ctx->d_key, n));
+    ctx->cap = n;
+    return DUST_OK;
+}
+
+template <typename Real>
+int run_sort(dust_ctx *ctx, double dt)
+{
+    SortArgs<Real> a;
+    a.g = ctx->g;
+    a.ph = phys_of(ctx, ctx->t, dt);
+    a.dt = dt;
+    a.src = store_of<Real>(ctx, ctx->cur);
+    a.dst = store_of<Real>(ctx, 1 - ctx->cur);
+    a.key = ctx->d_key;
+    a.count = ctx->d_count;
+    a.cursor = ctx->d_cursor;
+    const int64_t m = ctx->g.nkeys + 1;
+    GroupTimer timer(ctx, dust_ctx::GROUP_SORT);
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += 5;
+    CU(cudaMemsetAsync(ctx->d_count, 0, m * sizeof(int32_t), ctx->stream));
+    cudaError_t e = cudaSuccess;
+    switch (ctx->geom.kind) {
+    case DUST_CARTESIAN: e = launch_sort_keys<Real, GEOM_CART>(a, ctx->stream); break;
+    case DUST_SHEARING_BOX: e = launch_sort_keys<Real, GEOM_SB>(a, ctx->stream); break;
+    case DUST_CYLINDRICAL: e = launch_sort_keys<Real, GEOM_CYL>(a, ctx->stream); break;
+    default: e = launch_sort_keys<Real, GEOM_SPH>(a, ctx->stream); break;
+    }
+    CU(e);
+    CU(launch_exclusive_scan(ctx->d_count, m, ctx->d_blocksums, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->d_cursor, ctx->d_count, m * sizeof(int32_t),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(launch_sort_scatter<Real>(a, ctx->stream));
+    ctx->cur = 1 - ctx->cur;
+    return DUST_OK;
+}
+
+template <typename Real, int GEOM>
+cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, bool tiled,
+                             const int32_t *key_off, cudaStream_t s)
+{
+    if (tiled) {
+        TiledArgs<Real> ta;
+        ta.s = a;
+        ta.key_off = key_off;
+        return weight == DUST_WEIGHT_TSC ? launch_step_tiled<Real, GEOM, 1>(ta, s)
+                                         : launch_step_tiled<Real, GEOM, 0>(ta, s);
+    }
+    return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<Real, GEOM, 1>(a, s)
+                                     : launch_step_per_grain<Real, GEOM, 0>(a, s);
+}
+
+template <typename Real>
+int run_step(dust_ctx *ctx, double dt)
+{
+    StepArgs<Real> a;
+    a.g = ctx->g;
+    a.ph = phys_of(ctx, ctx->t, dt);
+    a.sp = ctx->sp;
+    a.t = ctx->t;
+    a.dt = dt;
+    a.inv_quantum = 1.0 / ctx->quantum;
+    a.s = store_of<Real>(ctx, ctx->cur);
+    a.gas = static_cast<const Real *>(ctx->d_gas);
+    a.dep = ctx->d_dep;
+    a.status = ctx->d_status;
+    {
+        GroupTimer timer(ctx, dust_ctx::GROUP_OTHER);
+        CU(cudaMemsetAsync(ctx->d_dep, 0, ctx->ncell * 4 * sizeof(unsigned long long), ctx->stream));
+    }
+    cudaError_t e;
+    GroupTimer *step_timer = new GroupTimer(ctx, dust_ctx::GROUP_STEP);
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_STEP] += 1;
+    const bool tiled = ctx->opt.kernel != DUST_KERNEL_PER_GRAIN;
+    const int wt = ctx->opt.weight;
+    const int32_t *ko = ctx->d_count;
+    cudaStream_t st = ctx->stream;
+    switch (ctx->geom.kind) {
+    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, tiled, ko, st); break;
+    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, tiled, ko, st); break;
+    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, tiled, ko, st); break;
+    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, tiled, ko, st); break;
+    }
+    delete step_timer;
+    CU(e);
+    if (ctx->opt.feedback_apply) {
+        GroupTimer timer(ctx, dust_ctx::GROUP_OTHER);
+        ctx->launches[dust_ctx::GROUP_OTHER] += 1;
+        apply_feedback_kernel<Real><<<blocks_for(ctx->ncell), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->quantum, static_cast<Real *>(ctx->d_gas), ctx->d_dep);
+        CU(cudaGetLastError());
+    }
+    return DUST_OK;
+}
+
+}  // namespace
+
+// ================================================================ C API ====
+
+extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust_grid *grid,
+                           const dust_species *species, int n_species, const dust_options *opt)
+{
+    if (!out) return fail(nullptr, DUST_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!geom || !grid || !species || !opt) return fail(nullptr, DUST_EINVAL, "NULL descriptor");
+    if (geom->kind < DUST_CARTESIAN || geom->kind > DUST_SPHERICAL)
+        return fail(nullptr, DUST_EINVAL, "bad geometry kind %d", geom->kind);
+    if (n_species < 1 || n_species > kMaxSpecies)
+        return fail(nullptr, DUST_EINVAL, "n_species must be 1..%d", kMaxSpecies);
+    if (opt->precision != DUST_FP64 && opt->precision != DUST_MIXED)
+        return fail(nullptr, DUST_EINVAL, "bad precision");
+    if (opt->weight != DUST_WEIGHT_CIC && opt->weight != DUST_WEIGHT_TSC)
+        return fail(nullptr, DUST_EINVAL, "bad weight");
+    int64_t ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (grid->n[d] < 1 || !grid->edges[d])
+            return fail(nullptr, DUST_EINVAL, "direction %d: n < 1 or no edges", d);
+        for (int i = 0; i < grid->n[d]; ++i)
+            if (!(grid->edges[d][i] < grid->edges[d][i + 1]) || !std::isfinite(grid->edges[d][i + 1]))
+                return fail(nullptr, DUST_EINVAL, "direction %d: edges not increasing", d);
+        if (grid->bc[d] != DUST_BC_PERIODIC && grid->bc[d] != DUST_BC_OUTFLOW)
+            return fail(nullptr, DUST_EINVAL, "direction %d: bad boundary kind", d);
+        ncell *= grid->n[d];
+    }
+    if (ncell >= (int64_t)1 << 31) return fail(nullptr, DUST_EINVAL, "too many zones");
+    if (geom->kind == DUST_CYLINDRICAL && grid->edges[0][0] <= 0.0)
+        return fail(nullptr, DUST_EINVAL, "cylindrical R must be > 0");
+    if (geom->kind == DUST_SPHERICAL &&
+        (grid->edges[0][0] <= 0.0 || grid->edges[1][0] <= 0.0 ||
+         grid->edges[1][grid->n[1]] >= M_PI))
+        return fail(nullptr, DUST_EINVAL, "spherical r must be > 0 and theta in (0, pi)");
+    if ((geom->kind == DUST_CYLINDRICAL || geom->kind == DUST_SPHERICAL))
+        for (int s = 0; s < n_species; ++s)
+            if (species[s].tau_mode == DUST_TAU_STOKES && !(geom->gm > 0.0))
+                return fail(nullptr, DUST_EINVAL, "Stokes-number mode needs GM > 0");
+
+    dust_ctx *ctx = new (std::nothrow) dust_ctx();
+    if (!ctx) return fail(nullptr, DUST_ENOMEM, "host allocation failed");
+    ctx->geom = *geom;
+    ctx->opt = *opt;
+    ctx->mixed = opt->precision == DUST_MIXED;
+    ctx->rsz = ctx->mixed ? 4 : 8;
+    ctx->device = opt->device;
+    ctx->ncell = ncell;
+    ctx->sort_interval = opt->sort_interval > 0 ? opt->sort_interval : 1;
+    double mmax = 0.0;
+    ctx->sp.n = n_species;
+    for (int s = 0; s < n_species; ++s) {
+        ctx->sp.mass[s] = species[s].mass;
+        ctx->sp.tau[s] = species[s].tau_value;
+        ctx->sp.mode[s] = species[s].tau_mode;
+        mmax = fmax(mmax, fabs(species[s].mass));
+    }
+    ctx->quantum = opt->quantum > 0.0 ? opt->quantum : ldexp(mmax > 0 ? mmax : 1.0, -50);
+
+    auto bail = [&](int code) {
+        std::string msg = ctx->err;
+        dust_destroy(ctx);
+        return fail(nullptr, code, "%s", msg.c_str());
+    };
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        ctx->err = "cudaSetDevice failed";
+        return bail(DUST_ECUDA);
+    }
+    if (opt->stream) {
+        ctx->stream = static_cast<cudaStream_t>(opt->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            ctx->err = "stream creation failed";
+            return bail(DUST_ECUDA);
+        }
+        ctx->own_stream = true;
+    }
+    GridDev &g = ctx->g;
+    g.ncell = ncell;
+    for (int d = 0; d < 3; ++d) {
+        const int n = grid->n[d];
+        ctx->n[d] = n;
+        ctx->bc[d] = grid->bc[d];
+        ctx->edges[d].assign(grid->edges[d], grid->edges[d] + n + 1);
+        const std::vector<double> &e = ctx->edges[d];
+        g.n[d] = n;
+        g.bc[d] = grid->bc[d];
+        g.lo[d] = e[0];
+        g.hi[d] = e[n];
+        g.edge_kind[d] = edge_kind(e);
+        if (g.edge_kind[d] == EDGE_LOG) {
+            g.inv_d[d] = n / log(e[n] / e[0]);
+            g.log_lo_f[d] = logf((float)e[0]);
+        } else {
+            g.inv_d[d] = n / (e[n] - e[0]);
+            g.log_lo_f[d] = 0.f;
+        }
+        g.inv_df[d] = (float)g.inv_d[d];
+        std::vector<double> dv(n);
+        std::vector<float> dvf(n);
+        for (int i = 0; i < n; ++i) {
+            const double a = e[i], b = e[i + 1];
+            double v = b - a;
+            if (d == 0 && geom->kind == DUST_CYLINDRICAL) v = 0.5 * (b * b - a * a);
+            if (d == 0 && geom->kind == DUST_SPHERICAL) v = (b * b * b - a * a * a) / 3.0;
+            if (d == 1 && geom->kind == DUST_SPHERICAL) v = cos(a) - cos(b);
+            dv[i] = v;
+            dvf[i] = (float)v;
+        }
+        // per-zone centre, inverse width, centre/width and lower edges
+        std::vector<double> zc(n), ziw(n);
+        std::vector<float> ziwf(n), znuf(n), zlof(n + 1);
+        for (int i = 0; i < n; ++i) {
+            zc[i] = 0.5 * (e[i] + e[i + 1]);
+            ziw[i] = 1.0 / (e[i + 1] - e[i]);
+            ziwf[i] = (float)ziw[i];
+            znuf[i] = (float)(zc[i] * ziw[i]);
+        }
+        for (int i = 0; i <= n; ++i) zlof[i] = (float)e[i];
+        if (dalloc(&ctx->d_edges[d], n + 1) != cudaSuccess || dalloc(&ctx->d_dvol[d], n) != cudaSuccess ||
+            dalloc(&ctx->d_dvol_f[d], n) != cudaSuccess || dalloc(&ctx->d_zc[d], n) != cudaSuccess ||
+            dalloc(&ctx->d_ziw[d], n) != cudaSuccess || dalloc(&ctx->d_ziw_f[d], n) != cudaSuccess ||
+            dalloc(&ctx->d_znu_f[d], n) != cudaSuccess || dalloc(&ctx->d_zlo_f[d], n + 1) != cudaSuccess) {
+            ctx->err = "device allocation of grid arrays failed";
+            return bail(DUST_ENOMEM);
+        }
+        cudaMemcpy(ctx->d_edges[d], e.data(), (n + 1) * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_dvol[d], dv.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_dvol_f[d], dvf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_zc[d], zc.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_ziw[d], ziw.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_ziw_f[d], ziwf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_znu_f[d], znuf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_zlo_f[d], zlof.data(), (n + 1) * sizeof(float), cudaMemcpyHostToDevice);
+        g.edges[d] = ctx->d_edges[d];
+        g.dvol[d] = ctx->d_dvol[d];
+        g.dvol_f[d] = ctx->d_dvol_f[d];
+        g.zc[d] = ctx->d_zc[d];
+        g.ziw[d] = ctx->d_ziw[d];
+        g.ziw_f[d] = ctx->d_ziw_f[d];
+        g.znu_f[d] = ctx->d_znu_f[d];
+        g.zlo_f[d] = ctx->d_zlo_f[d];
+    }
+    // tile layout: default 8^3 zones in 3-D, 16^2 in 2-D, 256 in 1-D
+    {
+        int nd = 0;
+        for (int d = 0; d < 3; ++d) nd += grid->n[d] > 1;
+        const int def = nd >= 3 ? 8 : (nd == 2 ? 16 : 256);
+        g.tvol = 1;
+        g.nkeys = 1;
+        for (int d = 0; d < 3; ++d) {
+            int t = opt->tile[d] > 0 ? opt->tile[d] : def;
+            if (grid->n[d] <= 1) t = 1;
+            if (t > grid->n[d]) t = grid->n[d];
+            g.T[d] = t;
+            g.nt[d] = (grid->n[d] + t - 1) / t;
+            g.tvol *= t;
+        }
+        g.nkeys = (int64_t)g.nt[0] * g.nt[1] * g.nt[2] * g.tvol;
+        if (g.nkeys + 2 >= ((int64_t)1 << 31)) {
+            ctx->err = "too many sort keys for this tile layout";
+            return bail(DUST_EINVAL);
+        }
+        const size_t smem = (size_t)(g.T[0] + (grid->n[0] > 1 ? 2 : 0)) *
+                            (g.T[1] + (grid->n[1] > 1 ? 2 : 0)) *
+                            (g.T[2] + (grid->n[2] > 1 ? 2 : 0)) * (4 * ctx->rsz + 32);
+        if (smem > 200 * 1024) {
+            ctx->err = "tile too large for shared memory";
+            return bail(DUST_EINVAL);
+        }
+    }
+    const int64_t nk = g.nkeys;
+    if (cudaMalloc(&ctx->d_gas, ncell * 4 * ctx->rsz) != cudaSuccess ||
+        dalloc(&ctx->d_dep, ncell * 4) != cudaSuccess ||
+        dalloc(&ctx->d_status, ST_WORDS) != cudaSuccess ||
+        dalloc(&ctx->d_count, nk + 2) != cudaSuccess ||
+        dalloc(&ctx->d_cursor, nk + 2) != cudaSuccess ||
+        dalloc(&ctx->d_blocksums, scan_block_sums_size(nk + 2)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&ctx->h_status), ST_WORDS * sizeof(unsigned)) !=
+            cudaSuccess) {
+        ctx->err = "device allocation failed";
+        return bail(DUST_ENOMEM);
+    }
+    cudaMemset(ctx->d_gas, 0, ncell * 4 * ctx->rsz);
+    cudaMemset(ctx->d_dep, 0, ncell * 4 * sizeof(unsigned long long));
+    cudaMemset(ctx->d_status, 0, ST_WORDS * sizeof(unsigned));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        ctx->err = "device initialisation failed";
+        return bail(DUST_ECUDA);
+    }
+    *out = ctx;
+    return DUST_OK;
+}
+
+extern "C" int dust_set_gas(dust_ctx *ctx, const double *rho, const double *v0, const double *v1,
+                            const double *v2, int mem)
+{
+    if (!ctx) return DUST_EINVAL;
+    if (!rho || !v0 || !v1 || !v2) return fail(ctx, DUST_EINVAL, "NULL gas array");
+    CU(cudaSetDevice(ctx->device));
+    const int64_t nc = ctx->ncell;
+    if (mem == DUST_MEM_HOST) {
+        int r = ensure_stage(ctx, 4 * nc * sizeof(double));
+        if (r) return r;
+    }
+    const double *a = stage_in(ctx, rho, nc, 0, mem), *b = stage_in(ctx, v0, nc, 1, mem),
+                 *c = stage_in(ctx, v1, nc, 2, mem), *d = stage_in(ctx, v2, nc, 3, mem);
+    CU(cudaMemsetAsync(ctx->d_status + ST_LOAD_BAD, 0, sizeof(unsigned), ctx->stream));
+    if (ctx->mixed)
+        set_gas_kernel<float><<<blocks_for(nc), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->geom.kind, a, b, c, d, static_cast<float *>(ctx->d_gas), ctx->d_status);
+    else
+        set_gas_kernel<double><<<blocks_for(nc), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->geom.kind, a, b, c, d, static_cast<double *>(ctx->d_gas), ctx->d_status);
+    CU(cudaGetLastError());
+    unsigned bad = 0;
+    CU(cudaMemcpyAsync(&bad, ctx->d_status + ST_LOAD_BAD, sizeof bad, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (bad) return fail(ctx, DUST_EINVAL, "gas density must be positive and all values finite");
+    ctx->gas_set = true;
+    return DUST_OK;
+}
+
+extern "C" int dust_get_gas(dust_ctx *ctx, double *rho, double *v0, double *v1, double *v2, int mem)
+{
+    if (!ctx) return DUST_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    const int64_t nc = ctx->ncell;
+    double *outs[4] = {rho, v0, v1, v2};
+    double *dev[4] = {rho, v0, v1, v2};
+    if (mem == DUST_MEM_HOST) {
+        int r = ensure_stage(ctx, 4 * nc * sizeof(double));
+        if (r) return r;
+        for (int k = 0; k < 4; ++k) dev[k] = outs[k] ? ctx->d_stage + k * nc : nullptr;
+    }
+    if (ctx->mixed)
+        get_gas_kernel<float><<<blocks_for(nc), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->geom.kind, static_cast<const float *>(ctx->d_gas), dev[0], dev[1], dev[2], dev[3]);
+    else
+        get_gas_kernel<double><<<blocks_for(nc), 256, 0, ctx->stream>>>(
+            ctx->g, ctx->geom.kind, static_cast<const double *>(ctx->d_gas), dev[0], dev[1], dev[2], dev[3]);
+    CU(cudaGetLastError());
+    if (mem == DUST_MEM_HOST)
+        for (int k = 0; k < 4; ++k)
+            if (outs[k])
+                CU(cudaMemcpyAsync(outs[k], dev[k], nc * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DUST_OK;
+}
+
+extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, const double *q1,
+                                   const double *q2, const double *v0, const double *v1,
+                                   const double *v2, const uint8_t *species, const double *param,
+                                   int mem)
+{
+    if (!ctx) return DUST_EINVAL;
+    if (n < 0 || n >= ((int64_t)1 << 31) - 1) return fail(ctx, DUST_EINVAL, "bad grain count");
+    if (n > 0 && (!q0 || !q1 || !q2 || !v0 || !v1 || !v2))
+        return fail(ctx, DUST_EINVAL, "NULL particle array");
+    CU(cudaSetDevice(ctx->device));
+    const bool hs = species != nullptr, hp = param != nullptr;
+    if (n > ctx->cap || hs != ctx->has_species || hp != ctx->has_param) {
+        ctx->has_species = hs;
+        ctx->has_param = hp;
+        int r = alloc_store(ctx, n > 0 ? n : 1);
+        if (r) return r;
+    }
+    ctx->n_grains = n;
+    ctx->cur = 0;
+    ctx->need_sort = true;
+    if (n > 0) {
+        const uint8_t *sp_dev = species;
+        if (mem == DUST_MEM_HOST) {
+            const size_t need = (7 * n) * sizeof(double) + (hs ? n : 0) + 16;
+            int r = ensure_stage(ctx, need);
+            if (r) return r;
+        }
+        const double *a = stage_in(ctx, q0, n, 0, mem), *b = stage_in(ctx, q1, n, 1, mem),
+                     *c = stage_in(ctx, q2, n, 2, mem), *d = stage_in(ctx, v0, n, 3, mem),
+                     *e = stage_in(ctx, v1, n, 4, mem), *f = stage_in(ctx, v2, n, 5, mem),
+                     *pp = stage_in(ctx, param, n, 6, mem);
+        if (hs && mem == DUST_MEM_HOST) {
+            uint8_t *dst = reinterpret_cast<uint8_t *>(ctx->d_stage + 7 * n);
+            CU(cudaMemcpyAsync(dst, species, n, cudaMemcpyHostToDevice, ctx->stream));
+            sp_dev = dst;
+        }
+        CU(cudaMemsetAsync(ctx->d_status + ST_LOAD_BAD, 0, sizeof(unsigned), ctx->stream));
+        if (ctx->mixed)
+            load_kernel<float><<<blocks_for(n), 256, 0, ctx->stream>>>(
+                ctx->g, ctx->geom.kind, n, a, b, c, d, e, f, sp_dev, ctx->sp.n, pp,
+                store_of<float>(ctx, 0), ctx->d_status);
+        else
+            load_kernel<double><<<blocks_for(n), 256, 0, ctx->stream>>>(
+                ctx->g, ctx->geom.kind, n, a, b, c, d, e, f, sp_dev, ctx->sp.n, pp,
+                store_of<double>(ctx, 0), ctx->d_status);
+        CU(cudaGetLastError());
+        unsigned bad = 0;
+        CU(cudaMemcpyAsync(&bad, ctx->d_status + ST_LOAD_BAD, sizeof bad, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (bad) {
+            ctx->particles_set = false;
+            return fail(ctx, DUST_EINVAL,
+                        "grain data must be finite, inside the grid, with valid species/param");
+        }
+    }
+    ctx->particles_set = true;
+    return DUST_OK;
+}
+
+extern "C" int dust_step(dust_ctx *ctx, double dt)
+{
+    if (!ctx) return DUST_EINVAL;
+    if (!std::isfinite(dt)) return fail(ctx, DUST_EINVAL, "dt must be finite");
+    if (!ctx->gas_set || !ctx->particles_set)
+        return fail(ctx, DUST_ESTATE, "set the gas and load particles before stepping");
+    CU(cudaSetDevice(ctx->device));
+    int r;
+    if (ctx->need_sort || ctx->steps % ctx->sort_interval == 0) {
+        r = ctx->mixed ? run_sort<float>(ctx, dt) : run_sort<double>(ctx, dt);
+        if (r) return r;
+        ctx->need_sort = false;
+    }
+    r = ctx->mixed ? run_step<float>(ctx, dt) : run_step<double>(ctx, dt);
+    if (r) return r;
+    ctx->t += dt;
+    ctx->steps += 1;
+    ctx->timed_steps += 1;
+    ctx->have_deposit = true;
+    return DUST_OK;
+}
+
+extern "C" int dust_get_kernel_times(dust_ctx *ctx, dust_kernel_times *out, int reset)
+{
+    if (!ctx) return DUST_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int g = 0; g < dust_ctx::N_GROUPS; ++g) {
+        for (auto &pr : ctx->pending[g]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) ctx->group_ms[g] += ms;
+            ctx->event_pool.push_back(pr.first);
+            ctx->event_pool.push_back(pr.second);
+        }
+        ctx->pending[g].clear();
+    }
+    if (out) {
+        out->step_ms = ctx->group_ms[dust_ctx::GROUP_STEP];
+        out->sort_ms = ctx->group_ms[dust_ctx::GROUP_SORT];
+        out->other_ms = ctx->group_ms[dust_ctx::GROUP_OTHER];
+        out->step_launches = ctx->launches[dust_ctx::GROUP_STEP];
+        out->sort_launches = ctx->launches[dust_ctx::GROUP_SORT];
+        out->other_launches = ctx->launches[dust_ctx::GROUP_OTHER];
+        out->steps = ctx->timed_steps;
+    }
+    if (reset) {
+        for (int g = 0; g < dust_ctx::N_GROUPS; ++g) {
+            ctx->group_ms[g] = 0.0;
+            ctx->launches[g] = 0;
+        }
+        ctx->timed_steps = 0;
+    }
+    return DUST_OK;
+}
+
+extern "C" int dust_sync(dust_ctx *ctx, dust_stats *out)
+{
+    if (!ctx) return DUST_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaMemcpyAsync(ctx->h_status, ctx->d_status, ST_WORDS * sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    unsigned st[ST_WORDS];
+    memcpy(st, ctx->h_status, sizeof st);
+    CU(cudaMemsetAsync(ctx->d_status, 0, 4 * sizeof(unsigned), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const unsigned long long rem =
+        (unsigned long long)st[ST_REMOVED_LO] | ((unsigned long long)st[ST_REMOVED_HI] << 32);
+    ctx->removed_total += (int64_t)rem;
+    float mv;
+    memcpy(&mv, &st[ST_MAXMOVE], sizeof mv);
+    ctx->max_moved = fmaxf(ctx->max_moved, mv);
+    int flags = (int)st[ST_FLAGS];
+    if (mv > 1.8f) flags |= DUST_FLAG_CFL;
+    if (out) {
+        out->n_stored = ctx->n_grains;
+        out->n_removed = ctx->removed_total;
+        out->n_active = ctx->n_grains - ctx->removed_total;
+        out->max_cells_moved = ctx->max_moved;
+        out->flags = flags;
+        out->steps = ctx->steps;
+        out->time = ctx->t;
+    }
+    if (flags & DUST_FLAG_NAN) return fail(ctx, DUST_ENAN, "NaN/Inf produced on the device");
+    if (flags & DUST_FLAG_OVERFLOW)
+        return fail(ctx, DUST_EOVERFLOW, "fixed-point deposit piece beyond 2^52 quanta");
+    if (flags & DUST_FLAG_CFL)
+        return fail(ctx, DUST_ECFL, "a grain moved %.3g zones in one step (limit 1.8)", mv);
+    return DUST_OK;
+}
+
+extern "C" int dust_get_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double,
+                                double *quantum_out, int mem)
+{
+    if (!ctx) return DUST_EINVAL;
+    if (quantum_out) *quantum_out = ctx->quantum;
+    if (!fixed && !as_double) return DUST_OK;
+    CU(cudaSetDevice(ctx->device));
+    const int64_t m = ctx->ncell * 4;
+    const cudaMemcpyKind kind = mem == DUST_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (fixed) CU(cudaMemcpyAsync(fixed, ctx->d_dep, m * sizeof(int64_t), kind, ctx->stream));
+    if (as_double) {
+        double *dst = as_double;
+        if (mem == DUST_MEM_HOST) {
+            int r = ensure_stage(ctx, m * sizeof(double));
+            if (r) return r;
+            dst = ctx->d_stage;
+        }
+        dep_to_double_kernel<<<blocks_for(m), 256, 0, ctx->stream>>>(ctx->d_dep, m, ctx->quantum, dst);
+        CU(cudaGetLastError());
+        if (mem == DUST_MEM_HOST)
+            CU(cudaMemcpyAsync(as_double, dst, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DUST_OK;
+}
+
+extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
+                                  double *v0, double *v1, double *v2, int64_t *ids,
+                                  int64_t *n_out, int mem)
+{
+    if (!ctx || !n_out) return DUST_EINVAL;
+    *n_out = 0;
+    const int64_t n = ctx->n_grains;
+    if (cap < n) return fail(ctx, DUST_EINVAL, "capacity %lld < %lld grains", (long long)cap, (long long)n);
+    if (n == 0) return DUST_OK;
+    CU(cudaSetDevice(ctx->device));
+    double *outs[6] = {q0, q1, q2, v0, v1, v2};
+    double *dev[6] = {q0, q1, q2, v0, v1, v2};
+    int64_t *dids = ids;
+    if (mem == DUST_MEM_HOST) {
+        int r = ensure_stage(ctx, 7 * n * sizeof(double));
+        if (r) return r;
+        for (int k = 0; k < 6; ++k) dev[k] = outs[k] ? ctx->d_stage + k * n : nullptr;
+        dids = ids ? reinterpret_cast<int64_t *>(ctx->d_stage + 6 * n) : nullptr;
+    }
+    if (ctx->mixed)
+        get_particles_kernel<float><<<blocks_for(n), 256, 0, ctx->stream>>>(
+            ctx->geom.kind, store_of<float>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3], dev[4],
+            dev[5], dids);
+    else
+        get_particles_kernel<double><<<blocks_for(n), 256, 0, ctx->stream>>>(
+            ctx->geom.kind, store_of<double>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3], dev[4],
+            dev[5], dids);
+    CU(cudaGetLastError());
+    if (mem == DUST_MEM_HOST) {
+        for (int k = 0; k < 6; ++k)
+            if (outs[k])
+                CU(cudaMemcpyAsync(outs[k], dev[k], n * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+        if (ids) CU(cudaMemcpyAsync(ids, dids, n * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    *n_out = n;
+    return DUST_OK;
+}
+
+extern "C" const char *dust_last_error(const dust_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" void dust_destroy(dust_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_store(ctx);
+    for (int d = 0; d < 3; ++d) {
+        dfree(ctx->d_edges[d]);
+        dfree(ctx->d_dvol[d]);
+        dfree(ctx->d_dvol_f[d]);
+        dfree(ctx->d_zc[d]);
+        dfree(ctx->d_ziw[d]);
+        dfree(ctx->d_ziw_f[d]);
+        dfree(ctx->d_znu_f[d]);
+        dfree(ctx->d_zlo_f[d]);
+    }
+    dfree(ctx->d_gas);
+    dfree(ctx->d_dep);
+    dfree(ctx->d_status);
+    dfree(ctx->d_count);
+    dfree(ctx->d_cursor);
+    dfree(ctx->d_blocksums);
+    dfree(ctx->d_stage);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    for (int g = 0; g < dust_ctx::N_GROUPS; ++g)
+        for (auto &pr : ctx->pending[g]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}

@@ -1,0 +1,17 @@
+// Instantiations of the step and sort kernels for one geometry.
+#include "dust_tiled.cuh"
+
+namespace dust {
+
+template cudaError_t launch_step_per_grain<float, GEOM_CYL, 0>(const StepArgs<float> &, cudaStream_t);
+template cudaError_t launch_step_per_grain<float, GEOM_CYL, 1>(const StepArgs<float> &, cudaStream_t);
+template cudaError_t launch_step_per_grain<double, GEOM_CYL, 0>(const StepArgs<double> &, cudaStream_t);
+template cudaError_t launch_step_per_grain<double, GEOM_CYL, 1>(const StepArgs<double> &, cudaStream_t);
+template cudaError_t launch_step_tiled<float, GEOM_CYL, 0>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_step_tiled<float, GEOM_CYL, 1>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_step_tiled<double, GEOM_CYL, 0>(const TiledArgs<double> &, cudaStream_t);
+template cudaError_t launch_step_tiled<double, GEOM_CYL, 1>(const TiledArgs<double> &, cudaStream_t);
+template cudaError_t launch_sort_keys<float, GEOM_CYL>(const SortArgs<float> &, cudaStream_t);
+template cudaError_t launch_sort_keys<double, GEOM_CYL>(const SortArgs<double> &, cudaStream_t);
+
+}  // namespace dust

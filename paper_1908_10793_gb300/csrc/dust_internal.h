@@ -1,0 +1,129 @@
+// Internal declarations of the dust library (not part of the C interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dust.h"
+
+namespace dust {
+
+constexpr int kMaxSpecies = 16;
+
+enum GeomKind { GEOM_CART = 0, GEOM_SB = 1, GEOM_CYL = 2, GEOM_SPH = 3 };
+enum EdgeKind { EDGE_UNIFORM = 0, EDGE_LOG = 1, EDGE_GENERAL = 2 };
+
+// Status words on the device: [0] flag bits, [1] max zones moved (float
+// bits, non-negative so integer max orders them), [2] removed this step
+// (low), [3] high.
+enum { ST_FLAGS = 0, ST_MAXMOVE = 1, ST_REMOVED_LO = 2, ST_REMOVED_HI = 3, ST_WORDS = 8 };
+
+struct GridDev {
+    int n[3];
+    int bc[3];
+    int edge_kind[3];
+    const double *edges[3];  // device, n[d] + 1 each
+    double lo[3], hi[3];
+    double inv_d[3];         // uniform: n / (hi - lo); log: n / ln(hi / lo)
+    float inv_df[3];
+    float log_lo_f[3];
+    const double *dvol[3];   // per-direction factors of the zone volume
+    const float *dvol_f[3];
+    const double *zc[3];     // zone centres (edges midpoint)
+    const double *ziw[3];    // 1 / zone width
+    const float *ziw_f[3];
+    const float *znu_f[3];   // centre / width (curvilinear radial weights)
+    const float *zlo_f[3];   // lower edge (polar-angle weights)
+    int64_t ncell;
+    // tile layout of the zone sort: tiles of T[0] x T[1] x T[2] zones; key of
+    // zone (i,j,k) = tile index * tvol + position inside the tile
+    int T[3];
+    int nt[3];
+    int tvol;
+    int64_t nkeys;           // number of tiles * tvol (>= ncell)
+};
+
+__host__ __device__ __forceinline__ int64_t zone_key(const GridDev &g, int i, int j, int k)
+{
+    const int ti = i / g.T[0], tj = j / g.T[1], tk = k / g.T[2];
+    const int li = i - ti * g.T[0], lj = j - tj * g.T[1], lk = k - tk * g.T[2];
+    const int64_t tile = ti + (int64_t)g.nt[0] * (tj + (int64_t)g.nt[1] * tk);
+    return tile * g.tvol + li + g.T[0] * (lj + g.T[1] * lk);
+}
+
+struct PhysDev {
+    int geom;
+    int fargo;
+    int vgrav;
+    double omega, qshear, gm;
+    double q_om;             // q * Omega
+    double jump_v;           // q * Omega * Lx (standard-frame v_y jump)
+    double shift_mid;        // fmod(q Omega Lx (t + dt/2), Ly)
+    double shift_end;        // fmod(q Omega Lx (t + dt), Ly)
+};
+
+struct SpeciesDev {
+    int n;
+    double mass[kMaxSpecies];
+    double tau[kMaxSpecies];
+    int mode[kMaxSpecies];
+};
+
+template <typename Real>
+struct StoreDev {
+    double *q[3];
+    Real *p[3];
+    uint8_t *species;        // may be null (all species 0)
+    Real *param;             // may be null (species value)
+    int32_t *id;
+    int64_t n;
+};
+
+template <typename Real>
+struct StepArgs {
+    GridDev g;
+    PhysDev ph;
+    SpeciesDev sp;
+    double t, dt;
+    double inv_quantum;
+    StoreDev<Real> s;
+    const Real *gas;              // [ncell][4]: rho, p_g0, p_g1, p_g2
+    unsigned long long *dep;      // [ncell][4] two's complement int64
+    unsigned int *status;         // ST_WORDS words
+};
+
+template <typename Real>
+struct TiledArgs {
+    StepArgs<Real> s;
+    const int32_t *key_off;       // [nkeys + 1] start of each key in the sorted store
+};
+
+template <typename Real>
+struct SortArgs {
+    GridDev g;
+    PhysDev ph;
+    double dt;                    // step the key predicts (half drift of it)
+    StoreDev<Real> src, dst;
+    int32_t *key;                 // [n]
+    int32_t *count;               // [ncell + 1]
+    int32_t *cursor;              // [ncell + 1]
+};
+
+// Launch wrappers, explicitly instantiated per geometry.
+template <typename Real, int GEOM, int WEIGHT>
+cudaError_t launch_step_per_grain(const StepArgs<Real> &a, cudaStream_t s);
+
+template <typename Real, int GEOM, int WEIGHT>
+cudaError_t launch_step_tiled(const TiledArgs<Real> &a, cudaStream_t s);
+
+template <typename Real, int GEOM>
+cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s);
+
+template <typename Real>
+cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s);
+
+cudaError_t launch_exclusive_scan(int32_t *data, int64_t n, int32_t *block_sums,
+                                  cudaStream_t s);
+int64_t scan_block_sums_size(int64_t n);
+
+}  // namespace dust

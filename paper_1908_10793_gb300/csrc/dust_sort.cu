@@ -1,0 +1,129 @@
+// Counting sort of the grain store by zone: exclusive scan of the zone
+// counts and scatter of every store column (keys are computed by the
+// geometry-specific sort_keys kernel).
+#include "dust_internal.h"
+
+namespace dust {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+int64_t scan_block_sums_size(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *warp_sums, int32_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;  // inclusive
+    }
+    __syncthreads();
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    const int32_t before = warp > 0 ? warp_sums[warp - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+// Phase 1: sum of each tile.
+__global__ void scan_reduce_kernel(const int32_t *data, int64_t n, int32_t *block_sums)
+{
+    __shared__ int32_t ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += data[base + k];
+    int32_t total;
+    block_exclusive_scan(s, ws, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Phase 2: exclusive scan of the tile sums in one block.
+__global__ void scan_sums_kernel(int32_t *block_sums, int64_t nb)
+{
+    __shared__ int32_t ws[32];
+    int32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int32_t v = i < nb ? block_sums[i] : 0;
+        int32_t total;
+        const int32_t ex = block_exclusive_scan(v, ws, total);
+        if (i < nb) block_sums[i] = carry + ex;
+        carry += total;
+        __syncthreads();
+    }
+}
+
+// Phase 3: exclusive scan inside each tile plus the tile offset.
+__global__ void scan_apply_kernel(int32_t *data, int64_t n, const int32_t *block_sums)
+{
+    __shared__ int32_t ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? data[base + k] : 0;
+        s += v[k];
+    }
+    int32_t total;
+    int32_t run = block_exclusive_scan(s, ws, total) + block_sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) data[base + k] = run;
+        run += v[k];
+    }
+}
+
+cudaError_t launch_exclusive_scan(int32_t *data, int64_t n, int32_t *block_sums, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, block_sums);
+    scan_sums_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nb);
+    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, block_sums);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+__global__ void sort_scatter_kernel(const SortArgs<Real> A)
+{
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= A.src.n) return;
+    const int32_t pos = atomicAdd(&A.cursor[A.key[gi]], 1);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        A.dst.q[d][pos] = A.src.q[d][gi];
+        A.dst.p[d][pos] = A.src.p[d][gi];
+    }
+    A.dst.id[pos] = A.src.id[gi];
+    if (A.src.species) A.dst.species[pos] = A.src.species[gi];
+    if (A.src.param) A.dst.param[pos] = A.src.param[gi];
+}
+
+template <typename Real>
+cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s)
+{
+    if (a.src.n == 0) return cudaSuccess;
+    sort_scatter_kernel<Real><<<(unsigned)((a.src.n + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sort_scatter<float>(const SortArgs<float> &, cudaStream_t);
+template cudaError_t launch_sort_scatter<double>(const SortArgs<double> &, cudaStream_t);
+
+}  // namespace dust

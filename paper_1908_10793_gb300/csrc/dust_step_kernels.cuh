@@ -1,0 +1,232 @@
+// Step and sort kernels, templated on precision, geometry and weight order.
+// Instantiated by the per-geometry translation units.
+#pragma once
+
+#include "dust_device.cuh"
+
+namespace dust {
+
+constexpr int kStepThreads = 256;
+
+// Per-grain fixed-point deposit rule: for every channel c the grain's total
+// Q_c = rint(D_c / quantum) is split over the stencil; every node other than
+// the host gets rint(W_j D_c / quantum) and the host gets the remainder, so
+// sum over zones = sum over grains of Q_c exactly (integer addition is
+// order independent, so the grid does not depend on thread order).
+template <typename Real>
+__device__ __forceinline__ void deposit_fixed(const GridDev &g, unsigned long long *dep,
+                                              const int host[3], const Real w[3][3],
+                                              const Real Dq[4], unsigned int *status)
+{
+    long long rest[4];
+    bool big = false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        big |= !(fabs((double)Dq[c]) < 4.5e15);
+        rest[c] = rround(Dq[c]);
+    }
+    if (big) atomicOr(&status[ST_FLAGS], DUST_FLAG_OVERFLOW);
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    int ix[3], iy[3], iz[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        ix[o] = node_of(host[0], o - 1, n0, g.bc[0]);
+        iy[o] = node_of(host[1], o - 1, n1, g.bc[1]);
+        iz[o] = node_of(host[2], o - 1, n2, g.bc[2]);
+    }
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) {
+        if (n2 <= 1 && c3 != 1) continue;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (n1 <= 1 && b != 1) continue;
+            const Real wyz = w[1][b] * w[2][c3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (n0 <= 1 && a != 1) continue;
+                if (a == 1 && b == 1 && c3 == 1) continue;
+                const Real W = w[0][a] * wyz;
+                const int64_t idx = ix[a] + (int64_t)n0 * (iy[b] + (int64_t)n1 * iz[c3]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const long long piece = rround(W * Dq[c]);
+                    if (piece != 0) {
+                        atomicAdd(&dep[4 * idx + c], (unsigned long long)piece);
+                        rest[c] -= piece;
+                    }
+                }
+            }
+        }
+    }
+    const int64_t hidx = ix[1] + (int64_t)n0 * (iy[1] + (int64_t)n1 * iz[1]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (rest[c] != 0) atomicAdd(&dep[4 * hidx + c], (unsigned long long)rest[c]);
+}
+
+template <typename Real>
+__device__ __forceinline__ void load_gas(const Real *gas, int64_t idx, Real out[4]);
+
+template <>
+__device__ __forceinline__ void load_gas<float>(const float *gas, int64_t idx, float out[4])
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(gas) + idx);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+
+template <>
+__device__ __forceinline__ void load_gas<double>(const double *gas, int64_t idx, double out[4])
+{
+    const double2 *p = reinterpret_cast<const double2 *>(gas) + 2 * idx;
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+
+// One thread per grain: half drift, weights, gather, kick, half drift,
+// boundaries, fixed-point deposit through global 64-bit atomics.
+template <typename Real, int GEOM, int WEIGHT>
+__global__ void __launch_bounds__(kStepThreads)
+step_per_grain_kernel(const StepArgs<Real> A)
+{
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool removed = false;
+    float moved = 0.f;
+    if (gi < A.s.n) {
+        double q[3] = {A.s.q[0][gi], A.s.q[1][gi], A.s.q[2][gi]};
+        if (!isnan(q[0])) {
+            Real pn[3] = {A.s.p[0][gi], A.s.p[1][gi], A.s.p[2][gi]};
+            const int sp = A.s.species ? A.s.species[gi] : 0;
+            const Real h = (Real)(0.5 * A.dt);
+            Real inc1[3], inc2[3];
+            drift<Real, GEOM>(A.ph, q, q, pn, h, false, inc1);
+            if (!apply_bc<Real, GEOM>(A.g, A.ph, A.ph.shift_mid, q, pn)) {
+                removed = true;
+            } else {
+                const double qm[3] = {q[0], q[1], q[2]};
+                int host[3];
+                Real w[3][3];
+                float iw[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    zone_weights<Real, GEOM>(A.g, d, WEIGHT, qm[d], host[d], w[d], iw[d]);
+                // gather (Eq. Delta_vp)
+                Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
+                const int n0 = A.g.n[0], n1 = A.g.n[1], n2 = A.g.n[2];
+#pragma unroll
+                for (int c3 = 0; c3 < 3; ++c3) {
+                    if (n2 <= 1 && c3 != 1) continue;
+                    const int iz = node_of(host[2], c3 - 1, n2, A.g.bc[2]);
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        if (n1 <= 1 && b != 1) continue;
+                        const int iy = node_of(host[1], b - 1, n1, A.g.bc[1]);
+                        const Real wyz = w[1][b] * w[2][c3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (n0 <= 1 && a != 1) continue;
+                            const int ix = node_of(host[0], a - 1, n0, A.g.bc[0]);
+                            const Real W = w[0][a] * wyz;
+                            Real f[4];
+                            load_gas<Real>(A.gas, ix + (int64_t)n0 * (iy + (int64_t)n1 * iz), f);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) acc[c] += W * f[c];
+                        }
+                    }
+                }
+                const Real value = A.s.param ? A.s.param[gi] : (Real)A.sp.tau[sp];
+                const Real tau = stopping_time<Real, GEOM>(A.ph, A.sp.mode[sp], value, qm, acc[0]);
+                const Real dt = (Real)A.dt;
+                const Real x = dt / tau;
+                const Real E = rexp(-x);
+                const Real cg = -rexpm1(-x);
+                const Real h1 = (x == Real(0)) ? dt : dt * cg / x;
+                const Real vg[3] = {acc[1], acc[2], acc[3]};
+                Real pp[3], a[3], dH[3];
+                kick<Real, GEOM>(A.ph, qm, pn, vg, E, cg, h1, pp, a, dH);
+                drift<Real, GEOM>(A.ph, q, qm, pp, h, true, inc2);
+                Real pnew[3] = {pp[0], pp[1], pp[2]};
+                const bool alive = apply_bc<Real, GEOM>(A.g, A.ph, A.ph.shift_end, q, pnew);
+                // deposit: -m (dp - dt a), energy sum_c of that times dH/dp_c
+                const Real mq = (Real)(A.sp.mass[sp] * A.inv_quantum);
+                Real Dq[4];
+                Dq[3] = Real(0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Dq[c] = -mq * ((pp[c] - pn[c]) - dt * a[c]);
+                    Dq[3] += Dq[c] * dH[c];
+                }
+                deposit_fixed<Real>(A.g, A.dep, host, w, Dq, A.status);
+                if (!(isfinite(pp[0]) && isfinite(pp[1]) && isfinite(pp[2])))
+                    atomicOr(&A.status[ST_FLAGS], DUST_FLAG_NAN);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    moved = fmaxf(moved, fabsf((float)(inc1[d] + inc2[d])) * iw[d]);
+                if (!alive) {
+                    removed = true;
+                    q[0] = __longlong_as_double(0x7ff8000000000000LL);
+                }
+                A.s.q[0][gi] = q[0]; A.s.q[1][gi] = q[1]; A.s.q[2][gi] = q[2];
+                A.s.p[0][gi] = pnew[0]; A.s.p[1][gi] = pnew[1]; A.s.p[2][gi] = pnew[2];
+            }
+            if (removed && !(isnan(A.s.q[0][gi]))) A.s.q[0][gi] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+    }
+    // warp-aggregated status updates
+    const unsigned mask = __ballot_sync(0xffffffffu, removed);
+    const unsigned mv = __reduce_max_sync(0xffffffffu, __float_as_uint(moved));
+    if ((threadIdx.x & 31) == 0) {
+        if (mask) atomicAdd(reinterpret_cast<unsigned long long *>(&A.status[ST_REMOVED_LO]),
+                            (unsigned long long)__popc(mask));
+        if (mv) atomicMax(&A.status[ST_MAXMOVE], mv);
+    }
+}
+
+template <typename Real, int GEOM, int WEIGHT>
+cudaError_t launch_step_per_grain(const StepArgs<Real> &a, cudaStream_t s)
+{
+    if (a.s.n == 0) return cudaSuccess;
+    const int64_t blocks = (a.s.n + kStepThreads - 1) / kStepThreads;
+    step_per_grain_kernel<Real, GEOM, WEIGHT><<<(unsigned)blocks, kStepThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- sort ----
+// Key of a grain = zone of its predicted half-step position for the next
+// step (the zone the step kernel will gather from); removed grains get
+// key ncell and sort to the end.
+template <typename Real, int GEOM>
+__global__ void sort_keys_kernel(const SortArgs<Real> A)
+{
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= A.src.n) return;
+    int32_t key = (int32_t)A.g.nkeys;
+    double q[3] = {A.src.q[0][gi], A.src.q[1][gi], A.src.q[2][gi]};
+    if (!isnan(q[0])) {
+        Real p[3] = {A.src.p[0][gi], A.src.p[1][gi], A.src.p[2][gi]};
+        Real inc[3];
+        drift<Real, GEOM>(A.ph, q, q, p, (Real)(0.5 * A.dt), false, inc);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (q[d] < A.g.lo[d] || q[d] >= A.g.hi[d]) {
+                if (A.g.bc[d] == DUST_BC_PERIODIC) q[d] = wrap_once(q[d], A.g.lo[d], A.g.hi[d]);
+                if (q[d] < A.g.lo[d]) q[d] = A.g.lo[d];
+                if (q[d] >= A.g.hi[d]) q[d] = A.g.edges[d][A.g.n[d] - 1];
+            }
+        }
+        const int i = locate(A.g, 0, q[0]), j = locate(A.g, 1, q[1]), k = locate(A.g, 2, q[2]);
+        key = (int32_t)zone_key(A.g, i, j, k);
+    }
+    A.key[gi] = key;
+    atomicAdd(&A.count[key], 1);
+}
+
+template <typename Real, int GEOM>
+cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s)
+{
+    if (a.src.n == 0) return cudaSuccess;
+    const int64_t blocks = (a.src.n + 255) / 256;
+    sort_keys_kernel<Real, GEOM><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace dust

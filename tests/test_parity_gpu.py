@@ -1,0 +1,292 @@
+"""GPU parity: the CUDA library (through the C interface) against the FP64
+oracle on the same seeded inputs, element by element.
+
+Tolerances
+* FP64 path: positions and momentum-like variables within 1e-12 of the
+  grain's speed (times dt for positions) per step; deposit within 1e-11 of its
+  largest value plus half a fixed-point quantum for every piece a zone can
+  receive (27 per grain in 3-D, 9 in 2-D, times the grains that reach it).
+* Mixed path (FP32 push, FP64 positions): momentum-like variables within
+  1e-5 relative per step; coordinates within 1e-5 of the step's displacement
+  plus one ulp; the deposit is -m (p^{n+1} - p^n - dt a) with p in FP32, so
+  each piece carries an absolute error of a few FP32 ulps of m |p| (not of the
+  deposit itself): tolerance 16 eps32 m |p|max times the largest number of
+  grains that reach one zone, plus quanta.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1908_10793_gb300 import inputs as I
+from parity_util import periodic_diff, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+EPS32 = 2.0 ** -24
+
+
+def _grains_per_zone_max(w):
+    cells = [np.clip(np.searchsorted(w.edges[d], w.q[d], side="right") - 1, 0, len(w.edges[d]) - 2)
+             for d in range(3)]
+    n = w.n
+    lin = cells[0] + n[0] * (cells[1] + n[1] * cells[2])
+    return int(np.bincount(lin, minlength=w.ncell).max())
+
+
+def compare(w, steps, precision, dt=None, feedback=None, extra_v=0.0, **kw):
+    dt = w.dt if dt is None else dt
+    qo, vo, active, dep_o, pg_o = run_oracle(w, steps, dt, feedback)
+    g = run_gpu(w, steps, precision, dt, feedback, **kw)
+    assert g["rc"] in (0, -4), "device status %d" % g["rc"]
+    alive = active.astype(bool)
+    assert np.array_equal(~np.isnan(g["q"][0]), alive), "removed grains differ"
+    if precision == FP64:
+        rtol = 1e-12 * max(1, steps)
+    else:
+        rtol = 1e-5 * max(1, steps)
+    # scales: the grain's speed (momentum-like variables can cancel in one
+    # component, e.g. v_R on a Keplerian orbit) and the distance it can move
+    speed = np.sqrt(sum(vo[d][alive] ** 2 for d in range(3))) + 1e-300
+    if w.geom == O.OG_SHEARING_BOX and w.fargo:
+        # the y drift also carries the mean shear -q Omega x
+        speed = speed + w.qshear * w.omega * np.abs(qo[0][alive])
+    for d in range(3):
+        dq = np.abs(periodic_diff(w, d, g["q"][d][alive], qo[d][alive]))
+        L = w.edges[d][-1] - w.edges[d][0]
+        metric = 1.0 if d == 0 or w.geom in (O.OG_CARTESIAN, O.OG_SHEARING_BOX) else \
+            1.0 / np.maximum(qo[0][alive], 1e-3) / (np.sin(qo[1][alive]) if (d == 2 and w.geom == O.OG_SPHERICAL) else 1.0)
+        disp = speed * metric * abs(dt) * steps
+        ulps = (L + np.max(np.abs(w.edges[d]))) * 2.0 ** -52 * 4 * steps
+        assert np.all(dq <= rtol * disp + ulps), "coordinate %d: max err %.3e" % (d, dq.max())
+        dv = np.abs(g["v"][d][alive] - vo[d][alive])
+        assert np.all(dv <= rtol * speed + extra_v), "velocity %d: max rel err %.3e" % (
+            d, (dv / speed).max())
+    # deposit of the last step
+    dep_g = g["fixed"] * g["quantum"]
+    big = np.abs(dep_o).max(axis=0)
+    # a zone collects at most nz pieces, each rounded by half a quantum
+    nz = _grains_per_zone_max(w) * (27 if w.n[2] > 1 else 9) * 2
+    if precision == FP64:
+        tol = 1e-11 * big + (0.5 * nz + 4) * g["quantum"]
+    else:
+        from parity_util import to_momentum
+        p = to_momentum(w, w.q, w.v)
+        m = np.max(w.species_mass)
+        pmax = max(np.abs(x).max() for x in p)
+        tol = 16 * EPS32 * m * pmax * nz * np.array([1, 1, 1, 2.0 * pmax]) + 1e-5 * big + \
+            (0.5 * nz + 4) * g["quantum"]
+    err = np.abs(dep_g - dep_o).max(axis=0)
+    assert np.all(err <= tol), "deposit err %s tol %s" % (err, tol)
+    return g, (qo, vo, active, dep_o, pg_o)
+
+
+WORKLOADS = {
+    "box2d": lambda: I.box2d("small"),
+    "sbox3d": lambda: I.sbox3d("small"),
+    "cyldisk": lambda: I.cyldisk("small"),
+    "sphdisk": lambda: I.sphdisk("small"),
+}
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_parity_one_step(name, precision):
+    compare(WORKLOADS[name](), 1, precision)
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_parity_fp64_several_steps_with_feedback(name):
+    """Four steps with the deposit applied to the gas.  The gas update uses the
+    fixed-point deposit, so each zone's gas velocity differs from the oracle's
+    dense sum by at most (pieces per zone) * quantum / 2 / (rho dV) per step;
+    the grains see that difference through the drag term."""
+    w = WORKLOADS[name]()
+    steps = 4
+    qo, vo, active, dep_o, pg_o = run_oracle(w, steps, feedback=1)
+    g = run_gpu(w, steps, FP64, feedback=1)
+    from test_oracle_push import _zone_volumes
+    prob = O.Problem(geom=w.geom, edges=w.edges)
+    dV = _zone_volumes(prob)
+    nz = _grains_per_zone_max(w) * (27 if w.n[2] > 1 else 9)
+    dgas = steps * nz * 0.5 * g["quantum"] / (w.rho * dV)
+    compare(w, steps, FP64, feedback=1, extra_v=2 * steps * dgas.max())
+    ref_v = pg_o
+    if w.geom == O.OG_CYLINDRICAL:
+        R, _, _ = I._grid3(w.edges)
+        ref_v = [pg_o[0], pg_o[1] / R, pg_o[2]]
+        dgas = [dgas, dgas / R, dgas]
+    elif w.geom == O.OG_SPHERICAL:
+        r, th, _ = I._grid3(w.edges)
+        ref_v = [pg_o[0], pg_o[1] / r, pg_o[2] / (r * np.sin(th))]
+        dgas = [dgas, dgas / r, dgas / (r * np.sin(th))]
+    else:
+        dgas = [dgas] * 3
+    for d in range(3):
+        scale = np.abs(ref_v[d]).max() + 1e-300
+        assert np.all(np.abs(g["vgas"][d] - ref_v[d]) <= 1e-12 * scale + dgas[d])
+
+
+@pytest.mark.parametrize("weight", [I.CIC, I.TSC])
+@pytest.mark.parametrize("name", ["box2d", "cyldisk", "sphdisk"])
+def test_parity_weights(name, weight):
+    w = WORKLOADS[name]()
+    w.weight = weight
+    compare(w, 2, FP64)
+    compare(w, 1, MIXED)
+
+
+@pytest.mark.parametrize("fargo,vgrav", [(0, 1), (1, 1), (0, 0)])
+def test_parity_shearing_box_frames(fargo, vgrav):
+    w = I.sbox3d("small")
+    w.fargo, w.vertical_gravity = fargo, vgrav
+    w.v = [x * 30.0 for x in w.v]   # cross zone and x boundaries more often
+    compare(w, 3, FP64)
+    compare(w, 1, MIXED)
+
+
+def test_parity_shear_periodic_wrap():
+    w = I.sbox3d("small")
+    w = I.subsample(w, 3000)
+    # push grains out through both radial boundaries during the step
+    L = w.edges[0][-1] - w.edges[0][0]
+    w.q[0] = np.where(np.arange(w.ngrains) % 2 == 0, w.edges[0][-1] - 1e-4 * L, w.edges[0][0] + 1e-4 * L)
+    w.v[0] = np.where(np.arange(w.ngrains) % 2 == 0, 0.05, -0.05)
+    compare(w, 2, FP64, dt=w.dt, feedback=0)
+    w.fargo = 0
+    compare(w, 2, FP64, dt=w.dt, feedback=0)
+
+
+def test_parity_outflow_removal_cylindrical():
+    w = I.cyldisk("small")
+    w = I.subsample(w, 5000)
+    # grains close to the inner radius falling inward leave through outflow
+    w.q[0] = np.where(np.arange(w.ngrains) % 3 == 0, w.edges[0][0] + 1e-5, w.q[0])
+    w.v[0] = np.where(np.arange(w.ngrains) % 3 == 0, -0.5, w.v[0])
+    g, (qo, vo, active, dep_o, _) = compare(w, 2, FP64, feedback=0)
+    assert (active == 0).sum() > 100
+    assert g["stats"].n_removed == (active == 0).sum()
+
+
+def test_parity_epstein_tau_mode():
+    w = I.box2d("small")
+    w.species_tau_mode = [I.TAU_EPSTEIN]
+    w.species_tau = [0.05]
+    rng = np.random.default_rng(5)
+    w.rho = rng.uniform(0.5, 2.0, w.ncell)
+    compare(w, 2, FP64)
+    compare(w, 1, MIXED)
+
+
+def test_parity_negative_dt_and_infinite_tau():
+    w = I.sphdisk("small")
+    # reverse-time drag amplifies by exp(|dt|/tau): keep the grains non-stiff
+    w.param = np.where(np.arange(w.ngrains) % 2 == 0, np.inf, np.maximum(w.param, 0.5))
+    compare(w, 2, FP64, dt=-w.dt, feedback=0)
+
+
+def test_single_grain_and_empty():
+    w = I.subsample(I.box2d("small"), 1)
+    compare(w, 3, FP64)
+    w0 = I.subsample(I.box2d("small"), 0)
+    g = run_gpu(w0, 2, FP64)
+    assert g["rc"] == 0 and np.all(g["fixed"] == 0)
+
+
+def test_deposit_bitwise_reproducible_and_sort_independent():
+    w = I.sbox3d("small")
+    a = run_gpu(w, 3, MIXED, sort_interval=1)
+    b = run_gpu(w, 3, MIXED, sort_interval=1)
+    c = run_gpu(w, 3, MIXED, sort_interval=2)
+    assert np.array_equal(a["fixed"], b["fixed"])
+    assert np.array_equal(a["fixed"], c["fixed"])
+    for d in range(3):
+        assert np.array_equal(a["q"][d], c["q"][d]) and np.array_equal(a["v"][d], c["v"][d])
+
+
+def test_fixed_point_sum_equals_momentum_change():
+    # Cartesian, no forces: sum over zones of the deposit = -m sum(dv) to one
+    # quantum per grain and channel (per-grain remainder rule)
+    w = I.box2d("full")
+    g = run_gpu(w, 1, FP64, feedback=0)
+    m = w.species_mass[0]
+    for d in range(2):
+        total = g["fixed"][:, d].sum() * g["quantum"]
+        ref = -m * (g["v"][d] - w.v[d]).sum()
+        assert abs(total - ref) <= 0.5 * w.ngrains * g["quantum"] + 1e-14 * m * np.abs(w.v[d]).sum()
+
+
+def test_invalid_inputs_rejected():
+    from paper_1908_10793_gb300 import dust as D
+    w = I.subsample(I.box2d("small"), 10)
+    ctx = D.Context(w, precision=FP64)
+    try:
+        with pytest.raises(D.DustError):
+            ctx.step(0.01)                      # no data yet
+        bad = [x.copy() for x in w.q]
+        bad[0][3] = np.nan
+        with pytest.raises(D.DustError):
+            ctx.load(bad, w.v)
+        bad[0][3] = 2.0                         # outside the grid
+        with pytest.raises(D.DustError):
+            ctx.load(bad, w.v)
+        with pytest.raises(D.DustError):
+            ctx.set_gas(-w.rho, w.vgas)
+    finally:
+        ctx.close()
+
+
+def test_full_size_shearing_box_sampled_against_oracle():
+    """128^3 shearing box, 16.8M grains, mixed precision, one step in the
+    configuration the benchmark times: sampled grains against the oracle
+    computed one by one, and the deposit of a slab of zones against the oracle
+    run on every grain that can reach it."""
+    from paper_1908_10793_gb300 import dust as D
+    w = I.sbox3d("full")
+    g = run_gpu(w, 1, MIXED, feedback=1)
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(w.ngrains, 4000, replace=False))
+    s = I.subsample(w, w.ngrains)  # copy
+    s.q = [x[idx] for x in w.q]
+    s.v = [x[idx] for x in w.v]
+    qo, vo, active, _, _ = run_oracle(s, 1, feedback=0)
+    for d in range(3):
+        dq = np.abs(periodic_diff(w, d, g["q"][d][idx], qo[d]))
+        assert dq.max() <= 1e-5 * (np.abs(w.v[d]).max() + 0.15) * w.dt + 1e-16
+        dv = np.abs(g["v"][d][idx] - vo[d])
+        assert dv.max() <= 1e-5 * np.abs(vo[d]).max()
+    # slab of zones k in [k0, k0+3]: every grain starting in zones k0-2..k0+5
+    n = w.n[2]
+    k0 = 40
+    zc = np.clip(np.searchsorted(w.edges[2], w.q[2], side="right") - 1, 0, n - 1)
+    sel = np.nonzero((zc >= k0 - 2) & (zc <= k0 + 5))[0]
+    s.q = [x[sel] for x in w.q]
+    s.v = [x[sel] for x in w.v]
+    _, _, _, dep_o, _ = run_oracle(s, 1, feedback=0)
+    nx, ny = w.n[0], w.n[1]
+    cells = np.arange(k0 * nx * ny, (k0 + 4) * nx * ny)
+    dep_g = g["fixed"][cells] * g["quantum"]
+    p = w.v
+    m = w.species_mass[0]
+    pmax = max(np.abs(x).max() for x in p) + 0.2
+    tol = 16 * EPS32 * m * pmax * 27 * 16 + 1e-5 * np.abs(dep_o[cells]).max(axis=0) + 64 * g["quantum"]
+    assert np.all(np.abs(dep_g - dep_o[cells]).max(axis=0) <= tol)
+    del D
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_tiled_kernel_bitwise_equals_per_grain_kernel(name, precision):
+    """The tiled kernel stages gas and deposits in shared memory but applies
+    the same per-grain arithmetic and fixed-point rule: grain states and the
+    integer deposit must be identical to the one-thread-per-grain kernel, for
+    any tile shape and sort interval."""
+    from paper_1908_10793_gb300 import dust as D
+    w = WORKLOADS[name]()
+    ref = run_gpu(w, 3, precision, kernel=D.DUST_KERNEL_PER_GRAIN)
+    for tile, si in (((0, 0, 0), 1), ((4, 4, 2), 1), ((8, 2, 4), 2), ((0, 0, 0), 3)):
+        got = run_gpu(w, 3, precision, kernel=D.DUST_KERNEL_TILED, tile=tile, sort_interval=si)
+        assert np.array_equal(got["fixed"], ref["fixed"]), (tile, si)
+        for d in range(3):
+            assert np.array_equal(got["q"][d], ref["q"][d], equal_nan=True), (tile, si, d)
+            assert np.array_equal(got["v"][d], ref["v"][d], equal_nan=True), (tile, si, d)
