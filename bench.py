@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="16^3 grid (profiling runs)")
+    ap.add_argument("--grid", type=int, default=0, help="zones per side (profiling runs)")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 per-grain, 2 tiled")
+    ap.add_argument("--tile", type=str, default="0,0,0")
     return ap.parse_args()
 
 
@@ -152,7 +155,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = I.sbox3d("small" if args.small else "full")
+    w = I.sbox3d(args.grid if args.grid else ("small" if args.small else "full"))
     # a real stream (not the legacy default stream) shared by the library and
     # the timing events
     stream = torch.cuda.Stream(dev)
@@ -160,7 +163,8 @@ def run_ours(args):
 
     def make(precision, timing):
         ctx = D.Context(w, precision=precision, stream=stream.cuda_stream,
-                        sort_interval=args.sort_interval, timing=timing, device=local)
+                        sort_interval=args.sort_interval, timing=timing, device=local,
+                        kernel=args.kernel, tile=[int(x) for x in args.tile.split(",")])
         ctx.set_gas(w.rho, w.vgas)
         ctx.load(w.q, w.v)
         return ctx
@@ -265,7 +269,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Philox; shapes of the paper's shearing-box setup)",
-            "config": {"workload": WORKLOAD_NAME if not args.small else "sbox3d-small 16^3",
+            "config": {"workload": WORKLOAD_NAME if w.ncell == 128 ** 3 else
+                       "sbox3d %d^3 (profiling size)" % round(w.ncell ** (1 / 3)),
                        "precision": "mixed: f32 push/gather, f64 positions, int64 deposit",
                        "grains": ngr, "zones": w.ncell, "sort_interval": args.sort_interval or 1,
                        "l2": "inputs larger than L2 (grain store %d MB)" % (ngr * 36 // 2**20),

@@ -39,6 +39,7 @@ struct dust_ctx {
     double *d_dvol[3] = {nullptr, nullptr, nullptr};
     float *d_dvol_f[3] = {nullptr, nullptr, nullptr};
     double *d_zc[3] = {nullptr, nullptr, nullptr};
+    long long *d_ekey[3] = {nullptr, nullptr, nullptr};
     double *d_ziw[3] = {nullptr, nullptr, nullptr};
     float *d_ziw_f[3] = {nullptr, nullptr, nullptr};
     float *d_znu_f[3] = {nullptr, nullptr, nullptr};
@@ -556,6 +557,10 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         mmax = fmax(mmax, fabs(species[s].mass));
     }
     ctx->quantum = opt->quantum > 0.0 ? opt->quantum : ldexp(mmax > 0 ? mmax : 1.0, -50);
+    for (int s = 0; s < n_species; ++s) {
+        ctx->sp.mq[s] = species[s].mass / ctx->quantum;
+        ctx->sp.mqf[s] = (float)ctx->sp.mq[s];
+    }
 
     auto bail = [&](int code) {
         std::string msg = ctx->err;
@@ -620,7 +625,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         if (dalloc(&ctx->d_edges[d], n + 1) != cudaSuccess || dalloc(&ctx->d_dvol[d], n) != cudaSuccess ||
             dalloc(&ctx->d_dvol_f[d], n) != cudaSuccess || dalloc(&ctx->d_zc[d], n) != cudaSuccess ||
             dalloc(&ctx->d_ziw[d], n) != cudaSuccess || dalloc(&ctx->d_ziw_f[d], n) != cudaSuccess ||
-            dalloc(&ctx->d_znu_f[d], n) != cudaSuccess || dalloc(&ctx->d_zlo_f[d], n + 1) != cudaSuccess) {
+            dalloc(&ctx->d_znu_f[d], n) != cudaSuccess || dalloc(&ctx->d_zlo_f[d], n + 1) != cudaSuccess ||
+            dalloc(&ctx->d_ekey[d], n + 1) != cudaSuccess) {
             ctx->err = "device allocation of grid arrays failed";
             return bail(DUST_ENOMEM);
         }
@@ -632,6 +638,14 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         cudaMemcpy(ctx->d_ziw_f[d], ziwf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(ctx->d_znu_f[d], znuf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(ctx->d_zlo_f[d], zlof.data(), (n + 1) * sizeof(float), cudaMemcpyHostToDevice);
+        {
+            std::vector<long long> ek(n + 1);
+            for (int i = 0; i <= n; ++i) ek[i] = order_key(e[i]);
+            cudaMemcpy(ctx->d_ekey[d], ek.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+            g.ekey[d] = ctx->d_ekey[d];
+            g.lo_key[d] = ek[0];
+            g.hi_key[d] = ek[n];
+        }
         g.edges[d] = ctx->d_edges[d];
         g.dvol[d] = ctx->d_dvol[d];
         g.dvol_f[d] = ctx->d_dvol_f[d];
@@ -663,8 +677,9 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         }
         const size_t smem = (size_t)(g.T[0] + (grid->n[0] > 1 ? 2 : 0)) *
                             (g.T[1] + (grid->n[1] > 1 ? 2 : 0)) *
-                            (g.T[2] + (grid->n[2] > 1 ? 2 : 0)) * (4 * ctx->rsz + 32);
-        if (smem > 200 * 1024) {
+                            (g.T[2] + (grid->n[2] > 1 ? 2 : 0)) * (4 * ctx->rsz + 32) +
+                            256 * (8 + 13 * ctx->rsz + 64) + 16;
+        if (smem > 220 * 1024) {
             ctx->err = "tile too large for shared memory";
             return bail(DUST_EINVAL);
         }
@@ -983,6 +998,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
         dfree(ctx->d_dvol[d]);
         dfree(ctx->d_dvol_f[d]);
         dfree(ctx->d_zc[d]);
+        dfree(ctx->d_ekey[d]);
         dfree(ctx->d_ziw[d]);
         dfree(ctx->d_ziw_f[d]);
         dfree(ctx->d_znu_f[d]);

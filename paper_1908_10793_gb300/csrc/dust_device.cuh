@@ -44,23 +44,24 @@ __device__ __forceinline__ int locate(const GridDev &g, int d, double x)
 {
     const int n = g.n[d];
     if (n <= 1) return 0;
-    const double *e = g.edges[d];
+    const long long *ek = g.ekey[d];
+    const long long kx = order_key(x);
     int i;
     if (g.edge_kind[d] == EDGE_UNIFORM) {
-        i = (int)floorf((float)(x - g.lo[d]) * g.inv_df[d]);
+        i = (int)floorf(((float)x - (float)g.lo[d]) * g.inv_df[d]);
     } else if (g.edge_kind[d] == EDGE_LOG) {
         i = (int)floorf((logf((float)x) - g.log_lo_f[d]) * g.inv_df[d]);
     } else {
         int lo = 0, hi = n;
         while (hi - lo > 1) {
             int mid = (lo + hi) >> 1;
-            if (e[mid] <= x) lo = mid; else hi = mid;
+            if (ek[mid] <= kx) lo = mid; else hi = mid;
         }
         return lo;
     }
     i = i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
-    for (int it = 0; it < 4 && i > 0 && x < e[i]; ++it) --i;
-    for (int it = 0; it < 4 && i < n - 1 && x >= e[i + 1]; ++it) ++i;
+    for (int it = 0; it < 8 && i > 0 && kx < ek[i]; ++it) --i;
+    for (int it = 0; it < 8 && i < n - 1 && kx >= ek[i + 1]; ++it) ++i;
     return i;
 }
 
@@ -210,15 +211,23 @@ __device__ __forceinline__ double wrap_once(double x, double lo, double hi)
 // through an outflow boundary (or moved more than a period).  Shearing-box x
 // is shear-periodic: y shifts by +-shift and, in the standard frame, v_y by
 // +-q Omega Lx.
+__device__ __forceinline__ bool inside(const GridDev &g, int d, double x)
+{
+    const long long k = order_key(x);
+    return k >= g.lo_key[d] && k < g.hi_key[d];
+}
+
 template <typename Real, int GEOM>
 __device__ __forceinline__ bool apply_bc(const GridDev &g, const PhysDev &ph, double shift,
                                          double q[3], Real p[3])
 {
+    // common case first: every coordinate inside its range
+    if (inside(g, 0, q[0]) && inside(g, 1, q[1]) && inside(g, 2, q[2])) return true;
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double lo = g.lo[d], hi = g.hi[d];
-        if (q[d] >= lo && q[d] < hi) continue;
+        if (inside(g, d, q[d])) continue;
         if (g.bc[d] == DUST_BC_OUTFLOW) return false;
         if (GEOM == GEOM_SB && d == 0) {
             if (q[0] >= hi) {

@@ -18,7 +18,21 @@ enum EdgeKind { EDGE_UNIFORM = 0, EDGE_LOG = 1, EDGE_GENERAL = 2 };
 // (low), [3] high.
 enum { ST_FLAGS = 0, ST_MAXMOVE = 1, ST_REMOVED_LO = 2, ST_REMOVED_HI = 3, ST_WORDS = 8 };
 
+// Integer key that orders non-NaN doubles like their values (-0 and +0
+// equal): comparisons of grain coordinates against zone edges run on the
+// integer pipe instead of the (narrow) double-precision pipe.
+__host__ __device__ __forceinline__ long long order_key(double x)
+{
+    union { double d; long long i; } u;
+    u.d = x;
+    long long b = u.i;
+    if (b == (long long)0x8000000000000000ULL) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
 struct GridDev {
+    long long lo_key[3], hi_key[3];
+    const long long *ekey[3];  // order_key of every edge
     int n[3];
     int bc[3];
     int edge_kind[3];
@@ -67,6 +81,8 @@ struct SpeciesDev {
     double mass[kMaxSpecies];
     double tau[kMaxSpecies];
     int mode[kMaxSpecies];
+    double mq[kMaxSpecies];   // mass / fixed-point quantum
+    float mqf[kMaxSpecies];
 };
 
 template <typename Real>

@@ -11,7 +11,7 @@
 
 namespace dust {
 
-constexpr int kTiledThreads = 256;
+constexpr int kTiledThreads = 256;  // threads per CTA = grains per chunk
 
 // Index of zone k (possibly one beyond the grid) in a direction of n zones.
 __device__ __forceinline__ int map_zone(int k, int n, int bc)
@@ -51,14 +51,48 @@ __device__ __forceinline__ void smem_gas_load<double>(const double *s, int lin, 
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// Round-half-even of a single-precision value to int64 without a 64-bit
+// conversion instruction (those share the narrow double-precision pipe):
+// v = hi * 2^21 + lo with hi = rint(v / 2^21) and |lo| <= 2^20 both formed by
+// the 1.5 * 2^23 magic-number addition; lo is exact, hi * 2^21 is even, so
+// the sum is exactly rint(v).  Valid for |v| < 2^43; larger values use the
+// conversion instruction.
+__device__ __forceinline__ long long rint_to_ll(float v)
+{
+    if (!(fabsf(v) < 8.796093e12f)) return __float2ll_rn(v);
+    const float magic = 12582912.0f;  // 1.5 * 2^23
+    const float th = __fadd_rn(__fmul_rn(v, 4.76837158203125e-07f), magic);  // v / 2^21
+    const int hi = __float_as_int(th) - 0x4B400000;
+    const float lo = __fmaf_rn(-(float)hi, 2097152.0f, v);
+    const int l = __float_as_int(__fadd_rn(lo, magic)) - 0x4B400000;
+    return ((long long)hi << 21) + (long long)l;
+}
+__device__ __forceinline__ long long rint_to_ll(double v) { return __double2ll_rn(v); }
+
+constexpr int kChunk = kTiledThreads;
+
+// Shared memory of one CTA: deposit box (channel major), run tables, gas
+// box, and the per-grain records of one chunk.
 template <typename Real>
 __host__ __device__ inline size_t tiled_smem_bytes(const GridDev &g)
 {
     size_t bvol = 1;
     for (int d = 0; d < 3; ++d) bvol *= (size_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
-    return bvol * (4 * sizeof(Real) + 4 * sizeof(long long));
+    const size_t ch = kChunk;
+    return bvol * (4 * sizeof(Real) + 4 * sizeof(long long)) +
+           ch * (8 * sizeof(long long) + 13 * sizeof(Real) + 7 * sizeof(int)) + 64;
 }
 
+// Tiled step.  Grains of a tile are processed in chunks of whole sort keys
+// (at most kChunk grains).  The deposit of a chunk is formed per run: the
+// grains of one sort key that share their half-step host zone.  A run's node
+// contributions are summed in registers in grain-id order, each node
+// receives rint(sum / quantum), and the host zone receives the remainder
+// rint(sum of D / quantum) - (other nodes), so a run deposits exactly its
+// quantised total.  Runs are sets fixed by the sort keys, so the integer
+// grid depends neither on the tile shape nor on the order of the scatter or
+// of the threads.  Keys holding more than kChunk grains use the per-grain
+// rule.
 template <typename Real, int GEOM, int WEIGHT>
 __global__ void __launch_bounds__(kTiledThreads)
 step_tiled_kernel(const TiledArgs<Real> TA)
@@ -66,29 +100,56 @@ step_tiled_kernel(const TiledArgs<Real> TA)
     const StepArgs<Real> &A = TA.s;
     const GridDev &g = A.g;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int CH = kChunk;
 
     const int tile = blockIdx.x;
-    const int64_t g0 = TA.key_off[(int64_t)tile * g.tvol];
-    const int64_t g1 = TA.key_off[(int64_t)(tile + 1) * g.tvol];
+    const int64_t kbase = (int64_t)tile * g.tvol;
+    const int64_t g0 = TA.key_off[kbase];
+    const int64_t g1 = TA.key_off[kbase + g.tvol];
     if (g1 <= g0) return;  // no grains: nothing to deposit
 
-    int H[3], B[3], o[3];
+    int B[3], o[3];
     {
-        int t = tile;
+        const int t = tile;
         const int tc[3] = {t % g.nt[0], (t / g.nt[0]) % g.nt[1], t / (g.nt[0] * g.nt[1])};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            H[d] = g.n[d] > 1 ? 1 : 0;
-            B[d] = g.T[d] + 2 * H[d];
-            o[d] = tc[d] * g.T[d] - H[d];
+            const int H = g.n[d] > 1 ? 1 : 0;
+            B[d] = g.T[d] + 2 * H;
+            o[d] = tc[d] * g.T[d] - H;
         }
     }
     const int bvol = B[0] * B[1] * B[2];
-    Real *sgas = reinterpret_cast<Real *>(smem_raw);
-    unsigned long long *sdep =
-        reinterpret_cast<unsigned long long *>(smem_raw + (size_t)bvol * 4 * sizeof(Real));
+    unsigned char *ptr = smem_raw;
+    unsigned long long *sdep = reinterpret_cast<unsigned long long *>(ptr);
+    ptr += (size_t)bvol * 4 * sizeof(long long);
+    unsigned long long *run_sum = reinterpret_cast<unsigned long long *>(ptr);   // [4][CH]
+    ptr += (size_t)CH * 4 * sizeof(long long);
+    long long *run_q = reinterpret_cast<long long *>(ptr);                       // [4][CH]
+    ptr += (size_t)CH * 4 * sizeof(long long);
+    Real *sgas = reinterpret_cast<Real *>(ptr);
+    ptr += (size_t)bvol * 4 * sizeof(Real);
+    Real *rec_w = reinterpret_cast<Real *>(ptr);                                 // [9][CH]
+    ptr += (size_t)CH * 9 * sizeof(Real);
+    Real *rec_d = reinterpret_cast<Real *>(ptr);                                 // [4][CH]
+    ptr += (size_t)CH * 4 * sizeof(Real);
+    int *rec_host = reinterpret_cast<int *>(ptr);                                // [CH]
+    ptr += (size_t)CH * sizeof(int);
+    int *rec_id = reinterpret_cast<int *>(ptr);                                  // [CH]
+    ptr += (size_t)CH * sizeof(int);
+    int *rec_order = reinterpret_cast<int *>(ptr);                               // [CH]
+    ptr += (size_t)CH * sizeof(int);
+    int *run_start = reinterpret_cast<int *>(ptr);                               // [CH]
+    ptr += (size_t)CH * sizeof(int);
+    int *key_start = reinterpret_cast<int *>(ptr);                               // [CH] 1 = slot starts a key
+    ptr += (size_t)CH * sizeof(int);
+    int *seg_lo = reinterpret_cast<int *>(ptr);                                  // [CH] key segment of a slot
+    ptr += (size_t)CH * sizeof(int);
+    int *seg_hi = reinterpret_cast<int *>(ptr);                                  // [CH]
+    ptr += (size_t)CH * sizeof(int);
+    int *ctl = reinterpret_cast<int *>(ptr);  // [0] runs, [1] chunk end key, [2] chunk grains
 
-    // ---- stage the gas box, clear the deposit box
+    // ---- stage the gas box, clear the deposit box and the run sums
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
         const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
         const int i = map_zone(o[0] + bx, g.n[0], g.bc[0]);
@@ -98,153 +159,282 @@ step_tiled_kernel(const TiledArgs<Real> TA)
         load_gas<Real>(A.gas, i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), v);
         smem_gas_store<Real>(sgas, lin, v);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) sdep[4 * lin + c] = 0ull;
+        for (int c = 0; c < 4; ++c) sdep[c * bvol + lin] = 0ull;
     }
-    __syncthreads();
+    for (int k = threadIdx.x; k < 4 * CH; k += blockDim.x) run_sum[k] = 0ull;
 
     int nremoved = 0;
     float moved = 0.f;
     const int lane = threadIdx.x & 31;
-    for (int64_t gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
-        double q[3] = {A.s.q[0][gi], A.s.q[1][gi], A.s.q[2][gi]};
-        if (isnan(q[0])) continue;
-        Real pn[3] = {A.s.p[0][gi], A.s.p[1][gi], A.s.p[2][gi]};
-        const int sp = A.s.species ? A.s.species[gi] : 0;
-        const Real h = (Real)(0.5 * A.dt);
-        Real inc1[3], inc2[3];
-        drift<Real, GEOM>(A.ph, q, q, pn, h, false, inc1);
-        if (!apply_bc<Real, GEOM>(g, A.ph, A.ph.shift_mid, q, pn)) {
-            A.s.q[0][gi] = __longlong_as_double(0x7ff8000000000000LL);
-            ++nremoved;
-            continue;
-        }
-        const double qm[3] = {q[0], q[1], q[2]};
-        int host[3];
-        Real w[3][3];
-        float iw[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) zone_weights<Real, GEOM>(g, d, WEIGHT, qm[d], host[d], w[d], iw[d]);
+    const int na = g.n[0] > 1 ? 3 : 1, nb = g.n[1] > 1 ? 3 : 1, nc = g.n[2] > 1 ? 3 : 1;
+    const int ntask = na * nb;
+    const Real h = (Real)(0.5 * A.dt);
+    const Real dt = (Real)A.dt;
 
-        // host position inside the tile box (periodic images folded back)
-        int lb[3];
-        bool inbox = true;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            int l = host[d] - o[d];
-            if (g.n[d] > 1 && g.bc[d] == DUST_BC_PERIODIC) {
-                if (l < 0) l += g.n[d];
-                else if (l >= B[d]) l -= g.n[d];
+    int kcur = 0;          // first key (relative to the tile) of the chunk
+    int64_t split = 0;     // grains of an oversized key already processed
+    while (kcur < g.tvol) {
+        // ---- choose the chunk: whole keys with at most CH grains, or the
+        // next CH grains of one oversized key (per-grain rule)
+        if (threadIdx.x == 0) {
+            const int64_t base = TA.key_off[kbase + kcur] + split;
+            int lo = kcur, hi = g.tvol;  // largest end with key_off[end] - base <= CH
+            while (hi - lo > 0) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (TA.key_off[kbase + mid] - base <= CH) lo = mid; else hi = mid - 1;
             }
-            lb[d] = l;
-            if (g.n[d] > 1) inbox &= (l >= 1) && (l <= B[d] - 2);
+            ctl[0] = 0;
+            if (lo > kcur && split == 0) {
+                ctl[1] = lo;
+                ctl[2] = (int)(TA.key_off[kbase + lo] - base);
+            } else {  // key kcur alone has more than CH grains left
+                ctl[1] = -1;
+                ctl[2] = (int)min((int64_t)CH, TA.key_off[kbase + kcur + 1] - base);
+            }
         }
+        __syncthreads();  // gas box ready; previous chunk's records consumed
+        const int kend = ctl[1];
+        const int cn = ctl[2];
+        const bool per_grain = kend < 0;
+        const int64_t cb = TA.key_off[kbase + kcur] + split;
+        key_start[threadIdx.x] = 0;
 
-        // gather (Eq. Delta_vp)
-        Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
+        // ---- phase A: one grain per thread
+        const int slot = threadIdx.x;
+        const int64_t gi = cb + slot;
+        int hl = -1;
+        if (slot < cn) {
+            double q[3] = {A.s.q[0][gi], A.s.q[1][gi], A.s.q[2][gi]};
+            if (!isnan(q[0])) {
+                Real pn[3] = {A.s.p[0][gi], A.s.p[1][gi], A.s.p[2][gi]};
+                const int sp = A.s.species ? A.s.species[gi] : 0;
+                Real inc1[3], inc2[3];
+                drift<Real, GEOM>(A.ph, q, q, pn, h, false, inc1);
+                if (!apply_bc<Real, GEOM>(g, A.ph, A.ph.shift_mid, q, pn)) {
+                    A.s.q[0][gi] = __longlong_as_double(0x7ff8000000000000LL);
+                    ++nremoved;
+                } else {
+                    const double qm[3] = {q[0], q[1], q[2]};
+                    int host[3];
+                    Real w[3][3];
+                    float iw[3];
 #pragma unroll
-        for (int c3 = 0; c3 < 3; ++c3) {
-            if (g.n[2] <= 1 && c3 != 1) continue;
+                    for (int d = 0; d < 3; ++d)
+                        zone_weights<Real, GEOM>(g, d, WEIGHT, qm[d], host[d], w[d], iw[d]);
+                    int lb[3];
+                    bool inbox = true;
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                if (g.n[1] <= 1 && b != 1) continue;
-                const Real wyz = w[1][b] * w[2][c3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (g.n[0] <= 1 && a != 1) continue;
-                    const Real W = w[0][a] * wyz;
-                    Real f[4];
-                    if (inbox) {
-                        const int lin = (lb[0] + a - 1) + B[0] * ((lb[1] + b - 1) + B[1] * (lb[2] + c3 - 1));
-                        smem_gas_load<Real>(sgas, lin, f);
-                    } else {
-                        const int ix = node_of(host[0], a - 1, g.n[0], g.bc[0]);
-                        const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
-                        const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
-                        load_gas<Real>(A.gas, ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz), f);
+                    for (int d = 0; d < 3; ++d) {
+                        int l = host[d] - o[d];
+                        if (g.n[d] > 1 && g.bc[d] == DUST_BC_PERIODIC) {
+                            if (l < 0) l += g.n[d];
+                            else if (l >= B[d]) l -= g.n[d];
+                        }
+                        lb[d] = l;
+                        if (g.n[d] > 1) inbox &= (l >= 1) && (l <= B[d] - 2);
                     }
+                    // gather (Eq. Delta_vp)
+                    Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[c] += W * f[c];
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        if (nc == 1 && c3 != 1) continue;
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            if (nb == 1 && b != 1) continue;
+                            const Real wyz = w[1][b] * w[2][c3];
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                if (na == 1 && a != 1) continue;
+                                const Real W = w[0][a] * wyz;
+                                Real f[4];
+                                if (inbox) {
+                                    smem_gas_load<Real>(sgas, (lb[0] + a - 1) + B[0] * ((lb[1] + b - 1) + B[1] * (lb[2] + c3 - 1)), f);
+                                } else {
+                                    const int ix = node_of(host[0], a - 1, g.n[0], g.bc[0]);
+                                    const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
+                                    const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
+                                    load_gas<Real>(A.gas, ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz), f);
+                                }
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) acc[c] += W * f[c];
+                            }
+                        }
+                    }
+                    const Real value = A.s.param ? A.s.param[gi] : (Real)A.sp.tau[sp];
+                    const Real tau = stopping_time<Real, GEOM>(A.ph, A.sp.mode[sp], value, qm, acc[0]);
+                    const Real x = dt / tau;
+                    const Real E = rexp(-x);
+                    const Real cg = -rexpm1(-x);
+                    const Real h1 = (x == Real(0)) ? dt : dt * cg / x;
+                    const Real vg[3] = {acc[1], acc[2], acc[3]};
+                    Real pp[3], a[3], dH[3];
+                    kick<Real, GEOM>(A.ph, qm, pn, vg, E, cg, h1, pp, a, dH);
+                    drift<Real, GEOM>(A.ph, q, qm, pp, h, true, inc2);
+                    Real pnew[3] = {pp[0], pp[1], pp[2]};
+                    const bool alive = apply_bc<Real, GEOM>(g, A.ph, A.ph.shift_end, q, pnew);
+                    const Real mq = sizeof(Real) == 4 ? (Real)A.sp.mqf[sp] : (Real)A.sp.mq[sp];
+                    Real Dq[4];
+                    Dq[3] = Real(0);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        Dq[c] = -mq * ((pp[c] - pn[c]) - dt * a[c]);
+                        Dq[3] += Dq[c] * dH[c];
+                    }
+                    if (!(isfinite(pp[0]) && isfinite(pp[1]) && isfinite(pp[2])))
+                        atomicOr(&A.status[ST_FLAGS], DUST_FLAG_NAN);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        moved = fmaxf(moved, fabsf((float)(inc1[d] + inc2[d])) * iw[d]);
+                    if (inbox && !per_grain) {
+                        hl = lb[0] + B[0] * (lb[1] + B[1] * lb[2]);
+#pragma unroll
+                        for (int d = 0; d < 3; ++d)
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) rec_w[(3 * d + k) * CH + slot] = w[d][k];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) rec_d[c * CH + slot] = Dq[c];
+                        rec_id[slot] = A.s.id[gi];
+                    } else {
+                        deposit_fixed<Real>(g, A.dep, host, w, Dq, A.status);
+                    }
+                    if (!alive) {
+                        q[0] = __longlong_as_double(0x7ff8000000000000LL);
+                        ++nremoved;
+                    }
+                    A.s.q[0][gi] = q[0]; A.s.q[1][gi] = q[1]; A.s.q[2][gi] = q[2];
+                    A.s.p[0][gi] = pnew[0]; A.s.p[1][gi] = pnew[1]; A.s.p[2][gi] = pnew[2];
                 }
             }
         }
-        const Real value = A.s.param ? A.s.param[gi] : (Real)A.sp.tau[sp];
-        const Real tau = stopping_time<Real, GEOM>(A.ph, A.sp.mode[sp], value, qm, acc[0]);
-        const Real dt = (Real)A.dt;
-        const Real x = dt / tau;
-        const Real E = rexp(-x);
-        const Real cg = -rexpm1(-x);
-        const Real h1 = (x == Real(0)) ? dt : dt * cg / x;
-        const Real vg[3] = {acc[1], acc[2], acc[3]};
-        Real pp[3], a[3], dH[3];
-        kick<Real, GEOM>(A.ph, qm, pn, vg, E, cg, h1, pp, a, dH);
-        drift<Real, GEOM>(A.ph, q, qm, pp, h, true, inc2);
-        Real pnew[3] = {pp[0], pp[1], pp[2]};
-        const bool alive = apply_bc<Real, GEOM>(g, A.ph, A.ph.shift_end, q, pnew);
-
-        const Real mq = (Real)(A.sp.mass[sp] * A.inv_quantum);
-        Real Dq[4];
-        Dq[3] = Real(0);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Dq[c] = -mq * ((pp[c] - pn[c]) - dt * a[c]);
-            Dq[3] += Dq[c] * dH[c];
-        }
-        if (!(isfinite(pp[0]) && isfinite(pp[1]) && isfinite(pp[2])))
-            atomicOr(&A.status[ST_FLAGS], DUST_FLAG_NAN);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) moved = fmaxf(moved, fabsf((float)(inc1[d] + inc2[d])) * iw[d]);
-
-        if (inbox) {
-            // per-grain fixed-point rule into the shared box; lanes start at
-            // different stencil nodes so that grains of one zone do not hit
-            // the same shared word in the same instruction
-            long long rest[4];
-            bool big = false;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                big |= !(fabs((double)Dq[c]) < 4.5e15);
-                rest[c] = rround(Dq[c]);
+        rec_host[slot] = hl;
+        // key boundaries inside the chunk
+        if (!per_grain)
+            for (int k = kcur + threadIdx.x; k < kend; k += blockDim.x) {
+                const int s = (int)(TA.key_off[kbase + k] - cb);
+                if (s >= 0 && s < cn) key_start[s] = 1;
             }
-            if (big) atomicOr(&A.status[ST_FLAGS], DUST_FLAG_OVERFLOW);
-            for (int k = 0; k < 27; ++k) {
-                int nidx = k + lane;
-                nidx -= 27 * (nidx >= 27);
-                nidx -= 27 * (nidx >= 27);
-                const int na = nidx % 3, nb = (nidx / 3) % 3, nc = nidx / 9;
-                if (nidx == 13) continue;  // host node: remainder below
-                if ((g.n[0] <= 1 && na != 1) || (g.n[1] <= 1 && nb != 1) || (g.n[2] <= 1 && nc != 1))
-                    continue;
-                const Real wa = na == 0 ? w[0][0] : (na == 1 ? w[0][1] : w[0][2]);
-                const Real wb = nb == 0 ? w[1][0] : (nb == 1 ? w[1][1] : w[1][2]);
-                const Real wc = nc == 0 ? w[2][0] : (nc == 1 ? w[2][1] : w[2][2]);
-                const Real W = wa * (wb * wc);
-                const int lin = (lb[0] + na - 1) + B[0] * ((lb[1] + nb - 1) + B[1] * (lb[2] + nc - 1));
+        __syncthreads();
+
+        if (!per_grain) {
+            // ---- each key segment listed in grain-id order (one thread per
+            // key, insertion sort of its few slots)
+            if (slot < cn && (slot == 0 || key_start[slot])) {
+                int e = slot + 1;
+                while (e < cn && !key_start[e]) ++e;
+                for (int u = slot; u < e; ++u) {
+                    const int id = rec_host[u] >= 0 ? rec_id[u] : 0x7fffffff;
+                    int j = u - 1;
+                    while (j >= slot) {
+                        const int sj = rec_order[j];
+                        const int idj = rec_host[sj] >= 0 ? rec_id[sj] : 0x7fffffff;
+                        if (idj <= id) break;
+                        rec_order[j + 1] = sj;
+                        --j;
+                    }
+                    rec_order[j + 1] = u;
+                    seg_lo[u] = slot;
+                    seg_hi[u] = e;
+                }
+            }
+            __syncthreads();
+            // ---- runs: the grains of one key sharing a host zone; a run
+            // starts at its first grain in id order
+            if (slot < cn) {
+                const int hs = rec_host[rec_order[slot]];
+                bool first = hs >= 0;
+                for (int u = seg_lo[slot]; u < slot && first; ++u) first = rec_host[rec_order[u]] != hs;
+                if (first) run_start[atomicAdd(&ctl[0], 1)] = slot;
+            }
+            __syncthreads();
+
+            // ---- phase B: one task per (run, x node, y node); z nodes and
+            // the four channels are summed in registers over the run
+            const int R = ctl[0];
+            bool big = false;
+            for (int t = threadIdx.x; t < R * ntask; t += blockDim.x) {
+                const int r = t / ntask, ab = t - r * ntask;
+                const int a = na == 3 ? ab % 3 : 1;
+                const int b = nb == 3 ? ab / na : 1;
+                const bool htask = a == 1 && b == 1;
+                const int u0 = run_start[r];
+                const int hlin = rec_host[rec_order[u0]];
+                const int u1 = seg_hi[u0];
+                Real sum[3][4], S[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const long long piece = rround(W * Dq[c]);
-                    if (piece != 0) {
-                        atomicAdd(&sdep[4 * lin + c], (unsigned long long)piece);
-                        rest[c] -= piece;
+                    S[c] = Real(0);
+#pragma unroll
+                    for (int z = 0; z < 3; ++z) sum[z][c] = Real(0);
+                }
+                for (int u = u0; u < u1; ++u) {
+                    const int s = rec_order[u];
+                    if (rec_host[s] != hlin) continue;
+                    const Real wab = rec_w[a * CH + s] * rec_w[(3 + b) * CH + s];
+                    Real D[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) D[c] = rec_d[c * CH + s];
+#pragma unroll
+                    for (int z = 0; z < 3; ++z) {
+                        if (nc == 1 && z != 1) continue;
+                        const Real W = wab * rec_w[(6 + z) * CH + s];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) sum[z][c] += W * D[c];
+                    }
+                    if (htask) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) S[c] += D[c];
+                    }
+                }
+                long long ps[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int z = 0; z < 3; ++z) {
+                    if (nc == 1 && z != 1) continue;
+                    if (htask && z == 1) continue;  // the host node takes the remainder
+                    const int lin = hlin + (a - 1) + B[0] * ((b - 1) + B[1] * (z - 1));
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        big |= !(fabs(sum[z][c]) < Real(4.5e15));
+                        const long long piece = rint_to_ll(sum[z][c]);
+                        if (piece != 0) {
+                            atomicAdd(&sdep[c * bvol + lin], (unsigned long long)piece);
+                            ps[c] += piece;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (ps[c] != 0) atomicAdd(&run_sum[c * CH + r], (unsigned long long)ps[c]);
+                    if (htask) {
+                        big |= !(fabs(S[c]) < Real(4.5e15));
+                        run_q[c * CH + r] = rint_to_ll(S[c]);
                     }
                 }
             }
-            const int hl = lb[0] + B[0] * (lb[1] + B[1] * lb[2]);
+            if (big) atomicOr(&A.status[ST_FLAGS], DUST_FLAG_OVERFLOW);
+            __syncthreads();
+
+            // ---- host remainders
+            for (int r = threadIdx.x; r < R; r += blockDim.x) {
+                const int hlin = rec_host[rec_order[run_start[r]]];
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (rest[c] != 0) atomicAdd(&sdep[4 * hl + c], (unsigned long long)rest[c]);
+                for (int c = 0; c < 4; ++c) {
+                    const long long rest = run_q[c * CH + r] - (long long)run_sum[c * CH + r];
+                    run_sum[c * CH + r] = 0ull;
+                    if (rest != 0) atomicAdd(&sdep[c * bvol + hlin], (unsigned long long)rest);
+                }
+            }
+            kcur = kend;
+            split = 0;
         } else {
-            deposit_fixed<Real>(g, A.dep, host, w, Dq, A.status);
+            split += cn;
+            if (TA.key_off[kbase + kcur] + split >= TA.key_off[kbase + kcur + 1]) {
+                ++kcur;
+                split = 0;
+            }
         }
-
-        if (!alive) {
-            q[0] = __longlong_as_double(0x7ff8000000000000LL);
-            ++nremoved;
-        }
-        A.s.q[0][gi] = q[0]; A.s.q[1][gi] = q[1]; A.s.q[2][gi] = q[2];
-        A.s.p[0][gi] = pnew[0]; A.s.p[1][gi] = pnew[1]; A.s.p[2][gi] = pnew[2];
+        // skip keys without grains
+        __syncthreads();
     }
-
-    __syncthreads();
 
     // ---- flush the deposit box
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
@@ -255,7 +445,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
         const int64_t gz = i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const unsigned long long v = sdep[4 * lin + c];
+            const unsigned long long v = sdep[c * bvol + lin];
             if (v != 0ull) atomicAdd(&A.dep[4 * gz + c], v);
         }
     }

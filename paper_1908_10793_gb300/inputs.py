@@ -146,7 +146,7 @@ def _per_zone_positions(r, edges, ppc):
 def sbox3d(scale="full", seed=BASE_SEED + 1, ppc=8):
     """3-D shearing box in the orbital-advection frame, 128^3 zones."""
     r = _rng(seed)
-    n = 128 if scale == "full" else 16
+    n = 128 if scale == "full" else (16 if scale == "small" else int(scale))
     L = 0.2
     edges = [_uniform_edges(-0.5 * L, 0.5 * L, n) for _ in range(3)]
     ncell = n ** 3

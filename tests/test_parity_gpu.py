@@ -276,17 +276,45 @@ def test_full_size_shearing_box_sampled_against_oracle():
 
 @pytest.mark.parametrize("name", list(WORKLOADS))
 @pytest.mark.parametrize("precision", [FP64, MIXED])
-def test_tiled_kernel_bitwise_equals_per_grain_kernel(name, precision):
-    """The tiled kernel stages gas and deposits in shared memory but applies
-    the same per-grain arithmetic and fixed-point rule: grain states and the
-    integer deposit must be identical to the one-thread-per-grain kernel, for
-    any tile shape and sort interval."""
+def test_tiled_kernel_against_per_grain_kernel(name, precision):
+    """The tiled kernel pushes grains with the same arithmetic as the
+    one-thread-per-grain kernel (grain states identical in mixed precision,
+    equal to rounding in FP64) but quantises the deposit once per run of grains
+    sharing a sort key and host zone: the integer deposit is reproducible bit
+    for bit and does not depend on the tile shape, and it matches the
+    per-grain kernel's deposit within the fixed-point and summation rounding."""
     from paper_1908_10793_gb300 import dust as D
     w = WORKLOADS[name]()
     ref = run_gpu(w, 3, precision, kernel=D.DUST_KERNEL_PER_GRAIN)
-    for tile, si in (((0, 0, 0), 1), ((4, 4, 2), 1), ((8, 2, 4), 2), ((0, 0, 0), 3)):
-        got = run_gpu(w, 3, precision, kernel=D.DUST_KERNEL_TILED, tile=tile, sort_interval=si)
-        assert np.array_equal(got["fixed"], ref["fixed"]), (tile, si)
+    first = None
+    for tile in ((0, 0, 0), (4, 4, 2), (8, 2, 4), (0, 0, 0)):
+        got = run_gpu(w, 3, precision, kernel=D.DUST_KERNEL_TILED, tile=tile, sort_interval=1)
+        if first is None:
+            first = got
+        else:
+            assert np.array_equal(got["fixed"], first["fixed"]), tile
         for d in range(3):
-            assert np.array_equal(got["q"][d], ref["q"][d], equal_nan=True), (tile, si, d)
-            assert np.array_equal(got["v"][d], ref["v"][d], equal_nan=True), (tile, si, d)
+            a, b = got["q"][d], ref["q"][d]
+            assert np.array_equal(np.isnan(a), np.isnan(b))
+            if precision == MIXED:
+                assert np.array_equal(a, b, equal_nan=True), (tile, d)
+                assert np.array_equal(got["v"][d], ref["v"][d], equal_nan=True), (tile, d)
+            else:
+                assert np.nanmax(np.abs(a - b)) <= 1e-15 * (1 + np.nanmax(np.abs(b)))
+                assert np.nanmax(np.abs(got["v"][d] - ref["v"][d])) <= \
+                    1e-14 * (1 + np.nanmax(np.abs(ref["v"][d])))
+    big = np.abs(ref["fixed"]).max(axis=0).astype(np.float64)
+    nz = _grains_per_zone_max(w) * (27 if w.n[2] > 1 else 9) * 2
+    rel = 4e-6 if precision == MIXED else 1e-12
+    assert np.all(np.abs(first["fixed"] - ref["fixed"]).max(axis=0) <= rel * big + nz)
+
+
+def test_tiled_deposit_independent_of_sort_scatter_order():
+    """The zone sort scatters with atomics (arbitrary order inside a zone);
+    runs are summed in grain-id order, so repeated runs give the same integers."""
+    from paper_1908_10793_gb300 import dust as D
+    w = I.cyldisk("small")
+    a = run_gpu(w, 4, MIXED, kernel=D.DUST_KERNEL_TILED, sort_interval=2)
+    for _ in range(3):
+        b = run_gpu(w, 4, MIXED, kernel=D.DUST_KERNEL_TILED, sort_interval=2)
+        assert np.array_equal(a["fixed"], b["fixed"])
