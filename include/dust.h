@@ -72,10 +72,16 @@ enum { DUST_TAU_CONST = 0, DUST_TAU_STOKES = 1, DUST_TAU_EPSTEIN = 2 };
  * push in single precision, deposit in 64-bit fixed point. */
 enum { DUST_FP64 = 0, DUST_MIXED = 1 };
 enum { DUST_MEM_HOST = 0, DUST_MEM_DEVICE = 1 };
-/* kernel choice: DUST_KERNEL_AUTO picks the tiled kernel where it applies;
- * DUST_KERNEL_PER_GRAIN forces the one-thread-per-grain kernel that
- * deposits through global atomics. */
-enum { DUST_KERNEL_AUTO = 0, DUST_KERNEL_PER_GRAIN = 1, DUST_KERNEL_TILED = 2 };
+/* kernel choice.  DUST_KERNEL_PER_GRAIN: one thread per grain, every grain
+ * quantises its own 27 x 4 deposit pieces into global 64-bit atomics (the
+ * reference kernel; its integer grid does not depend on the store order).
+ * DUST_KERNEL_TILED: one block per tile of zones, gas stencil and deposit in
+ * shared memory, deposit quantised once per run (grains of one zone sharing
+ * their half-step host zone).  DUST_KERNEL_SLAB (mixed precision, x gridded):
+ * like the tiled kernel, but three lanes own one zone and keep its stencil
+ * and its deposit in registers.  DUST_KERNEL_AUTO: the slab kernel where it
+ * applies, else the tiled kernel. */
+enum { DUST_KERNEL_AUTO = 0, DUST_KERNEL_PER_GRAIN = 1, DUST_KERNEL_TILED = 2, DUST_KERNEL_SLAB = 3 };
 
 /* status flag bits returned in dust_stats.flags */
 #define DUST_FLAG_NAN 1
@@ -114,9 +120,10 @@ typedef struct dust_options {
     int weight;            /* DUST_WEIGHT_CIC or DUST_WEIGHT_TSC                */
     int feedback_apply;    /* 1: add the deposit to the gas momentum each step  */
     double quantum;        /* fixed-point quantum of the deposit (momentum
-                              units); 0 = 2^-50 * (largest species mass), i.e.
-                              velocity changes up to 4 code units per step fit
-                              the 2^52 exact range of one piece                 */
+                              units); 0 = 2^-44 * (largest species mass): a
+                              grain's velocity change of up to 256 code units
+                              per step stays below 2^52 quanta, and zone sums
+                              of a few thousand pieces fit int64              */
     void *stream;          /* cudaStream_t to enqueue on; NULL = own stream     */
     int sort_interval;     /* re-sort grains by zone every k steps (0 = 1)      */
     int kernel;            /* DUST_KERNEL_*                                     */

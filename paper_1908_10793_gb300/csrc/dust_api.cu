@@ -44,6 +44,7 @@ struct dust_ctx {
     float *d_ziw_f[3] = {nullptr, nullptr, nullptr};
     float *d_znu_f[3] = {nullptr, nullptr, nullptr};
     float *d_zlo_f[3] = {nullptr, nullptr, nullptr};
+    float *d_zc_f[3] = {nullptr, nullptr, nullptr};
     bool need_sort = true;
     void *d_gas = nullptr;
     unsigned long long *d_dep = nullptr;
@@ -60,6 +61,7 @@ struct dust_ctx {
     bool has_species = false, has_param = false;
 
     int32_t *d_key = nullptr, *d_count = nullptr, *d_cursor = nullptr, *d_blocksums = nullptr;
+    int32_t *d_pair_id = nullptr, *d_pair_src = nullptr;
     double *d_stage = nullptr;
     size_t stage_bytes = 0;
 
@@ -315,6 +317,11 @@ PhysDev phys_of(const dust_ctx *c, double t, double dt)
         ph.shift_mid = fmod(c->geom.q * c->geom.omega * Lx * (t + 0.5 * dt), Ly);
         ph.shift_end = fmod(c->geom.q * c->geom.omega * Lx * (t + dt), Ly);
     }
+    ph.omega_f = (float)ph.omega;
+    ph.qshear_f = (float)ph.qshear;
+    ph.gm_f = (float)ph.gm;
+    ph.q_om_f = (float)ph.q_om;
+    ph.jump_v_f = (float)ph.jump_v;
     return ph;
 }
 
@@ -387,6 +394,10 @@ void free_store(dust_ctx *c)
         c->d_id[w] = nullptr;
     }
     dfree(c->d_key);
+    dfree(c->d_pair_id);
+    dfree(c->d_pair_src);
+    c->d_pair_id = nullptr;
+    c->d_pair_src = nullptr;
     c->d_key = nullptr;
     c->cap = 0;
 }
@@ -404,6 +415,8 @@ int alloc_store(dust_ctx *ctx, int64_t n)
         if (ctx->has_param) CU(cudaMalloc(&ctx->d_param[w], n * ctx->rsz));
     }
     CU(dalloc(&ctx->d_key, n));
+    CU(dalloc(&ctx->d_pair_id, n));
+    CU(dalloc(&ctx->d_pair_src, n));
     ctx->cap = n;
     return DUST_OK;
 }
@@ -420,9 +433,12 @@ int run_sort(dust_ctx *ctx, double dt)
     a.key = ctx->d_key;
     a.count = ctx->d_count;
     a.cursor = ctx->d_cursor;
+    a.pair_id = ctx->d_pair_id;
+    a.pair_src = ctx->d_pair_src;
+    a.nkeys1 = ctx->g.nkeys + 1;
     const int64_t m = ctx->g.nkeys + 1;
     GroupTimer timer(ctx, dust_ctx::GROUP_SORT);
-    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += 5;
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += 7;
     CU(cudaMemsetAsync(ctx->d_count, 0, m * sizeof(int32_t), ctx->stream));
     cudaError_t e = cudaSuccess;
     switch (ctx->geom.kind) {
@@ -440,19 +456,70 @@ int run_sort(dust_ctx *ctx, double dt)
     return DUST_OK;
 }
 
+// Flat pattern the slab kernel supports for this grid: 0 (3-D), 1 (y not
+// gridded), 2 (z not gridded); -1 = not supported (x not gridded, or 1-D).
+inline int slab_flat(const GridDev &g)
+{
+    if (g.n[0] <= 1) return -1;
+    if (g.n[1] > 1 && g.n[2] > 1) return 0;
+    if (g.n[1] <= 1 && g.n[2] > 1) return 1;
+    if (g.n[1] > 1 && g.n[2] <= 1) return 2;
+    return -1;
+}
+
+template <int GEOM>
+cudaError_t launch_slab_geom(const TiledArgs<float> &ta, int flat, cudaStream_t s);
+
+template <>
+cudaError_t launch_slab_geom<GEOM_CART>(const TiledArgs<float> &ta, int flat, cudaStream_t s)
+{
+    return flat == 0 ? launch_step_slab<GEOM_CART, 0>(ta, s) : launch_step_slab<GEOM_CART, 2>(ta, s);
+}
+template <>
+cudaError_t launch_slab_geom<GEOM_SB>(const TiledArgs<float> &ta, int flat, cudaStream_t s)
+{
+    return flat == 0 ? launch_step_slab<GEOM_SB, 0>(ta, s)
+                     : (flat == 1 ? launch_step_slab<GEOM_SB, 1>(ta, s) : launch_step_slab<GEOM_SB, 2>(ta, s));
+}
+template <>
+cudaError_t launch_slab_geom<GEOM_CYL>(const TiledArgs<float> &ta, int, cudaStream_t s)
+{
+    return launch_step_slab<GEOM_CYL, 0>(ta, s);
+}
+template <>
+cudaError_t launch_slab_geom<GEOM_SPH>(const TiledArgs<float> &ta, int, cudaStream_t s)
+{
+    return launch_step_slab<GEOM_SPH, 0>(ta, s);
+}
+
+// Whether the slab kernel runs for this context: mixed precision, a
+// supported flat pattern, and the geometry's instantiation.
+inline bool slab_available(int geom, int flat)
+{
+    if (flat < 0) return false;
+    if (geom == GEOM_CYL || geom == GEOM_SPH) return flat == 0;
+    if (geom == GEOM_CART) return flat == 0 || flat == 2;
+    return true;
+}
+
 template <typename Real, int GEOM>
-cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, bool tiled,
+cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
                              const int32_t *key_off, cudaStream_t s)
 {
-    if (tiled) {
-        TiledArgs<Real> ta;
-        ta.s = a;
-        ta.key_off = key_off;
-        return weight == DUST_WEIGHT_TSC ? launch_step_tiled<Real, GEOM, 1>(ta, s)
-                                         : launch_step_tiled<Real, GEOM, 0>(ta, s);
+    TiledArgs<Real> ta;
+    ta.s = a;
+    ta.key_off = key_off;
+    ta.tsc = weight == DUST_WEIGHT_TSC;
+    if (kernel == DUST_KERNEL_PER_GRAIN)
+        return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<Real, GEOM, 1>(a, s)
+                                         : launch_step_per_grain<Real, GEOM, 0>(a, s);
+    if constexpr (sizeof(Real) == 4) {
+        const int flat = slab_flat(a.g);
+        if ((kernel == DUST_KERNEL_AUTO || kernel == DUST_KERNEL_SLAB) && slab_available(GEOM, flat))
+            return launch_slab_geom<GEOM>(ta, flat, s);
     }
-    return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<Real, GEOM, 1>(a, s)
-                                     : launch_step_per_grain<Real, GEOM, 0>(a, s);
+    return weight == DUST_WEIGHT_TSC ? launch_step_tiled<Real, GEOM, 1>(ta, s)
+                                     : launch_step_tiled<Real, GEOM, 0>(ta, s);
 }
 
 template <typename Real>
@@ -476,15 +543,15 @@ int run_step(dust_ctx *ctx, double dt)
     cudaError_t e;
     GroupTimer *step_timer = new GroupTimer(ctx, dust_ctx::GROUP_STEP);
     if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_STEP] += 1;
-    const bool tiled = ctx->opt.kernel != DUST_KERNEL_PER_GRAIN;
+    const int kn = ctx->opt.kernel;
     const int wt = ctx->opt.weight;
     const int32_t *ko = ctx->d_count;
     cudaStream_t st = ctx->stream;
     switch (ctx->geom.kind) {
-    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, tiled, ko, st); break;
-    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, tiled, ko, st); break;
-    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, tiled, ko, st); break;
-    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, tiled, ko, st); break;
+    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, st); break;
+    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, st); break;
+    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, st); break;
+    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, st); break;
     }
     delete step_timer;
     CU(e);
@@ -556,10 +623,11 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         ctx->sp.mode[s] = species[s].tau_mode;
         mmax = fmax(mmax, fabs(species[s].mass));
     }
-    ctx->quantum = opt->quantum > 0.0 ? opt->quantum : ldexp(mmax > 0 ? mmax : 1.0, -50);
+    ctx->quantum = opt->quantum > 0.0 ? opt->quantum : ldexp(mmax > 0 ? mmax : 1.0, -44);
     for (int s = 0; s < n_species; ++s) {
         ctx->sp.mq[s] = species[s].mass / ctx->quantum;
         ctx->sp.mqf[s] = (float)ctx->sp.mq[s];
+        ctx->sp.tau_f[s] = (float)ctx->sp.tau[s];
     }
 
     auto bail = [&](int code) {
@@ -614,19 +682,20 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         }
         // per-zone centre, inverse width, centre/width and lower edges
         std::vector<double> zc(n), ziw(n);
-        std::vector<float> ziwf(n), znuf(n), zlof(n + 1);
+        std::vector<float> ziwf(n), znuf(n), zlof(n + 1), zcf(n);
         for (int i = 0; i < n; ++i) {
             zc[i] = 0.5 * (e[i] + e[i + 1]);
             ziw[i] = 1.0 / (e[i + 1] - e[i]);
             ziwf[i] = (float)ziw[i];
             znuf[i] = (float)(zc[i] * ziw[i]);
+            zcf[i] = (float)zc[i];
         }
         for (int i = 0; i <= n; ++i) zlof[i] = (float)e[i];
         if (dalloc(&ctx->d_edges[d], n + 1) != cudaSuccess || dalloc(&ctx->d_dvol[d], n) != cudaSuccess ||
             dalloc(&ctx->d_dvol_f[d], n) != cudaSuccess || dalloc(&ctx->d_zc[d], n) != cudaSuccess ||
             dalloc(&ctx->d_ziw[d], n) != cudaSuccess || dalloc(&ctx->d_ziw_f[d], n) != cudaSuccess ||
             dalloc(&ctx->d_znu_f[d], n) != cudaSuccess || dalloc(&ctx->d_zlo_f[d], n + 1) != cudaSuccess ||
-            dalloc(&ctx->d_ekey[d], n + 1) != cudaSuccess) {
+            dalloc(&ctx->d_ekey[d], n + 1) != cudaSuccess || dalloc(&ctx->d_zc_f[d], n) != cudaSuccess) {
             ctx->err = "device allocation of grid arrays failed";
             return bail(DUST_ENOMEM);
         }
@@ -638,6 +707,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         cudaMemcpy(ctx->d_ziw_f[d], ziwf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(ctx->d_znu_f[d], znuf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(ctx->d_zlo_f[d], zlof.data(), (n + 1) * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_zc_f[d], zcf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        g.zc_f[d] = ctx->d_zc_f[d];
         {
             std::vector<long long> ek(n + 1);
             for (int i = 0; i <= n; ++i) ek[i] = order_key(e[i]);
@@ -1003,6 +1074,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
         dfree(ctx->d_ziw_f[d]);
         dfree(ctx->d_znu_f[d]);
         dfree(ctx->d_zlo_f[d]);
+        dfree(ctx->d_zc_f[d]);
     }
     dfree(ctx->d_gas);
     dfree(ctx->d_dep);

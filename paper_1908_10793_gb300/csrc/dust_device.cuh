@@ -25,12 +25,21 @@ __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ long long rround(float x) { return __float2ll_rn(x); }
 __device__ __forceinline__ long long rround(double x) { return __double2ll_rn(x); }
 
+// A uniform parameter in the working precision (single-precision copies are
+// prepared on the host, so the mixed path converts nothing per grain).
+template <typename Real>
+__device__ __forceinline__ Real pick(double d, float f);
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+
 // e - sin(e), without cancellation for small e (Taylor series, |e| < 0.5).
 template <typename R>
 __device__ __forceinline__ R e_minus_sin(R e)
 {
     R s = e * e;
-    if (fabs((double)e) < 0.5)
+    if (fabs(e) < R(0.5))
         return e * s * (R(1) / R(6)) *
                (R(1) - s * (R(1) / R(20)) * (R(1) - s * (R(1) / R(42)) * (R(1) - s * (R(1) / R(72)))));
     return e - rsin(e);
@@ -232,10 +241,10 @@ __device__ __forceinline__ bool apply_bc(const GridDev &g, const PhysDev &ph, do
         if (GEOM == GEOM_SB && d == 0) {
             if (q[0] >= hi) {
                 q[1] += shift;
-                if (!ph.fargo) p[1] += (Real)ph.jump_v;
+                if (!ph.fargo) p[1] += pick<Real>(ph.jump_v, ph.jump_v_f);
             } else {
                 q[1] -= shift;
-                if (!ph.fargo) p[1] -= (Real)ph.jump_v;
+                if (!ph.fargo) p[1] -= pick<Real>(ph.jump_v, ph.jump_v_f);
             }
             q[0] = wrap_once(q[0], lo, hi);
             q[1] = wrap_once(q[1], g.lo[1], g.hi[1]);
@@ -284,7 +293,7 @@ __device__ __forceinline__ void drift(const PhysDev &ph, double q[3], const doub
     } else if (GEOM == GEOM_SB) {
         inc[0] = h * p[0];
         q[0] += (double)inc[0];
-        if (ph.fargo) inc[1] = h * (p[1] - (Real)ph.q_om * (Real)(second ? qm[0] : q[0]));
+        if (ph.fargo) inc[1] = h * (p[1] - pick<Real>(ph.q_om, ph.q_om_f) * (Real)(second ? qm[0] : q[0]));
         else inc[1] = h * p[1];
         q[1] += (double)inc[1];
         inc[2] = h * p[2];
@@ -299,32 +308,33 @@ __device__ __forceinline__ void drift(const PhysDev &ph, double q[3], const doub
 }
 
 // ------------------------------------------------------ stopping time -----
-template <typename Real, int GEOM>
+// qm: half-step coordinates, in double or in the working precision.
+template <typename Real, int GEOM, typename QT>
 __device__ __forceinline__ Real stopping_time(const PhysDev &ph, int mode, Real value,
-                                              const double qm[3], Real rho_g)
+                                              const QT qm[3], Real rho_g)
 {
     if (mode == DUST_TAU_CONST) return value;
     if (mode == DUST_TAU_EPSTEIN) return value / rho_g;
     if (GEOM == GEOM_CYL || GEOM == GEOM_SPH) {
         Real R = (Real)qm[0];
         if (GEOM == GEOM_SPH) R *= rsin((Real)qm[1]);
-        return value * rsqrt_(R * R * R / (Real)ph.gm);
+        return value * rsqrt_(R * R * R / pick<Real>(ph.gm, ph.gm_f));
     }
-    return value / (Real)ph.omega;
+    return value / pick<Real>(ph.omega, ph.omega_f);
 }
 
 // ---------------------------------------------------------------- kick ----
 // Kick with E = exp(-dt/tau), cg = 1 - E = h1/tau, h1 = dt phi1(-dt/tau)
 // (Eqs. phi1, h1); returns the new p, the non-frictional acceleration a at
 // (q^{n+1/2}, p^{n+1/2}) and dH/dp at the half step.
-template <typename Real, int GEOM>
-__device__ __forceinline__ void kick(const PhysDev &ph, const double qm[3], const Real pn[3],
+template <typename Real, int GEOM, typename QT>
+__device__ __forceinline__ void kick(const PhysDev &ph, const QT qm[3], const Real pn[3],
                                      const Real vg[3], Real E, Real cg, Real h1, Real pp[3],
                                      Real a[3], Real dH[3])
 {
     if (GEOM == GEOM_SB) {
         // App. B.1: R v^{n+1} = E v^n + h1 G(x^{n+1/2}, v^n/2, v_g^{n+1/2})
-        const Real Om = (Real)ph.omega, q = (Real)ph.qshear;
+        const Real Om = pick<Real>(ph.omega, ph.omega_f), q = pick<Real>(ph.qshear, ph.qshear_f);
         const Real az = ph.vgrav ? -Om * Om * (Real)qm[2] : Real(0);
         const Real Om1 = Om * h1;
         Real G0, G1;
@@ -364,10 +374,10 @@ __device__ __forceinline__ void kick(const PhysDev &ph, const double qm[3], cons
                 const Real z = (Real)qm[2];
                 const Real r2 = R * R + z * z;
                 const Real ir3 = Real(1) / (r2 * rsqrt_(r2));
-                gR = -(Real)ph.gm * R * ir3;
-                gz = -(Real)ph.gm * z * ir3;
+                gR = -pick<Real>(ph.gm, ph.gm_f) * R * ir3;
+                gz = -pick<Real>(ph.gm, ph.gm_f) * z * ir3;
             } else {
-                gR = -(Real)ph.gm / (R * R);
+                gR = -pick<Real>(ph.gm, ph.gm_f) / (R * R);
             }
         }
         pp[2] = E * pn[2] + h1 * gz + cg * vg[2];
@@ -384,7 +394,7 @@ __device__ __forceinline__ void kick(const PhysDev &ph, const double qm[3], cons
         const Real r = (Real)qm[0];
         const Real th = (Real)qm[1];
         const Real st = rsin(th), ct = rcos(th);
-        const Real gr = ph.gm != 0.0 ? -(Real)ph.gm / (r * r) : Real(0);
+        const Real gr = ph.gm != 0.0 ? -pick<Real>(ph.gm, ph.gm_f) / (r * r) : Real(0);
         pp[2] = E * pn[2] + cg * vg[2];
         const Real lp2 = Real(0.5) * (pn[2] * pn[2] + pp[2] * pp[2]);
         const Real ath = lp2 * ct / (r * r * st * st * st);

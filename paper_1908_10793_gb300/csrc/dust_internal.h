@@ -48,6 +48,7 @@ struct GridDev {
     const float *ziw_f[3];
     const float *znu_f[3];   // centre / width (curvilinear radial weights)
     const float *zlo_f[3];   // lower edge (polar-angle weights)
+    const float *zc_f[3];    // zone centres, single precision
     int64_t ncell;
     // tile layout of the zone sort: tiles of T[0] x T[1] x T[2] zones; key of
     // zone (i,j,k) = tile index * tvol + position inside the tile
@@ -74,6 +75,8 @@ struct PhysDev {
     double jump_v;           // q * Omega * Lx (standard-frame v_y jump)
     double shift_mid;        // fmod(q Omega Lx (t + dt/2), Ly)
     double shift_end;        // fmod(q Omega Lx (t + dt), Ly)
+    // single-precision copies for the mixed path
+    float omega_f, qshear_f, gm_f, q_om_f, jump_v_f;
 };
 
 struct SpeciesDev {
@@ -83,6 +86,7 @@ struct SpeciesDev {
     int mode[kMaxSpecies];
     double mq[kMaxSpecies];   // mass / fixed-point quantum
     float mqf[kMaxSpecies];
+    float tau_f[kMaxSpecies];
 };
 
 template <typename Real>
@@ -112,6 +116,7 @@ template <typename Real>
 struct TiledArgs {
     StepArgs<Real> s;
     const int32_t *key_off;       // [nkeys + 1] start of each key in the sorted store
+    int tsc;                      // 1: TSC weights, 0: CIC
 };
 
 template <typename Real>
@@ -121,8 +126,11 @@ struct SortArgs {
     double dt;                    // step the key predicts (half drift of it)
     StoreDev<Real> src, dst;
     int32_t *key;                 // [n]
-    int32_t *count;               // [ncell + 1]
-    int32_t *cursor;              // [ncell + 1]
+    int32_t *count;               // [nkeys + 1] key offsets after the scan
+    int32_t *cursor;              // [nkeys + 1]
+    int32_t *pair_id;             // [n] grain id at its sorted position
+    int32_t *pair_src;            // [n] source position of that grain
+    int64_t nkeys1;               // nkeys + 1 (the removed-grain key included)
 };
 
 // Launch wrappers, explicitly instantiated per geometry.
@@ -131,6 +139,10 @@ cudaError_t launch_step_per_grain(const StepArgs<Real> &a, cudaStream_t s);
 
 template <typename Real, int GEOM, int WEIGHT>
 cudaError_t launch_step_tiled(const TiledArgs<Real> &a, cudaStream_t s);
+
+// FLAT: 0 = all directions gridded, 1 = y not gridded, 2 = z not gridded
+template <int GEOM, int FLAT>
+cudaError_t launch_step_slab(const TiledArgs<float> &a, cudaStream_t s);
 
 template <typename Real, int GEOM>
 cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s);

@@ -1,6 +1,7 @@
-// Counting sort of the grain store by zone: exclusive scan of the zone
-// counts and scatter of every store column (keys are computed by the
-// geometry-specific sort_keys kernel).
+// Counting sort of the grain store by zone key: exclusive scan of the key
+// counts, scatter of (id, source) pairs, an id sort inside every key and a
+// gather of the store columns (keys are computed by the geometry-specific
+// sort_keys kernel).  The sorted order is deterministic: by key, then id.
 #include "dust_internal.h"
 
 namespace dust {
@@ -99,27 +100,76 @@ cudaError_t launch_exclusive_scan(int32_t *data, int64_t n, int32_t *block_sums,
     return cudaGetLastError();
 }
 
+// Scatter of (id, source position) pairs to their key segments.  Positions
+// inside a segment come from atomics (arbitrary order); the segment sort
+// below puts every segment in grain-id order, so the sorted store is
+// reproducible.
 template <typename Real>
-__global__ void sort_scatter_kernel(const SortArgs<Real> A)
+__global__ void sort_scatter_pairs_kernel(const SortArgs<Real> A)
 {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= A.src.n) return;
-    const int32_t pos = atomicAdd(&A.cursor[A.key[gi]], 1);
+    const bool valid = gi < A.src.n;
+    const int32_t key = valid ? A.key[gi] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&A.cursor[key], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!valid) return;
+    const int32_t pos = base + __popc(peers & ((1u << lane) - 1u));
+    A.pair_id[pos] = A.src.id[gi];
+    A.pair_src[pos] = (int32_t)gi;
+}
+
+// One thread per key: insertion sort of the key's (id, source) pairs by id.
+template <typename Real>
+__global__ void sort_segments_kernel(const SortArgs<Real> A)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.nkeys1) return;
+    const int32_t b = A.count[k], e = A.count[k + 1];
+    for (int32_t u = b + 1; u < e; ++u) {
+        const int32_t id = A.pair_id[u], src = A.pair_src[u];
+        int32_t j = u - 1;
+        while (j >= b) {
+            const int32_t idj = A.pair_id[j];
+            if (idj <= id) break;
+            A.pair_id[j + 1] = idj;
+            A.pair_src[j + 1] = A.pair_src[j];
+            --j;
+        }
+        A.pair_id[j + 1] = id;
+        A.pair_src[j + 1] = src;
+    }
+}
+
+// Gather every store column into sorted order (coalesced writes; the
+// sources are nearly in order because grains move little between sorts).
+template <typename Real>
+__global__ void sort_gather_kernel(const SortArgs<Real> A)
+{
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= A.src.n) return;
+    const int32_t src = A.pair_src[pos];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        A.dst.q[d][pos] = A.src.q[d][gi];
-        A.dst.p[d][pos] = A.src.p[d][gi];
+        A.dst.q[d][pos] = A.src.q[d][src];
+        A.dst.p[d][pos] = A.src.p[d][src];
     }
-    A.dst.id[pos] = A.src.id[gi];
-    if (A.src.species) A.dst.species[pos] = A.src.species[gi];
-    if (A.src.param) A.dst.param[pos] = A.src.param[gi];
+    A.dst.id[pos] = A.pair_id[pos];
+    if (A.src.species) A.dst.species[pos] = A.src.species[src];
+    if (A.src.param) A.dst.param[pos] = A.src.param[src];
 }
 
 template <typename Real>
 cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s)
 {
     if (a.src.n == 0) return cudaSuccess;
-    sort_scatter_kernel<Real><<<(unsigned)((a.src.n + 255) / 256), 256, 0, s>>>(a);
+    const unsigned nb = (unsigned)((a.src.n + 255) / 256);
+    sort_scatter_pairs_kernel<Real><<<nb, 256, 0, s>>>(a);
+    sort_segments_kernel<Real><<<(unsigned)((a.nkeys1 + 255) / 256), 256, 0, s>>>(a);
+    sort_gather_kernel<Real><<<nb, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

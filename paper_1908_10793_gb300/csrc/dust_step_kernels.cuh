@@ -198,10 +198,13 @@ template <typename Real, int GEOM>
 __global__ void sort_keys_kernel(const SortArgs<Real> A)
 {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= A.src.n) return;
-    int32_t key = (int32_t)A.g.nkeys;
-    double q[3] = {A.src.q[0][gi], A.src.q[1][gi], A.src.q[2][gi]};
-    if (!isnan(q[0])) {
+    const bool valid = gi < A.src.n;
+    int32_t key = valid ? (int32_t)A.g.nkeys : -1;
+    double q[3] = {0.0, 0.0, 0.0};
+    if (valid) {
+        q[0] = A.src.q[0][gi]; q[1] = A.src.q[1][gi]; q[2] = A.src.q[2][gi];
+    }
+    if (valid && !isnan(q[0])) {
         Real p[3] = {A.src.p[0][gi], A.src.p[1][gi], A.src.p[2][gi]};
         Real inc[3];
         drift<Real, GEOM>(A.ph, q, q, p, (Real)(0.5 * A.dt), false, inc);
@@ -216,8 +219,11 @@ __global__ void sort_keys_kernel(const SortArgs<Real> A)
         const int i = locate(A.g, 0, q[0]), j = locate(A.g, 1, q[1]), k = locate(A.g, 2, q[2]);
         key = (int32_t)zone_key(A.g, i, j, k);
     }
-    A.key[gi] = key;
-    atomicAdd(&A.count[key], 1);
+    if (valid) A.key[gi] = key;
+    // consecutive grains mostly share a key: one atomic per distinct key in
+    // the warp
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&A.count[key], __popc(peers));
 }
 
 template <typename Real, int GEOM>

@@ -23,7 +23,7 @@ DUST_WEIGHT_CIC, DUST_WEIGHT_TSC = 0, 1
 DUST_TAU_CONST, DUST_TAU_STOKES, DUST_TAU_EPSTEIN = 0, 1, 2
 DUST_FP64, DUST_MIXED = 0, 1
 DUST_MEM_HOST, DUST_MEM_DEVICE = 0, 1
-DUST_KERNEL_AUTO, DUST_KERNEL_PER_GRAIN, DUST_KERNEL_TILED = 0, 1, 2
+DUST_KERNEL_AUTO, DUST_KERNEL_PER_GRAIN, DUST_KERNEL_TILED, DUST_KERNEL_SLAB = 0, 1, 2, 3
 DUST_FLAG_NAN, DUST_FLAG_OVERFLOW, DUST_FLAG_CFL, DUST_FLAG_WRAP = 1, 2, 4, 8
 
 
