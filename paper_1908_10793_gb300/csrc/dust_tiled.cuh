@@ -63,7 +63,8 @@ __device__ __forceinline__ long long rint_to_ll(float v)
     const float magic = 12582912.0f;  // 1.5 * 2^23
     const float th = __fadd_rn(__fmul_rn(v, 4.76837158203125e-07f), magic);  // v / 2^21
     const int hi = __float_as_int(th) - 0x4B400000;
-    const float lo = __fmaf_rn(-(float)hi, 2097152.0f, v);
+    const float hf = __fsub_rn(th, magic);  // == (float)hi, exactly
+    const float lo = __fmaf_rn(-hf, 2097152.0f, v);
     const int l = __float_as_int(__fadd_rn(lo, magic)) - 0x4B400000;
     return ((long long)hi << 21) + (long long)l;
 }
