@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "dust_internal.h"
@@ -62,6 +63,10 @@ struct dust_ctx {
 
     int32_t *d_key = nullptr, *d_count = nullptr, *d_cursor = nullptr, *d_blocksums = nullptr;
     int32_t *d_pair_id = nullptr, *d_pair_src = nullptr;
+    // key counts for the next sort (d_count holds the current key offsets)
+    int32_t *d_count_next = nullptr;
+    bool keys_ready = false;   // d_key / d_count_next predicted by the last step
+    double keys_dt = 0.0;      // the step length they were predicted for
     double *d_stage = nullptr;
     size_t stage_bytes = 0;
 
@@ -431,28 +436,35 @@ int run_sort(dust_ctx *ctx, double dt)
     a.src = store_of<Real>(ctx, ctx->cur);
     a.dst = store_of<Real>(ctx, 1 - ctx->cur);
     a.key = ctx->d_key;
-    a.count = ctx->d_count;
+    a.count = ctx->d_count_next;
     a.cursor = ctx->d_cursor;
     a.pair_id = ctx->d_pair_id;
     a.pair_src = ctx->d_pair_src;
     a.nkeys1 = ctx->g.nkeys + 1;
     const int64_t m = ctx->g.nkeys + 1;
     GroupTimer timer(ctx, dust_ctx::GROUP_SORT);
-    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += 7;
-    CU(cudaMemsetAsync(ctx->d_count, 0, m * sizeof(int32_t), ctx->stream));
-    cudaError_t e = cudaSuccess;
-    switch (ctx->geom.kind) {
-    case DUST_CARTESIAN: e = launch_sort_keys<Real, GEOM_CART>(a, ctx->stream); break;
-    case DUST_SHEARING_BOX: e = launch_sort_keys<Real, GEOM_SB>(a, ctx->stream); break;
-    case DUST_CYLINDRICAL: e = launch_sort_keys<Real, GEOM_CYL>(a, ctx->stream); break;
-    default: e = launch_sort_keys<Real, GEOM_SPH>(a, ctx->stream); break;
+    // keys predicted by the previous step for this dt are reused; otherwise
+    // the key kernel computes them
+    const bool reuse = ctx->keys_ready && ctx->keys_dt == dt;
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += reuse ? 6 : 7;
+    if (!reuse) {
+        CU(cudaMemsetAsync(ctx->d_count_next, 0, m * sizeof(int32_t), ctx->stream));
+        cudaError_t e = cudaSuccess;
+        switch (ctx->geom.kind) {
+        case DUST_CARTESIAN: e = launch_sort_keys<Real, GEOM_CART>(a, ctx->stream); break;
+        case DUST_SHEARING_BOX: e = launch_sort_keys<Real, GEOM_SB>(a, ctx->stream); break;
+        case DUST_CYLINDRICAL: e = launch_sort_keys<Real, GEOM_CYL>(a, ctx->stream); break;
+        default: e = launch_sort_keys<Real, GEOM_SPH>(a, ctx->stream); break;
+        }
+        CU(e);
     }
-    CU(e);
-    CU(launch_exclusive_scan(ctx->d_count, m, ctx->d_blocksums, ctx->stream));
-    CU(cudaMemcpyAsync(ctx->d_cursor, ctx->d_count, m * sizeof(int32_t),
+    CU(launch_exclusive_scan(ctx->d_count_next, m, ctx->d_blocksums, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->d_cursor, ctx->d_count_next, m * sizeof(int32_t),
                        cudaMemcpyDeviceToDevice, ctx->stream));
     CU(launch_sort_scatter<Real>(a, ctx->stream));
     ctx->cur = 1 - ctx->cur;
+    std::swap(ctx->d_count, ctx->d_count_next);
+    ctx->keys_ready = false;
     return DUST_OK;
 }
 
@@ -504,12 +516,16 @@ inline bool slab_available(int geom, int flat)
 
 template <typename Real, int GEOM>
 cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
-                             const int32_t *key_off, cudaStream_t s)
+                             const int32_t *key_off, int32_t *key_out, int32_t *count_out,
+                             cudaStream_t s)
 {
     TiledArgs<Real> ta;
     ta.s = a;
     ta.key_off = key_off;
     ta.tsc = weight == DUST_WEIGHT_TSC;
+    ta.emit_keys = key_out != nullptr;
+    ta.key_out = key_out;
+    ta.count_out = count_out;
     if (kernel == DUST_KERNEL_PER_GRAIN)
         return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<Real, GEOM, 1>(a, s)
                                          : launch_step_per_grain<Real, GEOM, 0>(a, s);
@@ -518,8 +534,18 @@ cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
         if ((kernel == DUST_KERNEL_AUTO || kernel == DUST_KERNEL_SLAB) && slab_available(GEOM, flat))
             return launch_slab_geom<GEOM>(ta, flat, s);
     }
+    ta.emit_keys = 0;
     return weight == DUST_WEIGHT_TSC ? launch_step_tiled<Real, GEOM, 1>(ta, s)
                                      : launch_step_tiled<Real, GEOM, 0>(ta, s);
+}
+
+// Whether the step kernel of this context predicts the next sort's keys: the
+// slab kernel does (single-precision push, a supported flat pattern).
+inline bool step_emits_keys(const dust_ctx *ctx)
+{
+    const int kn = ctx->opt.kernel;
+    return ctx->mixed && (kn == DUST_KERNEL_AUTO || kn == DUST_KERNEL_SLAB) &&
+           slab_available(ctx->geom.kind, slab_flat(ctx->g));
 }
 
 template <typename Real>
@@ -547,14 +573,23 @@ int run_step(dust_ctx *ctx, double dt)
     const int wt = ctx->opt.weight;
     const int32_t *ko = ctx->d_count;
     cudaStream_t st = ctx->stream;
+    // the step before a sort predicts that sort's keys (for the same dt)
+    const bool emit = step_emits_keys(ctx) && ctx->n_grains > 0 &&
+                      (ctx->steps + 1) % ctx->sort_interval == 0;
+    int32_t *kout = emit ? ctx->d_key : nullptr;
+    int32_t *cout_ = emit ? ctx->d_count_next : nullptr;
+    if (emit)
+        CU(cudaMemsetAsync(ctx->d_count_next, 0, (ctx->g.nkeys + 1) * sizeof(int32_t), st));
     switch (ctx->geom.kind) {
-    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, st); break;
-    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, st); break;
-    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, st); break;
-    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, st); break;
+    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, st); break;
+    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, st); break;
+    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, kout, cout_, st); break;
+    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, kout, cout_, st); break;
     }
     delete step_timer;
     CU(e);
+    ctx->keys_ready = emit;
+    ctx->keys_dt = dt;
     if (ctx->opt.feedback_apply) {
         GroupTimer timer(ctx, dust_ctx::GROUP_OTHER);
         ctx->launches[dust_ctx::GROUP_OTHER] += 1;
@@ -760,6 +795,7 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         dalloc(&ctx->d_dep, ncell * 4) != cudaSuccess ||
         dalloc(&ctx->d_status, ST_WORDS) != cudaSuccess ||
         dalloc(&ctx->d_count, nk + 2) != cudaSuccess ||
+        dalloc(&ctx->d_count_next, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_cursor, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_blocksums, scan_block_sums_size(nk + 2)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void **>(&ctx->h_status), ST_WORDS * sizeof(unsigned)) !=
@@ -856,6 +892,7 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
     ctx->n_grains = n;
     ctx->cur = 0;
     ctx->need_sort = true;
+    ctx->keys_ready = false;
     if (n > 0) {
         const uint8_t *sp_dev = species;
         if (mem == DUST_MEM_HOST) {
@@ -1080,6 +1117,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     dfree(ctx->d_dep);
     dfree(ctx->d_status);
     dfree(ctx->d_count);
+    dfree(ctx->d_count_next);
     dfree(ctx->d_cursor);
     dfree(ctx->d_blocksums);
     dfree(ctx->d_stage);

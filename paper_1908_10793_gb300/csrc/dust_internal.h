@@ -117,6 +117,10 @@ struct TiledArgs {
     StepArgs<Real> s;
     const int32_t *key_off;       // [nkeys + 1] start of each key in the sorted store
     int tsc;                      // 1: TSC weights, 0: CIC
+    // optional: the step kernel predicts every grain's key for the next sort
+    int emit_keys;
+    int32_t *key_out;             // [n]
+    int32_t *count_out;           // [nkeys + 1], zeroed before the step
 };
 
 template <typename Real>

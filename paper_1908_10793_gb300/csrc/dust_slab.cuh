@@ -55,6 +55,16 @@ step_slab_kernel(const TiledArgs<float> TA)
     const unsigned FULL = 0xffffffffu;
 
     const int tile = blockIdx.x;
+    if (TA.emit_keys) {
+        // grains removed before the last sort sit after every zone's group and
+        // keep the removed-grain key
+        const int64_t D0 = TA.key_off[g.nkeys], D1 = A.s.n;
+        for (int64_t gi = D0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < D1;
+             gi += (int64_t)gridDim.x * blockDim.x)
+            TA.key_out[gi] = (int32_t)g.nkeys;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && D1 > D0)
+            atomicAdd(&TA.count_out[g.nkeys], (int32_t)(D1 - D0));
+    }
     const int64_t kbase = (int64_t)tile * g.tvol;
     if (TA.key_off[kbase + g.tvol] <= TA.key_off[kbase]) return;
 
@@ -177,6 +187,8 @@ step_slab_kernel(const TiledArgs<float> TA)
                 float iw[3] = {0.f, 0.f, 0.f};
                 float inc1[3] = {0.f, 0.f, 0.f};
                 float qf[3] = {0.f, 0.f, 0.f};  // half-step coordinates
+                float u[3] = {0.f, 0.f, 0.f}, zc3[3] = {0.f, 0.f, 0.f};
+                int32_t nkey = (int32_t)g.nkeys;   // next sort key (removed: nkeys)
                 int host[3] = {0, 0, 0};
                 int sp = 0;
                 bool live = false, ingroup = false;
@@ -186,7 +198,6 @@ step_slab_kernel(const TiledArgs<float> TA)
                     if (live) {
                         pn[0] = A.s.p[0][gi]; pn[1] = A.s.p[1][gi]; pn[2] = A.s.p[2][gi];
                         sp = A.s.species ? A.s.species[gi] : 0;
-                        float u[3], zc3[3];
     #pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             if (g.n[d] > 1) { u[d] = (float)(q[d] - zcd[d]); zc3[d] = zcf[d]; }
@@ -392,6 +403,57 @@ step_slab_kernel(const TiledArgs<float> TA)
                     }
                     A.s.q[0][gi] = q[0]; A.s.q[1][gi] = q[1]; A.s.q[2][gi] = q[2];
                     A.s.p[0][gi] = pnew[0]; A.s.p[1][gi] = pnew[1]; A.s.p[2][gi] = pnew[2];
+                    if (TA.emit_keys && alive) {
+                        // key for the next sort: the zone of the next step's
+                        // half-step position (same dt), relative to this key
+                        // zone in single precision; the exact prediction when
+                        // the grain moves more than one zone or crosses the grid
+                        bool fast = ingroup;
+                        int zn[3] = {zx, zy, zz};
+                        if (fast) {
+                            float un[3];
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) un[d] = u[d] + inc2[d];
+                            if (GEOM == GEOM_CYL) {
+                                un[0] += h * pnew[0];
+                                const float R = zc3[0] + un[0];
+                                un[1] += h * pnew[1] / (R * R);
+                                un[2] += h * pnew[2];
+                            } else if (GEOM == GEOM_SPH) {
+                                un[0] += h * pnew[0];
+                                const float r = zc3[0] + un[0];
+                                un[1] += h * pnew[1] / (r * r);
+                                const float st = sinf(zc3[1] + un[1]);
+                                un[2] += h * pnew[2] / (r * r * st * st);
+                            } else if (GEOM == GEOM_SB) {
+                                un[0] += h * pnew[0];
+                                un[1] += A.ph.fargo ? h * (pnew[1] - A.ph.q_om_f * (zc3[0] + un[0])) : h * pnew[1];
+                                un[2] += h * pnew[2];
+                            } else {
+#pragma unroll
+                                for (int d = 0; d < 3; ++d) un[d] += h * pnew[d];
+                            }
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                if (g.n[d] <= 1) continue;
+                                const int k = (int)floorf(un[d] * zif[d] + 0.5f);
+                                zn[d] += k;
+                                fast &= k >= -1 && k <= 1 && zn[d] >= 0 && zn[d] < g.n[d];
+                            }
+                        }
+                        if (fast) {
+                            nkey = (int32_t)zone_key(g, zn[0], zn[1], zn[2]);
+                        } else {
+                            double qk[3] = {q[0], q[1], q[2]};
+                            nkey = predict_key<float, GEOM>(g, A.ph, qk, pnew, h);
+                        }
+                    }
+                }
+                if (TA.emit_keys) {
+                    TA.key_out[gi] = nkey;
+                    const unsigned am = __activemask();
+                    const unsigned peers = __match_any_sync(am, nkey);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&TA.count_out[nkey], __popc(peers));
                 }
                 // record for the zone's deposit owners
                 const int slot = (int)(gi - P0);

@@ -191,6 +191,27 @@ cudaError_t launch_step_per_grain(const StepArgs<Real> &a, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------- sort ----
+// Sort key of a grain for a step of half length h: the zone of its predicted
+// half-step position (first half drift, periodic wrap, clamped onto the grid
+// otherwise).  q is overwritten.
+template <typename Real, int GEOM>
+__device__ __forceinline__ int32_t predict_key(const GridDev &g, const PhysDev &ph, double q[3],
+                                               const Real p[3], Real h)
+{
+    Real inc[3];
+    drift<Real, GEOM>(ph, q, q, p, h, false, inc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (!inside(g, d, q[d])) {
+            if (g.bc[d] == DUST_BC_PERIODIC) q[d] = wrap_once(q[d], g.lo[d], g.hi[d]);
+            if (q[d] < g.lo[d]) q[d] = g.lo[d];
+            if (q[d] >= g.hi[d]) q[d] = g.edges[d][g.n[d] - 1];
+        }
+    }
+    const int i = locate(g, 0, q[0]), j = locate(g, 1, q[1]), k = locate(g, 2, q[2]);
+    return (int32_t)zone_key(g, i, j, k);
+}
+
 // Key of a grain = zone of its predicted half-step position for the next
 // step (the zone the step kernel will gather from); removed grains get
 // key ncell and sort to the end.
@@ -206,18 +227,7 @@ __global__ void sort_keys_kernel(const SortArgs<Real> A)
     }
     if (valid && !isnan(q[0])) {
         Real p[3] = {A.src.p[0][gi], A.src.p[1][gi], A.src.p[2][gi]};
-        Real inc[3];
-        drift<Real, GEOM>(A.ph, q, q, p, (Real)(0.5 * A.dt), false, inc);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (q[d] < A.g.lo[d] || q[d] >= A.g.hi[d]) {
-                if (A.g.bc[d] == DUST_BC_PERIODIC) q[d] = wrap_once(q[d], A.g.lo[d], A.g.hi[d]);
-                if (q[d] < A.g.lo[d]) q[d] = A.g.lo[d];
-                if (q[d] >= A.g.hi[d]) q[d] = A.g.edges[d][A.g.n[d] - 1];
-            }
-        }
-        const int i = locate(A.g, 0, q[0]), j = locate(A.g, 1, q[1]), k = locate(A.g, 2, q[2]);
-        key = (int32_t)zone_key(A.g, i, j, k);
+        key = predict_key<Real, GEOM>(A.g, A.ph, q, p, (Real)(0.5 * A.dt));
     }
     if (valid) A.key[gi] = key;
     // consecutive grains mostly share a key: one atomic per distinct key in

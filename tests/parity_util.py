@@ -56,8 +56,9 @@ def run_gpu(w, steps, precision, dt=None, feedback=None, **kw):
     try:
         ctx.set_gas(w.rho, w.vgas)
         ctx.load(w.q, w.v, w.species, w.param)
-        for _ in range(steps):
-            ctx.step(dt)
+        # dt may be a sequence of step lengths, one per step
+        for s in range(steps):
+            ctx.step(dt[s] if isinstance(dt, (list, tuple)) else dt)
         rc, st = ctx.sync(check=False)
         fixed, quantum = ctx.deposit()
         q, v, ids = ctx.particles()
