@@ -122,9 +122,8 @@ void dfree(void *p)
     if (p) cudaFree(p);
 }
 
-int edge_kind(const std::vector<double> &e)
+int edge_kind(const double *e, int n)
 {
-    const int n = (int)e.size() - 1;
     if (n <= 1) return EDGE_UNIFORM;
     const double lo = e[0], hi = e[n];
     bool uni = true, lg = lo > 0.0;
@@ -137,6 +136,121 @@ int edge_kind(const std::vector<double> &e)
         }
     }
     return uni ? EDGE_UNIFORM : (lg ? EDGE_LOG : EDGE_GENERAL);
+}
+
+// Checks of the geometry, grid, species and weight descriptors shared by
+// dust_create and dust_step_noalloc; *ncell_out = number of zones.
+int validate_descriptors(const dust_geometry *geom, const dust_grid *grid,
+                         const dust_species *species, int n_species, int weight,
+                         int64_t *ncell_out)
+{
+    if (!geom || !grid || !species) return fail(nullptr, DUST_EINVAL, "NULL descriptor");
+    if (geom->kind < DUST_CARTESIAN || geom->kind > DUST_SPHERICAL)
+        return fail(nullptr, DUST_EINVAL, "bad geometry kind %d", geom->kind);
+    if (n_species < 1 || n_species > kMaxSpecies)
+        return fail(nullptr, DUST_EINVAL, "n_species must be 1..%d", kMaxSpecies);
+    if (weight != DUST_WEIGHT_CIC && weight != DUST_WEIGHT_TSC)
+        return fail(nullptr, DUST_EINVAL, "bad weight");
+    int64_t ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (grid->n[d] < 1 || !grid->edges[d])
+            return fail(nullptr, DUST_EINVAL, "direction %d: n < 1 or no edges", d);
+        if (!std::isfinite(grid->edges[d][0]))
+            return fail(nullptr, DUST_EINVAL, "direction %d: edges not finite", d);
+        for (int i = 0; i < grid->n[d]; ++i)
+            if (!(grid->edges[d][i] < grid->edges[d][i + 1]) || !std::isfinite(grid->edges[d][i + 1]))
+                return fail(nullptr, DUST_EINVAL, "direction %d: edges not increasing", d);
+        if (grid->bc[d] != DUST_BC_PERIODIC && grid->bc[d] != DUST_BC_OUTFLOW)
+            return fail(nullptr, DUST_EINVAL, "direction %d: bad boundary kind", d);
+        ncell *= grid->n[d];
+    }
+    if (ncell >= (int64_t)1 << 31) return fail(nullptr, DUST_EINVAL, "too many zones");
+    if (geom->kind == DUST_CYLINDRICAL && grid->edges[0][0] <= 0.0)
+        return fail(nullptr, DUST_EINVAL, "cylindrical R must be > 0");
+    if (geom->kind == DUST_SPHERICAL &&
+        (grid->edges[0][0] <= 0.0 || grid->edges[1][0] <= 0.0 ||
+         grid->edges[1][grid->n[1]] >= M_PI))
+        return fail(nullptr, DUST_EINVAL, "spherical r must be > 0 and theta in (0, pi)");
+    if ((geom->kind == DUST_CYLINDRICAL || geom->kind == DUST_SPHERICAL))
+        for (int s = 0; s < n_species; ++s)
+            if (species[s].tau_mode == DUST_TAU_STOKES && !(geom->gm > 0.0))
+                return fail(nullptr, DUST_EINVAL, "Stokes-number mode needs GM > 0");
+    *ncell_out = ncell;
+    return DUST_OK;
+}
+
+// Species constants; quantum <= 0 selects the default 2^-44 * largest mass.
+SpeciesDev make_species(const dust_species *species, int n_species, double quantum,
+                        double *quantum_out)
+{
+    SpeciesDev sp{};
+    double mmax = 0.0;
+    sp.n = n_species;
+    for (int s = 0; s < n_species; ++s) {
+        sp.mass[s] = species[s].mass;
+        sp.tau[s] = species[s].tau_value;
+        sp.mode[s] = species[s].tau_mode;
+        mmax = fmax(mmax, fabs(species[s].mass));
+    }
+    const double qu = quantum > 0.0 ? quantum : ldexp(mmax > 0 ? mmax : 1.0, -44);
+    for (int s = 0; s < n_species; ++s) {
+        sp.mq[s] = species[s].mass / qu;
+        sp.mqf[s] = (float)sp.mq[s];
+        sp.tau_f[s] = (float)sp.tau[s];
+    }
+    *quantum_out = qu;
+    return sp;
+}
+
+// Scalar description of direction d of the grid (host side).
+void grid_direction(GridDev &g, int d, const double *e, int n, int bc)
+{
+    g.n[d] = n;
+    g.bc[d] = bc;
+    g.lo[d] = e[0];
+    g.hi[d] = e[n];
+    g.edge_kind[d] = edge_kind(e, n);
+    if (g.edge_kind[d] == EDGE_LOG) {
+        g.inv_d[d] = n / log(e[n] / e[0]);
+        g.log_lo_f[d] = logf((float)e[0]);
+    } else {
+        g.inv_d[d] = n / (e[n] - e[0]);
+        g.log_lo_f[d] = 0.f;
+    }
+    g.inv_df[d] = (float)g.inv_d[d];
+    g.lo_key[d] = order_key(e[0]);
+    g.hi_key[d] = order_key(e[n]);
+}
+
+// Per-zone tables of one direction, written to host arrays: volume factors
+// (Sec. 3.4: dR, d(R^2/2), d(r^3/3), -d cos(theta)), centres, inverse
+// widths, centre / width, lower edges and edge order keys.
+struct ZoneTables {
+    double *dvol, *zc, *ziw;
+    float *dvol_f, *ziw_f, *znu_f, *zlo_f, *zc_f;   // zlo_f: n + 1 entries
+    long long *ekey;                                 // n + 1 entries
+};
+
+void fill_zone_tables(int kind, int d, const double *e, int n, const ZoneTables &t)
+{
+    for (int i = 0; i < n; ++i) {
+        const double a = e[i], b = e[i + 1];
+        double v = b - a;
+        if (d == 0 && kind == DUST_CYLINDRICAL) v = 0.5 * (b * b - a * a);
+        if (d == 0 && kind == DUST_SPHERICAL) v = (b * b * b - a * a * a) / 3.0;
+        if (d == 1 && kind == DUST_SPHERICAL) v = cos(a) - cos(b);
+        t.dvol[i] = v;
+        t.dvol_f[i] = (float)v;
+        t.zc[i] = 0.5 * (a + b);
+        t.ziw[i] = 1.0 / (b - a);
+        t.ziw_f[i] = (float)t.ziw[i];
+        t.znu_f[i] = (float)(t.zc[i] * t.ziw[i]);
+        t.zc_f[i] = (float)t.zc[i];
+    }
+    for (int i = 0; i <= n; ++i) {
+        t.zlo_f[i] = (float)e[i];
+        t.ekey[i] = order_key(e[i]);
+    }
 }
 
 // --------------------------------------------------------- aux kernels ----
@@ -304,23 +418,25 @@ StoreDev<Real> store_of(dust_ctx *c, int which)
     return s;
 }
 
-PhysDev phys_of(const dust_ctx *c, double t, double dt)
+// Geometry constants of the step starting at t (the shear-periodic shifts of
+// the shearing box at the half and the full step).
+PhysDev make_phys(const dust_geometry &geo, const GridDev &g, double t, double dt)
 {
     PhysDev ph{};
-    ph.geom = c->geom.kind;
-    ph.fargo = c->geom.fargo;
-    ph.vgrav = c->geom.vertical_gravity;
-    ph.omega = c->geom.omega;
-    ph.qshear = c->geom.q;
-    ph.gm = c->geom.gm;
-    ph.q_om = c->geom.q * c->geom.omega;
-    const double Lx = c->g.hi[0] - c->g.lo[0];
-    const double Ly = c->g.hi[1] - c->g.lo[1];
-    ph.jump_v = c->geom.q * c->geom.omega * Lx;
-    if (c->geom.kind == DUST_SHEARING_BOX) {
+    ph.geom = geo.kind;
+    ph.fargo = geo.fargo;
+    ph.vgrav = geo.vertical_gravity;
+    ph.omega = geo.omega;
+    ph.qshear = geo.q;
+    ph.gm = geo.gm;
+    ph.q_om = geo.q * geo.omega;
+    const double Lx = g.hi[0] - g.lo[0];
+    const double Ly = g.hi[1] - g.lo[1];
+    ph.jump_v = geo.q * geo.omega * Lx;
+    if (geo.kind == DUST_SHEARING_BOX) {
         // same expression order as q Omega Lx t, reduced modulo Ly
-        ph.shift_mid = fmod(c->geom.q * c->geom.omega * Lx * (t + 0.5 * dt), Ly);
-        ph.shift_end = fmod(c->geom.q * c->geom.omega * Lx * (t + dt), Ly);
+        ph.shift_mid = fmod(geo.q * geo.omega * Lx * (t + 0.5 * dt), Ly);
+        ph.shift_end = fmod(geo.q * geo.omega * Lx * (t + dt), Ly);
     }
     ph.omega_f = (float)ph.omega;
     ph.qshear_f = (float)ph.qshear;
@@ -328,6 +444,11 @@ PhysDev phys_of(const dust_ctx *c, double t, double dt)
     ph.q_om_f = (float)ph.q_om;
     ph.jump_v_f = (float)ph.jump_v;
     return ph;
+}
+
+PhysDev phys_of(const dust_ctx *c, double t, double dt)
+{
+    return make_phys(c->geom, c->g, t, dt);
 }
 
 int ensure_stage(dust_ctx *ctx, size_t bytes)
@@ -610,36 +731,11 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     if (!out) return fail(nullptr, DUST_EINVAL, "out is NULL");
     *out = nullptr;
     if (!geom || !grid || !species || !opt) return fail(nullptr, DUST_EINVAL, "NULL descriptor");
-    if (geom->kind < DUST_CARTESIAN || geom->kind > DUST_SPHERICAL)
-        return fail(nullptr, DUST_EINVAL, "bad geometry kind %d", geom->kind);
-    if (n_species < 1 || n_species > kMaxSpecies)
-        return fail(nullptr, DUST_EINVAL, "n_species must be 1..%d", kMaxSpecies);
     if (opt->precision != DUST_FP64 && opt->precision != DUST_MIXED)
         return fail(nullptr, DUST_EINVAL, "bad precision");
-    if (opt->weight != DUST_WEIGHT_CIC && opt->weight != DUST_WEIGHT_TSC)
-        return fail(nullptr, DUST_EINVAL, "bad weight");
-    int64_t ncell = 1;
-    for (int d = 0; d < 3; ++d) {
-        if (grid->n[d] < 1 || !grid->edges[d])
-            return fail(nullptr, DUST_EINVAL, "direction %d: n < 1 or no edges", d);
-        for (int i = 0; i < grid->n[d]; ++i)
-            if (!(grid->edges[d][i] < grid->edges[d][i + 1]) || !std::isfinite(grid->edges[d][i + 1]))
-                return fail(nullptr, DUST_EINVAL, "direction %d: edges not increasing", d);
-        if (grid->bc[d] != DUST_BC_PERIODIC && grid->bc[d] != DUST_BC_OUTFLOW)
-            return fail(nullptr, DUST_EINVAL, "direction %d: bad boundary kind", d);
-        ncell *= grid->n[d];
-    }
-    if (ncell >= (int64_t)1 << 31) return fail(nullptr, DUST_EINVAL, "too many zones");
-    if (geom->kind == DUST_CYLINDRICAL && grid->edges[0][0] <= 0.0)
-        return fail(nullptr, DUST_EINVAL, "cylindrical R must be > 0");
-    if (geom->kind == DUST_SPHERICAL &&
-        (grid->edges[0][0] <= 0.0 || grid->edges[1][0] <= 0.0 ||
-         grid->edges[1][grid->n[1]] >= M_PI))
-        return fail(nullptr, DUST_EINVAL, "spherical r must be > 0 and theta in (0, pi)");
-    if ((geom->kind == DUST_CYLINDRICAL || geom->kind == DUST_SPHERICAL))
-        for (int s = 0; s < n_species; ++s)
-            if (species[s].tau_mode == DUST_TAU_STOKES && !(geom->gm > 0.0))
-                return fail(nullptr, DUST_EINVAL, "Stokes-number mode needs GM > 0");
+    int64_t ncell = 0;
+    const int rv = validate_descriptors(geom, grid, species, n_species, opt->weight, &ncell);
+    if (rv) return rv;
 
     dust_ctx *ctx = new (std::nothrow) dust_ctx();
     if (!ctx) return fail(nullptr, DUST_ENOMEM, "host allocation failed");
@@ -650,20 +746,7 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     ctx->device = opt->device;
     ctx->ncell = ncell;
     ctx->sort_interval = opt->sort_interval > 0 ? opt->sort_interval : 1;
-    double mmax = 0.0;
-    ctx->sp.n = n_species;
-    for (int s = 0; s < n_species; ++s) {
-        ctx->sp.mass[s] = species[s].mass;
-        ctx->sp.tau[s] = species[s].tau_value;
-        ctx->sp.mode[s] = species[s].tau_mode;
-        mmax = fmax(mmax, fabs(species[s].mass));
-    }
-    ctx->quantum = opt->quantum > 0.0 ? opt->quantum : ldexp(mmax > 0 ? mmax : 1.0, -44);
-    for (int s = 0; s < n_species; ++s) {
-        ctx->sp.mq[s] = species[s].mass / ctx->quantum;
-        ctx->sp.mqf[s] = (float)ctx->sp.mq[s];
-        ctx->sp.tau_f[s] = (float)ctx->sp.tau[s];
-    }
+    ctx->sp = make_species(species, n_species, opt->quantum, &ctx->quantum);
 
     auto bail = [&](int code) {
         std::string msg = ctx->err;
@@ -691,41 +774,13 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         ctx->bc[d] = grid->bc[d];
         ctx->edges[d].assign(grid->edges[d], grid->edges[d] + n + 1);
         const std::vector<double> &e = ctx->edges[d];
-        g.n[d] = n;
-        g.bc[d] = grid->bc[d];
-        g.lo[d] = e[0];
-        g.hi[d] = e[n];
-        g.edge_kind[d] = edge_kind(e);
-        if (g.edge_kind[d] == EDGE_LOG) {
-            g.inv_d[d] = n / log(e[n] / e[0]);
-            g.log_lo_f[d] = logf((float)e[0]);
-        } else {
-            g.inv_d[d] = n / (e[n] - e[0]);
-            g.log_lo_f[d] = 0.f;
-        }
-        g.inv_df[d] = (float)g.inv_d[d];
-        std::vector<double> dv(n);
-        std::vector<float> dvf(n);
-        for (int i = 0; i < n; ++i) {
-            const double a = e[i], b = e[i + 1];
-            double v = b - a;
-            if (d == 0 && geom->kind == DUST_CYLINDRICAL) v = 0.5 * (b * b - a * a);
-            if (d == 0 && geom->kind == DUST_SPHERICAL) v = (b * b * b - a * a * a) / 3.0;
-            if (d == 1 && geom->kind == DUST_SPHERICAL) v = cos(a) - cos(b);
-            dv[i] = v;
-            dvf[i] = (float)v;
-        }
-        // per-zone centre, inverse width, centre/width and lower edges
-        std::vector<double> zc(n), ziw(n);
-        std::vector<float> ziwf(n), znuf(n), zlof(n + 1), zcf(n);
-        for (int i = 0; i < n; ++i) {
-            zc[i] = 0.5 * (e[i] + e[i + 1]);
-            ziw[i] = 1.0 / (e[i + 1] - e[i]);
-            ziwf[i] = (float)ziw[i];
-            znuf[i] = (float)(zc[i] * ziw[i]);
-            zcf[i] = (float)zc[i];
-        }
-        for (int i = 0; i <= n; ++i) zlof[i] = (float)e[i];
+        grid_direction(g, d, e.data(), n, grid->bc[d]);
+        std::vector<double> dv(n), zc(n), ziw(n);
+        std::vector<float> dvf(n), ziwf(n), znuf(n), zlof(n + 1), zcf(n);
+        std::vector<long long> ek(n + 1);
+        fill_zone_tables(geom->kind, d, e.data(), n,
+                         ZoneTables{dv.data(), zc.data(), ziw.data(), dvf.data(), ziwf.data(),
+                                    znuf.data(), zlof.data(), zcf.data(), ek.data()});
         if (dalloc(&ctx->d_edges[d], n + 1) != cudaSuccess || dalloc(&ctx->d_dvol[d], n) != cudaSuccess ||
             dalloc(&ctx->d_dvol_f[d], n) != cudaSuccess || dalloc(&ctx->d_zc[d], n) != cudaSuccess ||
             dalloc(&ctx->d_ziw[d], n) != cudaSuccess || dalloc(&ctx->d_ziw_f[d], n) != cudaSuccess ||
@@ -743,15 +798,9 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         cudaMemcpy(ctx->d_znu_f[d], znuf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(ctx->d_zlo_f[d], zlof.data(), (n + 1) * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(ctx->d_zc_f[d], zcf.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(ctx->d_ekey[d], ek.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice);
         g.zc_f[d] = ctx->d_zc_f[d];
-        {
-            std::vector<long long> ek(n + 1);
-            for (int i = 0; i <= n; ++i) ek[i] = order_key(e[i]);
-            cudaMemcpy(ctx->d_ekey[d], ek.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice);
-            g.ekey[d] = ctx->d_ekey[d];
-            g.lo_key[d] = ek[0];
-            g.hi_key[d] = ek[n];
-        }
+        g.ekey[d] = ctx->d_ekey[d];
         g.edges[d] = ctx->d_edges[d];
         g.dvol[d] = ctx->d_dvol[d];
         g.dvol_f[d] = ctx->d_dvol_f[d];
