@@ -194,6 +194,58 @@ int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, const double
  * momentum.  Asynchronous on the context stream. */
 int dust_step(dust_ctx *ctx, double dt);
 
+/* Allocation-free variant of one dust_step() of the one-thread-per-grain
+ * kernel (DUST_KERNEL_PER_GRAIN, FP64, no zone sort, no feedback
+ * application) on caller-owned device arrays.  The paper has no counterpart:
+ * it exists for callers that cannot let a library allocate device memory
+ * while they step (a host code that gives the device memory to its own pool
+ * at start-up, or one whose other streams must not be stalled by the
+ * device-wide synchronisation of cudaMalloc/cudaFree).  It calls no
+ * cudaMalloc/cudaFree and no allocating library; its only scratch (grid
+ * tables and status words, 512 KiB) is a fixed device array of the library.
+ *
+ *   geom, grid, species, n_species, weight: as for dust_create (host
+ *       structs; grid edges are host arrays).  Each direction may have at
+ *       most 2048 zones; a larger grid is rejected with DUST_EINVAL.
+ *   quantum: fixed-point quantum of the deposit (0 = 2^-44 * largest mass).
+ *   t, dt: time at the start of the step and step length (the shearing-box
+ *       shift of Sec. 2.1 uses t).
+ *   n: grains (0 <= n < 2^31).  q0..q2: device float64 [n] coordinates,
+ *       updated in place (a grain removed through an outflow boundary gets
+ *       q0 = NaN and is skipped by later calls); they must lie inside the
+ *       grid or be NaN.  p0..p2: device float64 [n] momentum-like variables
+ *       of Sec. 2.2 (cylindrical: v_R, R v_phi, v_z; spherical: v_r,
+ *       r v_theta, r sin(theta) v_phi; shearing box with fargo = 1: the
+ *       residual velocity), updated in place.  species_idx: device uint8 [n]
+ *       or NULL (species 0).  param: device float64 [n] stopping-time values
+ *       or NULL.
+ *   gas: device float64 [ncell][4]: rho, then the momentum-like gas
+ *       velocity p_g0..p_g2 of each zone (zone-centre radius factors).
+ *   dep: device int64 [ncell][4], overwritten with this step's deposit in
+ *       units of the quantum (channels as in dust_get_deposit).
+ *   status_out: device uint32 [4] or NULL: DUST_FLAG_* bits, the largest
+ *       displacement in zones (float bits), grains removed (low, high word).
+ *   device: CUDA device ordinal (0..63), made current by the call.
+ *   stream: cudaStream_t (NULL = the legacy default stream).
+ *
+ * Everything is enqueued on `stream`; the call does not wait for the GPU.
+ * The first call on a device looks up the scratch's address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  Each call
+ * copies the grid tables from a host image of the library and zeroes the
+ * status words and `dep` before the kernel.  The scratch and the host image
+ * are shared by all calls: calls that overlap (from two host threads, or on
+ * two streams without ordering between them) race.  Errors: DUST_EINVAL
+ * (bad descriptor, oversize grid, NULL array), DUST_ECUDA; the message is
+ * dust_last_error(NULL). */
+int dust_step_noalloc(const dust_geometry *geom, const dust_grid *grid,
+                      const dust_species *species, int n_species, int weight,
+                      double quantum, double t, double dt, int64_t n,
+                      double *q0, double *q1, double *q2,
+                      double *p0, double *p1, double *p2,
+                      const uint8_t *species_idx, const double *param,
+                      const double *gas, int64_t *dep, uint32_t *status_out,
+                      int device, void *stream);
+
 /* Wait for the context stream, fill *out (may be NULL) and return
  * DUST_ENAN / DUST_EOVERFLOW / DUST_ECFL if the matching flag was raised
  * since the previous dust_sync, else DUST_OK.  Flags are then cleared. */

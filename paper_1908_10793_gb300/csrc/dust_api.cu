@@ -1180,3 +1180,188 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
+
+// ------------------------------------------------ allocation-free step ----
+//
+// dust_step_noalloc is for callers that cannot let the library allocate
+// device memory while they step.  One kind is a host code that hands the
+// device's memory to its own pool when it starts: a later cudaMalloc fails or
+// breaks the budget that pool was sized for.  Another keeps work running on
+// other streams: cudaMalloc and cudaFree synchronise the whole device and
+// would stall that work.  Here the grains, the gas and the deposit are the
+// caller's device arrays, and the only scratch the kernel needs (the grid
+// tables and the status words) lives in a fixed device array of this library.
+
+namespace {
+
+constexpr int kNoAllocMaxZones = 2048;               // zones per direction
+constexpr size_t kNoAllocScratchBytes = 512 * 1024;  // fits 3 x 2048-zone tables
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+// Device address of g_noalloc_scratch per device ordinal (null until the
+// first call on that device looks it up).
+void *g_noalloc_addr[kNoAllocMaxDevices];
+// Host image of the scratch contents, copied to the device by each call.
+alignas(256) unsigned char g_noalloc_image[kNoAllocScratchBytes];
+
+// Byte offsets inside the scratch: status words, then per direction the grid
+// tables, each region on a 256-byte boundary.
+struct NoAllocLayout {
+    size_t status;
+    size_t edges[3], ekey[3], dvol[3], zc[3], ziw[3];
+    size_t dvol_f[3], ziw_f[3], znu_f[3], zlo_f[3], zc_f[3];
+    size_t total;
+};
+
+NoAllocLayout noalloc_layout(const int n[3])
+{
+    NoAllocLayout L{};
+    size_t off = 0;
+    auto take = [&off](size_t bytes) {
+        const size_t at = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    L.status = take(ST_WORDS * sizeof(unsigned));
+    for (int d = 0; d < 3; ++d) {
+        const size_t m = (size_t)n[d];
+        L.edges[d] = take((m + 1) * sizeof(double));
+        L.ekey[d] = take((m + 1) * sizeof(long long));
+        L.dvol[d] = take(m * sizeof(double));
+        L.zc[d] = take(m * sizeof(double));
+        L.ziw[d] = take(m * sizeof(double));
+        L.dvol_f[d] = take(m * sizeof(float));
+        L.ziw_f[d] = take(m * sizeof(float));
+        L.znu_f[d] = take(m * sizeof(float));
+        L.zlo_f[d] = take((m + 1) * sizeof(float));
+        L.zc_f[d] = take(m * sizeof(float));
+    }
+    L.total = off;
+    return L;
+}
+
+template <int GEOM>
+cudaError_t launch_noalloc(const StepArgs<double> &a, int weight, cudaStream_t s)
+{
+    return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<double, GEOM, 1>(a, s)
+                                     : launch_step_per_grain<double, GEOM, 0>(a, s);
+}
+
+}  // namespace
+
+extern "C" int dust_step_noalloc(const dust_geometry *geom, const dust_grid *grid,
+                                 const dust_species *species, int n_species, int weight,
+                                 double quantum, double t, double dt, int64_t n,
+                                 double *q0, double *q1, double *q2,
+                                 double *p0, double *p1, double *p2,
+                                 const uint8_t *species_idx, const double *param,
+                                 const double *gas, int64_t *dep, uint32_t *status_out,
+                                 int device, void *stream)
+{
+    dust_ctx *ctx = nullptr;  // errors are reported through dust_last_error(NULL)
+    int64_t ncell = 0;
+    const int rv = validate_descriptors(geom, grid, species, n_species, weight, &ncell);
+    if (rv) return rv;
+    for (int d = 0; d < 3; ++d)
+        if (grid->n[d] > kNoAllocMaxZones)
+            return fail(nullptr, DUST_EINVAL,
+                        "direction %d has %d zones; dust_step_noalloc holds grid tables for at "
+                        "most %d zones per direction",
+                        d, grid->n[d], kNoAllocMaxZones);
+    if (!std::isfinite(t) || !std::isfinite(dt) || !(quantum >= 0.0))
+        return fail(nullptr, DUST_EINVAL, "t and dt must be finite and quantum >= 0");
+    if (n < 0 || n >= ((int64_t)1 << 31))
+        return fail(nullptr, DUST_EINVAL, "grain count out of range");
+    if (!gas || !dep || (n > 0 && (!q0 || !q1 || !q2 || !p0 || !p1 || !p2)))
+        return fail(nullptr, DUST_EINVAL, "NULL device array");
+    if (device < 0 || device >= kNoAllocMaxDevices)
+        return fail(nullptr, DUST_EINVAL, "device ordinal out of range");
+    const NoAllocLayout L = noalloc_layout(grid->n);
+    if (L.total > kNoAllocScratchBytes)
+        return fail(nullptr, DUST_EINVAL, "grid tables exceed the %zu-byte scratch",
+                    kNoAllocScratchBytes);
+
+    CU(cudaSetDevice(device));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // setup, first call on this device only: the scratch's device address
+    if (!g_noalloc_addr[device]) {
+        void *addr = nullptr;
+        CU(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+        g_noalloc_addr[device] = addr;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_noalloc_addr[device]);
+    unsigned char *img = g_noalloc_image;
+
+    StepArgs<double> a{};
+    GridDev &g = a.g;
+    g.ncell = ncell;
+    std::memset(img + L.status, 0, ST_WORDS * sizeof(unsigned));  // status words start at zero
+    for (int d = 0; d < 3; ++d) {
+        const int m = grid->n[d];
+        const double *e = grid->edges[d];
+        grid_direction(g, d, e, m, grid->bc[d]);
+        std::memcpy(img + L.edges[d], e, (m + 1) * sizeof(double));
+        fill_zone_tables(geom->kind, d, e, m,
+                         ZoneTables{reinterpret_cast<double *>(img + L.dvol[d]),
+                                    reinterpret_cast<double *>(img + L.zc[d]),
+                                    reinterpret_cast<double *>(img + L.ziw[d]),
+                                    reinterpret_cast<float *>(img + L.dvol_f[d]),
+                                    reinterpret_cast<float *>(img + L.ziw_f[d]),
+                                    reinterpret_cast<float *>(img + L.znu_f[d]),
+                                    reinterpret_cast<float *>(img + L.zlo_f[d]),
+                                    reinterpret_cast<float *>(img + L.zc_f[d]),
+                                    reinterpret_cast<long long *>(img + L.ekey[d])});
+        g.edges[d] = reinterpret_cast<const double *>(base + L.edges[d]);
+        g.ekey[d] = reinterpret_cast<const long long *>(base + L.ekey[d]);
+        g.dvol[d] = reinterpret_cast<const double *>(base + L.dvol[d]);
+        g.zc[d] = reinterpret_cast<const double *>(base + L.zc[d]);
+        g.ziw[d] = reinterpret_cast<const double *>(base + L.ziw[d]);
+        g.dvol_f[d] = reinterpret_cast<const float *>(base + L.dvol_f[d]);
+        g.ziw_f[d] = reinterpret_cast<const float *>(base + L.ziw_f[d]);
+        g.znu_f[d] = reinterpret_cast<const float *>(base + L.znu_f[d]);
+        g.zlo_f[d] = reinterpret_cast<const float *>(base + L.zlo_f[d]);
+        g.zc_f[d] = reinterpret_cast<const float *>(base + L.zc_f[d]);
+        // the per-grain kernel has no tiles: one zone per key
+        g.T[d] = 1;
+        g.nt[d] = m;
+    }
+    g.tvol = 1;
+    g.nkeys = ncell;
+    double qu = 0.0;
+    a.sp = make_species(species, n_species, quantum, &qu);
+    a.ph = make_phys(*geom, g, t, dt);
+    a.t = t;
+    a.dt = dt;
+    a.inv_quantum = 1.0 / qu;
+    a.s.q[0] = q0; a.s.q[1] = q1; a.s.q[2] = q2;
+    a.s.p[0] = p0; a.s.p[1] = p1; a.s.p[2] = p2;
+    a.s.species = const_cast<uint8_t *>(species_idx);
+    a.s.param = const_cast<double *>(param);
+    a.s.id = nullptr;
+    a.s.n = n;
+    a.gas = gas;
+    a.dep = reinterpret_cast<unsigned long long *>(dep);
+    a.status = reinterpret_cast<unsigned *>(base + L.status);
+
+    // tables and zeroed status words in one copy; the deposit starts at zero
+    CU(cudaMemcpyAsync(base, img, L.total, cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(dep, 0, (size_t)ncell * 4 * sizeof(int64_t), st));
+    cudaError_t e;
+    switch (geom->kind) {
+    case DUST_CARTESIAN: e = launch_noalloc<GEOM_CART>(a, weight, st); break;
+    case DUST_SHEARING_BOX: e = launch_noalloc<GEOM_SB>(a, weight, st); break;
+    case DUST_CYLINDRICAL: e = launch_noalloc<GEOM_CYL>(a, weight, st); break;
+    default: e = launch_noalloc<GEOM_SPH>(a, weight, st); break;
+    }
+    CU(e);
+    if (status_out)
+        CU(cudaMemcpyAsync(status_out, base + L.status, 4 * sizeof(unsigned),
+                           cudaMemcpyDeviceToDevice, st));
+    return DUST_OK;
+}

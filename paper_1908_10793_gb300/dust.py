@@ -94,6 +94,9 @@ def load_library():
         "dust_get_deposit": (I, [P, P, P, ctypes.POINTER(D), I]),
         "dust_get_particles": (I, [P, I64, P, P, P, P, P, P, P, ctypes.POINTER(I64), I]),
         "dust_get_kernel_times": (I, [P, ctypes.POINTER(dust_kernel_times), I]),
+        "dust_step_noalloc": (I, [ctypes.POINTER(dust_geometry), ctypes.POINTER(dust_grid),
+                                  ctypes.POINTER(dust_species), I, I, D, D, D, I64,
+                                  P, P, P, P, P, P, P, P, P, P, P, I, P]),
         "dust_last_error": (ctypes.c_char_p, [P]),
         "dust_destroy": (None, [P]),
     }
@@ -198,6 +201,28 @@ def dust_get_kernel_times(ctx, reset=False):
     t = dust_kernel_times()
     _check(ctx, load_library().dust_get_kernel_times(ctx, ctypes.byref(t), int(bool(reset))))
     return t
+
+
+def dust_step_noalloc(geometry, grid, species, weight, quantum, t, dt, q, p, gas, dep,
+                      species_idx=None, param=None, status_out=None, device=0, stream=None):
+    """q, p: three CUDA float64 tensors each (updated in place); gas: CUDA
+    float64 [ncell, 4]; dep: CUDA int64 [ncell, 4] (overwritten);
+    species_idx / param / status_out: CUDA tensors or None; stream: a
+    cudaStream_t handle (int) or None."""
+    for a in list(q) + list(p) + [gas, dep, species_idx, param, status_out]:
+        if a is not None and _ptr(a)[1] != DUST_MEM_DEVICE:
+            raise ValueError("dust_step_noalloc takes device arrays only")
+    lib = load_library()
+    arr = (dust_species * len(species))(*species)
+    rc = lib.dust_step_noalloc(ctypes.byref(geometry), ctypes.byref(grid), arr, len(species),
+                               int(weight), float(quantum), float(t), float(dt), len(q[0]),
+                               _ptr(q[0])[0], _ptr(q[1])[0], _ptr(q[2])[0],
+                               _ptr(p[0])[0], _ptr(p[1])[0], _ptr(p[2])[0],
+                               _ptr(species_idx)[0], _ptr(param)[0], _ptr(gas)[0], _ptr(dep)[0],
+                               _ptr(status_out)[0], int(device), stream)
+    if rc != DUST_OK:
+        raise DustError(rc, lib.dust_last_error(None).decode())
+    return rc
 
 
 def dust_last_error(ctx):
