@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sort-interval", type=int, default=0)
@@ -75,17 +75,20 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, ngrains):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def profiled_traffic(ngrains):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic_step_sbox3d.txt")
     try:
+        rec = {}
         with open(path) as f:
-            t = json.load(f)
-        e = t[kernel]
-        if e.get("source_digest") != source_digest():
+            for line in f:
+                if line.strip() and not line.startswith("#"):
+                    k, v = line.split(None, 1)
+                    rec[k] = v.strip()
+        if rec.get("source_digest") != source_digest():
             return None
-        return float(e["dram_bytes_per_grain"]) * ngrains
+        return float(rec["dram_bytes_per_grain"]) * ngrains
     except Exception:
         return None
 
@@ -133,6 +136,23 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(x, device):
+    """Largest value of x over all ranks (x itself with one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world, units_per_rank, seconds):
+    """Whole-job throughput: every rank processed units_per_rank in at most
+    `seconds` (the slowest rank's time)."""
+    return world * units_per_rank / seconds
 
 
 def algorithmic_bytes(w, precision_bytes):
@@ -185,11 +205,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ck = clocks.stop() if clocks else None
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dev)
         rc, st = ctx.sync(check=False)
         kt = ctx.kernel_times(reset=True)
         return ms, rc, st, kt, ck
@@ -198,7 +214,7 @@ def run_ours(args):
     ctx = make(D.DUST_MIXED, 1)
     ms, rc, st, kt, clocks = timed(ctx, args.steps, args.warmup, sample_clocks=True)
     ngr = w.ngrains
-    value = world * ngr * args.steps / (ms / 1e3)
+    value = weak_value(world, ngr * args.steps, ms / 1e3)
     step_ms_avg = kt.step_ms / max(1, kt.step_launches)
     ab, per_grain, per_zone = algorithmic_bytes(w, 4)
     achieved = ab / (step_ms_avg / 1e3) / 1e9
@@ -212,7 +228,7 @@ def run_ours(args):
         ctx = make(D.DUST_FP64, 1)
         k64 = max(2, args.steps // 4)
         ms64, rc64, _, kt64, _ = timed(ctx, k64, min(args.warmup, 3))
-        fp64 = {"value": world * ngr * k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64,
+        fp64 = {"value": weak_value(world, ngr * k64, ms64 / 1e3), "ms_per_step": ms64 / k64,
                 "steps": k64, "status": rc64,
                 "step_kernel_ms": kt64.step_ms / max(1, kt64.step_launches)}
         ctx.close()
@@ -247,14 +263,10 @@ def run_ours(args):
         for _ in range(ke):
             one()
         torch.cuda.synchronize(dev)
-        te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(time.perf_counter() - t0, dev)
         h2d = ngr * 6 * 8 + w.ncell * 4 * 8
         d2h = ngr * (6 * 8 + 8) + w.ncell * 4 * 8
-        e2e = {"value": world * ngr * ke / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": weak_value(world, ngr * ke, te), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke}
         ctx.close()
 
@@ -283,7 +295,7 @@ def run_ours(args):
                          "kernel": "step (gather+push+deposit)",
                          "algorithmic_bytes_per_launch": ab,
                          "bytes_per_grain": per_grain, "bytes_per_zone": per_zone,
-                         "traffic": profiled_traffic("step", ngr)},
+                         "traffic": profiled_traffic(ngr)},
             "gpu_launches": launches,
             "fp64": fp64,
             "e2e": e2e,

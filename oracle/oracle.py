@@ -26,7 +26,11 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the oracle shared library (gcc, plain C, FP64)."""
+    """Compile the oracle shared library (gcc, plain C, FP64).  The mutation
+    tests point DUST_ORACLE_LIB at a deliberately broken build instead."""
+    planted = os.environ.get("DUST_ORACLE_LIB")
+    if planted:
+        return planted
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if (not force and os.path.exists(_OUT)
             and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC)):

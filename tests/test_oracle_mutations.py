@@ -1,0 +1,82 @@
+"""The oracle's pins catch plausible mistakes: each case below plants one
+mistake in a copy of oracle/dust_oracle.c (a dropped term, a wrong sign, a
+wrong index or factor), builds it, and runs the pin suites against it; at
+least one pin must fail.  Everything runs on the CPU."""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "dust_oracle.c")
+PIN_SUITES = [os.path.join(ROOT, "tests", "test_oracle_weights.py"),
+              os.path.join(ROOT, "tests", "test_oracle_push.py")]
+
+# (name, original text, planted text); the original must occur exactly once
+MUTATIONS = [
+    ("cartesian TSC centre weight", "w[1] = 0.75 - d * d;", "w[1] = 0.7 - d * d;"),
+    ("cylindrical TSC outer factor", "w[2] = (d + 3.0 * nu + 2.0) / den",
+     "w[2] = (d + 3.0 * nu + 1.0) / den"),
+    ("theta-CIC lower weight sign", "w[0] = -(cos(lo) - cos(lo + d)) / D;",
+     "w[0] = (cos(lo) - cos(lo + d)) / D;"),
+    ("zone location not half-open", "if (edges[mid] <= x) lo = mid;",
+     "if (edges[mid] < x) lo = mid;"),
+    ("drag term with h1 instead of c_g", "pp[d] = E * pn[d] + cg * vg[d];",
+     "pp[d] = E * pn[d] + h1 * vg[d];"),
+    ("h1 dropped to dt E", "double h1 = (x == 0.0) ? dt : dt * cg / x;", "double h1 = dt * E;"),
+    ("orbital-advection Omega2 without (1 - q/2)", "double Om2 = Om1 * (1.0 - 0.5 * qq);",
+     "double Om2 = Om1;"),
+    ("standard-frame Coriolis sign", "double G1 = -2.0 * (0.5 * pn[0]) * Om;",
+     "double G1 = 2.0 * (0.5 * pn[0]) * Om;"),
+    ("cylindrical l^2 not averaged", "double l2 = 0.5 * (pn[1] * pn[1] + pp[1] * pp[1]);",
+     "double l2 = pn[1] * pn[1];"),
+    ("spherical second square repeats l_phi",
+     "double ar = lt2 / (r * r * r) + lp2 / (r * r * r * st * st) + g[0];",
+     "double ar = lp2 / (r * r * r) + lp2 / (r * r * r * st * st) + g[0];"),
+    ("second drift with end-point radius",
+     "        q[1] = q[1] + h * p[1] / (qm[0] * qm[0]);\n        q[2] = q[2] + h * p[2];\n        break;",
+     "        q[1] = q[1] + h * p[1] / (q[0] * q[0]);\n        q[2] = q[2] + h * p[2];\n        break;"),
+    ("Stokes-number stopping time exponent", "return value * sqrt(R * R * R / P->gm);",
+     "return value * sqrt(R * R / P->gm);"),
+    ("energy channel with p^n", "D[3] += D[c] * dHdp[c];", "D[3] += D[c] * pn[c];"),
+    ("deposit sign", "D[c] = -m * ((pp[c] - pn[c]) - dt * a[c]);",
+     "D[c] = m * ((pp[c] - pn[c]) - dt * a[c]);"),
+    ("cylindrical zone volume", "dV = 0.5 * (a1 * a1 - a0 * a0) * (b1 - b0) * (c1 - c0);",
+     "dV = (a1 - a0) * (b1 - b0) * (c1 - c0);"),
+]
+
+
+def _run_mutant(case, workdir):
+    name, orig, planted = case
+    src = open(SRC).read()
+    assert src.count(orig) == 1, name
+    d = os.path.join(workdir, "m%d" % MUTATIONS.index(case))
+    os.makedirs(d)
+    c = os.path.join(d, "dust_oracle.c")
+    with open(c, "w") as f:
+        f.write(src.replace(orig, planted))
+    lib = os.path.join(d, "liboracle.so")
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared", "-std=c99", "-o", lib, c, "-lm"])
+    env = dict(os.environ, DUST_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"]
+                       + PIN_SUITES, cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    return name, r.returncode
+
+
+def test_every_planted_mistake_fails_a_pin():
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    work = tempfile.mkdtemp(prefix="oracle_mut_")
+    try:
+        with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+            results = list(ex.map(lambda c: _run_mutant(c, work), MUTATIONS))
+    finally:
+        shutil.rmtree(work, ignore_errors=True)
+    survived = [name for name, rc in results if rc == 0]
+    assert not survived, "pins did not catch: %s" % survived

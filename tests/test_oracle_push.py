@@ -177,11 +177,11 @@ def test_time_reversibility_shearing_box(fargo):
         assert abs(q[d][0] - q0[d][0]) < 1e-12 and abs(p[d][0] - p0[d][0]) < 1e-12
 
 
-def _cyl_problem(nR=16, nphi=32, nz=8, weight=O.OW_TSC):
+def _cyl_problem(nR=16, nphi=32, nz=8, weight=O.OW_TSC, **kw):
     edges = [np.geomspace(0.5, 2.0, nR + 1), np.linspace(0, 2 * np.pi, nphi + 1),
              np.linspace(-0.3, 0.3, nz + 1)]
     return O.Problem(geom=O.OG_CYLINDRICAL, edges=edges, bc=(O.OB_OUTFLOW, 0, 0),
-                     weight=weight, gm=1.0, vertical_gravity=1)
+                     weight=weight, gm=1.0, vertical_gravity=1, **kw)
 
 
 def test_time_reversibility_cylindrical_with_drag():
@@ -197,11 +197,11 @@ def test_time_reversibility_cylindrical_with_drag():
         assert abs(q[d][0] - q0[d][0]) < 1e-12 and abs(p[d][0] - p0[d][0]) < 1e-12
 
 
-def _sph_problem(weight=O.OW_TSC, dth=0.6):
+def _sph_problem(weight=O.OW_TSC, dth=0.6, **kw):
     edges = [np.geomspace(0.5, 1.6, 17), np.linspace(np.pi / 2 - dth, np.pi / 2 + dth, 17),
              np.linspace(0, 2 * np.pi, 33)]
     return O.Problem(geom=O.OG_SPHERICAL, edges=edges, bc=(O.OB_OUTFLOW, O.OB_OUTFLOW, 0),
-                     weight=weight, gm=1.0)
+                     weight=weight, gm=1.0, **kw)
 
 
 def test_time_reversibility_spherical_with_drag():
@@ -539,3 +539,31 @@ def test_no_drag_means_no_back_reaction(geom):
     _, p, _, dep = run(prob, q0, p0, 0.05, 3, rho, pg, param=np.array([INF]))
     assert np.abs(dep[:, :3]).max() < 1e-15
     assert np.abs(p[0][0] - p0[0][0]) > 1e-4   # the grain was accelerated
+
+
+@pytest.mark.parametrize("geom", ["cyl", "sph"])
+def test_stokes_number_mode_is_st_over_local_keplerian_frequency(geom):
+    """Secs. 4.5-4.6 fix the Stokes number St = tau_s Omega_K with Omega_K =
+    sqrt(GM / R^3) at the grain's cylindrical radius.  A grain with no radial
+    (and no polar) motion keeps its radius through the half drift, so one step
+    in Stokes-number mode must equal one step with the constant stopping time
+    St / Omega_K(R) (R = r sin(theta) in spherical coordinates), and differ
+    from the one at R = 1."""
+    st = 0.3
+    if geom == "cyl":
+        mk, Rc = _cyl_problem, 1.5
+        q0, p0 = [[1.5], [0.4], [0.05]], [[0.0], [1.5 ** 0.5 * 0.9], [0.0]]
+    else:
+        mk, Rc = _sph_problem, 1.3 * np.sin(1.2)
+        q0, p0 = [[1.3], [1.2], [0.5]], [[0.0], [0.0], [0.8]]
+    results = []
+    for mode, value in ((O.OT_STOKES, st), (O.OT_CONST, st * np.sqrt(Rc ** 3)),
+                        (O.OT_CONST, st)):
+        prob = mk(species_tau_mode=(mode,), species_tau=(value,))
+        R, _, _ = I._grid3(prob.edges)
+        rho = np.ones(prob.ncell)
+        pg = O.gas_momentum(prob, [np.zeros_like(R), 0.8 * R ** -0.5, np.zeros_like(R)])
+        q, p, _, dep = run(prob, q0, p0, 0.05, 1, rho, pg)
+        results.append(np.concatenate([np.ravel(q), np.ravel(p)]))
+    assert np.allclose(results[0], results[1], rtol=1e-14, atol=1e-15)
+    assert np.abs(results[0] - results[2]).max() > 1e-6
