@@ -28,6 +28,11 @@ namespace dust {
 
 constexpr int kSlabThreads = 256;
 constexpr int kSlabCap = 128;  // grains per warp record pass
+// Record slots: a grain of zone kq (0..9 in the group) at pass position s
+// uses slot s + kq, so the owner lanes of different zones, which read their
+// zones' grains in step, fall on different shared-memory banks.
+constexpr int kRecStride = kSlabCap + 16;
+constexpr int kRecFields = 13;  // 3 x 3 weights, 4 deposit channels
 
 template <int FLAT>
 struct SlabShape {
@@ -83,7 +88,7 @@ step_slab_kernel(const TiledArgs<float> TA)
     float *sgas = reinterpret_cast<float *>(smem_raw + (size_t)bvol * 4 * sizeof(long long));
     // tile-local key -> zone offsets (x | y << 10 | z << 20), no runtime division
     int *kdec = reinterpret_cast<int *>(sgas + (size_t)bvol * 4);
-    float *srec = reinterpret_cast<float *>(kdec + ((g.tvol + 31) & ~31));  // [warps][14][kSlabCap]
+    float *srec = reinterpret_cast<float *>(kdec + ((g.tvol + 31) & ~31));  // [warps][13][kRecStride]
     for (int k = threadIdx.x; k < g.tvol; k += blockDim.x) {
         const int kx = k % g.T[0], ky = (k / g.T[0]) % g.T[1], kz = k / (g.T[0] * g.T[1]);
         kdec[k] = kx | (ky << 10) | (kz << 20);
@@ -141,17 +146,25 @@ step_slab_kernel(const TiledArgs<float> TA)
         const int okd = kok ? kdec[kl] : 0;
         const int ohx = (okd & 1023) + 1, ohy = ((okd >> 10) & 1023) + (NB == 3 ? 1 : 0),
                   ohz = (okd >> 20) + (NC == 3 ? 1 : 0);
-        float acc[NB][NC][4], S[4] = {0.f, 0.f, 0.f, 0.f};
+        // Passes of at most kSlabCap grains that end on chunk boundaries
+        // (a zone's end, or its start plus a multiple of kSlabCap), so each
+        // zone's part of a pass is one whole chunk of its run and is
+        // quantised at the end of the pass: nothing is carried between passes.
+        for (int64_t P0 = G0, P1; P0 < G1; P0 = P1) {
+            {
+                const int64_t lim = min(G1, P0 + (int64_t)kSlabCap);
+                P1 = P0;
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) acc[b][c][ch] = 0.f;
-
-        for (int64_t P0 = G0; P0 < G1; P0 += kSlabCap) {
-            const int64_t P1 = min(G1, P0 + (int64_t)kSlabCap);
-            float *rb = srec + warp * (14 * kSlabCap);
+                for (int j = 0; j < 10; ++j) {
+                    const int64_t zs = koff[j], ze = koff[j + 1];
+                    if (ze <= lim) {
+                        P1 = max(P1, ze);
+                    } else if (zs < lim) {
+                        P1 = max(P1, zs + ((lim - zs) / kSlabCap) * kSlabCap);
+                    }
+                }
+            }
+            float *rb = srec + warp * (kRecFields * kRecStride);
             // ---- push: one grain per lane, consecutive grains on consecutive
             // lanes (coalesced), each relative to its own key zone
             for (int64_t gi = P0 + lane; gi < P1; gi += 32) {
@@ -455,77 +468,90 @@ step_slab_kernel(const TiledArgs<float> TA)
                     const unsigned peers = __match_any_sync(am, nkey);
                     if (lane == __ffs(peers) - 1) atomicAdd(&TA.count_out[nkey], __popc(peers));
                 }
-                // record for the zone's deposit owners
-                const int slot = (int)(gi - P0);
-                rb[0 * kSlabCap + slot] = grp_ok ? 1.f : 0.f;
+                // record for the zone's deposit owners (grains outside their
+                // key zone, and removed ones, carry a zero impulse)
+                const int slot = (int)(gi - P0) + kq2;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    rb[(1 + k) * kSlabCap + slot] = w[0][k];
-                    rb[(4 + k) * kSlabCap + slot] = w[1][k];
-                    rb[(7 + k) * kSlabCap + slot] = w[2][k];
+                    rb[k * kRecStride + slot] = w[0][k];
+                    rb[(3 + k) * kRecStride + slot] = w[1][k];
+                    rb[(6 + k) * kRecStride + slot] = w[2][k];
                 }
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) rb[(10 + ch) * kSlabCap + slot] = D[ch];
+                for (int ch = 0; ch < 4; ++ch) rb[(9 + ch) * kRecStride + slot] = grp_ok ? D[ch] : 0.f;
             }
             __syncwarp();
             // ---- deposit: the three owner lanes of a zone accumulate its
-            // grains (id order) into their x slabs
-            if (kok && cnt > 0) {
-                const int s0 = (int)(max(off0, P0) - P0), s1 = (int)(min(off0 + cnt, P1) - P0);
-                for (int sl = s0; sl < s1; ++sl) {
-                    if (rb[sl] == 0.f) continue;
-                    const float wx = rb[(1 + a) * kSlabCap + sl];
+            // chunk in this pass (id order) into their x slabs
+            const int64_t za = max(off0, P0), zb = min(off0 + cnt, P1);
+            const bool own = kok && zb > za;
+            float acc[NB][NC][4], S[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) acc[b][c][ch] = 0.f;
+            if (own) {
+                const int s0 = (int)(za - P0) + kq, s1 = (int)(zb - P0) + kq;
+                const float *rx = rb + a * kRecStride;
+                auto one = [&](int sl) {
+                    const float wx = rx[sl];
                     float De[4];
 #pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) De[ch] = rb[(10 + ch) * kSlabCap + sl];
+                    for (int ch = 0; ch < 4; ++ch) De[ch] = rb[(9 + ch) * kRecStride + sl];
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
-                        const float wxy = wx * rb[(4 + (NB == 3 ? b : 1)) * kSlabCap + sl];
+                        const float wxy = wx * rb[(3 + (NB == 3 ? b : 1)) * kRecStride + sl];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
-                            const float W = wxy * rb[(7 + (NC == 3 ? c : 1)) * kSlabCap + sl];
+                            const float W = wxy * rb[(6 + (NC == 3 ? c : 1)) * kRecStride + sl];
 #pragma unroll
                             for (int ch = 0; ch < 4; ++ch) acc[b][c][ch] += W * De[ch];
                         }
                     }
-                    if (a == 1) {
 #pragma unroll
-                        for (int ch = 0; ch < 4; ++ch) S[ch] += De[ch];
-                    }
+                    for (int ch = 0; ch < 4; ++ch) S[ch] += De[ch];
+                };
+                int sl = s0;
+                for (; sl + 1 < s1; sl += 2) {
+                    one(sl);
+                    one(sl + 1);
                 }
+                if (sl < s1) one(sl);
             }
             __syncwarp();
-        }
 
-        // ---- quantise this zone's run and flush it to the deposit box
-        long long ps[4] = {0, 0, 0, 0};
-        if (kok && cnt > 0) {
+            // ---- quantise the chunk and add it to the deposit box
+            long long ps[4] = {0, 0, 0, 0};
+            if (own) {
 #pragma unroll
-            for (int b = 0; b < NB; ++b)
+                for (int b = 0; b < NB; ++b)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    if (a == 1 && b == Sh::BC && c == Sh::CC) continue;  // host: remainder
-                    const int lin = (ohx + a - 1) + B[0] * ((ohy + b - Sh::BC) + B[1] * (ohz + c - Sh::CC));
+                    for (int c = 0; c < NC; ++c) {
+                        if (a == 1 && b == Sh::BC && c == Sh::CC) continue;  // host: remainder
+                        const int lin = (ohx + a - 1) + B[0] * ((ohy + b - Sh::BC) + B[1] * (ohz + c - Sh::CC));
 #pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) {
-                        big |= !(fabsf(acc[b][c][ch]) < 4.5e15f);
-                        const long long piece = rint_to_ll(acc[b][c][ch]);
-                        if (piece != 0) {
-                            atomicAdd(&sdep[ch * bvol + lin], (unsigned long long)piece);
-                            ps[ch] += piece;
+                        for (int ch = 0; ch < 4; ++ch) {
+                            big |= !(fabsf(acc[b][c][ch]) < 4.5e15f);
+                            const long long piece = rint_to_ll(acc[b][c][ch]);
+                            if (piece != 0) {
+                                atomicAdd(&sdep[ch * bvol + lin], (unsigned long long)piece);
+                                ps[ch] += piece;
+                            }
                         }
                     }
-                }
-        }
+            }
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-            const long long s1 = __shfl_sync(FULL, ps[ch], base + 0);
-            const long long s2 = __shfl_sync(FULL, ps[ch], base + 2);
-            if (a == 1 && kok && cnt > 0) {
-                big |= !(fabsf(S[ch]) < 4.5e15f);
-                const long long rest = rint_to_ll(S[ch]) - (ps[ch] + s1 + s2);
-                if (rest != 0)
-                    atomicAdd(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], (unsigned long long)rest);
+            for (int ch = 0; ch < 4; ++ch) {
+                const long long s1 = __shfl_sync(FULL, ps[ch], base + 0);
+                const long long s2 = __shfl_sync(FULL, ps[ch], base + 2);
+                if (a == 1 && own) {
+                    big |= !(fabsf(S[ch]) < 4.5e15f);
+                    const long long rest = rint_to_ll(S[ch]) - (ps[ch] + s1 + s2);
+                    if (rest != 0)
+                        atomicAdd(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], (unsigned long long)rest);
+                }
             }
         }
     }
@@ -559,7 +585,8 @@ inline size_t slab_smem_bytes(const GridDev &g)
     size_t bvol = 1;
     for (int d = 0; d < 3; ++d) bvol *= (size_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
     return bvol * (4 * sizeof(float) + 4 * sizeof(long long)) +
-           (size_t)((g.tvol + 31) & ~31) * sizeof(int) + (kSlabThreads / 32) * 14 * kSlabCap * sizeof(float);
+           (size_t)((g.tvol + 31) & ~31) * sizeof(int) +
+           (size_t)(kSlabThreads / 32) * kRecFields * kRecStride * sizeof(float);
 }
 
 template <int GEOM, int FLAT>

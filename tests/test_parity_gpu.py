@@ -194,6 +194,30 @@ def test_slab_kernel_outflow_removal_over_sorts():
         assert np.abs(a["v"][d][alive] - b["v"][d][alive]).max() <= 256 * EPS32 * scale
 
 
+def test_slab_kernel_dense_zones_split_into_chunks():
+    """Zones holding more than 128 grains: the slab kernel quantises each
+    zone's run in chunks of 128 grains (by rank in id order).  Parity with the
+    oracle, and the integers do not depend on the tile shape."""
+    from paper_1908_10793_gb300 import dust as D
+    w = I.box2d("small")
+    rng = np.random.default_rng(11)
+    n = w.ngrains
+    # 600 grains in one zone, 300 in another, the rest spread out
+    dx = w.edges[0][1] - w.edges[0][0]
+    for sel, (cx, cy) in ((slice(0, 600), (3, 5)), (slice(600, 900), (10, 12))):
+        k = sel.stop - sel.start
+        w.q[0][sel] = w.edges[0][cx] + dx * rng.uniform(0.05, 0.95, k)
+        w.q[1][sel] = w.edges[1][cy] + dx * rng.uniform(0.05, 0.95, k)
+    assert _grains_per_zone_max(w) >= 600 and n == 1024
+    compare(w, 2, MIXED, kernel=D.DUST_KERNEL_SLAB, sort_interval=1)
+    first = None
+    for tile in ((0, 0, 0), (4, 4, 1), (8, 2, 1)):
+        got = run_gpu(w, 2, MIXED, kernel=D.DUST_KERNEL_SLAB, tile=tile, sort_interval=1)
+        if first is None:
+            first = got
+        assert np.array_equal(got["fixed"], first["fixed"]), tile
+
+
 def test_parity_epstein_tau_mode():
     w = I.box2d("small")
     w.species_tau_mode = [I.TAU_EPSTEIN]
