@@ -89,6 +89,29 @@ step_slab_kernel(const TiledArgs<float> TA)
     // tile-local key -> zone offsets (x | y << 10 | z << 20), no runtime division
     int *kdec = reinterpret_cast<int *>(sgas + (size_t)bvol * 4);
     float *srec = reinterpret_cast<float *>(kdec + ((g.tvol + 31) & ~31));  // [warps][13][kRecStride]
+    // the tile's zone geometry, per direction d at toff[d]: centre (double and
+    // float) and inverse width; radial centre / width; polar lower edges
+    const int toff[3] = {0, g.T[0], g.T[0] + g.T[1]};
+    const int tsum = g.T[0] + g.T[1] + g.T[2];
+    double *szcd = reinterpret_cast<double *>(srec + (kSlabThreads / 32) * kRecFields * kRecStride);
+    float *szcf = reinterpret_cast<float *>(szcd + tsum);
+    float *szif = szcf + tsum;
+    float *sznu = szif + tsum;          // [T0]
+    float *szlo = sznu + g.T[0];        // [T1 + 1]
+    for (int t = threadIdx.x; t < tsum + g.T[1] + 1; t += blockDim.x) {
+        if (t < tsum) {
+            const int d = t < toff[1] ? 0 : (t < toff[2] ? 1 : 2);
+            const int z = tc[d] * g.T[d] + (t - toff[d]);
+            const bool ok = g.n[d] > 1 && z < g.n[d];
+            szcd[t] = ok ? g.zc[d][z] : 0.0;
+            szcf[t] = ok ? g.zc_f[d][z] : 0.f;
+            szif[t] = ok ? g.ziw_f[d][z] : 0.f;
+            if (d == 0 && (GEOM == GEOM_CYL || GEOM == GEOM_SPH)) sznu[t] = ok ? g.znu_f[0][z] : 0.f;
+        } else if (GEOM == GEOM_SPH) {
+            const int z = tc[1] * g.T[1] + (t - tsum);
+            szlo[t - tsum] = (g.n[1] > 1 && z <= g.n[1]) ? g.zlo_f[1][z] : 0.f;
+        }
+    }
     for (int k = threadIdx.x; k < g.tvol; k += blockDim.x) {
         const int kx = k % g.T[0], ky = (k / g.T[0]) % g.T[1], kz = k / (g.T[0] * g.T[1]);
         kdec[k] = kx | (ky << 10) | (kz << 20);
@@ -123,24 +146,25 @@ step_slab_kernel(const TiledArgs<float> TA)
         const int kl = kg0 + kq;
         const bool kok = lane < 30 && kl < g.tvol;
         // the group's 10 keys: grain range [koff[0], koff[10]) in the store
-        const int64_t offl = lane <= 10 ? TA.key_off[kbase + min(kg0 + lane, g.tvol)] : 0;
-        int64_t koff[11];
+        // store positions fit in 32 bits (fewer than 2^31 grains)
+        const int offl = lane <= 10 ? TA.key_off[kbase + min(kg0 + lane, g.tvol)] : 0;
+        int koff[11];
 #pragma unroll
         for (int j = 0; j <= 10; ++j) koff[j] = __shfl_sync(FULL, offl, j);
-        const int64_t G0 = koff[0], G1 = koff[10];
+        const int G0 = koff[0], G1 = koff[10];
         if (G1 == G0) continue;
-        int64_t off0 = 0;
+        int off0 = 0;
         int cnt = 0;
         if (kok) {
             off0 = koff[0];
 #pragma unroll
             for (int j = 1; j < 10; ++j)
                 if (kq == j) off0 = koff[j];
-            int64_t off1 = koff[1];
+            int off1 = koff[1];
 #pragma unroll
             for (int j = 1; j < 10; ++j)
                 if (kq == j) off1 = koff[j + 1];
-            cnt = (int)(off1 - off0);
+            cnt = off1 - off0;
         }
         // owner zone's position in the tile box
         const int okd = kok ? kdec[kl] : 0;
@@ -150,13 +174,13 @@ step_slab_kernel(const TiledArgs<float> TA)
         // (a zone's end, or its start plus a multiple of kSlabCap), so each
         // zone's part of a pass is one whole chunk of its run and is
         // quantised at the end of the pass: nothing is carried between passes.
-        for (int64_t P0 = G0, P1; P0 < G1; P0 = P1) {
+        for (int P0 = G0, P1; P0 < G1; P0 = P1) {
             {
-                const int64_t lim = min(G1, P0 + (int64_t)kSlabCap);
+                const int lim = min(G1, P0 + kSlabCap);
                 P1 = P0;
 #pragma unroll
                 for (int j = 0; j < 10; ++j) {
-                    const int64_t zs = koff[j], ze = koff[j + 1];
+                    const int zs = koff[j], ze = koff[j + 1];
                     if (ze <= lim) {
                         P1 = max(P1, ze);
                     } else if (zs < lim) {
@@ -167,7 +191,7 @@ step_slab_kernel(const TiledArgs<float> TA)
             float *rb = srec + warp * (kRecFields * kRecStride);
             // ---- push: one grain per lane, consecutive grains on consecutive
             // lanes (coalesced), each relative to its own key zone
-            for (int64_t gi = P0 + lane; gi < P1; gi += 32) {
+            for (int gi = P0 + lane; gi < P1; gi += 32) {
                 int kq2 = 0;
 #pragma unroll
                 for (int j = 1; j < 10; ++j) kq2 += gi >= koff[j] ? 1 : 0;
@@ -175,21 +199,20 @@ step_slab_kernel(const TiledArgs<float> TA)
                 const int lx = kd & 1023, ly = (kd >> 10) & 1023, lz = kd >> 20;
                 const int zx = tc[0] * g.T[0] + lx, zy = tc[1] * g.T[1] + ly, zz = tc[2] * g.T[2] + lz;
                 const int hx = lx + 1, hy = ly + (NB == 3 ? 1 : 0), hz = lz + (NC == 3 ? 1 : 0);
-                const int zid[3] = {zx, zy, zz};
-                double zcd[3] = {0.0, 0.0, 0.0};
-                float zcf[3] = {0.f, 0.f, 0.f}, zif[3] = {0.f, 0.f, 0.f};
+                const int lid[3] = {toff[0] + lx, toff[1] + ly, toff[2] + lz};
+                double zcd[3];
+                float zcf[3], zif[3];
                 float znu = 0.f, zlo = 0.f, zhi = 0.f, zhw = 0.f;
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    if (g.n[d] > 1) {
-                        zcd[d] = g.zc[d][zid[d]];
-                        zcf[d] = g.zc_f[d][zid[d]];
-                        zif[d] = g.ziw_f[d][zid[d]];
-                    }
-                if (GEOM == GEOM_CYL || GEOM == GEOM_SPH) znu = g.znu_f[0][zid[0]];
+                for (int d = 0; d < 3; ++d) {
+                    zcd[d] = szcd[lid[d]];
+                    zcf[d] = szcf[lid[d]];
+                    zif[d] = szif[lid[d]];
+                }
+                if (GEOM == GEOM_CYL || GEOM == GEOM_SPH) znu = sznu[lx];
                 if (GEOM == GEOM_SPH) {
-                    zlo = g.zlo_f[1][zid[1]];
-                    zhi = g.zlo_f[1][zid[1] + 1];
+                    zlo = szlo[ly];
+                    zhi = szlo[ly + 1];
                     zhw = 0.5f / zif[1];
                 }
                 // ---- own grain: first half drift and weights, relative to the
@@ -422,7 +445,7 @@ step_slab_kernel(const TiledArgs<float> TA)
                         // zone in single precision; the exact prediction when
                         // the grain moves more than one zone or crosses the grid
                         bool fast = ingroup;
-                        int zn[3] = {zx, zy, zz};
+                        int zn[3] = {zx, zy, zz}, kk[3] = {0, 0, 0};
                         if (fast) {
                             float un[3];
 #pragma unroll
@@ -451,11 +474,25 @@ step_slab_kernel(const TiledArgs<float> TA)
                                 if (g.n[d] <= 1) continue;
                                 const int k = (int)floorf(un[d] * zif[d] + 0.5f);
                                 zn[d] += k;
+                                kk[d] = k;
                                 fast &= k >= -1 && k <= 1 && zn[d] >= 0 && zn[d] < g.n[d];
                             }
                         }
                         if (fast) {
-                            nkey = (int32_t)zone_key(g, zn[0], zn[1], zn[2]);
+                            // key of the neighbouring zone from this tile's
+                            // coordinates (no division)
+                            const int lloc[3] = {lx, ly, lz};
+                            int tt[3], ll[3];
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                int l = lloc[d] + kk[d], t = tc[d];
+                                if (l < 0) { l += g.T[d]; --t; }
+                                else if (l >= g.T[d]) { l -= g.T[d]; ++t; }
+                                ll[d] = l;
+                                tt[d] = t;
+                            }
+                            nkey = (tt[0] + g.nt[0] * (tt[1] + g.nt[1] * tt[2])) * g.tvol +
+                                   ll[0] + g.T[0] * (ll[1] + g.T[1] * ll[2]);
                         } else {
                             double qk[3] = {q[0], q[1], q[2]};
                             nkey = predict_key<float, GEOM>(g, A.ph, qk, pnew, h);
@@ -464,13 +501,22 @@ step_slab_kernel(const TiledArgs<float> TA)
                 }
                 if (TA.emit_keys) {
                     TA.key_out[gi] = nkey;
-                    const unsigned am = __activemask();
-                    const unsigned peers = __match_any_sync(am, nkey);
-                    if (lane == __ffs(peers) - 1) atomicAdd(&TA.count_out[nkey], __popc(peers));
+                    // count runs of equal keys on consecutive lanes (the lanes
+                    // of this pass iteration are 0 .. m-1): one atomic per run
+                    const int m = min(32, P1 - (gi - lane));
+                    const unsigned pm = m == 32 ? FULL : ((1u << m) - 1u);
+                    const int prev = __shfl_up_sync(pm, nkey, 1);
+                    const bool start = lane == 0 || prev != nkey;
+                    const unsigned starts = __ballot_sync(pm, start);
+                    if (start) {
+                        const unsigned later = starts & ~((2u << lane) - 1u);
+                        const int end = later ? __ffs(later) - 1 : m;
+                        atomicAdd(&TA.count_out[nkey], end - lane);
+                    }
                 }
                 // record for the zone's deposit owners (grains outside their
                 // key zone, and removed ones, carry a zero impulse)
-                const int slot = (int)(gi - P0) + kq2;
+                const int slot = gi - P0 + kq2;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     rb[k * kRecStride + slot] = w[0][k];
@@ -483,7 +529,7 @@ step_slab_kernel(const TiledArgs<float> TA)
             __syncwarp();
             // ---- deposit: the three owner lanes of a zone accumulate its
             // chunk in this pass (id order) into their x slabs
-            const int64_t za = max(off0, P0), zb = min(off0 + cnt, P1);
+            const int za = max(off0, P0), zb = min(off0 + cnt, P1);
             const bool own = kok && zb > za;
             float acc[NB][NC][4], S[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -493,7 +539,7 @@ step_slab_kernel(const TiledArgs<float> TA)
 #pragma unroll
                     for (int ch = 0; ch < 4; ++ch) acc[b][c][ch] = 0.f;
             if (own) {
-                const int s0 = (int)(za - P0) + kq, s1 = (int)(zb - P0) + kq;
+                const int s0 = za - P0 + kq, s1 = zb - P0 + kq;
                 const float *rx = rb + a * kRecStride;
                 auto one = [&](int sl) {
                     const float wx = rx[sl];
@@ -584,9 +630,11 @@ inline size_t slab_smem_bytes(const GridDev &g)
 {
     size_t bvol = 1;
     for (int d = 0; d < 3; ++d) bvol *= (size_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
+    const size_t tsum = (size_t)g.T[0] + g.T[1] + g.T[2];
     return bvol * (4 * sizeof(float) + 4 * sizeof(long long)) +
            (size_t)((g.tvol + 31) & ~31) * sizeof(int) +
-           (size_t)(kSlabThreads / 32) * kRecFields * kRecStride * sizeof(float);
+           (size_t)(kSlabThreads / 32) * kRecFields * kRecStride * sizeof(float) +
+           tsum * (sizeof(double) + 2 * sizeof(float)) + ((size_t)g.T[0] + g.T[1] + 1) * sizeof(float);
 }
 
 template <int GEOM, int FLAT>
