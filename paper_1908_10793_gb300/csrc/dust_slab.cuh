@@ -230,13 +230,13 @@ step_slab_kernel(const TiledArgs<float> TA)
                 bool live = false, ingroup = false;
                 {
                     q[0] = A.s.q[0][gi]; q[1] = A.s.q[1][gi]; q[2] = A.s.q[2][gi];
-                    live = !isnan(q[0]);
+                    live = !is_nan_f64(q[0]);
                     if (live) {
                         pn[0] = A.s.p[0][gi]; pn[1] = A.s.p[1][gi]; pn[2] = A.s.p[2][gi];
                         sp = A.s.species ? A.s.species[gi] : 0;
     #pragma unroll
                         for (int d = 0; d < 3; ++d) {
-                            if (g.n[d] > 1) { u[d] = (float)(q[d] - zcd[d]); zc3[d] = zcf[d]; }
+                            if (g.n[d] > 1) { u[d] = f64_to_f32_rn(q[d] - zcd[d]); zc3[d] = zcf[d]; }
                             else { u[d] = 0.f; zc3[d] = (float)q[d]; }
                         }
                         // first half drift (Eq. exp_midpoint; Eq. drift1_cylindrical;
@@ -380,7 +380,7 @@ step_slab_kernel(const TiledArgs<float> TA)
                             for (int d = 0; d < 3; ++d) inc2[d] = h * pp[d];
                         }
     #pragma unroll
-                        for (int d = 0; d < 3; ++d) q[d] += (double)(inc1[d] + inc2[d]);
+                        for (int d = 0; d < 3; ++d) q[d] += f32_to_f64(inc1[d] + inc2[d]);
                     } else {
                         const double qm[3] = {q[0], q[1], q[2]};
                         drift<float, GEOM>(A.ph, q, qm, pp, h, true, inc2);
@@ -472,10 +472,12 @@ step_slab_kernel(const TiledArgs<float> TA)
 #pragma unroll
                             for (int d = 0; d < 3; ++d) {
                                 if (g.n[d] <= 1) continue;
-                                const int k = (int)floorf(un[d] * zif[d] + 0.5f);
+                                // zone offset floor(t + 1/2) for |t| < 3/2, by comparisons
+                                const float t = un[d] * zif[d];
+                                const int k = (t >= 0.5f ? 1 : 0) - (t < -0.5f ? 1 : 0);
                                 zn[d] += k;
                                 kk[d] = k;
-                                fast &= k >= -1 && k <= 1 && zn[d] >= 0 && zn[d] < g.n[d];
+                                fast &= fabsf(t) < 1.5f && zn[d] >= 0 && zn[d] < g.n[d];
                             }
                         }
                         if (fast) {
