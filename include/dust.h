@@ -246,6 +246,41 @@ int dust_step_noalloc(const dust_geometry *geom, const dust_grid *grid,
                       const double *gas, int64_t *dep, uint32_t *status_out,
                       int device, void *stream);
 
+/* ---- batched stepping ---------------------------------------------------
+ * Many independent contexts (instances with their own grids, sizes, species
+ * and step lengths, e.g. a set of streaming-instability shearing boxes,
+ * Sec. 4.3) advanced together.  dust_batch_step captures, once, one period of
+ * two steps of every instance into a CUDA graph (each instance a branch on
+ * its own stream: sort, deposit clear, step kernel, feedback, time advance)
+ * and replays it nsteps / 2 times with one launch each; an odd last step is
+ * taken with dust_step.  Results equal those of calling dust_step on each
+ * context with the same dt (captured steps sort before every step and read
+ * their time from the device).  The graph is captured again when a dt
+ * changes, particles are reloaded, or a context was stepped on its own in
+ * between.  Per-group timing (dust_options.timing) is not recorded for
+ * captured steps.  Contexts must be on one device and on streams that can
+ * be captured (not the legacy default stream); the batch does not own them
+ * and must be destroyed before them. */
+typedef struct dust_batch dust_batch;
+
+/* insts: n (1..4096) distinct contexts.  opt may be NULL; opt->stream, if
+ * set, is the stream the graph is launched on (else the batch creates one).
+ * Errors: DUST_EINVAL, DUST_ECUDA, DUST_ENOMEM (message:
+ * dust_batch_last_error(NULL)). */
+int dust_batch_create(dust_batch **out, dust_ctx *const *insts, int n, const dust_options *opt);
+
+/* Advance every instance i by nsteps steps of length dt[i] (dt: n values).
+ * Asynchronous: each context's stream is ordered after the batch's work, so
+ * dust_sync and the getters on a context see its result.  Errors:
+ * DUST_EINVAL, DUST_ESTATE (gas or particles missing), DUST_ECUDA. */
+int dust_batch_step(dust_batch *b, const double *dt, int nsteps);
+
+/* Message of the last error of a batch (NULL: of the last failed create). */
+const char *dust_batch_last_error(const dust_batch *b);
+
+/* Wait for the batch's work and free the batch (not its contexts). */
+void dust_batch_destroy(dust_batch *b);
+
 /* Wait for the context stream, fill *out (may be NULL) and return
  * DUST_ENAN / DUST_EOVERFLOW / DUST_ECFL if the matching flag was raised
  * since the previous dust_sync, else DUST_OK.  Flags are then cleared. */

@@ -1,5 +1,6 @@
 // Host side of the C interface declared in include/dust.h: context
 // management, data movement, unit conversion, step sequencing.
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -67,6 +68,11 @@ struct dust_ctx {
     int32_t *d_count_next = nullptr;
     bool keys_ready = false;   // d_key / d_count_next predicted by the last step
     double keys_dt = 0.0;      // the step length they were predicted for
+    // steps replayed from a captured graph read their time from the device:
+    // d_time = [t, shift_mid, shift_end, -]
+    double *d_time = nullptr;
+    bool capture_mode = false;  // enqueueing into a stream capture
+    uint64_t gen = 0;           // bumped when the grain store is reallocated
     double *d_stage = nullptr;
     size_t stage_bytes = 0;
 
@@ -481,7 +487,8 @@ struct GroupTimer {
     cudaEvent_t a = nullptr;
     GroupTimer(dust_ctx *c, int g) : ctx(c), group(g)
     {
-        if (ctx->opt.timing && (a = take_event(ctx))) cudaEventRecord(a, ctx->stream);
+        if (ctx->opt.timing && !ctx->capture_mode && (a = take_event(ctx)))
+            cudaEventRecord(a, ctx->stream);
     }
     ~GroupTimer()
     {
@@ -562,7 +569,9 @@ int run_sort(dust_ctx *ctx, double dt)
     a.pair_id = ctx->d_pair_id;
     a.pair_src = ctx->d_pair_src;
     a.nkeys1 = ctx->g.nkeys + 1;
-    const int64_t m = ctx->g.nkeys + 1;
+    // counts of the nkeys + 1 keys and a zero: the exclusive scan then also
+    // gives the end of the last (removed-grain) key's segment
+    const int64_t m = ctx->g.nkeys + 2;
     GroupTimer timer(ctx, dust_ctx::GROUP_SORT);
     // keys predicted by the previous step for this dt are reused; otherwise
     // the key kernel computes them
@@ -683,6 +692,7 @@ int run_step(dust_ctx *ctx, double dt)
     a.gas = static_cast<const Real *>(ctx->d_gas);
     a.dep = ctx->d_dep;
     a.status = ctx->d_status;
+    a.tdev = ctx->capture_mode ? ctx->d_time : nullptr;
     {
         GroupTimer timer(ctx, dust_ctx::GROUP_OTHER);
         CU(cudaMemsetAsync(ctx->d_dep, 0, ctx->ncell * 4 * sizeof(unsigned long long), ctx->stream));
@@ -694,13 +704,14 @@ int run_step(dust_ctx *ctx, double dt)
     const int wt = ctx->opt.weight;
     const int32_t *ko = ctx->d_count;
     cudaStream_t st = ctx->stream;
-    // the step before a sort predicts that sort's keys (for the same dt)
+    // the step before a sort predicts that sort's keys (for the same dt);
+    // captured steps sort every step
     const bool emit = step_emits_keys(ctx) && ctx->n_grains > 0 &&
-                      (ctx->steps + 1) % ctx->sort_interval == 0;
+                      (ctx->capture_mode || (ctx->steps + 1) % ctx->sort_interval == 0);
     int32_t *kout = emit ? ctx->d_key : nullptr;
     int32_t *cout_ = emit ? ctx->d_count_next : nullptr;
     if (emit)
-        CU(cudaMemsetAsync(ctx->d_count_next, 0, (ctx->g.nkeys + 1) * sizeof(int32_t), st));
+        CU(cudaMemsetAsync(ctx->d_count_next, 0, (ctx->g.nkeys + 2) * sizeof(int32_t), st));
     switch (ctx->geom.kind) {
     case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, st); break;
     case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, st); break;
@@ -845,6 +856,7 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         dalloc(&ctx->d_status, ST_WORDS) != cudaSuccess ||
         dalloc(&ctx->d_count, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_count_next, nk + 2) != cudaSuccess ||
+        dalloc(&ctx->d_time, 4) != cudaSuccess ||
         dalloc(&ctx->d_cursor, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_blocksums, scan_block_sums_size(nk + 2)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void **>(&ctx->h_status), ST_WORDS * sizeof(unsigned)) !=
@@ -942,6 +954,7 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
     ctx->cur = 0;
     ctx->need_sort = true;
     ctx->keys_ready = false;
+    ctx->gen += 1;
     if (n > 0) {
         const uint8_t *sp_dev = species;
         if (mem == DUST_MEM_HOST) {
@@ -1167,6 +1180,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     dfree(ctx->d_status);
     dfree(ctx->d_count);
     dfree(ctx->d_count_next);
+    dfree(ctx->d_time);
     dfree(ctx->d_cursor);
     dfree(ctx->d_blocksums);
     dfree(ctx->d_stage);
@@ -1179,6 +1193,335 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+}
+
+// ------------------------------------------------------- batched steps ----
+//
+// A batch steps many independent contexts (instances of different grids,
+// sizes and species) with one graph launch per two steps.  The graph is
+// captured once from the contexts' own streams: each instance is a branch
+// (sort, deposit clear, step, feedback, time advance, twice), so the
+// instances run concurrently and the per-kernel launch cost is paid once per
+// capture.  Captured steps read their time and shear-periodic shifts from
+// the device (a small kernel advances them), sort before every step and let
+// the step kernel predict the next sort's keys.  Two steps make one period
+// because the sort alternates the grain store and the key-count buffers.
+
+struct dust_batch {
+    int device = 0;
+    std::vector<dust_ctx *> ctx;
+    cudaStream_t root = nullptr;
+    bool own_root = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> join;
+    // what the captured graph assumed about each instance
+    std::vector<double> dt;
+    std::vector<uint64_t> gen;
+    std::vector<int> cur;
+    std::vector<int32_t *> count;
+    std::vector<std::array<int64_t, dust_ctx::N_GROUPS>> period_launches;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int bfail(dust_batch *b, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    g_batch_error = buf;
+    return code;
+}
+
+#define BCU(call)                                                                    \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return bfail(b, DUST_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+__global__ void set_time_kernel(double *tm, double t, double shift_mid, double shift_end)
+{
+    tm[0] = t;
+    tm[1] = shift_mid;
+    tm[2] = shift_end;
+}
+
+// t += dt, then the shifts of the step that starts at the new t, with the
+// same operations as make_phys: fmod(((q Omega) Lx) (t + dt/2), Ly).
+__global__ void time_advance_kernel(double *tm, double dt, double q_om_lx, double ly, int sb)
+{
+    const double t = __dadd_rn(tm[0], dt);
+    tm[0] = t;
+    if (sb) {
+        tm[1] = fmod(__dmul_rn(q_om_lx, __dadd_rn(t, __dmul_rn(0.5, dt))), ly);
+        tm[2] = fmod(__dmul_rn(q_om_lx, __dadd_rn(t, dt)), ly);
+    }
+}
+
+// Keys of the first sort of a captured period, computed now for the current
+// store (the graph's sorts reuse the keys the previous step predicted).
+template <typename Real>
+int prime_keys(dust_ctx *ctx, double dt)
+{
+    SortArgs<Real> a;
+    a.g = ctx->g;
+    a.ph = phys_of(ctx, ctx->t, dt);
+    a.dt = dt;
+    a.src = store_of<Real>(ctx, ctx->cur);
+    a.dst = store_of<Real>(ctx, 1 - ctx->cur);
+    a.key = ctx->d_key;
+    a.count = ctx->d_count_next;
+    a.cursor = ctx->d_cursor;
+    a.pair_id = ctx->d_pair_id;
+    a.pair_src = ctx->d_pair_src;
+    a.nkeys1 = ctx->g.nkeys + 1;
+    CU(cudaMemsetAsync(ctx->d_count_next, 0, (ctx->g.nkeys + 2) * sizeof(int32_t), ctx->stream));
+    cudaError_t e;
+    switch (ctx->geom.kind) {
+    case DUST_CARTESIAN: e = launch_sort_keys<Real, GEOM_CART>(a, ctx->stream); break;
+    case DUST_SHEARING_BOX: e = launch_sort_keys<Real, GEOM_SB>(a, ctx->stream); break;
+    case DUST_CYLINDRICAL: e = launch_sort_keys<Real, GEOM_CYL>(a, ctx->stream); break;
+    default: e = launch_sort_keys<Real, GEOM_SPH>(a, ctx->stream); break;
+    }
+    CU(e);
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += 1;
+    ctx->keys_ready = true;
+    ctx->keys_dt = dt;
+    return DUST_OK;
+}
+
+// Enqueue one period (two steps) of a context into the running capture.
+template <typename Real>
+int capture_period(dust_ctx *ctx, double dt)
+{
+    const double Lx = ctx->g.hi[0] - ctx->g.lo[0], Ly = ctx->g.hi[1] - ctx->g.lo[1];
+    const double q_om_lx = ctx->geom.q * ctx->geom.omega * Lx;
+    const int sb = ctx->geom.kind == DUST_SHEARING_BOX;
+    for (int k = 0; k < 2; ++k) {
+        int r = run_sort<Real>(ctx, dt);
+        if (r) return r;
+        r = run_step<Real>(ctx, dt);
+        if (r) return r;
+        time_advance_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_time, dt, q_om_lx, Ly, sb);
+        CU(cudaGetLastError());
+    }
+    return DUST_OK;
+}
+
+void drop_graph(dust_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+int capture(dust_batch *b, const double *dt)
+{
+    drop_graph(b);
+    const size_t n = b->ctx.size();
+    // host state the capture changes and a failed capture must restore
+    struct Saved { int cur; int32_t *count, *count_next; bool keys_ready; double keys_dt;
+                   int64_t launches[dust_ctx::N_GROUPS]; };
+    std::vector<Saved> saved(n);
+    for (size_t i = 0; i < n; ++i) {
+        dust_ctx *c = b->ctx[i];
+        saved[i] = Saved{c->cur, c->d_count, c->d_count_next, c->keys_ready, c->keys_dt, {}};
+        for (int g = 0; g < dust_ctx::N_GROUPS; ++g) saved[i].launches[g] = c->launches[g];
+    }
+    auto restore = [&](bool state) {
+        for (size_t i = 0; i < n; ++i) {
+            dust_ctx *c = b->ctx[i];
+            c->capture_mode = false;
+            for (int g = 0; g < dust_ctx::N_GROUPS; ++g) c->launches[g] = saved[i].launches[g];
+            if (!state) continue;
+            c->cur = saved[i].cur;
+            c->d_count = saved[i].count;
+            c->d_count_next = saved[i].count_next;
+            c->keys_ready = saved[i].keys_ready;
+            c->keys_dt = saved[i].keys_dt;
+        }
+    };
+    BCU(cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal));
+    int rc = DUST_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->root);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->ctx[i]->stream, b->fork, 0);
+    for (size_t i = 0; i < n && e == cudaSuccess && rc == DUST_OK; ++i) {
+        dust_ctx *c = b->ctx[i];
+        c->capture_mode = true;
+        rc = c->mixed ? capture_period<float>(c, dt[i]) : capture_period<double>(c, dt[i]);
+        c->capture_mode = false;
+        if (rc == DUST_OK) {
+            for (int g = 0; g < dust_ctx::N_GROUPS; ++g)
+                b->period_launches[i][g] = c->launches[g] - saved[i].launches[g];
+            e = cudaEventRecord(b->join[i], c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->root, b->join[i], 0);
+        } else {
+            b->err = c->err;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->root, &graph);
+    if (rc != DUST_OK || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        restore(true);
+        if (rc != DUST_OK) return bfail(b, rc, "capture: %s", b->err.c_str());
+        return bfail(b, DUST_ECUDA, "capture: %s",
+                     cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    // the period leaves every store, count buffer and key flag as it found
+    // them; launch counts are added per replay
+    restore(false);
+    b->graph = graph;
+    BCU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    for (size_t i = 0; i < n; ++i) {
+        dust_ctx *c = b->ctx[i];
+        b->dt[i] = dt[i];
+        b->gen[i] = c->gen;
+        b->cur[i] = c->cur;
+        b->count[i] = c->d_count;
+    }
+    return DUST_OK;
+}
+
+}  // namespace
+
+extern "C" int dust_batch_create(dust_batch **out, dust_ctx *const *insts, int n,
+                                 const dust_options *opt)
+{
+    if (!out) return bfail(nullptr, DUST_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!insts || n < 1 || n > 4096) return bfail(nullptr, DUST_EINVAL, "need 1..4096 contexts");
+    for (int i = 0; i < n; ++i) {
+        if (!insts[i]) return bfail(nullptr, DUST_EINVAL, "context %d is NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (insts[j] == insts[i]) return bfail(nullptr, DUST_EINVAL, "context %d appears twice", i);
+        if (insts[i]->device != insts[0]->device)
+            return bfail(nullptr, DUST_EINVAL, "contexts on different devices");
+    }
+    dust_batch *b = new (std::nothrow) dust_batch();
+    if (!b) return bfail(nullptr, DUST_ENOMEM, "host allocation failed");
+    b->device = insts[0]->device;
+    b->ctx.assign(insts, insts + n);
+    b->dt.assign(n, 0.0);
+    b->gen.assign(n, 0);
+    b->cur.assign(n, -1);
+    b->count.assign(n, nullptr);
+    b->period_launches.assign(n, {});
+    b->join.assign(n, nullptr);
+    auto bail = [&](const char *what) {
+        std::string m = what;
+        dust_batch_destroy(b);
+        return bfail(nullptr, DUST_ECUDA, "%s", m.c_str());
+    };
+    if (cudaSetDevice(b->device) != cudaSuccess) return bail("cudaSetDevice failed");
+    if (opt && opt->stream) {
+        b->root = static_cast<cudaStream_t>(opt->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) != cudaSuccess)
+            return bail("stream creation failed");
+        b->own_root = true;
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
+        return bail("event creation failed");
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail("event creation failed");
+    *out = b;
+    return DUST_OK;
+}
+
+extern "C" int dust_batch_step(dust_batch *b, const double *dt, int nsteps)
+{
+    if (!b) return bfail(nullptr, DUST_EINVAL, "batch is NULL");
+    if (nsteps < 0 || (nsteps > 0 && !dt)) return bfail(b, DUST_EINVAL, "bad nsteps or dt");
+    const size_t n = b->ctx.size();
+    for (size_t i = 0; i < n; ++i) {
+        if (nsteps > 0 && !std::isfinite(dt[i])) return bfail(b, DUST_EINVAL, "dt[%zu] not finite", i);
+        if (!b->ctx[i]->gas_set || !b->ctx[i]->particles_set)
+            return bfail(b, DUST_ESTATE, "context %zu: set the gas and load particles first", i);
+    }
+    if (nsteps == 0) return DUST_OK;
+    BCU(cudaSetDevice(b->device));
+    const int pairs = nsteps / 2;
+    if (pairs > 0) {
+        // keys for the first captured sort
+        for (size_t i = 0; i < n; ++i) {
+            dust_ctx *c = b->ctx[i];
+            if (step_emits_keys(c) && c->n_grains > 0 && !(c->keys_ready && c->keys_dt == dt[i])) {
+                const int r = c->mixed ? prime_keys<float>(c, dt[i]) : prime_keys<double>(c, dt[i]);
+                if (r) return bfail(b, r, "context %zu: %s", i, c->err.c_str());
+            }
+        }
+        bool fresh = b->exec != nullptr;
+        for (size_t i = 0; i < n && fresh; ++i) {
+            const dust_ctx *c = b->ctx[i];
+            fresh = b->dt[i] == dt[i] && b->gen[i] == c->gen && b->cur[i] == c->cur &&
+                    b->count[i] == c->d_count;
+        }
+        if (!fresh) {
+            const int r = capture(b, dt);
+            if (r) return r;
+        }
+        // each instance's time of this call, after its pending work
+        for (size_t i = 0; i < n; ++i) {
+            dust_ctx *c = b->ctx[i];
+            const PhysDev ph = phys_of(c, c->t, dt[i]);
+            set_time_kernel<<<1, 1, 0, c->stream>>>(c->d_time, c->t, ph.shift_mid, ph.shift_end);
+            BCU(cudaGetLastError());
+            BCU(cudaEventRecord(b->join[i], c->stream));
+            BCU(cudaStreamWaitEvent(b->root, b->join[i], 0));
+        }
+        for (int k = 0; k < pairs; ++k) BCU(cudaGraphLaunch(b->exec, b->root));
+        BCU(cudaEventRecord(b->done, b->root));
+        for (size_t i = 0; i < n; ++i) {
+            dust_ctx *c = b->ctx[i];
+            BCU(cudaStreamWaitEvent(c->stream, b->done, 0));
+            for (int s = 0; s < 2 * pairs; ++s) c->t += dt[i];
+            c->steps += 2 * pairs;
+            c->timed_steps += 2 * pairs;
+            c->have_deposit = true;
+            c->need_sort = false;
+            for (int g = 0; g < dust_ctx::N_GROUPS; ++g)
+                c->launches[g] += b->period_launches[i][g] * pairs;
+        }
+    }
+    if (nsteps % 2) {
+        for (size_t i = 0; i < n; ++i) {
+            const int r = dust_step(b->ctx[i], dt[i]);
+            if (r) return bfail(b, r, "context %zu: %s", i, b->ctx[i]->err.c_str());
+        }
+    }
+    return DUST_OK;
+}
+
+extern "C" const char *dust_batch_last_error(const dust_batch *b)
+{
+    return b ? b->err.c_str() : g_batch_error.c_str();
+}
+
+extern "C" void dust_batch_destroy(dust_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->root) cudaStreamSynchronize(b->root);
+    drop_graph(b);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->own_root && b->root) cudaStreamDestroy(b->root);
+    delete b;
 }
 
 // ------------------------------------------------ allocation-free step ----

@@ -67,6 +67,19 @@ __device__ __forceinline__ bool is_nan_f64(double x)
     return hi > 0x7ff00000u || (hi == 0x7ff00000u && lo != 0u);
 }
 
+// Shear-periodic shifts of the step at its half and full time: from the
+// kernel arguments, or from device memory for steps replayed from a graph.
+template <typename Real>
+__device__ __forceinline__ double shift_mid_of(const StepArgs<Real> &A)
+{
+    return A.tdev ? A.tdev[1] : A.ph.shift_mid;
+}
+template <typename Real>
+__device__ __forceinline__ double shift_end_of(const StepArgs<Real> &A)
+{
+    return A.tdev ? A.tdev[2] : A.ph.shift_end;
+}
+
 // A uniform parameter in the working precision (single-precision copies are
 // prepared on the host, so the mixed path converts nothing per grain).
 template <typename Real>

@@ -110,6 +110,9 @@ struct StepArgs {
     const Real *gas;              // [ncell][4]: rho, p_g0, p_g1, p_g2
     unsigned long long *dep;      // [ncell][4] two's complement int64
     unsigned int *status;         // ST_WORDS words
+    // null: the shear-periodic shifts are ph.shift_mid / ph.shift_end; else
+    // device memory [t, shift_mid, shift_end] of the step (graph replays)
+    const double *tdev;
 };
 
 template <typename Real>

@@ -290,7 +290,7 @@ step_slab_kernel(const TiledArgs<float> TA)
     #pragma unroll
                             for (int d = 0; d < 3; ++d) inc1[d] = 0.f;
                             drift<float, GEOM>(A.ph, q, q, pn, h, false, inc1);
-                            if (!apply_bc<float, GEOM>(g, A.ph, A.ph.shift_mid, q, pn)) {
+                            if (!apply_bc<float, GEOM>(g, A.ph, shift_mid_of(A), q, pn)) {
                                 A.s.q[0][gi] = __longlong_as_double(0x7ff8000000000000LL);
                                 ++nremoved;
                                 live = false;
@@ -386,7 +386,7 @@ step_slab_kernel(const TiledArgs<float> TA)
                         drift<float, GEOM>(A.ph, q, qm, pp, h, true, inc2);
                     }
                     float pnew[3] = {pp[0], pp[1], pp[2]};
-                    const bool alive = apply_bc<float, GEOM>(g, A.ph, A.ph.shift_end, q, pnew);
+                    const bool alive = apply_bc<float, GEOM>(g, A.ph, shift_end_of(A), q, pnew);
                     const float mq = A.sp.mqf[sp];
     #pragma unroll
                     for (int c = 0; c < 3; ++c) {

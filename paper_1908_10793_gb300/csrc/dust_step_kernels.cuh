@@ -99,7 +99,7 @@ step_per_grain_kernel(const StepArgs<Real> A)
             const Real h = (Real)(0.5 * A.dt);
             Real inc1[3], inc2[3];
             drift<Real, GEOM>(A.ph, q, q, pn, h, false, inc1);
-            if (!apply_bc<Real, GEOM>(A.g, A.ph, A.ph.shift_mid, q, pn)) {
+            if (!apply_bc<Real, GEOM>(A.g, A.ph, shift_mid_of(A), q, pn)) {
                 removed = true;
             } else {
                 const double qm[3] = {q[0], q[1], q[2]};
@@ -145,7 +145,7 @@ step_per_grain_kernel(const StepArgs<Real> A)
                 kick<Real, GEOM>(A.ph, qm, pn, vg, E, cg, h1, pp, a, dH);
                 drift<Real, GEOM>(A.ph, q, qm, pp, h, true, inc2);
                 Real pnew[3] = {pp[0], pp[1], pp[2]};
-                const bool alive = apply_bc<Real, GEOM>(A.g, A.ph, A.ph.shift_end, q, pnew);
+                const bool alive = apply_bc<Real, GEOM>(A.g, A.ph, shift_end_of(A), q, pnew);
                 // deposit: -m (dp - dt a), energy sum_c of that times dH/dp_c
                 const Real mq = (Real)(A.sp.mass[sp] * A.inv_quantum);
                 Real Dq[4];

@@ -211,7 +211,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
                 const int sp = A.s.species ? A.s.species[gi] : 0;
                 Real inc1[3], inc2[3];
                 drift<Real, GEOM>(A.ph, q, q, pn, h, false, inc1);
-                if (!apply_bc<Real, GEOM>(g, A.ph, A.ph.shift_mid, q, pn)) {
+                if (!apply_bc<Real, GEOM>(g, A.ph, shift_mid_of(A), q, pn)) {
                     A.s.q[0][gi] = __longlong_as_double(0x7ff8000000000000LL);
                     ++nremoved;
                 } else {
@@ -272,7 +272,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
                     kick<Real, GEOM>(A.ph, qm, pn, vg, E, cg, h1, pp, a, dH);
                     drift<Real, GEOM>(A.ph, q, qm, pp, h, true, inc2);
                     Real pnew[3] = {pp[0], pp[1], pp[2]};
-                    const bool alive = apply_bc<Real, GEOM>(g, A.ph, A.ph.shift_end, q, pnew);
+                    const bool alive = apply_bc<Real, GEOM>(g, A.ph, shift_end_of(A), q, pnew);
                     const Real mq = sizeof(Real) == 4 ? (Real)A.sp.mqf[sp] : (Real)A.sp.mq[sp];
                     Real Dq[4];
                     Dq[3] = Real(0);

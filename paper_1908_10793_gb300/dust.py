@@ -97,6 +97,11 @@ def load_library():
         "dust_step_noalloc": (I, [ctypes.POINTER(dust_geometry), ctypes.POINTER(dust_grid),
                                   ctypes.POINTER(dust_species), I, I, D, D, D, I64,
                                   P, P, P, P, P, P, P, P, P, P, P, I, P]),
+        "dust_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I,
+                                  ctypes.POINTER(dust_options)]),
+        "dust_batch_step": (I, [P, ctypes.POINTER(D), I]),
+        "dust_batch_last_error": (ctypes.c_char_p, [P]),
+        "dust_batch_destroy": (None, [P]),
         "dust_last_error": (ctypes.c_char_p, [P]),
         "dust_destroy": (None, [P]),
     }
@@ -223,6 +228,37 @@ def dust_step_noalloc(geometry, grid, species, weight, quantum, t, dt, q, p, gas
     if rc != DUST_OK:
         raise DustError(rc, lib.dust_last_error(None).decode())
     return rc
+
+
+def dust_batch_create(ctxs, options=None):
+    """ctxs: context handles.  Returns an opaque batch handle."""
+    lib = load_library()
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    rc = lib.dust_batch_create(ctypes.byref(out), arr, len(ctxs),
+                               ctypes.byref(options) if options is not None else None)
+    if rc != DUST_OK:
+        raise DustError(rc, lib.dust_batch_last_error(None).decode())
+    return out.value
+
+
+def dust_batch_step(batch, dt, nsteps):
+    """dt: one step length per instance."""
+    lib = load_library()
+    arr = (ctypes.c_double * len(dt))(*[float(x) for x in dt])
+    rc = lib.dust_batch_step(batch, arr, int(nsteps))
+    if rc != DUST_OK:
+        raise DustError(rc, lib.dust_batch_last_error(batch).decode())
+    return rc
+
+
+def dust_batch_last_error(batch):
+    m = load_library().dust_batch_last_error(batch)
+    return m.decode() if m else ""
+
+
+def dust_batch_destroy(batch):
+    load_library().dust_batch_destroy(batch)
 
 
 def dust_last_error(ctx):
