@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--small", action="store_true", help="16^3 grid (profiling runs)")
     ap.add_argument("--grid", type=int, default=0, help="zones per side (profiling runs)")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 per-grain, 2 tiled")
@@ -270,6 +272,12 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "steps": ke}
         ctx.close()
 
+    # ---- batched instances (64 streaming-instability boxes, one graph launch
+    # per two steps) against the same instances stepped one at a time
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, D, torch, dev, stream)
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu and world == 1:
@@ -298,6 +306,7 @@ def run_ours(args):
                          "traffic": profiled_traffic(ngr)},
             "gpu_launches": launches,
             "fp64": fp64,
+            "batch": batch,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -306,6 +315,68 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batch(args, D, torch, dev, stream):
+    """64 independent 2-D shearing boxes (32^2 .. 512^2 zones, 1-16 grains per
+    zone, St in {0.01, 0.1, 1}), mixed precision: dust_batch_step through one
+    graph versus dust_step on each context in turn on one stream."""
+    ws = I.si2d_batch("full")
+    ngr = sum(w.ngrains for w in ws)
+    dts = [w.dt for w in ws]
+    K = max(2, args.batch_steps - args.batch_steps % 2)
+
+    def make(one_stream):
+        cs = []
+        for w in ws:
+            c = D.Context(w, precision=D.DUST_MIXED, sort_interval=1, device=dev.index,
+                          stream=stream.cuda_stream if one_stream else None)
+            c.set_gas(w.rho, w.vgas)
+            c.load(w.q, w.v)
+            cs.append(c)
+        return cs
+
+    def timed(run):
+        run()  # warm-up (and capture)
+        run()
+        for c in cs:
+            c.sync()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    cs = make(False)
+    opt = D.dust_options(stream=stream.cuda_stream)
+    b = D.dust_batch_create([c.handle for c in cs], opt)
+    try:
+        ms_b = timed(lambda: D.dust_batch_step(b, dts, K))
+        rcs = [c.sync(check=False)[0] for c in cs]
+    finally:
+        D.dust_batch_destroy(b)
+        for c in cs:
+            c.close()
+    cs = make(True)
+    try:
+        def serial():
+            for c, x in zip(cs, dts):
+                for _ in range(K):
+                    c.step(x)
+        ms_s = timed(serial)
+    finally:
+        for c in cs:
+            c.close()
+    return {"value": ngr * K / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / K,
+            "instances": len(ws), "grains": ngr, "zones": sum(w.ncell for w in ws),
+            "steps": K, "graph_launches": K // 2,
+            "one_at_a_time": {"value": ngr * K / (ms_s / 1e3), "ms_per_step": ms_s / K},
+            "status": min(rcs),
+            "workload": "64 2-D (x,z) orbital-advection shearing boxes, 32^2..512^2 zones, "
+                        "1-16 grains/zone, St 0.01/0.1/1, dust/gas 0.01/0.02/0.1, TSC, "
+                        "feedback on, mixed precision"}
 
 
 def cpu_baseline(w, steps=2, ngrains=None):
