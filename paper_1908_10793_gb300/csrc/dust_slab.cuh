@@ -8,11 +8,13 @@
 // three lanes own one zone; lane a keeps, in registers, the accumulators of
 // the nine stencil nodes at x-offset a - 1 and sums the zone's records into
 // them.  A zone's deposit (its run: the grains sorted into it whose half-step
-// host is the zone itself) is then quantised once per node and added to the
-// shared deposit box; the host node receives the remainder of the run's
-// quantised total.  Grains are stored in id order inside a zone (see the
-// sort), so the summation order, hence the integers, is reproducible.  Grains
-// whose host is not their key zone (stale sort) use the per-grain rule.
+// host is the zone itself), cut into chunks of kSlabCap grains by rank, is
+// quantised once per chunk and node and added to the shared deposit box; the
+// host node receives the remainder of the chunk's quantised total.  Grains
+// are stored in id order inside a zone (see the sort), so the summation
+// order, hence the integers, is reproducible and independent of the tile
+// shape.  Grains whose host is not their key zone (stale sort) use the
+// per-grain rule.
 //
 // The push runs relative to the key zone: each coordinate's offset from the
 // zone centre is formed once in double precision and rounded to single;
