@@ -50,6 +50,48 @@ __device__ __forceinline__ float sel3(const float v[3], int i)
     return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
 }
 
+// The per-grain fixed-point rule (see deposit_fixed) for a grain whose
+// stencil leaves the staged box: global atomics, the same nodes and order,
+// in a rolled loop.
+template <int NB, int NC>
+__device__ __forceinline__ void deposit_fixed_rolled(const GridDev &g, unsigned long long *dep,
+                                                     const int host[3], const float w[3][3],
+                                                     const float Dq[4], unsigned int *status)
+{
+    long long rest[4];
+    bool big = false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        big |= !(fabs((double)Dq[c]) < 4.5e15);
+        rest[c] = rround(Dq[c]);
+    }
+    if (big) atomicOr(&status[ST_FLAGS], DUST_FLAG_OVERFLOW);
+#pragma unroll 1
+    for (int nd = 0; nd < 27; ++nd) {
+        const int a = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
+        if ((NB == 1 && b != 1) || (NC == 1 && c3 != 1) || nd == 13) continue;
+        const float W = sel3(w[0], a) * (sel3(w[1], b) * sel3(w[2], c3));
+        const int ix = node_of(host[0], a - 1, g.n[0], g.bc[0]);
+        const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
+        const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
+        const int64_t idx = ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long piece = rround(W * Dq[c]);
+            if (piece != 0) {
+                atomicAdd(&dep[4 * idx + c], (unsigned long long)piece);
+                rest[c] -= piece;
+            }
+        }
+    }
+    const int64_t hidx = node_of(host[0], 0, g.n[0], g.bc[0]) +
+                         (int64_t)g.n[0] * (node_of(host[1], 0, g.n[1], g.bc[1]) +
+                                            (int64_t)g.n[1] * node_of(host[2], 0, g.n[2], g.bc[2]));
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (rest[c] != 0) atomicAdd(&dep[4 * hidx + c], (unsigned long long)rest[c]);
+}
+
 template <int GEOM, int FLAT>
 __global__ void __launch_bounds__(kSlabThreads, 2)
 step_slab_kernel(const TiledArgs<float> TA)
@@ -327,7 +369,7 @@ step_slab_kernel(const TiledArgs<float> TA)
                     }
                     // 27-node gather (Eq. Delta_vp) from the staged gas box; the
                     // grains of one zone read the same nodes (broadcast loads)
-                    {
+                    if (inbox) {
     #pragma unroll
                         for (int c3 = 0; c3 < 3; ++c3) {
                             if (NC == 1 && c3 != 1) continue;
@@ -338,18 +380,28 @@ step_slab_kernel(const TiledArgs<float> TA)
                                 for (int aa = 0; aa < 3; ++aa) {
                                     const float W = w[0][aa] * (w[1][b] * w[2][c3]);
                                     float fv[4];
-                                    if (inbox) {
-                                        smem_gas_load<float>(sgas, (lb[0] + aa - 1) + B[0] * ((lb[1] + b - 1) + B[1] * (lb[2] + c3 - 1)), fv);
-                                    } else {
-                                        const int ix = node_of(host[0], aa - 1, g.n[0], g.bc[0]);
-                                        const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
-                                        const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
-                                        load_gas<float>(A.gas, ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz), fv);
-                                    }
+                                    smem_gas_load<float>(sgas, (lb[0] + aa - 1) + B[0] * ((lb[1] + b - 1) + B[1] * (lb[2] + c3 - 1)), fv);
     #pragma unroll
                                     for (int ch = 0; ch < 4; ++ch) G[ch] += W * fv[ch];
                                 }
                             }
+                        }
+                    } else {
+                        // rare: the stencil leaves the staged box; the same
+                        // nodes in the same order from global memory, in a
+                        // rolled loop (keeps the hot code small)
+    #pragma unroll 1
+                        for (int nd = 0; nd < 27; ++nd) {
+                            const int aa = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
+                            if ((NB == 1 && b != 1) || (NC == 1 && c3 != 1)) continue;
+                            const float W = sel3(w[0], aa) * (sel3(w[1], b) * sel3(w[2], c3));
+                            const int ix = node_of(host[0], aa - 1, g.n[0], g.bc[0]);
+                            const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
+                            const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
+                            float fv[4];
+                            load_gas<float>(A.gas, ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz), fv);
+    #pragma unroll
+                            for (int ch = 0; ch < 4; ++ch) G[ch] += W * fv[ch];
                         }
                     }
                     const float value = A.s.param ? A.s.param[gi] : A.sp.tau_f[sp];
@@ -406,25 +458,18 @@ step_slab_kernel(const TiledArgs<float> TA)
     #pragma unroll
                             for (int ch = 0; ch < 4; ++ch) rest[ch] = rint_to_ll(D[ch]);
                             const int hl = lb[0] + B[0] * (lb[1] + B[1] * lb[2]);
+    #pragma unroll 1
+                            for (int nd = 0; nd < 27; ++nd) {
+                                const int aa = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
+                                if ((NB == 1 && b != 1) || (NC == 1 && c3 != 1) || nd == 13) continue;
+                                const float W = sel3(w[0], aa) * (sel3(w[1], b) * sel3(w[2], c3));
+                                const int lin = hl + (aa - 1) + B[0] * ((b - 1) + B[1] * (c3 - 1));
     #pragma unroll
-                            for (int c3 = 0; c3 < 3; ++c3) {
-                                if (NC == 1 && c3 != 1) continue;
-    #pragma unroll
-                                for (int b = 0; b < 3; ++b) {
-                                    if (NB == 1 && b != 1) continue;
-    #pragma unroll
-                                    for (int aa = 0; aa < 3; ++aa) {
-                                        if (aa == 1 && b == 1 && c3 == 1) continue;
-                                        const float W = w[0][aa] * (w[1][b] * w[2][c3]);
-                                        const int lin = hl + (aa - 1) + B[0] * ((b - 1) + B[1] * (c3 - 1));
-    #pragma unroll
-                                        for (int ch = 0; ch < 4; ++ch) {
-                                            const long long piece = rint_to_ll(W * D[ch]);
-                                            if (piece != 0) {
-                                                atomicAdd(&sdep[ch * bvol + lin], (unsigned long long)piece);
-                                                rest[ch] -= piece;
-                                            }
-                                        }
+                                for (int ch = 0; ch < 4; ++ch) {
+                                    const long long piece = rint_to_ll(W * D[ch]);
+                                    if (piece != 0) {
+                                        atomicAdd(&sdep[ch * bvol + lin], (unsigned long long)piece);
+                                        rest[ch] -= piece;
                                     }
                                 }
                             }
@@ -432,7 +477,7 @@ step_slab_kernel(const TiledArgs<float> TA)
                             for (int ch = 0; ch < 4; ++ch)
                                 if (rest[ch] != 0) atomicAdd(&sdep[ch * bvol + hl], (unsigned long long)rest[ch]);
                         } else {
-                            deposit_fixed<float>(g, A.dep, host, w, D, A.status);
+                            deposit_fixed_rolled<NB, NC>(g, A.dep, host, w, D, A.status);
                         }
                     }
                     if (!alive) {
