@@ -92,9 +92,45 @@ __device__ __forceinline__ void deposit_fixed_rolled(const GridDev &g, unsigned 
         if (rest[c] != 0) atomicAdd(&dep[4 * hidx + c], (unsigned long long)rest[c]);
 }
 
+// Out-of-line rare paths.  They work on copies (their addresses are taken
+// here, not the hot loop's registers); the kernel argument is a grid
+// constant, so the geometry structures are passed by reference to it.
+
+// A grain that left its key zone in the first half drift: exact drift,
+// boundaries, zone search and weights.  Returns false if it left the grid.
+struct SlabExact {
+    double q[3];
+    float p[3], inc[3], w[3][3], iw[3], qf[3];
+    int host[3];
+};
+
+template <int GEOM>
+__device__ __noinline__ bool slab_exact_first_half(const GridDev &g, const PhysDev &ph, double shift,
+                                                   int tsc, float h, SlabExact &e)
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) e.inc[d] = 0.f;
+    drift<float, GEOM>(ph, e.q, e.q, e.p, h, false, e.inc);
+    if (!apply_bc<float, GEOM>(g, ph, shift, e.q, e.p)) return false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        zone_weights<float, GEOM>(g, d, tsc, e.q[d], e.host[d], e.w[d], e.iw[d]);
+        e.qf[d] = (float)e.q[d];
+    }
+    return true;
+}
+
+// Key of the next sort for a grain the in-zone prediction cannot place.
+template <int GEOM>
+__device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev &ph, double q[3],
+                                                 const float p[3], float h)
+{
+    return predict_key<float, GEOM>(g, ph, q, p, h);
+}
+
 template <int GEOM, int FLAT>
 __global__ void __launch_bounds__(kSlabThreads, 2)
-step_slab_kernel(const TiledArgs<float> TA)
+step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
 {
     using Sh = SlabShape<FLAT>;
     constexpr int NB = Sh::NB, NC = Sh::NC;
@@ -330,19 +366,25 @@ step_slab_kernel(const TiledArgs<float> TA)
                             }
                         } else {
                             // exact path: double-precision half drift, boundaries
-                            // and zone search
-    #pragma unroll
-                            for (int d = 0; d < 3; ++d) inc1[d] = 0.f;
-                            drift<float, GEOM>(A.ph, q, q, pn, h, false, inc1);
-                            if (!apply_bc<float, GEOM>(g, A.ph, shift_mid_of(A), q, pn)) {
+                            // and zone search (out of line)
+                            SlabExact ex;
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) { ex.q[d] = q[d]; ex.p[d] = pn[d]; }
+                            const bool in = slab_exact_first_half<GEOM>(g, A.ph, shift_mid_of(A), TA.tsc, h, ex);
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) { q[d] = ex.q[d]; pn[d] = ex.p[d]; inc1[d] = ex.inc[d]; }
+                            if (!in) {
                                 A.s.q[0][gi] = __longlong_as_double(0x7ff8000000000000LL);
                                 ++nremoved;
                                 live = false;
                             } else {
-    #pragma unroll
+#pragma unroll
                                 for (int d = 0; d < 3; ++d) {
-                                    zone_weights<float, GEOM>(g, d, TA.tsc, q[d], host[d], w[d], iw[d]);
-                                    qf[d] = (float)q[d];
+                                    host[d] = ex.host[d];
+                                    iw[d] = ex.iw[d];
+                                    qf[d] = ex.qf[d];
+#pragma unroll
+                                    for (int k = 0; k < 3; ++k) w[d][k] = ex.w[d][k];
                                 }
                             }
                         }
@@ -544,7 +586,8 @@ step_slab_kernel(const TiledArgs<float> TA)
                                    ll[0] + g.T[0] * (ll[1] + g.T[1] * ll[2]);
                         } else {
                             double qk[3] = {q[0], q[1], q[2]};
-                            nkey = predict_key<float, GEOM>(g, A.ph, qk, pnew, h);
+                            const float pk[3] = {pnew[0], pnew[1], pnew[2]};
+                            nkey = slab_predict_key<GEOM>(g, A.ph, qk, pk, h);
                         }
                     }
                 }
