@@ -510,14 +510,14 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                                 for (int ch = 0; ch < 4; ++ch) {
                                     const long long piece = rint_to_ll(W * D[ch]);
                                     if (piece != 0) {
-                                        atomicAdd(&sdep[ch * bvol + lin], (unsigned long long)piece);
+                                        shared_add_i64(&sdep[ch * bvol + lin], piece);
                                         rest[ch] -= piece;
                                     }
                                 }
                             }
     #pragma unroll
                             for (int ch = 0; ch < 4; ++ch)
-                                if (rest[ch] != 0) atomicAdd(&sdep[ch * bvol + hl], (unsigned long long)rest[ch]);
+                                if (rest[ch] != 0) shared_add_i64(&sdep[ch * bvol + hl], rest[ch]);
                         } else {
                             deposit_fixed_rolled<NB, NC>(g, A.dep, host, w, D, A.status);
                         }
@@ -674,7 +674,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                             big |= !(fabsf(acc[b][c][ch]) < 4.5e15f);
                             const long long piece = rint_to_ll(acc[b][c][ch]);
                             if (piece != 0) {
-                                atomicAdd(&sdep[ch * bvol + lin], (unsigned long long)piece);
+                                shared_add_i64(&sdep[ch * bvol + lin], piece);
                                 ps[ch] += piece;
                             }
                         }
@@ -687,8 +687,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                 if (a == 1 && own) {
                     big |= !(fabsf(S[ch]) < 4.5e15f);
                     const long long rest = rint_to_ll(S[ch]) - (ps[ch] + s1 + s2);
-                    if (rest != 0)
-                        atomicAdd(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], (unsigned long long)rest);
+                    if (rest != 0) shared_add_i64(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], rest);
                 }
             }
         }

@@ -70,6 +70,20 @@ __device__ __forceinline__ long long rint_to_ll(float v)
 }
 __device__ __forceinline__ long long rint_to_ll(double v) { return __double2ll_rn(v); }
 
+// Adds v to the 64-bit integer at p (shared memory) with two 32-bit atomics:
+// the low word's carry goes into the high word, so the sum is exact modulo
+// 2^64 and mixes freely with 64-bit atomic adds to the same word.  On this
+// GPU 32-bit shared atomics are much cheaper than 64-bit ones.
+__device__ __forceinline__ void shared_add_i64(unsigned long long *p, long long v)
+{
+    unsigned *w = reinterpret_cast<unsigned *>(p);
+    const unsigned lo = (unsigned)(unsigned long long)v;
+    const unsigned hi = (unsigned)((unsigned long long)v >> 32);
+    const unsigned old = atomicAdd(w, lo);
+    const unsigned up = hi + ((old + lo < old) ? 1u : 0u);
+    if (up != 0u) atomicAdd(w + 1, up);
+}
+
 constexpr int kChunk = kTiledThreads;
 
 // Shared memory of one CTA: deposit box (channel major), run tables, gas
@@ -397,14 +411,14 @@ step_tiled_kernel(const TiledArgs<Real> TA)
                         big |= !(fabs(sum[z][c]) < Real(4.5e15));
                         const long long piece = rint_to_ll(sum[z][c]);
                         if (piece != 0) {
-                            atomicAdd(&sdep[c * bvol + lin], (unsigned long long)piece);
+                            shared_add_i64(&sdep[c * bvol + lin], piece);
                             ps[c] += piece;
                         }
                     }
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if (ps[c] != 0) atomicAdd(&run_sum[c * CH + r], (unsigned long long)ps[c]);
+                    if (ps[c] != 0) shared_add_i64(&run_sum[c * CH + r], ps[c]);
                     if (htask) {
                         big |= !(fabs(S[c]) < Real(4.5e15));
                         run_q[c * CH + r] = rint_to_ll(S[c]);
@@ -421,7 +435,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
                 for (int c = 0; c < 4; ++c) {
                     const long long rest = run_q[c * CH + r] - (long long)run_sum[c * CH + r];
                     run_sum[c * CH + r] = 0ull;
-                    if (rest != 0) atomicAdd(&sdep[c * bvol + hlin], (unsigned long long)rest);
+                    if (rest != 0) shared_add_i64(&sdep[c * bvol + hlin], rest);
                 }
             }
             kcur = kend;
