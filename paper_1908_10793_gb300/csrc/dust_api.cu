@@ -72,6 +72,7 @@ struct dust_ctx {
     // d_time = [t, shift_mid, shift_end, -]
     double *d_time = nullptr;
     bool capture_mode = false;  // enqueueing into a stream capture
+    bool perm_pending = false;  // sorted order computed, gather left to the step
     uint64_t gen = 0;           // bumped when the grain store is reallocated
     double *d_stage = nullptr;
     size_t stage_bytes = 0;
@@ -555,7 +556,7 @@ int alloc_store(dust_ctx *ctx, int64_t n)
 }
 
 template <typename Real>
-int run_sort(dust_ctx *ctx, double dt)
+int run_sort(dust_ctx *ctx, double dt, bool fused)
 {
     SortArgs<Real> a;
     a.g = ctx->g;
@@ -576,7 +577,7 @@ int run_sort(dust_ctx *ctx, double dt)
     // keys predicted by the previous step for this dt are reused; otherwise
     // the key kernel computes them
     const bool reuse = ctx->keys_ready && ctx->keys_dt == dt;
-    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += reuse ? 6 : 7;
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += (reuse ? 6 : 7) - (fused ? 1 : 0);
     if (!reuse) {
         CU(cudaMemsetAsync(ctx->d_count_next, 0, m * sizeof(int32_t), ctx->stream));
         cudaError_t e = cudaSuccess;
@@ -591,8 +592,10 @@ int run_sort(dust_ctx *ctx, double dt)
     CU(launch_exclusive_scan(ctx->d_count_next, m, ctx->d_blocksums, ctx->stream));
     CU(cudaMemcpyAsync(ctx->d_cursor, ctx->d_count_next, m * sizeof(int32_t),
                        cudaMemcpyDeviceToDevice, ctx->stream));
-    CU(launch_sort_scatter<Real>(a, ctx->stream));
-    ctx->cur = 1 - ctx->cur;
+    CU(launch_sort_scatter<Real>(a, ctx->stream, !fused));
+    // fused: the step kernel moves the grains (and then flips the store)
+    if (fused) ctx->perm_pending = true;
+    else ctx->cur = 1 - ctx->cur;
     std::swap(ctx->d_count, ctx->d_count_next);
     ctx->keys_ready = false;
     return DUST_OK;
@@ -647,6 +650,7 @@ inline bool slab_available(int geom, int flat)
 template <typename Real, int GEOM>
 cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
                              const int32_t *key_off, int32_t *key_out, int32_t *count_out,
+                             const int32_t *perm, const int32_t *perm_id, const StoreDev<Real> &dst,
                              cudaStream_t s)
 {
     TiledArgs<Real> ta;
@@ -656,15 +660,21 @@ cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
     ta.emit_keys = key_out != nullptr;
     ta.key_out = key_out;
     ta.count_out = count_out;
-    if (kernel == DUST_KERNEL_PER_GRAIN)
+    ta.perm = perm;
+    ta.perm_id = perm_id;
+    ta.dst = dst;
+    if (kernel == DUST_KERNEL_PER_GRAIN) {
+        if (perm) return cudaErrorInvalidValue;  // only the slab kernel gathers
         return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<Real, GEOM, 1>(a, s)
                                          : launch_step_per_grain<Real, GEOM, 0>(a, s);
+    }
     if constexpr (sizeof(Real) == 4) {
         const int flat = slab_flat(a.g);
         if ((kernel == DUST_KERNEL_AUTO || kernel == DUST_KERNEL_SLAB) && slab_available(GEOM, flat))
             return launch_slab_geom<GEOM>(ta, flat, s);
     }
     ta.emit_keys = 0;
+    if (perm) return cudaErrorInvalidValue;  // only the slab kernel gathers
     return weight == DUST_WEIGHT_TSC ? launch_step_tiled<Real, GEOM, 1>(ta, s)
                                      : launch_step_tiled<Real, GEOM, 0>(ta, s);
 }
@@ -710,16 +720,26 @@ int run_step(dust_ctx *ctx, double dt)
                       (ctx->capture_mode || (ctx->steps + 1) % ctx->sort_interval == 0);
     int32_t *kout = emit ? ctx->d_key : nullptr;
     int32_t *cout_ = emit ? ctx->d_count_next : nullptr;
+    // a fused sort left its gather to this step: read the old store through
+    // the permutation, write the other one
+    const bool pend = ctx->perm_pending;
+    const int32_t *perm = pend ? ctx->d_pair_src : nullptr;
+    const int32_t *perm_id = pend ? ctx->d_pair_id : nullptr;
+    const StoreDev<Real> dst = store_of<Real>(ctx, 1 - ctx->cur);
     if (emit)
         CU(cudaMemsetAsync(ctx->d_count_next, 0, (ctx->g.nkeys + 2) * sizeof(int32_t), st));
     switch (ctx->geom.kind) {
-    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, st); break;
-    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, st); break;
-    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, kout, cout_, st); break;
-    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, kout, cout_, st); break;
+    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
+    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
+    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
+    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
     }
     delete step_timer;
     CU(e);
+    if (pend) {
+        ctx->cur = 1 - ctx->cur;
+        ctx->perm_pending = false;
+    }
     ctx->keys_ready = emit;
     ctx->keys_dt = dt;
     if (ctx->opt.feedback_apply) {
@@ -954,6 +974,7 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
     ctx->cur = 0;
     ctx->need_sort = true;
     ctx->keys_ready = false;
+    ctx->perm_pending = false;
     ctx->gen += 1;
     if (n > 0) {
         const uint8_t *sp_dev = species;
@@ -1004,7 +1025,8 @@ extern "C" int dust_step(dust_ctx *ctx, double dt)
     CU(cudaSetDevice(ctx->device));
     int r;
     if (ctx->need_sort || ctx->steps % ctx->sort_interval == 0) {
-        r = ctx->mixed ? run_sort<float>(ctx, dt) : run_sort<double>(ctx, dt);
+        const bool fused = step_emits_keys(ctx);  // the slab kernel will move the grains
+        r = ctx->mixed ? run_sort<float>(ctx, dt, fused) : run_sort<double>(ctx, dt, fused);
         if (r) return r;
         ctx->need_sort = false;
     }
@@ -1307,7 +1329,7 @@ int capture_period(dust_ctx *ctx, double dt)
     const double q_om_lx = ctx->geom.q * ctx->geom.omega * Lx;
     const int sb = ctx->geom.kind == DUST_SHEARING_BOX;
     for (int k = 0; k < 2; ++k) {
-        int r = run_sort<Real>(ctx, dt);
+        int r = run_sort<Real>(ctx, dt, step_emits_keys(ctx));
         if (r) return r;
         r = run_step<Real>(ctx, dt);
         if (r) return r;
@@ -1342,6 +1364,7 @@ int capture(dust_batch *b, const double *dt)
         for (size_t i = 0; i < n; ++i) {
             dust_ctx *c = b->ctx[i];
             c->capture_mode = false;
+            c->perm_pending = false;
             for (int g = 0; g < dust_ctx::N_GROUPS; ++g) c->launches[g] = saved[i].launches[g];
             if (!state) continue;
             c->cur = saved[i].cur;

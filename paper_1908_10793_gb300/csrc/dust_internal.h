@@ -123,7 +123,13 @@ struct TiledArgs {
     // optional: the step kernel predicts every grain's key for the next sort
     int emit_keys;
     int32_t *key_out;             // [n]
-    int32_t *count_out;           // [nkeys + 1], zeroed before the step
+    int32_t *count_out;           // [nkeys + 2], zeroed before the step
+    // optional: the sort's gather fused into the step.  The grain at sorted
+    // position i is read from s at perm[i] and written, with id perm_id[i],
+    // to dst at i (null: read and write s in place)
+    const int32_t *perm;
+    const int32_t *perm_id;
+    StoreDev<Real> dst;
 };
 
 template <typename Real>
@@ -155,7 +161,7 @@ template <typename Real, int GEOM>
 cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s);
 
 template <typename Real>
-cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s);
+cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s, bool gather);
 
 cudaError_t launch_exclusive_scan(int32_t *data, int64_t n, int32_t *block_sums,
                                   cudaStream_t s);

@@ -140,14 +140,29 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     const unsigned FULL = 0xffffffffu;
 
     const int tile = blockIdx.x;
-    if (TA.emit_keys) {
-        // grains removed before the last sort sit after every zone's group and
-        // keep the removed-grain key
-        const int64_t D0 = TA.key_off[g.nkeys], D1 = A.s.n;
-        for (int64_t gi = D0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < D1;
-             gi += (int64_t)gridDim.x * blockDim.x)
-            TA.key_out[gi] = (int32_t)g.nkeys;
-        if (blockIdx.x == 0 && threadIdx.x == 0 && D1 > D0)
+    // grains are read from S and written to O (the other store when the
+    // sort's gather is fused into this kernel)
+    const StoreDev<float> &S = A.s;
+    const StoreDev<float> &O = TA.perm ? TA.dst : A.s;
+    if (TA.emit_keys || TA.perm) {
+        // grains removed before the last sort sit after every zone's group:
+        // they keep the removed-grain key and are moved as they are
+        const int D0 = TA.key_off[g.nkeys], D1 = (int)A.s.n;
+        for (int gi = D0 + blockIdx.x * blockDim.x + threadIdx.x; gi < D1; gi += gridDim.x * blockDim.x) {
+            if (TA.emit_keys) TA.key_out[gi] = (int32_t)g.nkeys;
+            if (TA.perm) {
+                const int src = TA.perm[gi];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    O.q[d][gi] = S.q[d][src];
+                    O.p[d][gi] = S.p[d][src];
+                }
+                O.id[gi] = TA.perm_id[gi];
+                if (S.species) O.species[gi] = S.species[src];
+                if (S.param) O.param[gi] = S.param[src];
+            }
+        }
+        if (TA.emit_keys && blockIdx.x == 0 && threadIdx.x == 0 && D1 > D0)
             atomicAdd(&TA.count_out[g.nkeys], (int32_t)(D1 - D0));
     }
     const int64_t kbase = (int64_t)tile * g.tvol;
@@ -271,7 +286,12 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
             float *rb = srec + warp * (kRecFields * kRecStride);
             // ---- push: one grain per lane, consecutive grains on consecutive
             // lanes (coalesced), each relative to its own key zone
+            // source positions one iteration ahead (the permutation load is
+            // off the grain loads' dependency chain)
+            int src_next = (TA.perm && P0 + lane < P1) ? TA.perm[P0 + lane] : 0;
             for (int gi = P0 + lane; gi < P1; gi += 32) {
+                const int src = TA.perm ? src_next : gi;
+                if (TA.perm && gi + 32 < P1) src_next = TA.perm[gi + 32];
                 int kq2 = 0;
 #pragma unroll
                 for (int j = 1; j < 10; ++j) kq2 += gi >= koff[j] ? 1 : 0;
@@ -307,13 +327,13 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                 int32_t nkey = (int32_t)g.nkeys;   // next sort key (removed: nkeys)
                 int host[3] = {0, 0, 0};
                 int sp = 0;
-                bool live = false, ingroup = false;
+                bool live = false, ingroup = false, gone = false;
                 {
-                    q[0] = A.s.q[0][gi]; q[1] = A.s.q[1][gi]; q[2] = A.s.q[2][gi];
+                    q[0] = S.q[0][src]; q[1] = S.q[1][src]; q[2] = S.q[2][src];
                     live = !is_nan_f64(q[0]);
                     if (live) {
-                        pn[0] = A.s.p[0][gi]; pn[1] = A.s.p[1][gi]; pn[2] = A.s.p[2][gi];
-                        sp = A.s.species ? A.s.species[gi] : 0;
+                        pn[0] = S.p[0][src]; pn[1] = S.p[1][src]; pn[2] = S.p[2][src];
+                        sp = S.species ? S.species[src] : 0;
     #pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             if (g.n[d] > 1) { u[d] = f64_to_f32_rn(q[d] - zcd[d]); zc3[d] = zcf[d]; }
@@ -374,9 +394,11 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
 #pragma unroll
                             for (int d = 0; d < 3; ++d) { q[d] = ex.q[d]; pn[d] = ex.p[d]; inc1[d] = ex.inc[d]; }
                             if (!in) {
-                                A.s.q[0][gi] = __longlong_as_double(0x7ff8000000000000LL);
+                                q[0] = __longlong_as_double(0x7ff8000000000000LL);
+                                if (!TA.perm) S.q[0][gi] = q[0];
                                 ++nremoved;
                                 live = false;
+                                gone = true;
                             } else {
 #pragma unroll
                                 for (int d = 0; d < 3; ++d) {
@@ -446,7 +468,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                             for (int ch = 0; ch < 4; ++ch) G[ch] += W * fv[ch];
                         }
                     }
-                    const float value = A.s.param ? A.s.param[gi] : A.sp.tau_f[sp];
+                    const float value = S.param ? S.param[src] : A.sp.tau_f[sp];
                     const float tau = stopping_time<float, GEOM>(A.ph, A.sp.mode[sp], value, qf, G[0]);
                     const float x = dt / tau;
                     const float E = expf(-x);
@@ -526,8 +548,8 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                         q[0] = __longlong_as_double(0x7ff8000000000000LL);
                         ++nremoved;
                     }
-                    A.s.q[0][gi] = q[0]; A.s.q[1][gi] = q[1]; A.s.q[2][gi] = q[2];
-                    A.s.p[0][gi] = pnew[0]; A.s.p[1][gi] = pnew[1]; A.s.p[2][gi] = pnew[2];
+                    O.q[0][gi] = q[0]; O.q[1][gi] = q[1]; O.q[2][gi] = q[2];
+                    O.p[0][gi] = pnew[0]; O.p[1][gi] = pnew[1]; O.p[2][gi] = pnew[2];
                     if (TA.emit_keys && alive) {
                         // key for the next sort: the zone of the next step's
                         // half-step position (same dt), relative to this key
@@ -590,6 +612,17 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                             nkey = slab_predict_key<GEOM>(g, A.ph, qk, pk, h);
                         }
                     }
+                }
+                if (TA.perm) {
+                    // the rest of the gather: a grain removed in the first
+                    // half drift, and the columns the step does not change
+                    if (gone) {
+                        O.q[0][gi] = q[0]; O.q[1][gi] = q[1]; O.q[2][gi] = q[2];
+                        O.p[0][gi] = pn[0]; O.p[1][gi] = pn[1]; O.p[2][gi] = pn[2];
+                    }
+                    O.id[gi] = TA.perm_id[gi];
+                    if (S.species) O.species[gi] = S.species[src];
+                    if (S.param) O.param[gi] = S.param[src];
                 }
                 if (TA.emit_keys) {
                     TA.key_out[gi] = nkey;

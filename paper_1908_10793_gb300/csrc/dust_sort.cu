@@ -163,17 +163,17 @@ __global__ void sort_gather_kernel(const SortArgs<Real> A)
 }
 
 template <typename Real>
-cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s)
+cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s, bool gather)
 {
     if (a.src.n == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((a.src.n + 255) / 256);
     sort_scatter_pairs_kernel<Real><<<nb, 256, 0, s>>>(a);
     sort_segments_kernel<Real><<<(unsigned)((a.nkeys1 + 255) / 256), 256, 0, s>>>(a);
-    sort_gather_kernel<Real><<<nb, 256, 0, s>>>(a);
+    if (gather) sort_gather_kernel<Real><<<nb, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_sort_scatter<float>(const SortArgs<float> &, cudaStream_t);
-template cudaError_t launch_sort_scatter<double>(const SortArgs<double> &, cudaStream_t);
+template cudaError_t launch_sort_scatter<float>(const SortArgs<float> &, cudaStream_t, bool);
+template cudaError_t launch_sort_scatter<double>(const SortArgs<double> &, cudaStream_t, bool);
 
 }  // namespace dust
