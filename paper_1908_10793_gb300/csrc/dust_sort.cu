@@ -108,39 +108,83 @@ template <typename Real>
 __global__ void sort_scatter_pairs_kernel(const SortArgs<Real> A)
 {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = gi < A.src.n;
-    const int32_t key = valid ? A.key[gi] : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int64_t w0 = gi - (threadIdx.x & 31);
+    if (w0 >= A.src.n) return;  // whole warp past the end
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
+    const int m = (int)min((int64_t)32, A.src.n - w0);  // lanes 0 .. m-1 hold grains
+    const unsigned pm = m == 32 ? 0xffffffffu : ((1u << m) - 1u);
+    if (lane >= m) return;
+    // runs of equal keys on consecutive lanes (keys arrive nearly sorted):
+    // one cursor atomic per run, positions inside the run by lane
+    const int32_t key = A.key[gi];
+    const int32_t prev = __shfl_up_sync(pm, key, 1);
+    const bool start = lane == 0 || prev != key;
+    const unsigned starts = __ballot_sync(pm, start);
+    const int first = 31 - __clz(starts & ((2u << lane) - 1u));  // this lane's run start
+    const unsigned later = starts & ~((2u << lane) - 1u);
+    const int end = later ? __ffs(later) - 1 : m;
     int32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&A.cursor[key], __popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (!valid) return;
-    const int32_t pos = base + __popc(peers & ((1u << lane) - 1u));
+    if (start) base = atomicAdd(&A.cursor[key], end - lane);
+    base = __shfl_sync(pm, base, first);
+    const int32_t pos = base + (lane - first);
     A.pair_id[pos] = A.src.id[gi];
     A.pair_src[pos] = (int32_t)gi;
 }
 
-// One thread per key: insertion sort of the key's (id, source) pairs by id.
-template <typename Real>
-__global__ void sort_segments_kernel(const SortArgs<Real> A)
+// Insertion sort by id of the (id, source) pairs of every key.  A warp
+// takes 32 consecutive keys; their segments are contiguous, so the warp
+// stages them in shared memory with coalesced loads, each lane sorts its
+// key's segment there, and the warp writes them back.  Segments of more
+// than kSegStage pairs in total are sorted in place in global memory.
+constexpr int kSegThreads = 256;
+constexpr int kSegStage = 512;  // pairs staged per warp
+
+__device__ __forceinline__ void insertion_sort_pairs(int32_t *id, int32_t *src, int32_t b, int32_t e)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= A.nkeys1) return;
-    const int32_t b = A.count[k], e = A.count[k + 1];
     for (int32_t u = b + 1; u < e; ++u) {
-        const int32_t id = A.pair_id[u], src = A.pair_src[u];
+        const int32_t x = id[u], y = src[u];
         int32_t j = u - 1;
         while (j >= b) {
-            const int32_t idj = A.pair_id[j];
-            if (idj <= id) break;
-            A.pair_id[j + 1] = idj;
-            A.pair_src[j + 1] = A.pair_src[j];
+            const int32_t idj = id[j];
+            if (idj <= x) break;
+            id[j + 1] = idj;
+            src[j + 1] = src[j];
             --j;
         }
-        A.pair_id[j + 1] = id;
-        A.pair_src[j + 1] = src;
+        id[j + 1] = x;
+        src[j + 1] = y;
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kSegThreads) sort_segments_kernel(const SortArgs<Real> A)
+{
+    __shared__ int32_t sid[kSegThreads / 32][kSegStage];
+    __shared__ int32_t ssrc[kSegThreads / 32][kSegStage];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k0 = k - lane;
+    if (k0 >= A.nkeys1) return;  // whole warp past the end
+    const int64_t klast = min(k0 + 32, A.nkeys1);  // one past the warp's last key
+    const int32_t W0 = A.count[k0], W1 = A.count[klast];
+    const bool mine = k < A.nkeys1;
+    const int32_t b = mine ? A.count[k] : W1, e = mine ? A.count[k + 1] : W1;
+    if (W1 - W0 > kSegStage) {
+        if (mine) insertion_sort_pairs(A.pair_id, A.pair_src, b, e);
+        return;
+    }
+    const unsigned FULL = 0xffffffffu;
+    __syncwarp(FULL);
+    for (int32_t u = W0 + lane; u < W1; u += 32) {
+        sid[warp][u - W0] = A.pair_id[u];
+        ssrc[warp][u - W0] = A.pair_src[u];
+    }
+    __syncwarp(FULL);
+    if (mine) insertion_sort_pairs(sid[warp], ssrc[warp], b - W0, e - W0);
+    __syncwarp(FULL);
+    for (int32_t u = W0 + lane; u < W1; u += 32) {
+        A.pair_id[u] = sid[warp][u - W0];
+        A.pair_src[u] = ssrc[warp][u - W0];
     }
 }
 
@@ -168,7 +212,7 @@ cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s, bool ga
     if (a.src.n == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((a.src.n + 255) / 256);
     sort_scatter_pairs_kernel<Real><<<nb, 256, 0, s>>>(a);
-    sort_segments_kernel<Real><<<(unsigned)((a.nkeys1 + 255) / 256), 256, 0, s>>>(a);
+    sort_segments_kernel<Real><<<(unsigned)((a.nkeys1 + kSegThreads - 1) / kSegThreads), kSegThreads, 0, s>>>(a);
     if (gather) sort_gather_kernel<Real><<<nb, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
