@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-disks", action="store_true")
+    ap.add_argument("--disk-steps", type=int, default=10)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--small", action="store_true", help="16^3 grid (profiling runs)")
     ap.add_argument("--grid", type=int, default=0, help="zones per side (profiling runs)")
@@ -159,10 +161,15 @@ def weak_value(world, units_per_rank, seconds):
 
 def algorithmic_bytes(w, precision_bytes):
     """Bytes one step kernel launch must move at minimum: every grain's state
-    read and written once (3 FP64 coordinates + 3 momentum-like values), each
+    read and written once (3 FP64 coordinates + 3 momentum-like values, and
+    the species index and stopping-time value where the workload has them), each
     zone's gas (rho + 3 velocities) read once and its 4-channel int64 deposit
     written once."""
     per_grain = 2 * (3 * 8 + 3 * precision_bytes)
+    if w.species is not None:
+        per_grain += 2 * 1
+    if w.param is not None:
+        per_grain += 2 * precision_bytes
     per_zone = 4 * precision_bytes + 4 * 8
     return w.ngrains * per_grain + w.ncell * per_zone, per_grain, per_zone
 
@@ -278,6 +285,11 @@ def run_ours(args):
     if not args.no_batch:
         batch = run_batch(args, D, torch, dev, stream)
 
+    # ---- the global disk workloads (cylindrical and spherical, mixed)
+    disks = None
+    if not args.no_disks:
+        disks = run_disks(args, D, torch, dev, stream)
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu and world == 1:
@@ -307,6 +319,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "fp64": fp64,
             "batch": batch,
+            "disks": disks,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -377,6 +390,50 @@ def run_batch(args, D, torch, dev, stream):
             "workload": "64 2-D (x,z) orbital-advection shearing boxes, 32^2..512^2 zones, "
                         "1-16 grains/zone, St 0.01/0.1/1, dust/gas 0.01/0.02/0.1, TSC, "
                         "feedback on, mixed precision"}
+
+
+def run_disks(args, D, torch, dev, stream):
+    """Cylindrical (384 x 1024 x 64, 50M grains, 4 species) and spherical
+    (256 x 128 x 512, 33M grains, St log-uniform in [1e-4, 10]) disks, mixed
+    precision, sort every step; grain-updates/s over the timed steps.  The
+    spherical disk keeps its gas fixed: with grains as stiff as St = 1e-4 in
+    zones whose gas density falls to ~1e-9 of the midplane value, the explicit
+    feedback alone (without the gas half-step drag predictor) is unstable."""
+    out = {}
+    peak, _ = measured_peaks()
+    for name, make, feedback in (("cyldisk", I.cyldisk, 1), ("sphdisk", I.sphdisk, 0)):
+        w = make("full")
+        ctx = D.Context(w, precision=D.DUST_MIXED, stream=stream.cuda_stream, timing=1,
+                        device=dev.index, feedback=feedback)
+        try:
+            ctx.set_gas(w.rho, w.vgas)
+            ctx.load(w.q, w.v, w.species, w.param)
+            for _ in range(3):
+                ctx.step(w.dt)
+            ctx.sync(check=False)
+            ctx.kernel_times(reset=True)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.disk_steps):
+                ctx.step(w.dt)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            rc, st = ctx.sync(check=False)
+            kt = ctx.kernel_times(reset=True)
+        finally:
+            ctx.close()
+        ab, per_grain, per_zone = algorithmic_bytes(w, 4)
+        step_ms = kt.step_ms / max(1, kt.step_launches)
+        out[name] = {"value": w.ngrains * args.disk_steps / (ms / 1e3), "unit": UNIT,
+                     "ms_per_step": ms / args.disk_steps, "grains": w.ngrains, "zones": w.ncell,
+                     "kernel_ms_per_step": {"step": kt.step_ms / args.disk_steps,
+                                            "sort": kt.sort_ms / args.disk_steps,
+                                            "other": kt.other_ms / args.disk_steps},
+                     "step_roofline_frac": ab / (step_ms / 1e3) / 1e9 / peak,
+                     "status": rc, "removed": st.n_removed, "feedback": feedback}
+    return out
 
 
 def cpu_baseline(w, steps=2, ngrains=None):
