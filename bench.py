@@ -159,7 +159,7 @@ def weak_value(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
-def algorithmic_bytes(w, precision_bytes):
+def algorithmic_bytes(w, precision_bytes, fused_gather=False):
     """Bytes one step kernel launch must move at minimum: every grain's state
     read and written once (3 FP64 coordinates + 3 momentum-like values, and
     the species index and stopping-time value where the workload has them), each
@@ -170,6 +170,10 @@ def algorithmic_bytes(w, precision_bytes):
         per_grain += 2 * 1
     if w.param is not None:
         per_grain += 2 * precision_bytes
+    if fused_gather:
+        # the step also finishes the zone sort: it reads the permutation and
+        # the sorted ids and writes the id column
+        per_grain += 3 * 4
     per_zone = 4 * precision_bytes + 4 * 8
     return w.ngrains * per_grain + w.ncell * per_zone, per_grain, per_zone
 
@@ -225,7 +229,7 @@ def run_ours(args):
     ngr = w.ngrains
     value = weak_value(world, ngr * args.steps, ms / 1e3)
     step_ms_avg = kt.step_ms / max(1, kt.step_launches)
-    ab, per_grain, per_zone = algorithmic_bytes(w, 4)
+    ab, per_grain, per_zone = algorithmic_bytes(w, 4, fused_gather=True)
     achieved = ab / (step_ms_avg / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     launches = int(kt.step_launches + kt.sort_launches + kt.other_launches)
@@ -424,7 +428,7 @@ def run_disks(args, D, torch, dev, stream):
             kt = ctx.kernel_times(reset=True)
         finally:
             ctx.close()
-        ab, per_grain, per_zone = algorithmic_bytes(w, 4)
+        ab, per_grain, per_zone = algorithmic_bytes(w, 4, fused_gather=True)
         step_ms = kt.step_ms / max(1, kt.step_launches)
         out[name] = {"value": w.ngrains * args.disk_steps / (ms / 1e3), "unit": UNIT,
                      "ms_per_step": ms / args.disk_steps, "grains": w.ngrains, "zones": w.ncell,
