@@ -52,6 +52,9 @@
 #define OW_CIC 0
 #define OW_TSC 1
 
+#define OP_EM 0             /* exponential midpoint, Sec. 3.2.2                */
+#define OP_SEMI_IMPLICIT 1  /* semi-implicit drift-kick-drift, Sec. 3.2.1       */
+
 #define OT_CONST 0   /* tau_s given directly                                  */
 #define OT_STOKES 1  /* St given: tau_s = St / Omega_K at the grain           */
 #define OT_EPSTEIN 2 /* tau_s = value / rho_gathered  (Sec. 2, tau_s ~ 1/rho) */
@@ -81,6 +84,7 @@ typedef struct {
     const int *sp_tau_mode;
     const double *sp_tau;
     int feedback_apply;   /* 1: add the deposit to the gas momentum           */
+    int pusher;           /* OP_EM or OP_SEMI_IMPLICIT (Cartesian, shearing box) */
 } oracle_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -490,7 +494,55 @@ int64_t oracle_step(const oracle_problem *P,
 
         /* 5. kick */
         double pp[3], a[3], dHdp[3];
-        if (P->geom == OG_SHEARING_BOX) {
+        if (P->pusher == OP_SEMI_IMPLICIT) {
+            /* Sec. 3.2.1: v^{n+1} = v^n + Lambda^{-1} dt a_tot(x^{n+1/2}, v^n, v_g)
+             * with Lambda = I - (dt/2) d a_tot / d v (Eqs. semi-implicit,
+             * a_linear, Lambda); drag -(v - v_g)/tau gives b = dt / (2 tau). */
+            double it = 1.0 / tau;            /* 0 for tau = infinity */
+            double b = 0.5 * dt * it;
+            double at[3], l00 = 1.0 + b, l01 = 0.0, l10 = 0.0;
+            if (P->geom == OG_SHEARING_BOX) {
+                double Om = P->omega, qq = P->q;
+                double zf = P->vertical_gravity ? -Om * Om * qm[2] : 0.0;
+                if (!P->fargo) {        /* standard frame, Eq. standard_SB_g */
+                    at[0] = 2.0 * Om * (pn[1] + qq * Om * qm[0]);
+                    at[1] = -2.0 * Om * pn[0];
+                    l01 = -Om * dt;
+                    l10 = Om * dt;
+                } else {                /* orbital advection, residual velocity */
+                    at[0] = 2.0 * Om * pn[1];
+                    at[1] = (qq - 2.0) * Om * pn[0];
+                    l01 = -Om * dt;
+                    l10 = (1.0 - 0.5 * qq) * Om * dt;
+                }
+                at[2] = zf;
+            } else {
+                at[0] = at[1] = at[2] = 0.0;
+            }
+            for (int d = 0; d < 3; d++) at[d] += (vg[d] - pn[d]) * it;
+            /* solve the 2x2 (x, y) block and the diagonal z entry */
+            double det = l00 * l00 - l01 * l10;
+            double r0 = dt * at[0], r1 = dt * at[1];
+            pp[0] = pn[0] + (l00 * r0 - l01 * r1) / det;
+            pp[1] = pn[1] + (-l10 * r0 + l00 * r1) / det;
+            pp[2] = pn[2] + dt * at[2] / l00;
+            /* non-frictional acceleration at (x^{n+1/2}, v^{n+1/2}) */
+            double vh[3] = {0.5 * (pn[0] + pp[0]), 0.5 * (pn[1] + pp[1]), 0.5 * (pn[2] + pp[2])};
+            if (P->geom == OG_SHEARING_BOX) {
+                double Om = P->omega, qq = P->q;
+                if (!P->fargo) {
+                    a[0] = 2.0 * Om * (vh[1] + qq * Om * qm[0]);
+                    a[1] = -2.0 * Om * vh[0];
+                } else {
+                    a[0] = 2.0 * Om * vh[1];
+                    a[1] = (qq - 2.0) * Om * vh[0];
+                }
+                a[2] = P->vertical_gravity ? -Om * Om * qm[2] : 0.0;
+            } else {
+                a[0] = a[1] = a[2] = 0.0;
+            }
+            dHdp[0] = vh[0]; dHdp[1] = vh[1]; dHdp[2] = vh[2];
+        } else if (P->geom == OG_SHEARING_BOX) {
             /* App. B.1: R v^{n+1} = E v^n + h1 G(x^{n+1/2}, v^n/2, v_g) */
             double Om = P->omega, qq = P->q;
             double zf = P->vertical_gravity ? -Om * Om * qm[2] : 0.0;

@@ -15,6 +15,7 @@ OG_CARTESIAN, OG_SHEARING_BOX, OG_CYLINDRICAL, OG_SPHERICAL = 0, 1, 2, 3
 OB_PERIODIC, OB_OUTFLOW = 0, 1
 OW_CIC, OW_TSC = 0, 1
 OT_CONST, OT_STOKES, OT_EPSTEIN = 0, 1, 2
+OP_EM, OP_SEMI_IMPLICIT = 0, 1
 (W1_CART_CIC, W1_CART_TSC, W1_CYL_R_CIC, W1_CYL_R_TSC, W1_SPH_R_CIC,
  W1_SPH_R_TSC, W1_SPH_TH_CIC, W1_SPH_TH_TSC) = range(8)
 
@@ -56,6 +57,7 @@ class _ProblemC(ctypes.Structure):
         ("sp_tau_mode", ctypes.POINTER(ctypes.c_int)),
         ("sp_tau", ctypes.POINTER(ctypes.c_double)),
         ("feedback_apply", ctypes.c_int),
+        ("pusher", ctypes.c_int),
     ]
 
 
@@ -106,7 +108,11 @@ class Problem:
 
     def __init__(self, geom, edges, bc=(OB_PERIODIC,) * 3, weight=OW_TSC,
                  species_mass=(1.0,), species_tau_mode=(OT_CONST,), species_tau=(1.0,),
-                 fargo=0, omega=1.0, q=1.5, gm=0.0, vertical_gravity=0, feedback_apply=0):
+                 fargo=0, omega=1.0, q=1.5, gm=0.0, vertical_gravity=0, feedback_apply=0,
+                 pusher=OP_EM):
+        if pusher == OP_SEMI_IMPLICIT and geom not in (OG_CARTESIAN, OG_SHEARING_BOX):
+            raise ValueError("the semi-implicit pusher is defined for Cartesian and "
+                             "shearing-box geometries (Sec. 3.2.1)")
         self.edges = [_f64(e) for e in edges]
         self.n = [len(e) - 1 for e in self.edges]
         self.sp_mass = _f64(species_mass)
@@ -126,6 +132,7 @@ class Problem:
         c.sp_tau_mode = self.sp_mode.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         c.sp_tau = _dp(self.sp_tau)
         c.feedback_apply = int(feedback_apply)
+        c.pusher = int(pusher)
         self.c = c
         self.geom = int(geom)
 

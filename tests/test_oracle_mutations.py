@@ -47,6 +47,11 @@ MUTATIONS = [
      "D[c] = m * ((pp[c] - pn[c]) - dt * a[c]);"),
     ("cylindrical zone volume", "dV = 0.5 * (a1 * a1 - a0 * a0) * (b1 - b0) * (c1 - c0);",
      "dV = (a1 - a0) * (b1 - b0) * (c1 - c0);"),
+    ("semi-implicit drag factor b = dt / tau", "double b = 0.5 * dt * it;", "double b = dt * it;"),
+    ("semi-implicit orbital-advection Lambda without (1 - q/2)",
+     "l10 = (1.0 - 0.5 * qq) * Om * dt;", "l10 = Om * dt;"),
+    ("semi-implicit standard-frame Lambda sign", "                    l10 = Om * dt;\n",
+     "                    l10 = -Om * dt;\n"),
 ]
 
 

@@ -448,7 +448,7 @@ def _read_golden():
     return rows
 
 
-def _deceleration_stiff(tau):
+def _deceleration_stiff(tau, pusher=O.OP_EM):
     """Sec. 4.1 stiff deceleration with the gas coupled through its half-step
     drag predictor (Eq. f_D with tau <- max(tau, dt)) and the corrector with
     the final deposit (Eq. dust_feedback_final).  One grain per zone, eps = 1."""
@@ -457,7 +457,7 @@ def _deceleration_stiff(tau):
     dV = 1.0 / n
     eps = 1.0
     prob = O.Problem(geom=O.OG_CARTESIAN, edges=edges, weight=O.OW_TSC,
-                     species_mass=(eps * dV,), species_tau=(tau,))
+                     species_mass=(eps * dV,), species_tau=(tau,), pusher=pusher)
     q = [(np.arange(n) + 0.5) / n, np.full(n, 0.5), np.full(n, 0.5)]
     p = [np.ones(n), np.zeros(n), np.zeros(n)]
     vg = -1.0
@@ -485,6 +485,50 @@ def test_stiff_deceleration_matches_printed_l1_errors(tau):
     if tau == 0.02:
         single = _read_golden()["single_step_tau0.02"]
         assert 0.3 * single < abs(hist[1]) < 3 * single
+
+
+@pytest.mark.parametrize("tau", [0.2, 0.02])
+def test_semi_implicit_deceleration_matches_printed_l1_errors(tau):
+    """Sec. 4.1: the semi-implicit scheme of Sec. 3.2.1 in the same coupled
+    stiff setup oscillates with little damping; printed L1 errors about 0.068
+    and 0.6 (one and two significant digits)."""
+    printed = _read_golden()["si_%s" % tau]
+    l1, hist = _deceleration_stiff(tau, O.OP_SEMI_IMPLICIT)
+    digits = 2 if tau == 0.2 else 1
+    assert abs(l1 - printed) <= 0.5 * 10 ** (np.floor(np.log10(printed)) - digits + 1), l1
+    # the oscillation the paper describes: the sign alternates every step
+    assert all(hist[k] * hist[k + 1] < 0 for k in range(len(hist) - 1))
+
+
+def test_semi_implicit_uniform_gas_is_the_trapezoidal_rule():
+    """For uniform fixed gas and no other force, the semi-implicit kick is the
+    trapezoidal (Crank-Nicolson) rule for dv/dt = -(v - v_g)/tau, whose
+    one-step factor on v - v_g is (1 - b)/(1 + b), b = dt/(2 tau)."""
+    prob = box_problem(geom=O.OG_CARTESIAN, species_tau=(0.3,), pusher=O.OP_SEMI_IMPLICIT)
+    rho, pg = gas_uniform(prob, 1.0, (0.2, -0.1, 0.05))
+    v0 = [[0.7, -0.4], [0.3, 0.2], [-0.5, 0.9]]
+    for dt in (0.01, 0.3, 2.0, 50.0):
+        _, p, _, _ = run(prob, [[1.0, -3.0], [2.0, 5.0], [0.5, -1.0]], v0, dt, 1, rho, pg)
+        b = dt / 0.6
+        for d, vg in enumerate((0.2, -0.1, 0.05)):
+            expect = vg + (np.array(v0[d]) - vg) * (1 - b) / (1 + b)
+            assert np.allclose(p[d], expect, rtol=1e-13, atol=1e-15), (dt, d)
+
+
+@pytest.mark.parametrize("fargo", [0, 1])
+def test_semi_implicit_equals_exponential_midpoint_without_drag(fargo):
+    """Sec. 3.2.2: for infinite stopping time the exponential midpoint kick
+    reduces to the semi-implicit one (shearing box, both frames)."""
+    res = []
+    for pusher in (O.OP_EM, O.OP_SEMI_IMPLICIT):
+        prob = box_problem(n=(4, 4, 4), lo=-1.0, hi=1.0, geom=O.OG_SHEARING_BOX, fargo=fargo,
+                           omega=1.0, q=1.5, vertical_gravity=1, pusher=pusher)
+        rho, pg = gas_uniform(prob, 1.0, (0.1, 0.2, 0.3))
+        q, p, _, _ = run(prob, [[0.3, -0.2], [0.1, 0.4], [0.2, -0.3]],
+                         [[0.05, -0.1], [-0.4, 0.2], [0.1, 0.0]], 0.05, 40, rho, pg,
+                         param=np.array([INF, INF]))
+        res.append(np.concatenate([np.ravel(q), np.ravel(p)]))
+    assert np.allclose(res[0], res[1], rtol=1e-13, atol=1e-14)
 
 
 # --------------------------------------------------------------------------
