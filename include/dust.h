@@ -71,6 +71,10 @@ enum { DUST_TAU_CONST = 0, DUST_TAU_STOKES = 1, DUST_TAU_EPSTEIN = 2 };
  * double precision, momentum-like variables, gas fields, weights, gather and
  * push in single precision, deposit in 64-bit fixed point. */
 enum { DUST_FP64 = 0, DUST_MIXED = 1 };
+/* particle pusher: the exponential midpoint rule (Sec. 3.2.2, default) or the
+ * semi-implicit drift-kick-drift scheme with the linearised drag kick
+ * (Sec. 3.2.1; Cartesian and shearing-box geometries only). */
+enum { DUST_PUSHER_EM = 0, DUST_PUSHER_SEMI_IMPLICIT = 1 };
 enum { DUST_MEM_HOST = 0, DUST_MEM_DEVICE = 1 };
 /* kernel choice.  DUST_KERNEL_PER_GRAIN: one thread per grain, every grain
  * quantises its own 27 x 4 deposit pieces into global 64-bit atomics (the
@@ -133,6 +137,7 @@ typedef struct dust_options {
     int tile[3];           /* zones per tile of the tiled kernel and of the
                               sort order (0 = default: 8x8x8 in 3-D, 16x16 in
                               2-D; clipped to the grid)                       */
+    int pusher;            /* DUST_PUSHER_EM (0) or DUST_PUSHER_SEMI_IMPLICIT */
 } dust_options;
 
 typedef struct dust_stats {

@@ -455,7 +455,9 @@ PhysDev make_phys(const dust_geometry &geo, const GridDev &g, double t, double d
 
 PhysDev phys_of(const dust_ctx *c, double t, double dt)
 {
-    return make_phys(c->geom, c->g, t, dt);
+    PhysDev ph = make_phys(c->geom, c->g, t, dt);
+    ph.pusher = c->opt.pusher;
+    return ph;
 }
 
 int ensure_stage(dust_ctx *ctx, size_t bytes)
@@ -764,6 +766,12 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     if (!geom || !grid || !species || !opt) return fail(nullptr, DUST_EINVAL, "NULL descriptor");
     if (opt->precision != DUST_FP64 && opt->precision != DUST_MIXED)
         return fail(nullptr, DUST_EINVAL, "bad precision");
+    if (opt->pusher != DUST_PUSHER_EM && opt->pusher != DUST_PUSHER_SEMI_IMPLICIT)
+        return fail(nullptr, DUST_EINVAL, "bad pusher");
+    if (opt->pusher == DUST_PUSHER_SEMI_IMPLICIT && geom->kind != DUST_CARTESIAN &&
+        geom->kind != DUST_SHEARING_BOX)
+        return fail(nullptr, DUST_EINVAL,
+                    "the semi-implicit pusher is defined for Cartesian and shearing-box geometries");
     int64_t ncell = 0;
     const int rv = validate_descriptors(geom, grid, species, n_species, opt->weight, &ncell);
     if (rv) return rv;

@@ -378,6 +378,65 @@ __device__ __forceinline__ Real stopping_time(const PhysDev &ph, int mode, Real 
     return value / pick<Real>(ph.omega, ph.omega_f);
 }
 
+// ------------------------------------------------------ semi-implicit ----
+// Semi-implicit kick (Sec. 3.2.1, Eqs. semi-implicit, a_linear, Lambda):
+// v^{n+1} = v^n + Lambda^{-1} dt a_tot(x^{n+1/2}, v^n, v_g), Lambda =
+// I - (dt/2) d a_tot / d v, with the drag -(v - v_g)/tau giving b = dt/(2 tau)
+// on the diagonal and the shearing-box Coriolis (standard frame) or
+// orbital-advection terms off it.  Cartesian and shearing-box geometries;
+// it = 1/tau (0 for tau = infinity).  Returns the same quantities as kick().
+template <typename Real, int GEOM, typename QT>
+__device__ __forceinline__ void kick_si(const PhysDev &ph, const QT qm[3], const Real pn[3],
+                                        const Real vg[3], Real it, Real dt, Real pp[3],
+                                        Real a[3], Real dH[3])
+{
+    const Real b = Real(0.5) * dt * it;
+    const Real l00 = Real(1) + b;
+    Real at[3] = {Real(0), Real(0), Real(0)};
+    Real l01 = Real(0), l10 = Real(0), Om = Real(0), q = Real(0), az = Real(0);
+    if (GEOM == GEOM_SB) {
+        Om = pick<Real>(ph.omega, ph.omega_f);
+        q = pick<Real>(ph.qshear, ph.qshear_f);
+        az = ph.vgrav ? -Om * Om * (Real)qm[2] : Real(0);
+        if (ph.fargo) {
+            at[0] = Real(2) * Om * pn[1];
+            at[1] = (q - Real(2)) * Om * pn[0];
+            l10 = (Real(1) - Real(0.5) * q) * Om * dt;
+        } else {
+            at[0] = Real(2) * Om * (pn[1] + q * Om * (Real)qm[0]);
+            at[1] = -Real(2) * Om * pn[0];
+            l10 = Om * dt;
+        }
+        l01 = -Om * dt;
+        at[2] = az;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) at[d] += (vg[d] - pn[d]) * it;
+    const Real det = l00 * l00 - l01 * l10;
+    const Real r0 = dt * at[0], r1 = dt * at[1];
+    pp[0] = pn[0] + (l00 * r0 - l01 * r1) / det;
+    pp[1] = pn[1] + (-l10 * r0 + l00 * r1) / det;
+    pp[2] = pn[2] + dt * at[2] / l00;
+    const Real vx = Real(0.5) * (pn[0] + pp[0]);
+    const Real vy = Real(0.5) * (pn[1] + pp[1]);
+    const Real vz = Real(0.5) * (pn[2] + pp[2]);
+    if (GEOM == GEOM_SB) {
+        if (ph.fargo) {
+            a[0] = Real(2) * Om * vy;
+            a[1] = (q - Real(2)) * Om * vx;
+        } else {
+            a[0] = Real(2) * Om * (vy + q * Om * (Real)qm[0]);
+            a[1] = -Real(2) * Om * vx;
+        }
+        a[2] = az;
+    } else {
+        a[0] = a[1] = a[2] = Real(0);
+    }
+    dH[0] = vx;
+    dH[1] = vy;
+    dH[2] = vz;
+}
+
 // ---------------------------------------------------------------- kick ----
 // Kick with E = exp(-dt/tau), cg = 1 - E = h1/tau, h1 = dt phi1(-dt/tau)
 // (Eqs. phi1, h1); returns the new p, the non-frictional acceleration a at
@@ -470,6 +529,19 @@ __device__ __forceinline__ void kick(const PhysDev &ph, const QT qm[3], const Re
             dH[d] = Real(0.5) * (pn[d] + pp[d]);
         }
     }
+}
+
+// The configured pusher: semi-implicit (Cartesian and shearing box only) or
+// exponential midpoint.
+template <typename Real, int GEOM, typename QT>
+__device__ __forceinline__ void kick_any(const PhysDev &ph, const QT qm[3], const Real pn[3],
+                                         const Real vg[3], Real tau, Real dt, Real E, Real cg,
+                                         Real h1, Real pp[3], Real a[3], Real dH[3])
+{
+    if ((GEOM == GEOM_CART || GEOM == GEOM_SB) && ph.pusher == DUST_PUSHER_SEMI_IMPLICIT)
+        kick_si<Real, GEOM>(ph, qm, pn, vg, Real(1) / tau, dt, pp, a, dH);
+    else
+        kick<Real, GEOM>(ph, qm, pn, vg, E, cg, h1, pp, a, dH);
 }
 
 }  // namespace dust

@@ -70,6 +70,7 @@ struct PhysDev {
     int geom;
     int fargo;
     int vgrav;
+    int pusher;              // DUST_PUSHER_EM or DUST_PUSHER_SEMI_IMPLICIT
     double omega, qshear, gm;
     double q_om;             // q * Omega
     double jump_v;           // q * Omega * Lx (standard-frame v_y jump)

@@ -476,7 +476,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                     const float h1 = (x == 0.f) ? dt : dt * cg / x;
                     const float vg[3] = {G[1], G[2], G[3]};
                     float pp[3], acc3[3], dH[3], inc2[3];
-                    kick<float, GEOM>(A.ph, qf, pn, vg, E, cg, h1, pp, acc3, dH);
+                    kick_any<float, GEOM>(A.ph, qf, pn, vg, tau, dt, E, cg, h1, pp, acc3, dH);
                     if (ingroup) {
                         // second half drift with the half-step metric factors, then
                         // one double-precision update by the summed increment

@@ -283,7 +283,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
                     const Real h1 = (x == Real(0)) ? dt : dt * cg / x;
                     const Real vg[3] = {acc[1], acc[2], acc[3]};
                     Real pp[3], a[3], dH[3];
-                    kick<Real, GEOM>(A.ph, qm, pn, vg, E, cg, h1, pp, a, dH);
+                    kick_any<Real, GEOM>(A.ph, qm, pn, vg, tau, dt, E, cg, h1, pp, a, dH);
                     drift<Real, GEOM>(A.ph, q, qm, pp, h, true, inc2);
                     Real pnew[3] = {pp[0], pp[1], pp[2]};
                     const bool alive = apply_bc<Real, GEOM>(g, A.ph, shift_end_of(A), q, pnew);

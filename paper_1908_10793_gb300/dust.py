@@ -22,6 +22,7 @@ DUST_BC_PERIODIC, DUST_BC_OUTFLOW = 0, 1
 DUST_WEIGHT_CIC, DUST_WEIGHT_TSC = 0, 1
 DUST_TAU_CONST, DUST_TAU_STOKES, DUST_TAU_EPSTEIN = 0, 1, 2
 DUST_FP64, DUST_MIXED = 0, 1
+DUST_PUSHER_EM, DUST_PUSHER_SEMI_IMPLICIT = 0, 1
 DUST_MEM_HOST, DUST_MEM_DEVICE = 0, 1
 DUST_KERNEL_AUTO, DUST_KERNEL_PER_GRAIN, DUST_KERNEL_TILED, DUST_KERNEL_SLAB = 0, 1, 2, 3
 DUST_FLAG_NAN, DUST_FLAG_OVERFLOW, DUST_FLAG_CFL, DUST_FLAG_WRAP = 1, 2, 4, 8
@@ -54,7 +55,7 @@ class dust_options(ctypes.Structure):
                 ("feedback_apply", ctypes.c_int), ("quantum", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("sort_interval", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("device", ctypes.c_int), ("timing", ctypes.c_int),
-                ("tile", ctypes.c_int * 3)]
+                ("tile", ctypes.c_int * 3), ("pusher", ctypes.c_int)]
 
 
 class dust_kernel_times(ctypes.Structure):
@@ -272,7 +273,8 @@ def dust_destroy(ctx):
 
 # ------------------------------------------------- descriptor helpers ----
 def make_descriptors(w, precision=DUST_MIXED, feedback=None, stream=None, sort_interval=0,
-                     kernel=DUST_KERNEL_AUTO, quantum=0.0, device=0, timing=0, tile=(0, 0, 0)):
+                     kernel=DUST_KERNEL_AUTO, quantum=0.0, device=0, timing=0, tile=(0, 0, 0),
+                     pusher=None):
     """C descriptors for a workload from paper_1908_10793_gb300.inputs.
     Returns (geometry, grid, species list, options, keepalive)."""
     geo = dust_geometry(kind=w.geom, fargo=w.fargo, omega=w.omega, q=w.qshear, gm=w.gm,
@@ -288,7 +290,8 @@ def make_descriptors(w, precision=DUST_MIXED, feedback=None, stream=None, sort_i
     opt = dust_options(precision=precision, weight=w.weight,
                        feedback_apply=w.feedback if feedback is None else feedback,
                        quantum=quantum, stream=stream, sort_interval=sort_interval,
-                       kernel=kernel, device=device, timing=timing)
+                       kernel=kernel, device=device, timing=timing,
+                       pusher=getattr(w, "pusher", DUST_PUSHER_EM) if pusher is None else pusher)
     for d in range(3):
         opt.tile[d] = int(tile[d])
     return geo, grid, sp, opt, edges

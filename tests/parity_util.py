@@ -10,7 +10,8 @@ def oracle_problem(w, feedback=None):
                      species_mass=w.species_mass, species_tau_mode=w.species_tau_mode,
                      species_tau=w.species_tau, fargo=w.fargo, omega=w.omega, q=w.qshear,
                      gm=w.gm, vertical_gravity=w.vertical_gravity,
-                     feedback_apply=w.feedback if feedback is None else feedback)
+                     feedback_apply=w.feedback if feedback is None else feedback,
+                     pusher=getattr(w, "pusher", O.OP_EM))
 
 
 def to_momentum(w, q, v):

@@ -49,3 +49,18 @@ def test_create_error_path_without_gpu(lib):
         D.dust_create(D.dust_geometry(kind=7), D.dust_grid(), [D.dust_species(mass=1.0)],
                       D.dust_options())
     assert e.value.code == D.DUST_EINVAL
+
+
+def test_semi_implicit_pusher_rejected_for_curvilinear_grids(lib):
+    # checked with the other descriptors, before any CUDA call
+    from paper_1908_10793_gb300 import dust as D
+    from paper_1908_10793_gb300 import inputs as I
+    w = I.cyldisk("small")
+    geo, grid, sp, opt, keep = D.make_descriptors(w, pusher=D.DUST_PUSHER_SEMI_IMPLICIT)
+    with pytest.raises(D.DustError) as e:
+        D.dust_create(geo, grid, sp, opt)
+    assert e.value.code == D.DUST_EINVAL and "semi-implicit" in str(e.value)
+    geo, grid, sp, opt, keep = D.make_descriptors(w, pusher=7)
+    with pytest.raises(D.DustError) as e:
+        D.dust_create(geo, grid, sp, opt)
+    assert e.value.code == D.DUST_EINVAL
