@@ -9,5 +9,5 @@ from .oracle import (  # noqa: F401
     OP_EM, OP_SEMI_IMPLICIT,
     W1_CART_CIC, W1_CART_TSC, W1_CYL_R_CIC, W1_CYL_R_TSC, W1_SPH_R_CIC,
     W1_SPH_R_TSC, W1_SPH_TH_CIC, W1_SPH_TH_TSC,
-    build, weights_1d, locate, Problem, step, gas_momentum,
+    build, weights_1d, locate, Problem, step, gas_momentum, gas_predictor,
 )

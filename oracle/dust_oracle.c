@@ -676,6 +676,102 @@ int64_t oracle_step(const oracle_problem *P,
     return removed;
 }
 
+/* Volume of zone (i, j, k): dR dphi dz R-weighted in cylindrical, r^2 dr
+ * sin(theta) dtheta dphi in spherical coordinates (Sec. 3.4). */
+static double zone_volume(const oracle_problem *P, int i, int j, int k)
+{
+    double a0 = P->edges[0][i], a1 = P->edges[0][i + 1];
+    double b0 = P->edges[1][j], b1 = P->edges[1][j + 1];
+    double c0 = P->edges[2][k], c1 = P->edges[2][k + 1];
+    if (P->geom == OG_CYLINDRICAL) return 0.5 * (a1 * a1 - a0 * a0) * (b1 - b0) * (c1 - c0);
+    if (P->geom == OG_SPHERICAL)
+        return (a1 * a1 * a1 - a0 * a0 * a0) / 3.0 * (cos(b0) - cos(b1)) * (c1 - c0);
+    return (a1 - a0) * (b1 - b0) * (c1 - c0);
+}
+
+/*
+ * Gas half-step predictor of the drag coupling (Sec. 3.1, Eqs. Delta_vp and
+ * f_D, with tau_s replaced by max(tau_s, dt) against the predictor's
+ * stiffness, as the paper adopts from BS10).  Every active grain gathers the
+ * gas at its position x^n (weights of Sec. 3.4 at x^n, stopping time from the
+ * gas gathered there) and the drag force density
+ *     f_D,i = (1/dV_i) sum_p (m_p / tau') W(x^n_p - x_i) (v_p - v_g(x^n_p))
+ * advances the gas by half a step:  (rho v)_i^{n+1/2} = (rho v)_i^n + dt/2 f_D,i.
+ * imp [ncell][3] receives the impulse dt/2 sum_p (...) per zone (FP64, dense),
+ * ph0..ph2 the half-step momentum-like gas velocity pg + imp / (rho dV).
+ * Reading: the predictor acts on the momentum-like channels of the deposit
+ * (l_phi = R v_phi etc.), like the corrector.
+ */
+void oracle_gas_predictor(const oracle_problem *P,
+                          const double *q0, const double *q1, const double *q2,
+                          const double *p0, const double *p1, const double *p2,
+                          const uint8_t *species, const double *param,
+                          const uint8_t *active, int64_t n, double dt,
+                          const double *rho, const double *pg0, const double *pg1,
+                          const double *pg2, double *imp,
+                          double *ph0, double *ph1, double *ph2)
+{
+    const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+    const int64_t ncell = (int64_t)n0 * n1 * n2;
+    int wk[3];
+    for (int d = 0; d < 3; d++) wk[d] = weight_kind(P, d);
+    memset(imp, 0, sizeof(double) * 3 * ncell);
+    for (int64_t g = 0; g < n; g++) {
+        if (!active[g]) continue;
+        int sp = species ? species[g] : 0;
+        double q[3] = {q0[g], q1[g], q2[g]};
+        double pn[3] = {p0[g], p1[g], p2[g]};
+        int host[3];
+        double w[3][3];
+        for (int d = 0; d < 3; d++) {
+            if (P->n[d] <= 1) {
+                host[d] = 0; w[d][0] = 0.0; w[d][1] = 1.0; w[d][2] = 0.0;
+                continue;
+            }
+            host[d] = oracle_locate(P->edges[d], P->n[d], q[d]);
+            oracle_weights_1d(wk[d], q[d], P->edges[d][host[d]], P->edges[d][host[d] + 1], w[d]);
+        }
+        double rg = 0.0, vg[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < 3; c++)
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    double W = w[0][a] * w[1][b] * w[2][c];
+                    int64_t idx = node_index(host[0], a - 1, n0, P->bc[0])
+                        + (int64_t)n0 * (node_index(host[1], b - 1, n1, P->bc[1])
+                        + (int64_t)n1 * node_index(host[2], c - 1, n2, P->bc[2]));
+                    rg += W * rho[idx];
+                    vg[0] += W * pg0[idx];
+                    vg[1] += W * pg1[idx];
+                    vg[2] += W * pg2[idx];
+                }
+        double value = param ? param[g] : P->sp_tau[sp];
+        double tau = stopping_time(P, P->sp_tau_mode[sp], value, q, rg);
+        double taup = fmax(tau, fabs(dt));
+        double coef = 0.5 * dt * P->sp_mass[sp] / taup;   /* 0 for tau = infinity */
+        double J[3];
+        for (int c = 0; c < 3; c++) J[c] = coef * (pn[c] - vg[c]);
+        for (int c = 0; c < 3; c++)
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    double W = w[0][a] * w[1][b] * w[2][c];
+                    if (W == 0.0) continue;
+                    int64_t idx = node_index(host[0], a - 1, n0, P->bc[0])
+                        + (int64_t)n0 * (node_index(host[1], b - 1, n1, P->bc[1])
+                        + (int64_t)n1 * node_index(host[2], c - 1, n2, P->bc[2]));
+                    for (int ch = 0; ch < 3; ch++) imp[3 * idx + ch] += W * J[ch];
+                }
+    }
+    for (int k = 0; k < n2; k++)
+        for (int j = 0; j < n1; j++)
+            for (int i = 0; i < n0; i++) {
+                int64_t idx = i + (int64_t)n0 * (j + (int64_t)n1 * k);
+                double s = 1.0 / (rho[idx] * zone_volume(P, i, j, k));
+                ph0[idx] = pg0[idx] + imp[3 * idx + 0] * s;
+                ph1[idx] = pg1[idx] + imp[3 * idx + 1] * s;
+                ph2[idx] = pg2[idx] + imp[3 * idx + 2] * s;
+            }
+}
+
 /* Gas momentum-like velocity per zone from physical velocity components
  * (Sec. 2.2: l_phi = R v_phi; spherical l_theta = r v_theta, l_phi = r
  * sin(theta) v_phi), evaluated at the zone centres (reading: the gathered

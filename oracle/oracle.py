@@ -78,6 +78,10 @@ def _load():
             lib.oracle_step.restype = ctypes.c_int64
             lib.oracle_gas_momentum.argtypes = [ctypes.POINTER(_ProblemC)] + [dp] * 6
             lib.oracle_gas_momentum.restype = None
+            lib.oracle_gas_predictor.argtypes = [ctypes.POINTER(_ProblemC)] + [dp] * 6 + [
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                ctypes.c_double] + [dp] * 8
+            lib.oracle_gas_predictor.restype = None
             _lib = lib
     return _lib
 
@@ -160,6 +164,29 @@ def step(prob, q, p, active, t, dt, rho, pg, species=None, param=None):
                               active.ctypes.data, n, float(t), float(dt),
                               _dp(rho), _dp(pg[0]), _dp(pg[1]), _dp(pg[2]), _dp(dep))
     return dep, removed
+
+
+def gas_predictor(prob, q, p, active, dt, rho, pg, species=None, param=None):
+    """Half-step gas prediction from the drag of the grains at x^n.  Returns
+    (impulse per zone [ncell, 3], half-step momentum-like gas velocity list)."""
+    lib = _load()
+    imp = np.zeros((prob.ncell, 3))
+    ph = [np.zeros(prob.ncell) for _ in range(3)]
+    qq = [_f64(x) for x in q]
+    pp = [_f64(x) for x in p]
+    rr = _f64(rho)
+    gg = [_f64(x) for x in pg]
+    sp = None if species is None else np.ascontiguousarray(species, dtype=np.uint8)
+    pa = None if param is None else _f64(param)
+    act = np.ascontiguousarray(active, dtype=np.uint8)
+    lib.oracle_gas_predictor(ctypes.byref(prob.c), _dp(qq[0]), _dp(qq[1]), _dp(qq[2]),
+                             _dp(pp[0]), _dp(pp[1]), _dp(pp[2]),
+                             None if sp is None else sp.ctypes.data,
+                             None if pa is None else pa.ctypes.data,
+                             act.ctypes.data, len(qq[0]), float(dt), _dp(rr),
+                             _dp(gg[0]), _dp(gg[1]), _dp(gg[2]), _dp(imp),
+                             _dp(ph[0]), _dp(ph[1]), _dp(ph[2]))
+    return imp, ph
 
 
 def gas_momentum(prob, v):

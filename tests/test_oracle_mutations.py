@@ -48,6 +48,12 @@ MUTATIONS = [
     ("cylindrical zone volume", "dV = 0.5 * (a1 * a1 - a0 * a0) * (b1 - b0) * (c1 - c0);",
      "dV = (a1 - a0) * (b1 - b0) * (c1 - c0);"),
     ("semi-implicit drag factor b = dt / tau", "double b = 0.5 * dt * it;", "double b = dt * it;"),
+    ("predictor without the stiffness limit", "double taup = fmax(tau, fabs(dt));",
+     "double taup = tau;"),
+    ("predictor advancing a full step", "double coef = 0.5 * dt * P->sp_mass[sp] / taup;",
+     "double coef = dt * P->sp_mass[sp] / taup;"),
+    ("predictor drag sign", "for (int c = 0; c < 3; c++) J[c] = coef * (pn[c] - vg[c]);",
+     "for (int c = 0; c < 3; c++) J[c] = coef * (vg[c] - pn[c]);"),
     ("semi-implicit orbital-advection Lambda without (1 - q/2)",
      "l10 = (1.0 - 0.5 * qq) * Om * dt;", "l10 = Om * dt;"),
     ("semi-implicit standard-frame Lambda sign", "                    l10 = Om * dt;\n",

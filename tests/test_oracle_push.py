@@ -449,9 +449,10 @@ def _read_golden():
 
 
 def _deceleration_stiff(tau, pusher=O.OP_EM):
-    """Sec. 4.1 stiff deceleration with the gas coupled through its half-step
-    drag predictor (Eq. f_D with tau <- max(tau, dt)) and the corrector with
-    the final deposit (Eq. dust_feedback_final).  One grain per zone, eps = 1."""
+    """Sec. 4.1 stiff deceleration with the gas coupled through the oracle's
+    half-step drag predictor (Eq. f_D with tau <- max(tau, dt)) and the
+    corrector with the final deposit (Eq. dust_feedback_final).  One grain per
+    zone, eps = 1."""
     n = 8
     edges = [np.linspace(0.0, 1.0, n + 1), np.array([0.0, 1.0]), np.array([0.0, 1.0])]
     dV = 1.0 / n
@@ -460,20 +461,36 @@ def _deceleration_stiff(tau, pusher=O.OP_EM):
                      species_mass=(eps * dV,), species_tau=(tau,), pusher=pusher)
     q = [(np.arange(n) + 0.5) / n, np.full(n, 0.5), np.full(n, 0.5)]
     p = [np.ones(n), np.zeros(n), np.zeros(n)]
-    vg = -1.0
+    pg = [np.full(n, -1.0), np.zeros(n), np.zeros(n)]
     rho = np.ones(n)
     active = np.ones(n, np.uint8)
     dt, tf = 1.0, 10
     vp_hist = [p[0].mean()]
     for s in range(tf):
-        vhalf = vg + 0.5 * dt * eps * (p[0].mean() - vg) / max(tau, dt)   # predictor
-        pg = [np.full(n, vhalf), np.zeros(n), np.zeros(n)]
-        dep, _ = O.step(prob, q, p, active, s * dt, dt, rho, pg)
-        vg = vg + dep[:, 0].mean() / (1.0 * dV)                            # corrector
+        _, half = O.gas_predictor(prob, q, p, active, dt, rho, pg)      # predictor
+        dep, _ = O.step(prob, q, p, active, s * dt, dt, rho, half)
+        pg = [pg[c] + dep[:, c] / (rho * dV) for c in range(3)]       # corrector
         vp_hist.append(p[0].mean())
     t = np.arange(tf + 1) * dt
     exact = np.exp(-(1 + eps) * t / tau)
     return np.abs(np.array(vp_hist) - exact).mean(), vp_hist
+
+
+def test_gas_predictor_single_zone_closed_form():
+    """Eqs. Delta_vp, f_D: a grain at rest in the middle of one zone of a
+    1-zone periodic box with uniform gas; the predicted half-step gas velocity
+    is v_g + (dt/2) (m / (rho dV)) (v_p - v_g) / max(tau, dt), for tau below and
+    above dt."""
+    edges = [np.array([0.0, 2.0]), np.array([0.0, 1.0]), np.array([0.0, 1.0])]
+    for tau, dt in ((0.3, 0.1), (0.3, 1.0), (INF, 0.5)):
+        prob = O.Problem(geom=O.OG_CARTESIAN, edges=edges, species_mass=(0.4,),
+                         species_tau=(tau,))
+        imp, half = O.gas_predictor(prob, [[1.0], [0.5], [0.5]], [[0.7], [-0.2], [0.1]],
+                                    np.ones(1, np.uint8), dt, np.array([1.5]),
+                                    [np.array([0.1]), np.array([0.3]), np.array([-0.4])])
+        k = 0.5 * dt * 0.4 / (1.5 * 2.0) / max(tau, dt)
+        for c, (vp, vg) in enumerate(((0.7, 0.1), (-0.2, 0.3), (0.1, -0.4))):
+            assert half[c][0] == pytest.approx(vg + k * (vp - vg), rel=1e-14, abs=1e-16)
 
 
 @pytest.mark.parametrize("tau", [0.2, 0.02])
