@@ -138,6 +138,13 @@ typedef struct dust_options {
                               sort order (0 = default: 8x8x8 in 3-D, 16x16 in
                               2-D; clipped to the grid)                       */
     int pusher;            /* DUST_PUSHER_EM (0) or DUST_PUSHER_SEMI_IMPLICIT */
+    int gas_predictor;     /* 1: before each step, advance the gas by half a
+                              step with the drag of the grains at x^n (Sec. 3.1,
+                              Eqs. Delta_vp and f_D, tau_s <- max(tau_s, dt));
+                              the step gathers from that prediction, and with
+                              feedback_apply the deposit corrects the gas at
+                              t^n, as the paper's predictor-corrector does for
+                              the drag term (no hydrodynamic fluxes here)    */
 } dust_options;
 
 typedef struct dust_stats {

@@ -50,6 +50,10 @@ struct dust_ctx {
     bool need_sort = true;
     void *d_gas = nullptr;
     unsigned long long *d_dep = nullptr;
+    // gas half-step predictor (dust_options.gas_predictor): its impulse and
+    // the predicted gas the step gathers from
+    unsigned long long *d_pred = nullptr;
+    void *d_gas_half = nullptr;
     unsigned int *d_status = nullptr;
     unsigned int *h_status = nullptr;
 
@@ -375,6 +379,25 @@ __global__ void get_particles_kernel(int geom, StoreDev<Real> s, double *q0, dou
 
 // Feedback on the gas momentum: rho p_g += dP / dV (corrector term of the
 // RK2 step, Sec. 3.1; the gas is otherwise held fixed).
+// Gas predicted to the half step: out = gas + impulse / (rho dV) in the three
+// momentum-like channels (Sec. 3.1 predictor with the drag term only).
+template <typename Real>
+__global__ void predict_apply_kernel(GridDev g, double quantum, const Real *gas,
+                                     const unsigned long long *imp, Real *out)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((int64_t)g.n[0] * g.n[1]));
+    const double s = quantum / ((double)gas[4 * c] * g.dvol[0][i] * g.dvol[1][j] * g.dvol[2][k]);
+    out[4 * c] = gas[4 * c];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+        out[4 * c + 1 + ch] = (Real)((double)gas[4 * c + 1 + ch] +
+                                     (double)(long long)imp[4 * c + ch] * s);
+}
+
 template <typename Real>
 __global__ void apply_feedback_kernel(GridDev g, double quantum, Real *gas,
                                       const unsigned long long *dep)
@@ -708,6 +731,33 @@ int run_step(dust_ctx *ctx, double dt)
     {
         GroupTimer timer(ctx, dust_ctx::GROUP_OTHER);
         CU(cudaMemsetAsync(ctx->d_dep, 0, ctx->ncell * 4 * sizeof(unsigned long long), ctx->stream));
+        if (ctx->opt.gas_predictor) {
+            // predictor: drag of the grains at x^n advances the gas by dt/2;
+            // the step gathers from the prediction, the feedback corrects the
+            // gas at t^n
+            CU(cudaMemsetAsync(ctx->d_pred, 0, ctx->ncell * 4 * sizeof(unsigned long long), ctx->stream));
+            StepArgs<Real> pa = a;
+            pa.dep = ctx->d_pred;
+            const int tsc = ctx->opt.weight == DUST_WEIGHT_TSC;
+            cudaError_t pe;
+            switch (ctx->geom.kind * 2 + tsc) {
+            case 0: pe = launch_predict_gas<Real, GEOM_CART, 0>(pa, ctx->stream); break;
+            case 1: pe = launch_predict_gas<Real, GEOM_CART, 1>(pa, ctx->stream); break;
+            case 2: pe = launch_predict_gas<Real, GEOM_SB, 0>(pa, ctx->stream); break;
+            case 3: pe = launch_predict_gas<Real, GEOM_SB, 1>(pa, ctx->stream); break;
+            case 4: pe = launch_predict_gas<Real, GEOM_CYL, 0>(pa, ctx->stream); break;
+            case 5: pe = launch_predict_gas<Real, GEOM_CYL, 1>(pa, ctx->stream); break;
+            case 6: pe = launch_predict_gas<Real, GEOM_SPH, 0>(pa, ctx->stream); break;
+            default: pe = launch_predict_gas<Real, GEOM_SPH, 1>(pa, ctx->stream); break;
+            }
+            CU(pe);
+            predict_apply_kernel<Real><<<blocks_for(ctx->ncell), 256, 0, ctx->stream>>>(
+                ctx->g, ctx->quantum, static_cast<const Real *>(ctx->d_gas), ctx->d_pred,
+                static_cast<Real *>(ctx->d_gas_half));
+            CU(cudaGetLastError());
+            if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_OTHER] += 2;
+            a.gas = static_cast<const Real *>(ctx->d_gas_half);
+        }
     }
     cudaError_t e;
     GroupTimer *step_timer = new GroupTimer(ctx, dust_ctx::GROUP_STEP);
@@ -768,6 +818,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         return fail(nullptr, DUST_EINVAL, "bad precision");
     if (opt->pusher != DUST_PUSHER_EM && opt->pusher != DUST_PUSHER_SEMI_IMPLICIT)
         return fail(nullptr, DUST_EINVAL, "bad pusher");
+    if (opt->gas_predictor != 0 && opt->gas_predictor != 1)
+        return fail(nullptr, DUST_EINVAL, "gas_predictor must be 0 or 1");
     if (opt->pusher == DUST_PUSHER_SEMI_IMPLICIT && geom->kind != DUST_CARTESIAN &&
         geom->kind != DUST_SHEARING_BOX)
         return fail(nullptr, DUST_EINVAL,
@@ -881,6 +933,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     const int64_t nk = g.nkeys;
     if (cudaMalloc(&ctx->d_gas, ncell * 4 * ctx->rsz) != cudaSuccess ||
         dalloc(&ctx->d_dep, ncell * 4) != cudaSuccess ||
+        (opt->gas_predictor && (dalloc(&ctx->d_pred, ncell * 4) != cudaSuccess ||
+                                cudaMalloc(&ctx->d_gas_half, ncell * 4 * ctx->rsz) != cudaSuccess)) ||
         dalloc(&ctx->d_status, ST_WORDS) != cudaSuccess ||
         dalloc(&ctx->d_count, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_count_next, nk + 2) != cudaSuccess ||
@@ -1207,6 +1261,8 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     }
     dfree(ctx->d_gas);
     dfree(ctx->d_dep);
+    dfree(ctx->d_pred);
+    dfree(ctx->d_gas_half);
     dfree(ctx->d_status);
     dfree(ctx->d_count);
     dfree(ctx->d_count_next);

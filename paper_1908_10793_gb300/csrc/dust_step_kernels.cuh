@@ -190,6 +190,71 @@ cudaError_t launch_step_per_grain(const StepArgs<Real> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------- predictor ----
+// Gas half-step drag predictor (Sec. 3.1, Eqs. Delta_vp and f_D, with
+// tau_s <- max(tau_s, |dt|) against the predictor's stiffness): one thread per
+// grain gathers the gas at the grain's position x^n (weights of Sec. 3.4),
+// and deposits the impulse dt/2 (m/tau') W (v_p - v_g(x^n)) per zone with the
+// per-grain fixed-point rule into A.dep (three momentum-like channels).
+template <typename Real, int GEOM, int WEIGHT>
+__global__ void __launch_bounds__(kStepThreads)
+predict_gas_kernel(const StepArgs<Real> A)
+{
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= A.s.n) return;
+    const double q[3] = {A.s.q[0][gi], A.s.q[1][gi], A.s.q[2][gi]};
+    if (isnan(q[0])) return;
+    const Real pn[3] = {A.s.p[0][gi], A.s.p[1][gi], A.s.p[2][gi]};
+    const int sp = A.s.species ? A.s.species[gi] : 0;
+    int host[3];
+    Real w[3][3];
+    float iw[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) zone_weights<Real, GEOM>(A.g, d, WEIGHT, q[d], host[d], w[d], iw[d]);
+    Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
+    const int n0 = A.g.n[0], n1 = A.g.n[1], n2 = A.g.n[2];
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) {
+        if (n2 <= 1 && c3 != 1) continue;
+        const int iz = node_of(host[2], c3 - 1, n2, A.g.bc[2]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (n1 <= 1 && b != 1) continue;
+            const int iy = node_of(host[1], b - 1, n1, A.g.bc[1]);
+            const Real wyz = w[1][b] * w[2][c3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (n0 <= 1 && a != 1) continue;
+                const int ix = node_of(host[0], a - 1, n0, A.g.bc[0]);
+                const Real W = w[0][a] * wyz;
+                Real f[4];
+                load_gas<Real>(A.gas, ix + (int64_t)n0 * (iy + (int64_t)n1 * iz), f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] += W * f[c];
+            }
+        }
+    }
+    const Real value = A.s.param ? A.s.param[gi] : (Real)A.sp.tau[sp];
+    const Real tau = stopping_time<Real, GEOM>(A.ph, A.sp.mode[sp], value, q, acc[0]);
+    const Real dt = (Real)A.dt;
+    const Real taup = fmax(tau, fabs(dt));
+    const Real coef = Real(0.5) * dt * (Real)(A.sp.mass[sp] * A.inv_quantum) / taup;
+    Real Dq[4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Dq[c] = coef * (pn[c] - acc[1 + c]);
+    Dq[3] = Real(0);
+    deposit_fixed<Real>(A.g, A.dep, host, w, Dq, A.status);
+}
+
+template <typename Real, int GEOM, int WEIGHT>
+cudaError_t launch_predict_gas(const StepArgs<Real> &a, cudaStream_t s)
+{
+    if (a.s.n == 0) return cudaSuccess;
+    const int64_t blocks = (a.s.n + kStepThreads - 1) / kStepThreads;
+    predict_gas_kernel<Real, GEOM, WEIGHT><<<(unsigned)blocks, kStepThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- sort ----
 // Sort key of a grain for a step of half length h: the zone of its predicted
 // half-step position (first half drift, periodic wrap, clamped onto the grid

@@ -35,19 +35,43 @@ def to_physical(w, q, p):
     return v
 
 
-def run_oracle(w, steps, dt=None, feedback=None):
-    """Returns (q, v physical, active, last deposit, gas pg, pg history)."""
+def run_oracle(w, steps, dt=None, feedback=None, predictor=False):
+    """Returns (q, v physical, active, last deposit, gas pg).  predictor: the
+    gas half-step drag predictor before every step; the step gathers from it
+    and the feedback (if on) corrects the gas at t^n."""
     dt = w.dt if dt is None else dt
-    prob = oracle_problem(w, feedback)
+    fb = w.feedback if feedback is None else feedback
+    prob = oracle_problem(w, 0 if predictor else feedback)
     q = [x.copy() for x in w.q]
     p = to_momentum(w, q, w.v)
     rho = w.rho.copy()
     pg = O.gas_momentum(prob, w.vgas)
     active = np.ones(w.ngrains, np.uint8)
     dep = None
+    if predictor:
+        dV = zone_volumes(w)
     for s in range(steps):
-        dep, _ = O.step(prob, q, p, active, s * dt, dt, rho, pg, w.species, w.param)
+        if predictor:
+            _, half = O.gas_predictor(prob, q, p, active, dt, rho, pg, w.species, w.param)
+            dep, _ = O.step(prob, q, p, active, s * dt, dt, rho, half, w.species, w.param)
+            if fb:
+                pg = [pg[c] + dep[:, c] / (rho * dV) for c in range(3)]
+        else:
+            dep, _ = O.step(prob, q, p, active, s * dt, dt, rho, pg, w.species, w.param)
     return q, to_physical(w, q, p), active, dep, pg
+
+
+def zone_volumes(w):
+    """Zone volumes in storage order (R dR dphi dz, r^2 dr sin dtheta dphi)."""
+    e = w.edges
+    d = [np.diff(x) for x in e]
+    if w.geom == O.OG_CYLINDRICAL:
+        d[0] = 0.5 * np.diff(e[0] ** 2)
+    elif w.geom == O.OG_SPHERICAL:
+        d[0] = np.diff(e[0] ** 3) / 3.0
+        d[1] = -np.diff(np.cos(e[1]))
+    Z, Y, X = np.meshgrid(d[2], d[1], d[0], indexing="ij")
+    return (X * Y * Z).ravel()
 
 
 def run_gpu(w, steps, precision, dt=None, feedback=None, **kw):
