@@ -740,15 +740,35 @@ int run_step(dust_ctx *ctx, double dt)
             pa.dep = ctx->d_pred;
             const int tsc = ctx->opt.weight == DUST_WEIGHT_TSC;
             cudaError_t pe;
-            switch (ctx->geom.kind * 2 + tsc) {
-            case 0: pe = launch_predict_gas<Real, GEOM_CART, 0>(pa, ctx->stream); break;
-            case 1: pe = launch_predict_gas<Real, GEOM_CART, 1>(pa, ctx->stream); break;
-            case 2: pe = launch_predict_gas<Real, GEOM_SB, 0>(pa, ctx->stream); break;
-            case 3: pe = launch_predict_gas<Real, GEOM_SB, 1>(pa, ctx->stream); break;
-            case 4: pe = launch_predict_gas<Real, GEOM_CYL, 0>(pa, ctx->stream); break;
-            case 5: pe = launch_predict_gas<Real, GEOM_CYL, 1>(pa, ctx->stream); break;
-            case 6: pe = launch_predict_gas<Real, GEOM_SPH, 0>(pa, ctx->stream); break;
-            default: pe = launch_predict_gas<Real, GEOM_SPH, 1>(pa, ctx->stream); break;
+            if (ctx->opt.kernel == DUST_KERNEL_PER_GRAIN) {
+                // one thread per grain, global atomics (any store order)
+                switch (ctx->geom.kind * 2 + tsc) {
+                case 0: pe = launch_predict_gas<Real, GEOM_CART, 0>(pa, ctx->stream); break;
+                case 1: pe = launch_predict_gas<Real, GEOM_CART, 1>(pa, ctx->stream); break;
+                case 2: pe = launch_predict_gas<Real, GEOM_SB, 0>(pa, ctx->stream); break;
+                case 3: pe = launch_predict_gas<Real, GEOM_SB, 1>(pa, ctx->stream); break;
+                case 4: pe = launch_predict_gas<Real, GEOM_CYL, 0>(pa, ctx->stream); break;
+                case 5: pe = launch_predict_gas<Real, GEOM_CYL, 1>(pa, ctx->stream); break;
+                case 6: pe = launch_predict_gas<Real, GEOM_SPH, 0>(pa, ctx->stream); break;
+                default: pe = launch_predict_gas<Real, GEOM_SPH, 1>(pa, ctx->stream); break;
+                }
+            } else {
+                // tiles of the last sort (through the pending permutation when
+                // the step kernel finishes the sort); same integers
+                TiledArgs<Real> pt{};
+                pt.s = pa;
+                pt.key_off = ctx->d_count;
+                pt.perm = ctx->perm_pending ? ctx->d_pair_src : nullptr;
+                switch (ctx->geom.kind * 2 + tsc) {
+                case 0: pe = launch_predict_tiled<Real, GEOM_CART, 0>(pt, ctx->stream); break;
+                case 1: pe = launch_predict_tiled<Real, GEOM_CART, 1>(pt, ctx->stream); break;
+                case 2: pe = launch_predict_tiled<Real, GEOM_SB, 0>(pt, ctx->stream); break;
+                case 3: pe = launch_predict_tiled<Real, GEOM_SB, 1>(pt, ctx->stream); break;
+                case 4: pe = launch_predict_tiled<Real, GEOM_CYL, 0>(pt, ctx->stream); break;
+                case 5: pe = launch_predict_tiled<Real, GEOM_CYL, 1>(pt, ctx->stream); break;
+                case 6: pe = launch_predict_tiled<Real, GEOM_SPH, 0>(pt, ctx->stream); break;
+                default: pe = launch_predict_tiled<Real, GEOM_SPH, 1>(pt, ctx->stream); break;
+                }
             }
             CU(pe);
             predict_apply_kernel<Real><<<blocks_for(ctx->ncell), 256, 0, ctx->stream>>>(

@@ -15,6 +15,10 @@ template cudaError_t launch_step_slab<GEOM_CART, 0>(const TiledArgs<float> &, cu
 template cudaError_t launch_step_slab<GEOM_CART, 2>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_CART>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_CART>(const SortArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<float, GEOM_CART, 0>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<float, GEOM_CART, 1>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<double, GEOM_CART, 0>(const TiledArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<double, GEOM_CART, 1>(const TiledArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_gas<float, GEOM_CART, 0>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_gas<float, GEOM_CART, 1>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_gas<double, GEOM_CART, 0>(const StepArgs<double> &, cudaStream_t);

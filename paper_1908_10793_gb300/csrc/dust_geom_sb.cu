@@ -16,6 +16,10 @@ template cudaError_t launch_step_slab<GEOM_SB, 1>(const TiledArgs<float> &, cuda
 template cudaError_t launch_step_slab<GEOM_SB, 2>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_SB>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_SB>(const SortArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<float, GEOM_SB, 0>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<float, GEOM_SB, 1>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<double, GEOM_SB, 0>(const TiledArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<double, GEOM_SB, 1>(const TiledArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_gas<float, GEOM_SB, 0>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_gas<float, GEOM_SB, 1>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_gas<double, GEOM_SB, 0>(const StepArgs<double> &, cudaStream_t);

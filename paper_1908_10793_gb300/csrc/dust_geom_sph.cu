@@ -14,6 +14,10 @@ template cudaError_t launch_step_tiled<double, GEOM_SPH, 1>(const TiledArgs<doub
 template cudaError_t launch_step_slab<GEOM_SPH, 0>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_SPH>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_SPH>(const SortArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<float, GEOM_SPH, 0>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<float, GEOM_SPH, 1>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<double, GEOM_SPH, 0>(const TiledArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<double, GEOM_SPH, 1>(const TiledArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_gas<float, GEOM_SPH, 0>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_gas<float, GEOM_SPH, 1>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_gas<double, GEOM_SPH, 0>(const StepArgs<double> &, cudaStream_t);

@@ -164,6 +164,9 @@ cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s);
 template <typename Real, int GEOM, int WEIGHT>
 cudaError_t launch_predict_gas(const StepArgs<Real> &a, cudaStream_t s);
 
+template <typename Real, int GEOM, int WEIGHT>
+cudaError_t launch_predict_tiled(const TiledArgs<Real> &a, cudaStream_t s);
+
 template <typename Real>
 cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s, bool gather);
 

@@ -488,3 +488,166 @@ cudaError_t launch_step_tiled(const TiledArgs<Real> &a, cudaStream_t s)
 }
 
 }  // namespace dust
+
+namespace dust {
+
+// Tiled gas half-step predictor (same arithmetic and fixed-point rule as
+// predict_gas_kernel): one block per tile of zones stages the tile's gas box
+// and an int64 impulse box in shared memory, takes the grains sorted into the
+// tile (through the sort's permutation when the step kernel will finish the
+// sort), gathers at x^n from the box and adds each grain's pieces to the box
+// with 32-bit atomics; grains whose stencil at x^n leaves the box use global
+// memory.  The per-grain rule makes the integers independent of the order.
+template <typename Real, int GEOM, int WEIGHT>
+__global__ void __launch_bounds__(kTiledThreads)
+predict_tiled_kernel(const __grid_constant__ TiledArgs<Real> TA)
+{
+    const StepArgs<Real> &A = TA.s;
+    const GridDev &g = A.g;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = blockIdx.x;
+    const int64_t kbase = (int64_t)tile * g.tvol;
+    const int g0 = TA.key_off[kbase], g1 = TA.key_off[kbase + g.tvol];
+    if (g1 <= g0) return;
+    int B[3], o[3];
+    {
+        const int tc[3] = {tile % g.nt[0], (tile / g.nt[0]) % g.nt[1], tile / (g.nt[0] * g.nt[1])};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int H = g.n[d] > 1 ? 1 : 0;
+            B[d] = g.T[d] + 2 * H;
+            o[d] = tc[d] * g.T[d] - H;
+        }
+    }
+    const int bvol = B[0] * B[1] * B[2];
+    unsigned long long *simp = reinterpret_cast<unsigned long long *>(smem_raw);   // [3][bvol]
+    Real *sgas = reinterpret_cast<Real *>(smem_raw + (size_t)bvol * 3 * sizeof(long long));
+    for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
+        const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
+        const int i = map_zone(o[0] + bx, g.n[0], g.bc[0]);
+        const int j = map_zone(o[1] + by, g.n[1], g.bc[1]);
+        const int k = map_zone(o[2] + bz, g.n[2], g.bc[2]);
+        Real v[4];
+        load_gas<Real>(A.gas, i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), v);
+        smem_gas_store<Real>(sgas, lin, v);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) simp[c * bvol + lin] = 0ull;
+    }
+    __syncthreads();
+    const Real dt = (Real)A.dt;
+    for (int gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
+        const int src = TA.perm ? TA.perm[gi] : gi;
+        const double q[3] = {A.s.q[0][src], A.s.q[1][src], A.s.q[2][src]};
+        if (isnan(q[0])) continue;
+        const Real pn[3] = {A.s.p[0][src], A.s.p[1][src], A.s.p[2][src]};
+        const int sp = A.s.species ? A.s.species[src] : 0;
+        int host[3];
+        Real w[3][3];
+        float iw[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) zone_weights<Real, GEOM>(g, d, WEIGHT, q[d], host[d], w[d], iw[d]);
+        int lb[3];
+        bool inbox = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int l = host[d] - o[d];
+            if (g.n[d] > 1 && g.bc[d] == DUST_BC_PERIODIC) {
+                if (l < 0) l += g.n[d];
+                else if (l >= B[d]) l -= g.n[d];
+            }
+            lb[d] = l;
+            if (g.n[d] > 1) inbox &= (l >= 1) && (l <= B[d] - 2);
+        }
+        Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll 1
+        for (int nd = 0; nd < 27; ++nd) {
+            const int a = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
+            if ((g.n[0] <= 1 && a != 1) || (g.n[1] <= 1 && b != 1) || (g.n[2] <= 1 && c3 != 1)) continue;
+            const Real W = w[0][a] * (w[1][b] * w[2][c3]);
+            Real f[4];
+            if (inbox) {
+                smem_gas_load<Real>(sgas, (lb[0] + a - 1) + B[0] * ((lb[1] + b - 1) + B[1] * (lb[2] + c3 - 1)), f);
+            } else {
+                const int ix = node_of(host[0], a - 1, g.n[0], g.bc[0]);
+                const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
+                const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
+                load_gas<Real>(A.gas, ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz), f);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] += W * f[c];
+        }
+        const Real value = A.s.param ? A.s.param[src] : (Real)A.sp.tau[sp];
+        const Real tau = stopping_time<Real, GEOM>(A.ph, A.sp.mode[sp], value, q, acc[0]);
+        const Real taup = fmax(tau, fabs(dt));
+        const Real coef = Real(0.5) * dt * (Real)(A.sp.mass[sp] * A.inv_quantum) / taup;
+        Real Dq[4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Dq[c] = coef * (pn[c] - acc[1 + c]);
+        Dq[3] = Real(0);
+        if (!inbox) {
+            deposit_fixed<Real>(g, A.dep, host, w, Dq, A.status);
+            continue;
+        }
+        // per-grain rule into the shared box: pieces for the other nodes,
+        // the host takes the remainder
+        long long rest[3];
+        bool big = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            big |= !(fabs((double)Dq[c]) < 4.5e15);
+            rest[c] = rround(Dq[c]);
+        }
+        if (big) atomicOr(&A.status[ST_FLAGS], DUST_FLAG_OVERFLOW);
+        const int hl = lb[0] + B[0] * (lb[1] + B[1] * lb[2]);
+#pragma unroll 1
+        for (int nd = 0; nd < 27; ++nd) {
+            const int a = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
+            if (nd == 13 || (g.n[0] <= 1 && a != 1) || (g.n[1] <= 1 && b != 1) ||
+                (g.n[2] <= 1 && c3 != 1))
+                continue;
+            const Real W = w[0][a] * (w[1][b] * w[2][c3]);
+            const int lin = hl + (a - 1) + B[0] * ((b - 1) + B[1] * (c3 - 1));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long piece = rround(W * Dq[c]);
+                if (piece != 0) {
+                    shared_add_i64(&simp[c * bvol + lin], piece);
+                    rest[c] -= piece;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (rest[c] != 0) shared_add_i64(&simp[c * bvol + hl], rest[c]);
+    }
+    __syncthreads();
+    for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
+        const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
+        const int i = map_zone(o[0] + bx, g.n[0], g.bc[0]);
+        const int j = map_zone(o[1] + by, g.n[1], g.bc[1]);
+        const int k = map_zone(o[2] + bz, g.n[2], g.bc[2]);
+        const int64_t gz = i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const unsigned long long v = simp[c * bvol + lin];
+            if (v != 0ull) atomicAdd(&A.dep[4 * gz + c], v);
+        }
+    }
+}
+
+template <typename Real, int GEOM, int WEIGHT>
+cudaError_t launch_predict_tiled(const TiledArgs<Real> &a, cudaStream_t s)
+{
+    const GridDev &g = a.s.g;
+    const int ntiles = g.nt[0] * g.nt[1] * g.nt[2];
+    size_t bvol = 1;
+    for (int d = 0; d < 3; ++d) bvol *= (size_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
+    const size_t smem = bvol * (3 * sizeof(long long) + 4 * sizeof(Real));
+    auto kern = predict_tiled_kernel<Real, GEOM, WEIGHT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ntiles, kTiledThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace dust
