@@ -15,7 +15,9 @@
  *
  *   1. half drift of the coordinates          (Eq. exp_midpoint; Eqs. B.1 drift)
  *   2. host zone and 1-D weights at x^{n+1/2}  (Sec. 3.4, Eqs. weight, b0, b1,
- *                                              CIC/TSC_cylindrical, App. C)
+ *                                              CIC/TSC_cylindrical, App. C;
+ *                                              or the volume weights of Eq.
+ *                                              CIC_vol)
  *   3. gather of gas rho and momentum-like velocity (Eq. Delta_vp)
  *   4. E = exp(-dt/tau), h1 = tau (1 - exp(-dt/tau))   (Eqs. phi1, h1)
  *   5. kick, per geometry                      (Eq. kick_modified; App. B.1, B.2)
@@ -51,6 +53,7 @@
 
 #define OW_CIC 0
 #define OW_TSC 1
+#define OW_VOLUME 2  /* traditional volume weighting, Eq. CIC_vol (comparator) */
 
 #define OP_EM 0             /* exponential midpoint, Sec. 3.2.2                */
 #define OP_SEMI_IMPLICIT 1  /* semi-implicit drift-kick-drift, Sec. 3.2.1       */
@@ -68,6 +71,9 @@
 #define W1_SPH_R_TSC 5
 #define W1_SPH_TH_CIC 6
 #define W1_SPH_TH_TSC 7
+#define W1_CYL_R_VOL 8   /* linear interpolation in R^2 between zone centres   */
+#define W1_SPH_R_VOL 9   /* ... in r^3                                          */
+#define W1_SPH_TH_VOL 10 /* ... in the polar-angle volume coordinate -cos(th)  */
 
 typedef struct {
     int geom;             /* OG_*                                             */
@@ -78,7 +84,7 @@ typedef struct {
     int n[3];             /* zones per direction (1 = direction not gridded)  */
     const double *edges[3]; /* n[d]+1 increasing zone edges per direction     */
     int bc[3];            /* OB_* per direction                               */
-    int weight;           /* OW_CIC or OW_TSC                                 */
+    int weight;           /* OW_CIC, OW_TSC or OW_VOLUME                      */
     int n_species;
     const double *sp_mass;
     const int *sp_tau_mode;
@@ -234,15 +240,105 @@ void oracle_weights_1d(int kind, double x, double lo, double hi, double w[3])
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Traditional volume weighting, Eq. CIC_vol (Sec. 3.4): the Cartesian CIC  */
+/* rule with the linear coordinate replaced by the volume coordinate, i.e.  */
+/* linear interpolation in V between the centres of the two zones around x. */
+/* The paper prints the cylindrical radial case, V = R^2; the same          */
+/* statement gives V = r^3 for the spherical radius and V = -cos(theta) for */
+/* the polar angle (the volume element is R dR, r^2 dr, sin(theta) dtheta). */
+/* Readings: the two nodes are the actual zone centres (on a non-uniform    */
+/* grid the neighbours' own centres), with a ghost centre one edge-zone     */
+/* width beyond each end of the grid; the volume-coordinate difference of   */
+/* two points is the volume of the shell between them, |dV| integrated from */
+/* one to the other, which stays positive when a ghost centre lies across   */
+/* the axis (R < 0) or a pole (theta < 0 or theta > pi).                     */
+/* ------------------------------------------------------------------------- */
+
+/* Volume (per unit of the other coordinates, up to a constant factor) of
+ * the shell between coordinates b <= a for a volume-weight kind. */
+static double shell_volume(int kind, double b, double a)
+{
+    if (kind == W1_CYL_R_VOL) {
+        /* int_b^a 2|R| dR: a^2 - b^2 on each side of the axis */
+        if (b >= 0.0 || a <= 0.0) return fabs((a - b) * (a + b));
+        return a * a + b * b;
+    }
+    if (kind == W1_SPH_R_VOL) {
+        /* int_b^a 3 r^2 dr = a^3 - b^3 */
+        return (a - b) * (a * a + a * b + b * b);
+    }
+    /* polar angle: int_b^a |sin t| dt, split where sin changes sign; on a
+     * piece [u, v] of one sign it is |cos u - cos v| = |2 sin((u+v)/2)
+     * sin((v-u)/2)| */
+    double cuts[4] = {b, 0.0, 3.14159265358979323846, a};
+    double total = 0.0;
+    double u = b;
+    for (int k = 1; k < 4; k++) {
+        double v = k < 3 ? cuts[k] : a;
+        if (v <= u) continue;
+        if (v > a) v = a;
+        total += fabs(2.0 * sin(0.5 * (u + v)) * sin(0.5 * (v - u)));
+        u = v;
+    }
+    return total;
+}
+
+/* Centre of zone k of a direction with n zones; ghost centres one edge-zone
+ * width beyond the ends. */
+static double zone_centre(const double *edges, int n, int k)
+{
+    if (k < 0) return 0.5 * (edges[0] + edges[1]) - (edges[1] - edges[0]);
+    if (k >= n) return 0.5 * (edges[n - 1] + edges[n]) + (edges[n] - edges[n - 1]);
+    return 0.5 * (edges[k] + edges[k + 1]);
+}
+
+/* Weights of zones (i-1, i, i+1) for a grain at x hosted by zone i. */
+void oracle_weights_vol(int kind, double x, const double *edges, int n, int i, double w[3])
+{
+    double c = zone_centre(edges, n, i);
+    w[0] = 0.0;
+    w[2] = 0.0;
+    if (x >= c) {
+        /* Eq. CIC_vol with R_i = c, R_{i+1} = the next centre */
+        double cp = zone_centre(edges, n, i + 1);
+        w[2] = shell_volume(kind, c, x) / shell_volume(kind, c, cp);
+        w[1] = 1.0 - w[2];
+    } else {
+        /* Eq. CIC_vol with R_i = the previous centre, R_{i+1} = c */
+        double cm = zone_centre(edges, n, i - 1);
+        w[0] = shell_volume(kind, x, c) / shell_volume(kind, cm, c);
+        w[1] = 1.0 - w[0];
+    }
+}
+
 /* Which 1-D weight formula each direction uses (Sec. 3.4: the product of
  * three 1-D factors, W = W(x1) W(x2) W(x3)). */
 static int weight_kind(const oracle_problem *P, int d)
 {
+    if (P->weight == OW_VOLUME) {
+        /* the volume coordinate of a Cartesian-like direction is the
+         * coordinate itself: plain CIC there */
+        if (P->geom == OG_CYLINDRICAL && d == 0) return W1_CYL_R_VOL;
+        if (P->geom == OG_SPHERICAL && d == 0) return W1_SPH_R_VOL;
+        if (P->geom == OG_SPHERICAL && d == 1) return W1_SPH_TH_VOL;
+        return W1_CART_CIC;
+    }
     int tsc = P->weight == OW_TSC;
     if (P->geom == OG_CYLINDRICAL && d == 0) return tsc ? W1_CYL_R_TSC : W1_CYL_R_CIC;
     if (P->geom == OG_SPHERICAL && d == 0) return tsc ? W1_SPH_R_TSC : W1_SPH_R_CIC;
     if (P->geom == OG_SPHERICAL && d == 1) return tsc ? W1_SPH_TH_TSC : W1_SPH_TH_CIC;
     return tsc ? W1_CART_TSC : W1_CART_CIC;
+}
+
+/* 1-D weights of direction d for a grain at x hosted by zone i. */
+static void direction_weights(const oracle_problem *P, int d, int kind, double x, int i,
+                              double w[3])
+{
+    if (kind >= W1_CYL_R_VOL)
+        oracle_weights_vol(kind, x, P->edges[d], P->n[d], i, w);
+    else
+        oracle_weights_1d(kind, x, P->edges[d][i], P->edges[d][i + 1], w);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -464,8 +560,7 @@ int64_t oracle_step(const oracle_problem *P,
                 continue;
             }
             host[d] = oracle_locate(P->edges[d], P->n[d], qm[d]);
-            oracle_weights_1d(wk[d], qm[d], P->edges[d][host[d]],
-                              P->edges[d][host[d] + 1], w[d]);
+            direction_weights(P, d, wk[d], qm[d], host[d], w[d]);
         }
 
         /* 3. gather (Eq. Delta_vp) */
@@ -729,7 +824,7 @@ void oracle_gas_predictor(const oracle_problem *P,
                 continue;
             }
             host[d] = oracle_locate(P->edges[d], P->n[d], q[d]);
-            oracle_weights_1d(wk[d], q[d], P->edges[d][host[d]], P->edges[d][host[d] + 1], w[d]);
+            direction_weights(P, d, wk[d], q[d], host[d], w[d]);
         }
         double rg = 0.0, vg[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c < 3; c++)

@@ -13,11 +13,12 @@ import numpy as np
 
 OG_CARTESIAN, OG_SHEARING_BOX, OG_CYLINDRICAL, OG_SPHERICAL = 0, 1, 2, 3
 OB_PERIODIC, OB_OUTFLOW = 0, 1
-OW_CIC, OW_TSC = 0, 1
+OW_CIC, OW_TSC, OW_VOLUME = 0, 1, 2
 OT_CONST, OT_STOKES, OT_EPSTEIN = 0, 1, 2
 OP_EM, OP_SEMI_IMPLICIT = 0, 1
 (W1_CART_CIC, W1_CART_TSC, W1_CYL_R_CIC, W1_CYL_R_TSC, W1_SPH_R_CIC,
- W1_SPH_R_TSC, W1_SPH_TH_CIC, W1_SPH_TH_TSC) = range(8)
+ W1_SPH_R_TSC, W1_SPH_TH_CIC, W1_SPH_TH_TSC, W1_CYL_R_VOL, W1_SPH_R_VOL,
+ W1_SPH_TH_VOL) = range(11)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dust_oracle.c")
@@ -70,6 +71,9 @@ def _load():
             lib.oracle_weights_1d.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, dp]
             lib.oracle_weights_1d.restype = None
+            lib.oracle_weights_vol.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
+                                               ctypes.c_int, dp]
+            lib.oracle_weights_vol.restype = None
             lib.oracle_locate.argtypes = [dp, ctypes.c_int, ctypes.c_double]
             lib.oracle_locate.restype = ctypes.c_int
             lib.oracle_step.argtypes = [ctypes.POINTER(_ProblemC)] + [dp] * 6 + [
@@ -99,6 +103,15 @@ def weights_1d(kind, x, lo, hi):
     """Weights of zones (i-1, i, i+1) for a grain at x hosted by zone [lo, hi)."""
     w = np.zeros(3)
     _load().oracle_weights_1d(int(kind), float(x), float(lo), float(hi), _dp(w))
+    return w
+
+
+def weights_vol(kind, x, edges, i):
+    """Volume weights (Eq. CIC_vol) of zones (i-1, i, i+1) for a grain at x
+    hosted by zone i of the grid with the given edges."""
+    e = _f64(edges)
+    w = np.zeros(3)
+    _load().oracle_weights_vol(int(kind), float(x), _dp(e), len(e) - 1, int(i), _dp(w))
     return w
 
 

@@ -58,6 +58,16 @@ MUTATIONS = [
      "l10 = (1.0 - 0.5 * qq) * Om * dt;", "l10 = Om * dt;"),
     ("semi-implicit standard-frame Lambda sign", "                    l10 = Om * dt;\n",
      "                    l10 = -Om * dt;\n"),
+    ("volume weighting linear in R", "if (b >= 0.0 || a <= 0.0) return fabs((a - b) * (a + b));",
+     "if (b >= 0.0 || a <= 0.0) return fabs(a - b);"),
+    ("volume weighting ghost centre half a zone out",
+     "if (k < 0) return 0.5 * (edges[0] + edges[1]) - (edges[1] - edges[0]);",
+     "if (k < 0) return 0.5 * (edges[0] + edges[1]) - 0.5 * (edges[1] - edges[0]);"),
+    ("volume weighting polar shell signed across the pole",
+     "total += fabs(2.0 * sin(0.5 * (u + v)) * sin(0.5 * (v - u)));",
+     "total += 2.0 * sin(0.5 * (u + v)) * sin(0.5 * (v - u));"),
+    ("volume weighting r^2 instead of r^3", "return (a - b) * (a * a + a * b + b * b);",
+     "return (a - b) * (a + b);"),
 ]
 
 

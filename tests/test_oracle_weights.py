@@ -143,3 +143,115 @@ def test_locate_half_open_zones():
     assert O.locate(e, 0.25) == 1
     assert O.locate(e, np.nextafter(0.25, 0)) == 0
     assert O.locate(e, np.nextafter(1.0, 0)) == 3
+
+
+# --------------------------------------------------------------------------
+# Traditional volume weighting (Eq. CIC_vol): linear interpolation in the
+# volume coordinate V between the centres of the two zones around the grain.
+# The pins below use only what that statement fixes: V is R^2, r^3 or
+# -cos(theta), so interpolating V itself must return V(x) exactly, the two
+# weights sum to one and lie in [0, 1], the weight a zone receives is
+# continuous as the grain crosses zone edges (the nodes are the zone
+# centres), and the printed cylindrical case at a point.
+
+VOL_V = {
+    O.W1_CYL_R_VOL: lambda x: x * x,
+    O.W1_SPH_R_VOL: lambda x: x ** 3,
+    O.W1_SPH_TH_VOL: lambda x: -np.cos(x),
+}
+
+
+def _vol_grids():
+    log = np.geomspace(0.4, 2.5, 25)
+    return {
+        O.W1_CYL_R_VOL: [np.linspace(0.7, 1.5, 9), log, np.linspace(0.0, 1.0, 11)],
+        O.W1_SPH_R_VOL: [np.linspace(0.7, 1.5, 9), log, np.linspace(0.0, 1.0, 11)],
+        O.W1_SPH_TH_VOL: [np.linspace(np.pi / 2 - 0.3, np.pi / 2 + 0.3, 17),
+                          np.linspace(0.0, np.pi, 13),
+                          np.pi / 2 + np.array([-0.4, -0.25, -0.05, 0.02, 0.2, 0.45])],
+    }
+
+
+def _centres(e):
+    c = 0.5 * (e[1:] + e[:-1])
+    return np.concatenate([[c[0] - (e[1] - e[0])], c, [c[-1] + (e[-1] - e[-2])]])
+
+
+def test_volume_weights_printed_cylindrical_case():
+    """Eq. CIC_vol at R_i = 1, R_{i+1} = 1.1, R_p = 1.05 (zone centres of a
+    uniform grid of width 0.1): W_i = (1.21 - 1.1025) / (1.21 - 1) by hand."""
+    edges = np.array([0.95, 1.05, 1.15, 1.25])
+    w = O.weights_vol(O.W1_CYL_R_VOL, 1.05, edges, 1)
+    assert abs(w[0] - 0.1075 / 0.21) < 1e-14 and abs(w[1] - 0.1025 / 0.21) < 1e-14
+    assert w[2] == 0.0
+
+
+@pytest.mark.parametrize("kind", [O.W1_CYL_R_VOL, O.W1_SPH_R_VOL, O.W1_SPH_TH_VOL])
+def test_volume_weights_interpolate_the_volume_coordinate_exactly(kind):
+    rng = np.random.default_rng(7 + kind)
+    V = VOL_V[kind]
+    for e in _vol_grids()[kind]:
+        n = len(e) - 1
+        c = _centres(e)
+        for _ in range(200):
+            i = int(rng.integers(0, n))
+            x = rng.uniform(e[i], e[i + 1])
+            w = O.weights_vol(kind, x, e, i)
+            assert abs(w.sum() - 1.0) < 1e-14
+            assert np.all(w >= -1e-15) and np.all(w <= 1.0 + 1e-15)
+            assert w[0] == 0.0 or w[2] == 0.0    # two nodes only
+            # V interpolated exactly where no node lies across the axis
+            # (cylindrical) or a pole (polar angle); r^3 is the shell volume
+            # on both sides of the origin
+            if kind == O.W1_SPH_R_VOL:
+                inside = True
+            elif kind == O.W1_CYL_R_VOL:
+                inside = c[i] >= 0.0
+            else:
+                inside = c[i] >= 0.0 and c[i + 2] <= np.pi
+            if inside:
+                got = w[0] * V(c[i]) + w[1] * V(c[i + 1]) + w[2] * V(c[i + 2])
+                scale = abs(V(c[i + 2]) - V(c[i]))
+                assert abs(got - V(x)) <= 1e-12 * scale, (kind, e[0], x)
+
+
+@pytest.mark.parametrize("kind", [O.W1_CYL_R_VOL, O.W1_SPH_R_VOL, O.W1_SPH_TH_VOL])
+def test_volume_weights_continuous_across_zone_edges(kind):
+    for e in _vol_grids()[kind]:
+        n = len(e) - 1
+        for k in range(1, n):
+            h = 1e-9 * (e[k + 1] - e[k - 1])
+            below = O.weights_vol(kind, e[k] - h, e, k - 1)   # zones k-2, k-1, k
+            above = O.weights_vol(kind, e[k] + h, e, k)       # zones k-1, k, k+1
+            assert abs(below[1] - above[0]) < 1e-7 and abs(below[2] - above[1]) < 1e-7
+            assert below[0] == 0.0 and above[2] == 0.0
+
+
+def test_volume_weights_at_axis_and_pole_stay_in_unit_interval():
+    """Next to the axis (R grid from 0) and the poles (theta from 0 to pi)
+    the ghost centre lies across them; the shell volume keeps the weights in
+    [0, 1] and equal to the ratio of the shell volumes between the nodes."""
+    e = np.linspace(0.0, 1.0, 11)          # centre 0.05, ghost centre -0.05
+    for x in (0.0, 0.01, 0.049):
+        w = O.weights_vol(O.W1_CYL_R_VOL, x, e, 0)
+        # shell from x to 0.05 over the shell from -0.05 to 0.05, |dV| = 2|R| dR
+        assert abs(w[0] - (0.05 ** 2 - x * x) / (2 * 0.05 ** 2)) < 1e-14
+    et = np.linspace(0.0, np.pi, 13)       # centre pi/24, ghost centre -pi/24
+    h = np.pi / 24
+    for x in (0.0, 0.05, h * 0.999):
+        w = O.weights_vol(O.W1_SPH_TH_VOL, x, et, 0)
+        assert abs(w[0] - (np.cos(x) - np.cos(h)) / (2 * (1 - np.cos(h)))) < 1e-13
+        w = O.weights_vol(O.W1_SPH_TH_VOL, np.pi - x, et, 11)
+        assert abs(w[2] - (np.cos(x) - np.cos(h)) / (2 * (1 - np.cos(h)))) < 1e-13
+
+
+def test_volume_weights_tend_to_cic_far_from_the_axis():
+    """Zero curvature: R^2 and r^3 are nearly linear over a zone far from the
+    origin, so the weights approach the Cartesian CIC ones."""
+    e = 1e6 + np.linspace(0.0, 1.0, 5)
+    for kind in (O.W1_CYL_R_VOL, O.W1_SPH_R_VOL):
+        for x in (1e6 + 0.3, 1e6 + 0.6):
+            i = O.locate(e, x)
+            w = O.weights_vol(kind, x, e, i)
+            cic = O.weights_1d(O.W1_CART_CIC, x, e[i], e[i + 1])
+            assert np.allclose(w, cic, atol=1e-5)
