@@ -61,7 +61,17 @@ extern "C" {
 /* ---- enumerations ------------------------------------------------------ */
 enum { DUST_CARTESIAN = 0, DUST_SHEARING_BOX = 1, DUST_CYLINDRICAL = 2, DUST_SPHERICAL = 3 };
 enum { DUST_BC_PERIODIC = 0, DUST_BC_OUTFLOW = 1 };
-enum { DUST_WEIGHT_CIC = 0, DUST_WEIGHT_TSC = 1 };
+/* weighting factors (Sec. 3.4): DUST_WEIGHT_CIC and DUST_WEIGHT_TSC are the
+ * b0 / b1 shapes integrated over each zone with the geometry's measure (Eqs.
+ * weight, shape_curv; App. C).  DUST_WEIGHT_VOLUME is the traditional volume
+ * weighting the paper compares against (Eq. CIC_vol): linear interpolation in
+ * the volume coordinate (R^2, r^3, -cos theta) between the centres of the two
+ * zones around the grain, with a ghost centre one edge-zone width beyond each
+ * end of the grid; in directions whose volume coordinate is the coordinate
+ * itself (all of them in Cartesian and shearing-box geometries) it is CIC.
+ * Volume weighting runs on the tiled and per-grain kernels and computes its
+ * weights in double precision. */
+enum { DUST_WEIGHT_CIC = 0, DUST_WEIGHT_TSC = 1, DUST_WEIGHT_VOLUME = 2 };
 /* stopping time: DUST_TAU_CONST tau_s = value; DUST_TAU_STOKES tau_s =
  * value / Omega_K (Omega_K = sqrt(GM / R^3) at the cylindrical radius of the
  * half-step position; shearing box: value / Omega); DUST_TAU_EPSTEIN tau_s =
@@ -121,7 +131,7 @@ typedef struct dust_species {
 
 typedef struct dust_options {
     int precision;         /* DUST_FP64 or DUST_MIXED                           */
-    int weight;            /* DUST_WEIGHT_CIC or DUST_WEIGHT_TSC                */
+    int weight;            /* DUST_WEIGHT_CIC, DUST_WEIGHT_TSC or DUST_WEIGHT_VOLUME */
     int feedback_apply;    /* 1: add the deposit to the gas momentum each step  */
     double quantum;        /* fixed-point quantum of the deposit (momentum
                               units); 0 = 2^-44 * (largest species mass): a

@@ -160,7 +160,7 @@ int validate_descriptors(const dust_geometry *geom, const dust_grid *grid,
         return fail(nullptr, DUST_EINVAL, "bad geometry kind %d", geom->kind);
     if (n_species < 1 || n_species > kMaxSpecies)
         return fail(nullptr, DUST_EINVAL, "n_species must be 1..%d", kMaxSpecies);
-    if (weight != DUST_WEIGHT_CIC && weight != DUST_WEIGHT_TSC)
+    if (weight != DUST_WEIGHT_CIC && weight != DUST_WEIGHT_TSC && weight != DUST_WEIGHT_VOLUME)
         return fail(nullptr, DUST_EINVAL, "bad weight");
     int64_t ncell = 1;
     for (int d = 0; d < 3; ++d) {
@@ -662,6 +662,13 @@ cudaError_t launch_slab_geom<GEOM_SPH>(const TiledArgs<float> &ta, int, cudaStre
     return launch_step_slab<GEOM_SPH, 0>(ta, s);
 }
 
+// Whether volume weighting differs from CIC in this geometry (it has a
+// curvilinear radius or polar angle); elsewhere it is CIC.
+inline bool uses_volume_weights(int geom, int weight)
+{
+    return weight == DUST_WEIGHT_VOLUME && (geom == GEOM_CYL || geom == GEOM_SPH);
+}
+
 // Whether the slab kernel runs for this context: mixed precision, a
 // supported flat pattern, and the geometry's instantiation.
 inline bool slab_available(int geom, int flat)
@@ -682,6 +689,7 @@ cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
     ta.s = a;
     ta.key_off = key_off;
     ta.tsc = weight == DUST_WEIGHT_TSC;
+    const bool vol = (GEOM == GEOM_CYL || GEOM == GEOM_SPH) && weight == DUST_WEIGHT_VOLUME;
     ta.emit_keys = key_out != nullptr;
     ta.key_out = key_out;
     ta.count_out = count_out;
@@ -690,16 +698,21 @@ cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
     ta.dst = dst;
     if (kernel == DUST_KERNEL_PER_GRAIN) {
         if (perm) return cudaErrorInvalidValue;  // only the slab kernel gathers
+        if constexpr (GEOM == GEOM_CYL || GEOM == GEOM_SPH)
+            if (vol) return launch_step_per_grain<Real, GEOM, 2>(a, s);
         return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<Real, GEOM, 1>(a, s)
                                          : launch_step_per_grain<Real, GEOM, 0>(a, s);
     }
     if constexpr (sizeof(Real) == 4) {
         const int flat = slab_flat(a.g);
-        if ((kernel == DUST_KERNEL_AUTO || kernel == DUST_KERNEL_SLAB) && slab_available(GEOM, flat))
+        if ((kernel == DUST_KERNEL_AUTO || kernel == DUST_KERNEL_SLAB) && !vol &&
+            slab_available(GEOM, flat))
             return launch_slab_geom<GEOM>(ta, flat, s);
     }
     ta.emit_keys = 0;
     if (perm) return cudaErrorInvalidValue;  // only the slab kernel gathers
+    if constexpr (GEOM == GEOM_CYL || GEOM == GEOM_SPH)
+        if (vol) return launch_step_tiled<Real, GEOM, 2>(ta, s);
     return weight == DUST_WEIGHT_TSC ? launch_step_tiled<Real, GEOM, 1>(ta, s)
                                      : launch_step_tiled<Real, GEOM, 0>(ta, s);
 }
@@ -710,7 +723,37 @@ inline bool step_emits_keys(const dust_ctx *ctx)
 {
     const int kn = ctx->opt.kernel;
     return ctx->mixed && (kn == DUST_KERNEL_AUTO || kn == DUST_KERNEL_SLAB) &&
+           !uses_volume_weights(ctx->geom.kind, ctx->opt.weight) &&
            slab_available(ctx->geom.kind, slab_flat(ctx->g));
+}
+
+// Gas predictor of one geometry and weighting: the tiled kernel when tile
+// arguments are given, else one thread per grain.
+template <typename Real, int GEOM, int WEIGHT>
+cudaError_t launch_predict_w(const StepArgs<Real> &pa, const TiledArgs<Real> *pt, cudaStream_t s)
+{
+    return pt ? launch_predict_tiled<Real, GEOM, WEIGHT>(*pt, s) : launch_predict_gas<Real, GEOM, WEIGHT>(pa, s);
+}
+
+template <typename Real, int GEOM>
+cudaError_t launch_predict_g(int weight, const StepArgs<Real> &pa, const TiledArgs<Real> *pt, cudaStream_t s)
+{
+    if constexpr (GEOM == GEOM_CYL || GEOM == GEOM_SPH)
+        if (weight == DUST_WEIGHT_VOLUME) return launch_predict_w<Real, GEOM, 2>(pa, pt, s);
+    if (weight == DUST_WEIGHT_TSC) return launch_predict_w<Real, GEOM, 1>(pa, pt, s);
+    return launch_predict_w<Real, GEOM, 0>(pa, pt, s);
+}
+
+template <typename Real>
+cudaError_t launch_predict(int geom, int weight, const StepArgs<Real> &pa, const TiledArgs<Real> *pt,
+                           cudaStream_t s)
+{
+    switch (geom) {
+    case DUST_CARTESIAN: return launch_predict_g<Real, GEOM_CART>(weight, pa, pt, s);
+    case DUST_SHEARING_BOX: return launch_predict_g<Real, GEOM_SB>(weight, pa, pt, s);
+    case DUST_CYLINDRICAL: return launch_predict_g<Real, GEOM_CYL>(weight, pa, pt, s);
+    default: return launch_predict_g<Real, GEOM_SPH>(weight, pa, pt, s);
+    }
 }
 
 template <typename Real>
@@ -738,20 +781,10 @@ int run_step(dust_ctx *ctx, double dt)
             CU(cudaMemsetAsync(ctx->d_pred, 0, ctx->ncell * 4 * sizeof(unsigned long long), ctx->stream));
             StepArgs<Real> pa = a;
             pa.dep = ctx->d_pred;
-            const int tsc = ctx->opt.weight == DUST_WEIGHT_TSC;
             cudaError_t pe;
             if (ctx->opt.kernel == DUST_KERNEL_PER_GRAIN) {
                 // one thread per grain, global atomics (any store order)
-                switch (ctx->geom.kind * 2 + tsc) {
-                case 0: pe = launch_predict_gas<Real, GEOM_CART, 0>(pa, ctx->stream); break;
-                case 1: pe = launch_predict_gas<Real, GEOM_CART, 1>(pa, ctx->stream); break;
-                case 2: pe = launch_predict_gas<Real, GEOM_SB, 0>(pa, ctx->stream); break;
-                case 3: pe = launch_predict_gas<Real, GEOM_SB, 1>(pa, ctx->stream); break;
-                case 4: pe = launch_predict_gas<Real, GEOM_CYL, 0>(pa, ctx->stream); break;
-                case 5: pe = launch_predict_gas<Real, GEOM_CYL, 1>(pa, ctx->stream); break;
-                case 6: pe = launch_predict_gas<Real, GEOM_SPH, 0>(pa, ctx->stream); break;
-                default: pe = launch_predict_gas<Real, GEOM_SPH, 1>(pa, ctx->stream); break;
-                }
+                pe = launch_predict<Real>(ctx->geom.kind, ctx->opt.weight, pa, nullptr, ctx->stream);
             } else {
                 // tiles of the last sort (through the pending permutation when
                 // the step kernel finishes the sort); same integers
@@ -759,16 +792,7 @@ int run_step(dust_ctx *ctx, double dt)
                 pt.s = pa;
                 pt.key_off = ctx->d_count;
                 pt.perm = ctx->perm_pending ? ctx->d_pair_src : nullptr;
-                switch (ctx->geom.kind * 2 + tsc) {
-                case 0: pe = launch_predict_tiled<Real, GEOM_CART, 0>(pt, ctx->stream); break;
-                case 1: pe = launch_predict_tiled<Real, GEOM_CART, 1>(pt, ctx->stream); break;
-                case 2: pe = launch_predict_tiled<Real, GEOM_SB, 0>(pt, ctx->stream); break;
-                case 3: pe = launch_predict_tiled<Real, GEOM_SB, 1>(pt, ctx->stream); break;
-                case 4: pe = launch_predict_tiled<Real, GEOM_CYL, 0>(pt, ctx->stream); break;
-                case 5: pe = launch_predict_tiled<Real, GEOM_CYL, 1>(pt, ctx->stream); break;
-                case 6: pe = launch_predict_tiled<Real, GEOM_SPH, 0>(pt, ctx->stream); break;
-                default: pe = launch_predict_tiled<Real, GEOM_SPH, 1>(pt, ctx->stream); break;
-                }
+                pe = launch_predict<Real>(ctx->geom.kind, ctx->opt.weight, pa, &pt, ctx->stream);
             }
             CU(pe);
             predict_apply_kernel<Real><<<blocks_for(ctx->ncell), 256, 0, ctx->stream>>>(
@@ -1699,6 +1723,8 @@ NoAllocLayout noalloc_layout(const int n[3])
 template <int GEOM>
 cudaError_t launch_noalloc(const StepArgs<double> &a, int weight, cudaStream_t s)
 {
+    if constexpr (GEOM == GEOM_CYL || GEOM == GEOM_SPH)
+        if (weight == DUST_WEIGHT_VOLUME) return launch_step_per_grain<double, GEOM, 2>(a, s);
     return weight == DUST_WEIGHT_TSC ? launch_step_per_grain<double, GEOM, 1>(a, s)
                                      : launch_step_per_grain<double, GEOM, 0>(a, s);
 }

@@ -231,11 +231,76 @@ __device__ __forceinline__ void w_theta(int tsc, R th, R lo, R hi, R dr, R hw, R
     w[1] = R(1) - w[0] - w[2];
 }
 
-// Host zone and weights of direction d for coordinate x.
+// Traditional volume weighting, Eq. CIC_vol: the CIC rule in the volume
+// coordinate, i.e. linear interpolation in V = R^2 (cylindrical radius),
+// r^3 (spherical radius) or -cos(theta) (polar angle) between the centres of
+// the two zones around x.  The nodes are the zones' own centres, with a ghost
+// centre one edge-zone width beyond each end of the grid; a difference of V
+// is the shell volume |dV| between the two points, so it stays positive when
+// a ghost centre lies across the axis or a pole.  Evaluated in double
+// precision from the edge tables in both precisions: this is the paper's
+// comparison weighting, not a fast path.
+__device__ __forceinline__ double vol_node(const GridDev &g, int d, int k)
+{
+    const int n = g.n[d];
+    const double *e = g.edges[d];
+    if (k < 0) return g.zc[d][0] - (e[1] - e[0]);
+    if (k >= n) return g.zc[d][n - 1] + (e[n] - e[n - 1]);
+    return g.zc[d][k];
+}
+
+// |cos u - cos v| for u <= v on one side of a pole, as a product of sines.
+__device__ __forceinline__ double polar_piece(double u, double v)
+{
+    return fabs(2.0 * sin(0.5 * (u + v)) * sin(0.5 * (v - u)));
+}
+
+// Shell volume between b <= a (per unit of the other coordinates, up to the
+// direction's constant factor).
+template <int GEOM>
+__device__ __forceinline__ double vol_shell(int d, double b, double a)
+{
+    if (GEOM == GEOM_CYL || d == 0) {
+        if (GEOM == GEOM_SPH) return (a - b) * (a * a + a * b + b * b);  // a^3 - b^3
+        return (b >= 0.0 || a <= 0.0) ? fabs((a - b) * (a + b)) : a * a + b * b;
+    }
+    // polar angle: |sin| integrated over [b, a], split at 0 and pi
+    const double kPi = 3.14159265358979323846;
+    double s = 0.0, u = b;
+    if (u < 0.0) {
+        const double v = fmin(a, 0.0);
+        s += polar_piece(u, v);
+        u = v;
+    }
+    if (u < kPi && a > u) {
+        const double v = fmin(a, kPi);
+        s += polar_piece(u, v);
+        u = v;
+    }
+    if (a > u) s += polar_piece(u, a);
+    return s;
+}
+
 template <typename R, int GEOM>
-__device__ __forceinline__ void zone_weights(const GridDev &g, int d, int tsc, double x, int &i,
+__device__ __forceinline__ void w_volume(const GridDev &g, int d, double x, int i, R w[3])
+{
+    const double c = g.zc[d][i];
+    double lo = 0.0, hi = 0.0;
+    if (x >= c) hi = vol_shell<GEOM>(d, c, x) / vol_shell<GEOM>(d, c, vol_node(g, d, i + 1));
+    else lo = vol_shell<GEOM>(d, x, c) / vol_shell<GEOM>(d, vol_node(g, d, i - 1), c);
+    w[0] = (R)lo;
+    w[2] = (R)hi;
+    w[1] = (R)(1.0 - lo - hi);
+}
+
+// Host zone and weights of direction d for coordinate x.  wk: 0 CIC, 1 TSC,
+// 2 volume weighting (plain CIC in the directions whose volume coordinate
+// is the coordinate itself).
+template <typename R, int GEOM>
+__device__ __forceinline__ void zone_weights(const GridDev &g, int d, int wk, double x, int &i,
                                              R w[3], float &inv_width)
 {
+    const int tsc = wk == 1;
     if (g.n[d] <= 1) {
         i = 0; w[0] = R(0); w[1] = R(1); w[2] = R(0);
         inv_width = 0.f;
@@ -248,7 +313,9 @@ __device__ __forceinline__ void zone_weights(const GridDev &g, int d, int tsc, d
     inv_width = g.ziw_f[d][i];
     const bool single = sizeof(R) == 4;
     const R dd = single ? (R)((float)off * g.ziw_f[d][i]) : (R)(off * g.ziw[d][i]);
-    if ((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && d == 0) {
+    if (wk == 2 && (((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && d == 0) || (GEOM == GEOM_SPH && d == 1))) {
+        w_volume<R, GEOM>(g, d, x, i, w);
+    } else if ((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && d == 0) {
         const R nu = single ? (R)g.znu_f[d][i] : (R)(g.zc[d][i] * g.ziw[d][i]);
         if (GEOM == GEOM_CYL) w_cyl<R>(tsc, dd, nu, w);
         else w_sphr<R>(tsc, dd, nu, w);

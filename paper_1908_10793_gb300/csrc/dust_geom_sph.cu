@@ -23,4 +23,13 @@ template cudaError_t launch_predict_gas<float, GEOM_SPH, 1>(const StepArgs<float
 template cudaError_t launch_predict_gas<double, GEOM_SPH, 0>(const StepArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_gas<double, GEOM_SPH, 1>(const StepArgs<double> &, cudaStream_t);
 
+template cudaError_t launch_step_per_grain<float, GEOM_SPH, 2>(const StepArgs<float> &, cudaStream_t);
+template cudaError_t launch_step_tiled<float, GEOM_SPH, 2>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<float, GEOM_SPH, 2>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_gas<float, GEOM_SPH, 2>(const StepArgs<float> &, cudaStream_t);
+template cudaError_t launch_step_per_grain<double, GEOM_SPH, 2>(const StepArgs<double> &, cudaStream_t);
+template cudaError_t launch_step_tiled<double, GEOM_SPH, 2>(const TiledArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_tiled<double, GEOM_SPH, 2>(const TiledArgs<double> &, cudaStream_t);
+template cudaError_t launch_predict_gas<double, GEOM_SPH, 2>(const StepArgs<double> &, cudaStream_t);
+
 }  // namespace dust

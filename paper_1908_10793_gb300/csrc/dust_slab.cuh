@@ -114,7 +114,9 @@ __device__ __noinline__ bool slab_exact_first_half(const GridDev &g, const PhysD
     if (!apply_bc<float, GEOM>(g, ph, shift, e.q, e.p)) return false;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        zone_weights<float, GEOM>(g, d, tsc, e.q[d], e.host[d], e.w[d], e.iw[d]);
+        // CIC or TSC only (the slab kernel does not run volume weighting):
+        // the mask lets the compiler drop the volume branch
+        zone_weights<float, GEOM>(g, d, tsc & 1, e.q[d], e.host[d], e.w[d], e.iw[d]);
         e.qf[d] = (float)e.q[d];
     }
     return true;

@@ -19,7 +19,7 @@ DUST_EINVAL, DUST_ENOMEM, DUST_ECUDA, DUST_ECFL, DUST_EOVERFLOW, DUST_ENAN = -1,
 DUST_ESTATE = -8
 DUST_CARTESIAN, DUST_SHEARING_BOX, DUST_CYLINDRICAL, DUST_SPHERICAL = 0, 1, 2, 3
 DUST_BC_PERIODIC, DUST_BC_OUTFLOW = 0, 1
-DUST_WEIGHT_CIC, DUST_WEIGHT_TSC = 0, 1
+DUST_WEIGHT_CIC, DUST_WEIGHT_TSC, DUST_WEIGHT_VOLUME = 0, 1, 2
 DUST_TAU_CONST, DUST_TAU_STOKES, DUST_TAU_EPSTEIN = 0, 1, 2
 DUST_FP64, DUST_MIXED = 0, 1
 DUST_PUSHER_EM, DUST_PUSHER_SEMI_IMPLICIT = 0, 1

@@ -38,7 +38,7 @@ import numpy as np
 
 CARTESIAN, SHEARING_BOX, CYLINDRICAL, SPHERICAL = 0, 1, 2, 3
 PERIODIC, OUTFLOW = 0, 1
-CIC, TSC = 0, 1
+CIC, TSC, VOLUME = 0, 1, 2
 TAU_CONST, TAU_STOKES, TAU_EPSTEIN = 0, 1, 2
 
 BASE_SEED = 20190828

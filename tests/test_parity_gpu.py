@@ -427,3 +427,85 @@ def test_tiled_deposit_independent_of_sort_scatter_order():
     for _ in range(3):
         b = run_gpu(w, 4, MIXED, kernel=D.DUST_KERNEL_TILED, sort_interval=2)
         assert np.array_equal(a["fixed"], b["fixed"])
+
+
+def _near_axis_cyl():
+    """Cylindrical grid whose inner edge is 0.04 zones from the axis (the
+    ghost centre of the volume weights lies across it), outflow in R."""
+    r = np.random.default_rng(11)
+    edges = [0.002 + 0.05 * np.arange(21), np.linspace(0.0, 2 * np.pi, 17), np.linspace(-0.1, 0.1, 5)]
+    ncell = 20 * 16 * 4
+    ng = 3000
+    return I.Workload(
+        name="near_axis", geom=I.CYLINDRICAL, edges=edges, bc=[I.OUTFLOW, I.PERIODIC, I.PERIODIC],
+        weight=I.VOLUME, species_mass=[1e-3], species_tau_mode=[I.TAU_CONST], species_tau=[0.1],
+        rho=r.uniform(0.5, 2.0, ncell),
+        vgas=[0.1 * r.standard_normal(ncell) for _ in range(3)],
+        q=[r.uniform(0.002, 1.002, ng), r.uniform(0, 2 * np.pi, ng), r.uniform(-0.1, 0.1, ng)],
+        v=[0.1 * r.standard_normal(ng) for _ in range(3)], dt=1e-3, steps=2, feedback=0)
+
+
+def _near_pole_sph():
+    """Spherical grid whose polar-angle range ends 0.05 zones from each pole
+    (ghost centres across the poles), outflow in r and theta."""
+    r = np.random.default_rng(12)
+    dth = (np.pi - 0.02) / 16
+    edges = [np.linspace(0.5, 1.5, 9), 0.01 + dth * np.arange(17), np.linspace(0.0, 2 * np.pi, 9)]
+    ncell = 8 * 16 * 8
+    ng = 3000
+    return I.Workload(
+        name="near_pole", geom=I.SPHERICAL, edges=edges, bc=[I.OUTFLOW, I.OUTFLOW, I.PERIODIC],
+        weight=I.VOLUME, species_mass=[1e-3], species_tau_mode=[I.TAU_CONST], species_tau=[0.1],
+        rho=r.uniform(0.5, 2.0, ncell),
+        vgas=[0.1 * r.standard_normal(ncell) for _ in range(3)],
+        q=[r.uniform(0.5, 1.5, ng), r.uniform(edges[1][0], edges[1][-1], ng),
+           r.uniform(0, 2 * np.pi, ng)],
+        v=[0.1 * r.standard_normal(ng) for _ in range(3)], dt=1e-3, steps=2, feedback=0)
+
+
+VOLUME_WORKLOADS = {
+    "cyldisk": lambda: WORKLOADS["cyldisk"](),
+    "sphdisk": lambda: WORKLOADS["sphdisk"](),
+    "near_axis": _near_axis_cyl,
+    "near_pole": _near_pole_sph,
+}
+
+
+@pytest.mark.parametrize("name", list(VOLUME_WORKLOADS))
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_parity_volume_weighting(name, precision):
+    """Traditional volume weighting (Eq. CIC_vol) on the tiled kernel (two
+    steps) and the one-thread-per-grain kernel (one step) against the
+    oracle's."""
+    from paper_1908_10793_gb300 import dust as D
+    w = VOLUME_WORKLOADS[name]()
+    w.weight = I.VOLUME
+    compare(w, 2, precision)
+    compare(w, 1, precision, kernel=D.DUST_KERNEL_PER_GRAIN)
+
+
+def test_parity_volume_weighting_with_gas_predictor():
+    from parity_util import zone_volumes
+    w = WORKLOADS["cyldisk"]()
+    w.weight = I.VOLUME
+    steps = 2
+    nz = _grains_per_zone_max(w) * 27
+    quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
+    dgas = (nz * 0.5 * quantum / (w.rho * zone_volumes(w))).max()
+    compare(w, steps, FP64, feedback=1, predictor=True, extra_v=4 * steps * dgas)
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_volume_weighting_equals_cic_in_cartesian_geometries(precision):
+    """Cartesian and shearing-box directions have the coordinate itself as
+    volume coordinate: the library must give the CIC results bit for bit."""
+    for name in ("box2d", "sbox3d"):
+        w = WORKLOADS[name]()
+        w.weight = I.CIC
+        a = run_gpu(w, 2, precision)
+        w.weight = I.VOLUME
+        b = run_gpu(w, 2, precision)
+        for key in ("q", "v"):
+            for d in range(3):
+                assert np.array_equal(a[key][d], b[key][d], equal_nan=True), (name, key, d)
+        assert np.array_equal(a["fixed"], b["fixed"])
