@@ -70,12 +70,25 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# Sources the shearing-box step kernel is compiled from (its translation
+# unit and the headers it includes); the profiled traffic is dropped when one
+# of them changes.
+STEP_KERNEL_SOURCES = [
+    "include/dust.h",
+    "paper_1908_10793_gb300/csrc/dust_internal.h",
+    "paper_1908_10793_gb300/csrc/dust_device.cuh",
+    "paper_1908_10793_gb300/csrc/dust_step_kernels.cuh",
+    "paper_1908_10793_gb300/csrc/dust_tiled.cuh",
+    "paper_1908_10793_gb300/csrc/dust_slab.cuh",
+    "paper_1908_10793_gb300/csrc/dust_geom_sb.cu",
+]
+
+
 def source_digest():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1908_10793_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for f in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -280,7 +293,9 @@ def run_ours(args):
         h2d = ngr * 6 * 8 + w.ncell * 4 * 8
         d2h = ngr * (6 * 8 + 8) + w.ncell * 4 * 8
         e2e = {"value": weak_value(world, ngr * ke, te), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": ke}
+               "d2h_bytes_per_step": d2h, "steps": ke,
+               "breakdown": e2e_breakdown(ctx, D, torch, dev, w, hq, hv, hrho, hg, oq, ov, oid,
+                                          odep)}
         ctx.close()
 
     # ---- batched instances (64 streaming-instability boxes, one graph launch
@@ -424,6 +439,49 @@ def run_batch(args, D, torch, dev, stream):
                         "feedback on, mixed precision"}
 
 
+def e2e_breakdown(ctx, D, torch, dev, w, hq, hv, hrho, hg, oq, ov, oid, odep):
+    """Untimed by the headline: one more end-to-end step with a device
+    synchronise around every call (ms per call), and the bandwidth of plain
+    pinned-memory copies of the grains' size in each direction and in both
+    at once, which bound the end-to-end figure."""
+    ngr = w.ngrains
+
+    def timed(f):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        f()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3
+
+    calls = {
+        "load_particles": timed(lambda: D.dust_load_particles(ctx.handle, *hq, *hv)),
+        "set_gas": timed(lambda: D.dust_set_gas(ctx.handle, hrho, *hg)),
+        "step": timed(lambda: D.dust_step(ctx.handle, w.dt)),
+        "get_particles": timed(lambda: D.dust_get_particles(ctx.handle, ngr, *oq, *ov, ids=oid)),
+        "get_deposit": timed(lambda: D.dust_get_deposit(ctx.handle, fixed=odep)),
+    }
+    nb = ngr * 6
+    host = torch.empty(nb, dtype=torch.float64).pin_memory()
+    host2 = torch.empty(nb, dtype=torch.float64).pin_memory()
+    devb = torch.empty(nb, dtype=torch.float64, device=dev)
+    devb2 = torch.empty(nb, dtype=torch.float64, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    link = {}
+    for _ in range(2):
+        link["h2d_gbs"] = nb * 8 / timed(lambda: devb.copy_(host, non_blocking=True)) / 1e6
+        link["d2h_gbs"] = nb * 8 / timed(lambda: host.copy_(devb, non_blocking=True)) / 1e6
+
+        def both():
+            with torch.cuda.stream(s1):
+                devb.copy_(host, non_blocking=True)
+            with torch.cuda.stream(s2):
+                host2.copy_(devb2, non_blocking=True)
+        link["both_directions_gbs"] = 2 * nb * 8 / timed(both) / 1e6
+    link["bytes_each"] = nb * 8
+    del host, host2, devb, devb2
+    return {"ms_per_call": calls, "link": link}
+
+
 def run_disks(args, D, torch, dev, stream):
     """Cylindrical (384 x 1024 x 64, 50M grains, 4 species) and spherical
     (256 x 128 x 512, 33M grains, St log-uniform in [1e-4, 10]) disks, mixed
@@ -432,13 +490,21 @@ def run_disks(args, D, torch, dev, stream):
     falls to ~1e-9 of the midplane value, where a single grain makes the local
     dust-to-gas ratio 1e4 or more, and neither the explicit feedback nor the
     predictor-corrector coupling is stable for grains as stiff as St = 1e-4
-    there."""
+    there.  Two more lines run the cylindrical disk with the gas half-step
+    drag predictor and with the traditional volume weighting (Eq. CIC_vol)
+    instead of TSC."""
     out = {}
     peak, _ = measured_peaks()
-    for name, make, feedback in (("cyldisk", I.cyldisk, 1), ("sphdisk", I.sphdisk, 0)):
+    legs = (("cyldisk", I.cyldisk, 1, {}, None),
+            ("sphdisk", I.sphdisk, 0, {}, None),
+            ("cyldisk_gas_predictor", I.cyldisk, 1, {"gas_predictor": 1}, None),
+            ("cyldisk_volume_weighting", I.cyldisk, 1, {}, I.VOLUME))
+    for name, make, feedback, extra, weight in legs:
         w = make("full")
+        if weight is not None:
+            w.weight = weight
         ctx = D.Context(w, precision=D.DUST_MIXED, stream=stream.cuda_stream, timing=1,
-                        device=dev.index, feedback=feedback)
+                        device=dev.index, feedback=feedback, **extra)
         try:
             ctx.set_gas(w.rho, w.vgas)
             ctx.load(w.q, w.v, w.species, w.param)
@@ -466,7 +532,9 @@ def run_disks(args, D, torch, dev, stream):
                                             "sort": kt.sort_ms / args.disk_steps,
                                             "other": kt.other_ms / args.disk_steps},
                      "step_roofline_frac": ab / (step_ms / 1e3) / 1e9 / peak,
-                     "status": rc, "removed": st.n_removed, "feedback": feedback}
+                     "status": rc, "removed": st.n_removed, "feedback": feedback,
+                     "weight": ("cic", "tsc", "volume")[w.weight],
+                     "gas_predictor": int(extra.get("gas_predictor", 0))}
     return out
 
 
