@@ -436,6 +436,9 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                     // 27-node gather (Eq. Delta_vp) from the staged gas box; the
                     // grains of one zone read the same nodes (broadcast loads)
                     if (inbox) {
+                        // channels in pairs on the packed single-precision
+                        // FMA (each lane rounded once, as a scalar FMA)
+                        float2 G01 = make_float2(0.f, 0.f), G23 = make_float2(0.f, 0.f);
     #pragma unroll
                         for (int c3 = 0; c3 < 3; ++c3) {
                             if (NC == 1 && c3 != 1) continue;
@@ -445,13 +448,15 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     #pragma unroll
                                 for (int aa = 0; aa < 3; ++aa) {
                                     const float W = w[0][aa] * (w[1][b] * w[2][c3]);
-                                    float fv[4];
-                                    smem_gas_load<float>(sgas, (lb[0] + aa - 1) + B[0] * ((lb[1] + b - 1) + B[1] * (lb[2] + c3 - 1)), fv);
-    #pragma unroll
-                                    for (int ch = 0; ch < 4; ++ch) G[ch] += W * fv[ch];
+                                    const float4 fv = reinterpret_cast<const float4 *>(sgas)[
+                                        (lb[0] + aa - 1) + B[0] * ((lb[1] + b - 1) + B[1] * (lb[2] + c3 - 1))];
+                                    const float2 W2 = make_float2(W, W);
+                                    G01 = __ffma2_rn(W2, make_float2(fv.x, fv.y), G01);
+                                    G23 = __ffma2_rn(W2, make_float2(fv.z, fv.w), G23);
                                 }
                             }
                         }
+                        G[0] = G01.x; G[1] = G01.y; G[2] = G23.x; G[3] = G23.y;
                     } else {
                         // rare: the stencil leaves the staged box; the same
                         // nodes in the same order from global memory, in a
@@ -658,33 +663,36 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
             // chunk in this pass (id order) into their x slabs
             const int za = max(off0, P0), zb = min(off0 + cnt, P1);
             const bool own = kok && zb > za;
-            float acc[NB][NC][4], S[4] = {0.f, 0.f, 0.f, 0.f};
+            // channels in pairs (0, 1) and (2, 3) on the packed single-precision
+            // FMA and add (each lane rounded once, as the scalar operations)
+            float2 acc[NB][NC][2];
+            float2 S2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
 #pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) acc[b][c][ch] = 0.f;
+                    for (int hc = 0; hc < 2; ++hc) acc[b][c][hc] = make_float2(0.f, 0.f);
             if (own) {
                 const int s0 = za - P0 + kq, s1 = zb - P0 + kq;
                 const float *rx = rb + a * kRecStride;
                 auto one = [&](int sl) {
                     const float wx = rx[sl];
-                    float De[4];
-#pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) De[ch] = rb[(9 + ch) * kRecStride + sl];
+                    const float2 De01 = make_float2(rb[9 * kRecStride + sl], rb[10 * kRecStride + sl]);
+                    const float2 De23 = make_float2(rb[11 * kRecStride + sl], rb[12 * kRecStride + sl]);
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         const float wxy = wx * rb[(3 + (NB == 3 ? b : 1)) * kRecStride + sl];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
                             const float W = wxy * rb[(6 + (NC == 3 ? c : 1)) * kRecStride + sl];
-#pragma unroll
-                            for (int ch = 0; ch < 4; ++ch) acc[b][c][ch] += W * De[ch];
+                            const float2 W2 = make_float2(W, W);
+                            acc[b][c][0] = __ffma2_rn(W2, De01, acc[b][c][0]);
+                            acc[b][c][1] = __ffma2_rn(W2, De23, acc[b][c][1]);
                         }
                     }
-#pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) S[ch] += De[ch];
+                    S2[0] = __fadd2_rn(S2[0], De01);
+                    S2[1] = __fadd2_rn(S2[1], De23);
                 };
                 int sl = s0;
                 for (; sl + 1 < s1; sl += 2) {
@@ -706,8 +714,9 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                         const int lin = (ohx + a - 1) + B[0] * ((ohy + b - Sh::BC) + B[1] * (ohz + c - Sh::CC));
 #pragma unroll
                         for (int ch = 0; ch < 4; ++ch) {
-                            big |= !(fabsf(acc[b][c][ch]) < 4.5e15f);
-                            const long long piece = rint_to_ll(acc[b][c][ch]);
+                            const float v = (ch & 1) ? acc[b][c][ch >> 1].y : acc[b][c][ch >> 1].x;
+                            big |= !(fabsf(v) < 4.5e15f);
+                            const long long piece = rint_to_ll(v);
                             if (piece != 0) {
                                 shared_add_i64(&sdep[ch * bvol + lin], piece);
                                 ps[ch] += piece;
@@ -720,8 +729,9 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                 const long long s1 = __shfl_sync(FULL, ps[ch], base + 0);
                 const long long s2 = __shfl_sync(FULL, ps[ch], base + 2);
                 if (a == 1 && own) {
-                    big |= !(fabsf(S[ch]) < 4.5e15f);
-                    const long long rest = rint_to_ll(S[ch]) - (ps[ch] + s1 + s2);
+                    const float Sc = (ch & 1) ? S2[ch >> 1].y : S2[ch >> 1].x;
+                    big |= !(fabsf(Sc) < 4.5e15f);
+                    const long long rest = rint_to_ll(Sc) - (ps[ch] + s1 + s2);
                     if (rest != 0) shared_add_i64(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], rest);
                 }
             }

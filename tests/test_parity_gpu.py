@@ -220,6 +220,37 @@ def test_slab_kernel_dense_zones_split_into_chunks():
         assert np.array_equal(got["fixed"], first["fixed"]), tile
 
 
+def test_gas_predictor_dense_zones_and_tile_independent():
+    """The gas predictor with zones of 600 and 300 grains (several chunks of
+    the slab step): parity with the oracle's predictor-corrector, and results
+    that do not depend on the tile shape (the predictor's per-grain rule is
+    independent of the grains' order)."""
+    from paper_1908_10793_gb300 import dust as D
+    from parity_util import zone_volumes
+    w = I.box2d("small")
+    rng = np.random.default_rng(11)
+    dx = w.edges[0][1] - w.edges[0][0]
+    for sel, (cx, cy) in ((slice(0, 600), (3, 5)), (slice(600, 900), (10, 12))):
+        k = sel.stop - sel.start
+        w.q[0][sel] = w.edges[0][cx] + dx * rng.uniform(0.05, 0.95, k)
+        w.q[1][sel] = w.edges[1][cy] + dx * rng.uniform(0.05, 0.95, k)
+    steps = 2
+    nz = _grains_per_zone_max(w) * 9
+    quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
+    dgas = (nz * 0.5 * quantum / (w.rho * zone_volumes(w))).max()
+    compare(w, steps, MIXED, feedback=1, predictor=True, extra_v=4 * steps * dgas,
+            kernel=D.DUST_KERNEL_SLAB, sort_interval=1)
+    first = None
+    for tile in ((0, 0, 0), (4, 4, 1), (8, 2, 1)):
+        got = run_gpu(w, steps, MIXED, feedback=1, kernel=D.DUST_KERNEL_SLAB, tile=tile,
+                      sort_interval=1, gas_predictor=1)
+        if first is None:
+            first = got
+        assert np.array_equal(got["fixed"], first["fixed"]), tile
+        for d in range(3):
+            assert np.array_equal(got["v"][d], first["v"][d], equal_nan=True), (tile, d)
+
+
 @pytest.mark.parametrize("name,fargo", [("box2d", None), ("sbox3d", 0), ("sbox3d", 1)])
 @pytest.mark.parametrize("precision", [FP64, MIXED])
 def test_parity_semi_implicit_pusher(name, fargo, precision):
