@@ -155,6 +155,21 @@ typedef struct dust_options {
                               feedback_apply the deposit corrects the gas at
                               t^n, as the paper's predictor-corrector does for
                               the drag term (no hydrodynamic fluxes here)    */
+    int host_io_async;     /* 0: calls with host memory (dust_load_particles,
+                              dust_set_gas, dust_get_particles, dust_get_deposit
+                              with DUST_MEM_HOST) return when their copies are
+                              done.  1: they only enqueue them, on two copy
+                              streams of the context with their own staging
+                              areas (two for each output), so that one step's
+                              read-back, the next step's load and the steps
+                              themselves overlap.  Host buffers should then be
+                              pinned; an input buffer must not be changed, and
+                              an output buffer not read, before the next
+                              dust_sync, which waits for every copy.  Invalid
+                              grain or gas data is then reported by dust_sync
+                              (DUST_EINVAL) instead of by the call, and invalid
+                              grains are dropped as removed.  dust_get_gas stays
+                              synchronous.                                    */
 } dust_options;
 
 typedef struct dust_stats {

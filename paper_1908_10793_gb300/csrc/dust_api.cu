@@ -80,6 +80,19 @@ struct dust_ctx {
     uint64_t gen = 0;           // bumped when the grain store is reallocated
     double *d_stage = nullptr;
     size_t stage_bytes = 0;
+    // asynchronous host I/O (dust_options.host_io_async): two copy streams
+    // and staging areas, each with an event for "data in place" and one for
+    // "free for reuse"; outputs alternate between two areas
+    struct IoBuf {
+        void *d = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t ready = nullptr;
+        cudaEvent_t done = nullptr;
+        bool used = false;  // `done` recorded at least once
+    };
+    cudaStream_t io_in = nullptr, io_out = nullptr;
+    IoBuf in_grains, in_gas, out_grains[2], out_dep[2];
+    int out_flip = 0, dep_flip = 0;
 
     double t = 0.0;
     int64_t steps = 0;
@@ -323,7 +336,8 @@ template <typename Real>
 __global__ void load_kernel(GridDev g, int geom, int64_t n, const double *q0, const double *q1,
                             const double *q2, const double *v0, const double *v1,
                             const double *v2, const uint8_t *species_in, int n_species,
-                            const double *param_in, StoreDev<Real> s, unsigned int *st)
+                            const double *param_in, StoreDev<Real> s, unsigned int *st,
+                            int drop_bad)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -351,7 +365,17 @@ __global__ void load_kernel(GridDev g, int geom, int64_t n, const double *q0, co
         if (!(v >= 0.0) || isnan(v)) bad = true;
         s.param[k] = (Real)v;
     }
-    if (bad) atomicOr(&st[ST_LOAD_BAD], 1u);
+    if (bad) {
+        atomicOr(&st[ST_LOAD_BAD], 1u);
+        if (drop_bad) {
+            // stored as a removed grain (NaN coordinate), species and
+            // stopping-time value made harmless
+            s.q[0][k] = __longlong_as_double(0x7ff8000000000000LL);
+            if (s.species) s.species[k] = 0;
+            if (s.param) s.param[k] = (Real)0;
+            atomicAdd(reinterpret_cast<unsigned long long *>(&st[ST_REMOVED_LO]), 1ull);
+        }
+    }
 }
 
 template <typename Real>
@@ -534,6 +558,101 @@ const double *stage_in(dust_ctx *ctx, const double *src, int64_t count, int slot
     double *dst = ctx->d_stage + (size_t)slot * count;
     cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
     return dst;
+}
+
+// ---- asynchronous host I/O helpers
+
+int io_streams(dust_ctx *ctx)
+{
+    if (!ctx->io_in) CU(cudaStreamCreateWithFlags(&ctx->io_in, cudaStreamNonBlocking));
+    if (!ctx->io_out) CU(cudaStreamCreateWithFlags(&ctx->io_out, cudaStreamNonBlocking));
+    return DUST_OK;
+}
+
+// Makes b hold at least `bytes`; a reallocation first waits for its last use.
+int io_ensure(dust_ctx *ctx, dust_ctx::IoBuf &b, size_t bytes)
+{
+    if (!b.ready) CU(cudaEventCreateWithFlags(&b.ready, cudaEventDisableTiming));
+    if (!b.done) CU(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+    if (b.bytes >= bytes) return DUST_OK;
+    if (b.d) {
+        if (b.used) CU(cudaEventSynchronize(b.done));
+        CU(cudaFree(b.d));
+        b.d = nullptr;
+        b.bytes = 0;
+    }
+    CU(cudaMalloc(&b.d, bytes));
+    b.bytes = bytes;
+    return DUST_OK;
+}
+
+void io_free(dust_ctx::IoBuf &b)
+{
+    if (b.d) cudaFree(b.d);
+    if (b.ready) cudaEventDestroy(b.ready);
+    if (b.done) cudaEventDestroy(b.done);
+    b = dust_ctx::IoBuf{};
+}
+
+// Input: after b's last consumer, copy the host arrays (src[k], bytes[k]) one
+// after the other into b on the input copy stream; the context stream waits
+// for them.  Returns the device address of each part in dev[k].
+int io_stage_in(dust_ctx *ctx, dust_ctx::IoBuf &b, int parts, const void *const *src,
+                const size_t *bytes, const void **dev)
+{
+    size_t total = 0;
+    for (int k = 0; k < parts; ++k) total += (bytes[k] + 255) & ~(size_t)255;
+    int r = io_ensure(ctx, b, total > 0 ? total : 256);
+    if (r) return r;
+    if (b.used) CU(cudaStreamWaitEvent(ctx->io_in, b.done, 0));
+    size_t off = 0;
+    for (int k = 0; k < parts; ++k) {
+        if (!src[k]) { dev[k] = nullptr; continue; }
+        void *d = static_cast<char *>(b.d) + off;
+        CU(cudaMemcpyAsync(d, src[k], bytes[k], cudaMemcpyHostToDevice, ctx->io_in));
+        dev[k] = d;
+        off += (bytes[k] + 255) & ~(size_t)255;
+    }
+    CU(cudaEventRecord(b.ready, ctx->io_in));
+    CU(cudaStreamWaitEvent(ctx->stream, b.ready, 0));
+    return DUST_OK;
+}
+
+// The context stream has enqueued the last reader of input area b.
+int io_consumed(dust_ctx *ctx, dust_ctx::IoBuf &b)
+{
+    CU(cudaEventRecord(b.done, ctx->stream));
+    b.used = true;
+    return DUST_OK;
+}
+
+// Output: the context stream waits until area b's previous read-back is done
+// (before its producer kernel overwrites it).
+int io_out_acquire(dust_ctx *ctx, dust_ctx::IoBuf &b, size_t bytes)
+{
+    int r = io_ensure(ctx, b, bytes);
+    if (r) return r;
+    if (b.used) CU(cudaStreamWaitEvent(ctx->stream, b.done, 0));
+    return DUST_OK;
+}
+
+// Output: after the producer (enqueued on the context stream), copy the
+// parts of b to the host on the output copy stream.
+int io_stage_out(dust_ctx *ctx, dust_ctx::IoBuf &b, int parts, void *const *dst,
+                 const void *const *dev, const size_t *bytes)
+{
+    CU(cudaEventRecord(b.ready, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->io_out, b.ready, 0));
+    for (int k = 0; k < parts; ++k)
+        if (dst[k]) CU(cudaMemcpyAsync(dst[k], dev[k], bytes[k], cudaMemcpyDeviceToHost, ctx->io_out));
+    CU(cudaEventRecord(b.done, ctx->io_out));
+    b.used = true;
+    return DUST_OK;
+}
+
+bool io_async(const dust_ctx *ctx, int mem)
+{
+    return ctx->opt.host_io_async && mem == DUST_MEM_HOST;
 }
 
 void free_store(dust_ctx *c)
@@ -864,6 +983,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         return fail(nullptr, DUST_EINVAL, "bad pusher");
     if (opt->gas_predictor != 0 && opt->gas_predictor != 1)
         return fail(nullptr, DUST_EINVAL, "gas_predictor must be 0 or 1");
+    if (opt->host_io_async != 0 && opt->host_io_async != 1)
+        return fail(nullptr, DUST_EINVAL, "host_io_async must be 0 or 1");
     if (opt->pusher == DUST_PUSHER_SEMI_IMPLICIT && geom->kind != DUST_CARTESIAN &&
         geom->kind != DUST_SHEARING_BOX)
         return fail(nullptr, DUST_EINVAL,
@@ -1008,6 +1129,30 @@ extern "C" int dust_set_gas(dust_ctx *ctx, const double *rho, const double *v0, 
     if (!rho || !v0 || !v1 || !v2) return fail(ctx, DUST_EINVAL, "NULL gas array");
     CU(cudaSetDevice(ctx->device));
     const int64_t nc = ctx->ncell;
+    if (io_async(ctx, mem)) {
+        // enqueue only; invalid values are reported by dust_sync
+        int r = io_streams(ctx);
+        if (r) return r;
+        const void *src[4] = {rho, v0, v1, v2};
+        const size_t by[4] = {nc * sizeof(double), nc * sizeof(double), nc * sizeof(double),
+                              nc * sizeof(double)};
+        const void *dv[4];
+        r = io_stage_in(ctx, ctx->in_gas, 4, src, by, dv);
+        if (r) return r;
+        const double *a = static_cast<const double *>(dv[0]), *b = static_cast<const double *>(dv[1]),
+                     *c = static_cast<const double *>(dv[2]), *d = static_cast<const double *>(dv[3]);
+        if (ctx->mixed)
+            set_gas_kernel<float><<<blocks_for(nc), 256, 0, ctx->stream>>>(
+                ctx->g, ctx->geom.kind, a, b, c, d, static_cast<float *>(ctx->d_gas), ctx->d_status);
+        else
+            set_gas_kernel<double><<<blocks_for(nc), 256, 0, ctx->stream>>>(
+                ctx->g, ctx->geom.kind, a, b, c, d, static_cast<double *>(ctx->d_gas), ctx->d_status);
+        CU(cudaGetLastError());
+        r = io_consumed(ctx, ctx->in_gas);
+        if (r) return r;
+        ctx->gas_set = true;
+        return DUST_OK;
+    }
     if (mem == DUST_MEM_HOST) {
         int r = ensure_stage(ctx, 4 * nc * sizeof(double));
         if (r) return r;
@@ -1070,7 +1215,10 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
         return fail(ctx, DUST_EINVAL, "NULL particle array");
     CU(cudaSetDevice(ctx->device));
     const bool hs = species != nullptr, hp = param != nullptr;
+    const bool async = io_async(ctx, mem);
     if (n > ctx->cap || hs != ctx->has_species || hp != ctx->has_param) {
+        // the store is about to be replaced: finish the work that reads it
+        CU(cudaStreamSynchronize(ctx->stream));
         ctx->has_species = hs;
         ctx->has_param = hp;
         int r = alloc_store(ctx, n > 0 ? n : 1);
@@ -1084,30 +1232,61 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
     ctx->gen += 1;
     if (n > 0) {
         const uint8_t *sp_dev = species;
-        if (mem == DUST_MEM_HOST) {
-            const size_t need = (7 * n) * sizeof(double) + (hs ? n : 0) + 16;
-            int r = ensure_stage(ctx, need);
+        const double *a, *b, *c, *d, *e, *f, *pp;
+        if (async) {
+            // enqueue only: copies on the input stream; invalid grains are
+            // dropped and reported by dust_sync
+            int r = io_streams(ctx);
             if (r) return r;
+            const size_t nb = n * sizeof(double);
+            const void *src[8] = {q0, q1, q2, v0, v1, v2, param, species};
+            const size_t by[8] = {nb, nb, nb, nb, nb, nb, nb, (size_t)n};
+            const void *dv[8];
+            r = io_stage_in(ctx, ctx->in_grains, 8, src, by, dv);
+            if (r) return r;
+            a = static_cast<const double *>(dv[0]);
+            b = static_cast<const double *>(dv[1]);
+            c = static_cast<const double *>(dv[2]);
+            d = static_cast<const double *>(dv[3]);
+            e = static_cast<const double *>(dv[4]);
+            f = static_cast<const double *>(dv[5]);
+            pp = static_cast<const double *>(dv[6]);
+            sp_dev = static_cast<const uint8_t *>(dv[7]);
+        } else {
+            if (mem == DUST_MEM_HOST) {
+                const size_t need = (7 * n) * sizeof(double) + (hs ? n : 0) + 16;
+                int r = ensure_stage(ctx, need);
+                if (r) return r;
+            }
+            a = stage_in(ctx, q0, n, 0, mem);
+            b = stage_in(ctx, q1, n, 1, mem);
+            c = stage_in(ctx, q2, n, 2, mem);
+            d = stage_in(ctx, v0, n, 3, mem);
+            e = stage_in(ctx, v1, n, 4, mem);
+            f = stage_in(ctx, v2, n, 5, mem);
+            pp = stage_in(ctx, param, n, 6, mem);
+            if (hs && mem == DUST_MEM_HOST) {
+                uint8_t *dst = reinterpret_cast<uint8_t *>(ctx->d_stage + 7 * n);
+                CU(cudaMemcpyAsync(dst, species, n, cudaMemcpyHostToDevice, ctx->stream));
+                sp_dev = dst;
+            }
+            CU(cudaMemsetAsync(ctx->d_status + ST_LOAD_BAD, 0, sizeof(unsigned), ctx->stream));
         }
-        const double *a = stage_in(ctx, q0, n, 0, mem), *b = stage_in(ctx, q1, n, 1, mem),
-                     *c = stage_in(ctx, q2, n, 2, mem), *d = stage_in(ctx, v0, n, 3, mem),
-                     *e = stage_in(ctx, v1, n, 4, mem), *f = stage_in(ctx, v2, n, 5, mem),
-                     *pp = stage_in(ctx, param, n, 6, mem);
-        if (hs && mem == DUST_MEM_HOST) {
-            uint8_t *dst = reinterpret_cast<uint8_t *>(ctx->d_stage + 7 * n);
-            CU(cudaMemcpyAsync(dst, species, n, cudaMemcpyHostToDevice, ctx->stream));
-            sp_dev = dst;
-        }
-        CU(cudaMemsetAsync(ctx->d_status + ST_LOAD_BAD, 0, sizeof(unsigned), ctx->stream));
         if (ctx->mixed)
             load_kernel<float><<<blocks_for(n), 256, 0, ctx->stream>>>(
                 ctx->g, ctx->geom.kind, n, a, b, c, d, e, f, sp_dev, ctx->sp.n, pp,
-                store_of<float>(ctx, 0), ctx->d_status);
+                store_of<float>(ctx, 0), ctx->d_status, async ? 1 : 0);
         else
             load_kernel<double><<<blocks_for(n), 256, 0, ctx->stream>>>(
                 ctx->g, ctx->geom.kind, n, a, b, c, d, e, f, sp_dev, ctx->sp.n, pp,
-                store_of<double>(ctx, 0), ctx->d_status);
+                store_of<double>(ctx, 0), ctx->d_status, async ? 1 : 0);
         CU(cudaGetLastError());
+        if (async) {
+            int r = io_consumed(ctx, ctx->in_grains);
+            if (r) return r;
+            ctx->particles_set = true;
+            return DUST_OK;
+        }
         unsigned bad = 0;
         CU(cudaMemcpyAsync(&bad, ctx->d_status + ST_LOAD_BAD, sizeof bad, cudaMemcpyDeviceToHost,
                            ctx->stream));
@@ -1182,12 +1361,17 @@ extern "C" int dust_sync(dust_ctx *ctx, dust_stats *out)
 {
     if (!ctx) return DUST_EINVAL;
     CU(cudaSetDevice(ctx->device));
+    // pending asynchronous host copies
+    if (ctx->io_in) CU(cudaStreamSynchronize(ctx->io_in));
+    if (ctx->io_out) CU(cudaStreamSynchronize(ctx->io_out));
     CU(cudaMemcpyAsync(ctx->h_status, ctx->d_status, ST_WORDS * sizeof(unsigned),
                        cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     unsigned st[ST_WORDS];
     memcpy(st, ctx->h_status, sizeof st);
     CU(cudaMemsetAsync(ctx->d_status, 0, 4 * sizeof(unsigned), ctx->stream));
+    const bool load_bad = ctx->opt.host_io_async && st[ST_LOAD_BAD];
+    if (load_bad) CU(cudaMemsetAsync(ctx->d_status + ST_LOAD_BAD, 0, sizeof(unsigned), ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     const unsigned long long rem =
         (unsigned long long)st[ST_REMOVED_LO] | ((unsigned long long)st[ST_REMOVED_HI] << 32);
@@ -1206,6 +1390,9 @@ extern "C" int dust_sync(dust_ctx *ctx, dust_stats *out)
         out->steps = ctx->steps;
         out->time = ctx->t;
     }
+    if (load_bad)
+        return fail(ctx, DUST_EINVAL,
+                    "invalid grain or gas data in an asynchronous load (invalid grains were dropped)");
     if (flags & DUST_FLAG_NAN) return fail(ctx, DUST_ENAN, "NaN/Inf produced on the device");
     if (flags & DUST_FLAG_OVERFLOW)
         return fail(ctx, DUST_EOVERFLOW, "fixed-point deposit piece beyond 2^52 quanta");
@@ -1222,6 +1409,28 @@ extern "C" int dust_get_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double
     if (!fixed && !as_double) return DUST_OK;
     CU(cudaSetDevice(ctx->device));
     const int64_t m = ctx->ncell * 4;
+    if (io_async(ctx, mem)) {
+        // enqueue only: snapshot into one of two staging areas (the next
+        // step overwrites the deposit), read back on the output stream
+        int r = io_streams(ctx);
+        if (r) return r;
+        dust_ctx::IoBuf &b = ctx->out_dep[ctx->dep_flip];
+        ctx->dep_flip ^= 1;
+        r = io_out_acquire(ctx, b, 2 * m * sizeof(int64_t));
+        if (r) return r;
+        int64_t *fx = fixed ? static_cast<int64_t *>(b.d) : nullptr;
+        double *dd = as_double ? reinterpret_cast<double *>(static_cast<int64_t *>(b.d) + m) : nullptr;
+        if (fixed)
+            CU(cudaMemcpyAsync(fx, ctx->d_dep, m * sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+        if (as_double) {
+            dep_to_double_kernel<<<blocks_for(m), 256, 0, ctx->stream>>>(ctx->d_dep, m, ctx->quantum, dd);
+            CU(cudaGetLastError());
+        }
+        void *dst[2] = {fixed, as_double};
+        const void *src[2] = {fx, dd};
+        const size_t by[2] = {m * sizeof(int64_t), m * sizeof(double)};
+        return io_stage_out(ctx, b, 2, dst, src, by);
+    }
     const cudaMemcpyKind kind = mem == DUST_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (fixed) CU(cudaMemcpyAsync(fixed, ctx->d_dep, m * sizeof(int64_t), kind, ctx->stream));
     if (as_double) {
@@ -1253,6 +1462,36 @@ extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double
     double *outs[6] = {q0, q1, q2, v0, v1, v2};
     double *dev[6] = {q0, q1, q2, v0, v1, v2};
     int64_t *dids = ids;
+    if (io_async(ctx, mem)) {
+        // enqueue only: convert into one of two staging areas, read back on
+        // the output stream (done at the next dust_sync)
+        int r = io_streams(ctx);
+        if (r) return r;
+        dust_ctx::IoBuf &b = ctx->out_grains[ctx->out_flip];
+        ctx->out_flip ^= 1;
+        r = io_out_acquire(ctx, b, 7 * n * sizeof(double));
+        if (r) return r;
+        double *base = static_cast<double *>(b.d);
+        for (int k = 0; k < 6; ++k) dev[k] = outs[k] ? base + k * n : nullptr;
+        dids = ids ? reinterpret_cast<int64_t *>(base + 6 * n) : nullptr;
+        if (ctx->mixed)
+            get_particles_kernel<float><<<blocks_for(n), 256, 0, ctx->stream>>>(
+                ctx->geom.kind, store_of<float>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3],
+                dev[4], dev[5], dids);
+        else
+            get_particles_kernel<double><<<blocks_for(n), 256, 0, ctx->stream>>>(
+                ctx->geom.kind, store_of<double>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3],
+                dev[4], dev[5], dids);
+        CU(cudaGetLastError());
+        void *dst[7] = {q0, q1, q2, v0, v1, v2, ids};
+        const void *src[7] = {dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dids};
+        const size_t nb = n * sizeof(double);
+        const size_t by[7] = {nb, nb, nb, nb, nb, nb, nb};
+        r = io_stage_out(ctx, b, 7, dst, src, by);
+        if (r) return r;
+        *n_out = n;
+        return DUST_OK;
+    }
     if (mem == DUST_MEM_HOST) {
         int r = ensure_stage(ctx, 7 * n * sizeof(double));
         if (r) return r;
@@ -1290,6 +1529,17 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (cudaStream_t io : {ctx->io_in, ctx->io_out})
+        if (io) {
+            cudaStreamSynchronize(io);
+            cudaStreamDestroy(io);
+        }
+    io_free(ctx->in_grains);
+    io_free(ctx->in_gas);
+    for (int k = 0; k < 2; ++k) {
+        io_free(ctx->out_grains[k]);
+        io_free(ctx->out_dep[k]);
+    }
     free_store(ctx);
     for (int d = 0; d < 3; ++d) {
         dfree(ctx->d_edges[d]);
