@@ -276,7 +276,7 @@ def run_ours(args):
                  torch.empty(ngr, dtype=torch.int64).pin_memory().numpy(),
                  torch.empty((w.ncell, 4), dtype=torch.int64).pin_memory().numpy())
                 for _ in range(2)]
-        ke = max(2, min(args.steps, 10))
+        ke = max(2, min(args.steps, 20))
 
         def run_e2e(async_io):
             ctx = make(D.DUST_MIXED, 0, host_io_async=async_io)
