@@ -180,6 +180,14 @@ typedef struct dust_stats {
     int flags;             /* DUST_FLAG_* raised since the previous dust_sync   */
     int64_t steps;         /* steps taken                                       */
     double time;           /* simulation time                                   */
+    double dt_dust;        /* dust time step of Eq. particles_dt (Sec. 3.5):
+                              1.8 / max over grains and directions of
+                              |v_d^{n+1/2}| / dl_d, from the largest displacement
+                              of the steps since the previous dust_sync and the
+                              last step's length (exact when those steps had
+                              equal lengths); +inf if no grain moved.  In the
+                              orbital-advection frame the displacement includes
+                              the shear transport -q Omega x                  */
 } dust_stats;
 
 /* Device time per kernel group, summed over the steps since the last reset

@@ -95,6 +95,7 @@ struct dust_ctx {
     int out_flip = 0, dep_flip = 0;
 
     double t = 0.0;
+    double last_dt = 0.0;       // length of the last step (dust time step estimate)
     int64_t steps = 0;
     int64_t removed_total = 0;
     float max_moved = 0.f;
@@ -1318,6 +1319,7 @@ extern "C" int dust_step(dust_ctx *ctx, double dt)
     r = ctx->mixed ? run_step<float>(ctx, dt) : run_step<double>(ctx, dt);
     if (r) return r;
     ctx->t += dt;
+    ctx->last_dt = dt;
     ctx->steps += 1;
     ctx->timed_steps += 1;
     ctx->have_deposit = true;
@@ -1389,6 +1391,9 @@ extern "C" int dust_sync(dust_ctx *ctx, dust_stats *out)
         out->flags = flags;
         out->steps = ctx->steps;
         out->time = ctx->t;
+        // Eq. particles_dt: the largest displacement of these steps in zones
+        // is dt max_{p,d} |v_d^{n+1/2}| / dl_d
+        out->dt_dust = mv > 0.f ? 1.8 * fabs(ctx->last_dt) / (double)mv : INFINITY;
     }
     if (load_bad)
         return fail(ctx, DUST_EINVAL,
@@ -1869,6 +1874,7 @@ extern "C" int dust_batch_step(dust_batch *b, const double *dt, int nsteps)
             dust_ctx *c = b->ctx[i];
             BCU(cudaStreamWaitEvent(c->stream, b->done, 0));
             for (int s = 0; s < 2 * pairs; ++s) c->t += dt[i];
+            c->last_dt = dt[i];
             c->steps += 2 * pairs;
             c->timed_steps += 2 * pairs;
             c->have_deposit = true;

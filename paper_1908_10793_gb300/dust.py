@@ -69,7 +69,8 @@ class dust_kernel_times(ctypes.Structure):
 class dust_stats(ctypes.Structure):
     _fields_ = [("n_stored", ctypes.c_int64), ("n_active", ctypes.c_int64),
                 ("n_removed", ctypes.c_int64), ("max_cells_moved", ctypes.c_double),
-                ("flags", ctypes.c_int), ("steps", ctypes.c_int64), ("time", ctypes.c_double)]
+                ("flags", ctypes.c_int), ("steps", ctypes.c_int64), ("time", ctypes.c_double),
+                ("dt_dust", ctypes.c_double)]
 
 
 _lib = None
