@@ -867,6 +867,45 @@ void oracle_gas_predictor(const oracle_problem *P,
             }
 }
 
+/* Dust mass per zone (Sec. 3.4, Eq. deposition with q_p = m_p): every active
+ * grain adds m_p W to the zones of its stencil at its position, with the
+ * weights of the problem's weighting (CIC, TSC or volume weighting); nodes
+ * beyond an outflow boundary fold onto the edge zone, as the deposit does.
+ * mass[ncell] is overwritten; dividing by the zone volume gives rho_d. */
+void oracle_deposit_mass(const oracle_problem *P,
+                         const double *q0, const double *q1, const double *q2,
+                         const uint8_t *species, const uint8_t *active, int64_t n,
+                         double *mass)
+{
+    const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+    int wk[3];
+    for (int d = 0; d < 3; d++) wk[d] = weight_kind(P, d);
+    memset(mass, 0, sizeof(double) * (size_t)n0 * n1 * n2);
+    for (int64_t g = 0; g < n; g++) {
+        if (!active[g]) continue;
+        double m = P->sp_mass[species ? species[g] : 0];
+        double q[3] = {q0[g], q1[g], q2[g]};
+        int host[3];
+        double w[3][3];
+        for (int d = 0; d < 3; d++) {
+            if (P->n[d] <= 1) {
+                host[d] = 0; w[d][0] = 0.0; w[d][1] = 1.0; w[d][2] = 0.0;
+                continue;
+            }
+            host[d] = oracle_locate(P->edges[d], P->n[d], q[d]);
+            direction_weights(P, d, wk[d], q[d], host[d], w[d]);
+        }
+        for (int c = 0; c < 3; c++)
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    int64_t idx = node_index(host[0], a - 1, n0, P->bc[0])
+                        + (int64_t)n0 * (node_index(host[1], b - 1, n1, P->bc[1])
+                        + (int64_t)n1 * node_index(host[2], c - 1, n2, P->bc[2]));
+                    mass[idx] += m * (w[0][a] * w[1][b] * w[2][c]);
+                }
+    }
+}
+
 /* Gas momentum-like velocity per zone from physical velocity components
  * (Sec. 2.2: l_phi = R v_phi; spherical l_theta = r v_theta, l_phi = r
  * sin(theta) v_phi), evaluated at the zone centres (reading: the gathered

@@ -86,6 +86,9 @@ def _load():
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                 ctypes.c_double] + [dp] * 8
             lib.oracle_gas_predictor.restype = None
+            lib.oracle_deposit_mass.argtypes = [ctypes.POINTER(_ProblemC)] + [dp] * 3 + [
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, dp]
+            lib.oracle_deposit_mass.restype = None
             _lib = lib
     return _lib
 
@@ -200,6 +203,20 @@ def gas_predictor(prob, q, p, active, dt, rho, pg, species=None, param=None):
                              _dp(gg[0]), _dp(gg[1]), _dp(gg[2]), _dp(imp),
                              _dp(ph[0]), _dp(ph[1]), _dp(ph[2]))
     return imp, ph
+
+
+def deposit_mass(prob, q, active=None, species=None):
+    """Dust mass per zone (Eq. deposition with q_p = m_p) of the grains at
+    positions q (active ones only), with the problem's weighting."""
+    q = [_f64(x) for x in q]
+    n = len(q[0])
+    active = np.ones(n, np.uint8) if active is None else np.ascontiguousarray(active, np.uint8)
+    sp = None if species is None else np.ascontiguousarray(species, np.uint8)
+    out = np.zeros(prob.ncell)
+    _load().oracle_deposit_mass(ctypes.byref(prob.c), _dp(q[0]), _dp(q[1]), _dp(q[2]),
+                                None if sp is None else sp.ctypes.data, active.ctypes.data, n,
+                                _dp(out))
+    return out
 
 
 def gas_momentum(prob, v):

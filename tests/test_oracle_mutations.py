@@ -68,6 +68,10 @@ MUTATIONS = [
      "total += 2.0 * sin(0.5 * (u + v)) * sin(0.5 * (v - u));"),
     ("volume weighting r^2 instead of r^3", "return (a - b) * (a * a + a * b + b * b);",
      "return (a - b) * (a + b);"),
+    ("mass deposit without the z weight", "mass[idx] += m * (w[0][a] * w[1][b] * w[2][c]);",
+     "mass[idx] += m * (w[0][a] * w[1][b]);"),
+    ("mass deposit with species 0 for every grain",
+     "double m = P->sp_mass[species ? species[g] : 0];", "double m = P->sp_mass[0];"),
 ]
 
 
