@@ -340,6 +340,20 @@ int dust_sync(dust_ctx *ctx, dust_stats *out);
 int dust_get_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double,
                      double *quantum_out, int mem);
 
+/* Dust mass per zone of the grains as they are now (Sec. 3.4, Eq.
+ * deposition with q_p = m_p), with the context's weighting (CIC, TSC or
+ * volume weighting) at the stored positions; divided by the zone volume it
+ * is the dust density the paper's rigid-disk test (Sec. 4.7) measures.
+ * fixed: [ncell] int64 in units of the context's quantum read as a mass,
+ * or NULL; as_double: [ncell], fixed * quantum, or NULL; *quantum_out may
+ * be NULL.  Per grain, the non-host stencil zones get rint(W m / quantum)
+ * and the host zone the rest of rint(m / quantum), so the zone sum equals
+ * the grain sum exactly.  Zones beyond an outflow boundary fold onto the
+ * edge zone.  Synchronous.  Errors: DUST_ESTATE (no particles loaded),
+ * DUST_ECUDA, DUST_ENOMEM. */
+int dust_get_mass_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double,
+                          double *quantum_out, int mem);
+
 /* Copy the stored grains (current storage order, which the zone sort
  * permutes): coordinates, physical velocities and original ids (int64).
  * Removed grains are included with NaN coordinates.  cap = capacity of the

@@ -53,6 +53,7 @@ struct dust_ctx {
     // gas half-step predictor (dust_options.gas_predictor): its impulse and
     // the predicted gas the step gathers from
     unsigned long long *d_pred = nullptr;
+    unsigned long long *d_mass = nullptr;   // dust_get_mass_deposit (on first use)
     void *d_gas_half = nullptr;
     unsigned int *d_status = nullptr;
     unsigned int *h_status = nullptr;
@@ -1454,6 +1455,57 @@ extern "C" int dust_get_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double
     return DUST_OK;
 }
 
+extern "C" int dust_get_mass_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double,
+                                     double *quantum_out, int mem)
+{
+    if (!ctx) return DUST_EINVAL;
+    if (quantum_out) *quantum_out = ctx->quantum;
+    if (!fixed && !as_double) return DUST_OK;
+    if (!ctx->particles_set) return fail(ctx, DUST_ESTATE, "load particles first");
+    CU(cudaSetDevice(ctx->device));
+    const int64_t nc = ctx->ncell;
+    if (!ctx->d_mass) CU(dalloc(&ctx->d_mass, nc));
+    CU(cudaMemsetAsync(ctx->d_mass, 0, nc * sizeof(unsigned long long), ctx->stream));
+    const double *q[3];
+    const uint8_t *species = nullptr;
+    if (ctx->mixed) {
+        const StoreDev<float> st = store_of<float>(ctx, ctx->cur);
+        for (int d = 0; d < 3; ++d) q[d] = st.q[d];
+        species = st.species;
+    } else {
+        const StoreDev<double> st = store_of<double>(ctx, ctx->cur);
+        for (int d = 0; d < 3; ++d) q[d] = st.q[d];
+        species = st.species;
+    }
+    // the current store holds every grain (when a sort's gather is pending,
+    // in the previous order; the per-grain rule does not depend on it)
+    cudaError_t e;
+    const int wk = ctx->opt.weight;
+    switch (ctx->geom.kind) {
+    case DUST_CARTESIAN: e = launch_deposit_mass<GEOM_CART>(ctx->g, ctx->sp, wk, ctx->n_grains, q, species, ctx->d_mass, ctx->d_status, ctx->stream); break;
+    case DUST_SHEARING_BOX: e = launch_deposit_mass<GEOM_SB>(ctx->g, ctx->sp, wk, ctx->n_grains, q, species, ctx->d_mass, ctx->d_status, ctx->stream); break;
+    case DUST_CYLINDRICAL: e = launch_deposit_mass<GEOM_CYL>(ctx->g, ctx->sp, wk, ctx->n_grains, q, species, ctx->d_mass, ctx->d_status, ctx->stream); break;
+    default: e = launch_deposit_mass<GEOM_SPH>(ctx->g, ctx->sp, wk, ctx->n_grains, q, species, ctx->d_mass, ctx->d_status, ctx->stream); break;
+    }
+    CU(e);
+    const cudaMemcpyKind kind = mem == DUST_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (fixed) CU(cudaMemcpyAsync(fixed, ctx->d_mass, nc * sizeof(int64_t), kind, ctx->stream));
+    if (as_double) {
+        double *dst = as_double;
+        if (mem == DUST_MEM_HOST) {
+            int r = ensure_stage(ctx, nc * sizeof(double));
+            if (r) return r;
+            dst = ctx->d_stage;
+        }
+        dep_to_double_kernel<<<blocks_for(nc), 256, 0, ctx->stream>>>(ctx->d_mass, nc, ctx->quantum, dst);
+        CU(cudaGetLastError());
+        if (mem == DUST_MEM_HOST)
+            CU(cudaMemcpyAsync(as_double, dst, nc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DUST_OK;
+}
+
 extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
                                   double *v0, double *v1, double *v2, int64_t *ids,
                                   int64_t *n_out, int mem)
@@ -1569,6 +1621,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     dfree(ctx->d_cursor);
     dfree(ctx->d_blocksums);
     dfree(ctx->d_stage);
+    dfree(ctx->d_mass);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     for (int g = 0; g < dust_ctx::N_GROUPS; ++g)
         for (auto &pr : ctx->pending[g]) {

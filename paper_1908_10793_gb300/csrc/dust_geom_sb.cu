@@ -25,4 +25,8 @@ template cudaError_t launch_predict_gas<float, GEOM_SB, 1>(const StepArgs<float>
 template cudaError_t launch_predict_gas<double, GEOM_SB, 0>(const StepArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_gas<double, GEOM_SB, 1>(const StepArgs<double> &, cudaStream_t);
 
+template cudaError_t launch_deposit_mass<GEOM_SB>(const GridDev &, const SpeciesDev &, int, int64_t,
+                                                   const double *const[3], const uint8_t *,
+                                                   unsigned long long *, unsigned int *, cudaStream_t);
+
 }  // namespace dust

@@ -32,4 +32,8 @@ template cudaError_t launch_step_tiled<double, GEOM_SPH, 2>(const TiledArgs<doub
 template cudaError_t launch_predict_tiled<double, GEOM_SPH, 2>(const TiledArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_gas<double, GEOM_SPH, 2>(const StepArgs<double> &, cudaStream_t);
 
+template cudaError_t launch_deposit_mass<GEOM_SPH>(const GridDev &, const SpeciesDev &, int, int64_t,
+                                                   const double *const[3], const uint8_t *,
+                                                   unsigned long long *, unsigned int *, cudaStream_t);
+
 }  // namespace dust

@@ -167,6 +167,11 @@ cudaError_t launch_predict_gas(const StepArgs<Real> &a, cudaStream_t s);
 template <typename Real, int GEOM, int WEIGHT>
 cudaError_t launch_predict_tiled(const TiledArgs<Real> &a, cudaStream_t s);
 
+template <int GEOM>
+cudaError_t launch_deposit_mass(const GridDev &g, const SpeciesDev &sp, int wk, int64_t n,
+                                const double *const q[3], const uint8_t *species,
+                                unsigned long long *out, unsigned int *status, cudaStream_t s);
+
 template <typename Real>
 cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s, bool gather);
 

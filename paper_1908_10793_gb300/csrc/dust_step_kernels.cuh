@@ -301,6 +301,59 @@ __global__ void sort_keys_kernel(const SortArgs<Real> A)
     if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&A.count[key], __popc(peers));
 }
 
+// Dust mass per zone (Eq. deposition with q_p = m_p) in int64 fixed point,
+// with the per-grain rule of the drag deposit: each grain gives the pieces
+// rint(W m / quantum) to the non-host nodes of its stencil and the host the
+// rest of rint(m / quantum), so the zone sum is the grain sum exactly and
+// independent of the order.  The weights (weighting wk: CIC, TSC or volume)
+// are evaluated in double precision at the stored positions.
+template <int GEOM>
+__global__ void deposit_mass_kernel(GridDev g, SpeciesDev sp, int wk, int64_t n, const double *q0,
+                                    const double *q1, const double *q2, const uint8_t *species,
+                                    unsigned long long *out, unsigned int *status)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double q[3] = {q0[k], q1[k], q2[k]};
+    if (isnan(q[0])) return;  // removed grain
+    int host[3];
+    double w[3][3];
+    float iw[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) zone_weights<double, GEOM>(g, d, wk, q[d], host[d], w[d], iw[d]);
+    const double M = sp.mq[species ? species[k] : 0];
+    if (!(fabs(M) < 4.5e15)) atomicOr(&status[ST_FLAGS], DUST_FLAG_OVERFLOW);
+    long long rest = rround(M);
+#pragma unroll 1
+    for (int nd = 0; nd < 27; ++nd) {
+        const int a = nd % 3, b = (nd / 3) % 3, c = nd / 9;
+        if (nd == 13 || (g.n[0] <= 1 && a != 1) || (g.n[1] <= 1 && b != 1) || (g.n[2] <= 1 && c != 1))
+            continue;
+        const long long piece = rround(w[0][a] * w[1][b] * w[2][c] * M);
+        if (piece == 0) continue;
+        const int ix = node_of(host[0], a - 1, g.n[0], g.bc[0]);
+        const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
+        const int iz = node_of(host[2], c - 1, g.n[2], g.bc[2]);
+        atomicAdd(&out[ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz)], (unsigned long long)piece);
+        rest -= piece;
+    }
+    const int64_t h = node_of(host[0], 0, g.n[0], g.bc[0]) +
+                      (int64_t)g.n[0] * (node_of(host[1], 0, g.n[1], g.bc[1]) +
+                                         (int64_t)g.n[1] * node_of(host[2], 0, g.n[2], g.bc[2]));
+    if (rest != 0) atomicAdd(&out[h], (unsigned long long)rest);
+}
+
+template <int GEOM>
+cudaError_t launch_deposit_mass(const GridDev &g, const SpeciesDev &sp, int wk, int64_t n,
+                                const double *const q[3], const uint8_t *species,
+                                unsigned long long *out, unsigned int *status, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    deposit_mass_kernel<GEOM><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, sp, wk, n, q[0], q[1], q[2],
+                                                                           species, out, status);
+    return cudaGetLastError();
+}
+
 template <typename Real, int GEOM>
 cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s)
 {

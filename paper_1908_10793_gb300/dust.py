@@ -95,6 +95,7 @@ def load_library():
         "dust_step": (I, [P, D]),
         "dust_sync": (I, [P, ctypes.POINTER(dust_stats)]),
         "dust_get_deposit": (I, [P, P, P, ctypes.POINTER(D), I]),
+        "dust_get_mass_deposit": (I, [P, P, P, ctypes.POINTER(D), I]),
         "dust_get_particles": (I, [P, I64, P, P, P, P, P, P, P, ctypes.POINTER(I64), I]),
         "dust_get_kernel_times": (I, [P, ctypes.POINTER(dust_kernel_times), I]),
         "dust_step_noalloc": (I, [ctypes.POINTER(dust_geometry), ctypes.POINTER(dust_grid),
@@ -193,6 +194,14 @@ def dust_get_deposit(ctx, fixed=None, as_double=None):
     qo = ctypes.c_double()
     _check(ctx, load_library().dust_get_deposit(ctx, _ptr(fixed)[0], _ptr(as_double)[0],
                                                 ctypes.byref(qo), mem))
+    return qo.value
+
+
+def dust_get_mass_deposit(ctx, fixed=None, as_double=None):
+    mem = _mem_of(fixed, as_double)
+    qo = ctypes.c_double()
+    _check(ctx, load_library().dust_get_mass_deposit(ctx, _ptr(fixed)[0], _ptr(as_double)[0],
+                                                     ctypes.byref(qo), mem))
     return qo.value
 
 
@@ -324,6 +333,12 @@ class Context:
     def deposit(self):
         fixed = np.zeros((self.ncell, 4), np.int64)
         quantum = dust_get_deposit(self.handle, fixed=fixed)
+        return fixed, quantum
+
+    def mass_deposit(self):
+        """Dust mass per zone (int64 in units of the quantum) and the quantum."""
+        fixed = np.zeros(self.ncell, np.int64)
+        quantum = dust_get_mass_deposit(self.handle, fixed=fixed)
         return fixed, quantum
 
     def particles(self):
