@@ -578,3 +578,65 @@ def test_mass_deposit_matches_oracle(name, weight, precision):
     nz = _grains_per_zone_max(w) * (27 if w.n[2] > 1 else 9)
     tol = (0.5 * nz + 1) * quantum + 1e-12 * dense.max()
     assert np.abs(fixed * quantum - dense).max() <= tol
+
+
+def _take(w, idx):
+    import copy
+    s = copy.copy(w)
+    s.q = [x[idx] for x in w.q]
+    s.v = [x[idx] for x in w.v]
+    s.species = None if w.species is None else w.species[idx]
+    s.param = None if w.param is None else w.param[idx]
+    return s
+
+
+@pytest.mark.parametrize("name", ["cyldisk", "sphdisk"])
+def test_full_size_disks_sampled_against_oracle(name):
+    """The cylindrical (384 x 1024 x 64, 50M grains, feedback on) and
+    spherical (256 x 128 x 512, 33M grains) disks at full size, mixed
+    precision, one step in the configuration the benchmark times: 4000
+    sampled grains against the oracle run on them alone (a grain's push does
+    not depend on the others within a step), and the deposit of a slab of
+    four zone layers in the last direction against the oracle run on every
+    grain that can reach it."""
+    from parity_util import to_momentum
+    w = {"cyldisk": I.cyldisk, "sphdisk": I.sphdisk}[name]("full")
+    feedback = 1 if name == "cyldisk" else 0
+    g = run_gpu(w, 1, MIXED, feedback=feedback)
+    assert g["rc"] in (0, -4)
+    rng = np.random.default_rng(12)
+    idx = np.sort(rng.choice(w.ngrains, 4000, replace=False))
+    qo, vo, active, _, _ = run_oracle(_take(w, idx), 1, feedback=0)
+    alive = active.astype(bool)
+    assert np.array_equal(~np.isnan(g["q"][0][idx]), alive)
+    speed = np.sqrt(sum(vo[d][alive] ** 2 for d in range(3)))
+    for d in range(3):
+        metric = 1.0
+        if d > 0:
+            metric = 1.0 / qo[0][alive]
+            if d == 2 and w.geom == O.OG_SPHERICAL:
+                metric = metric / np.sin(qo[1][alive])
+        L = w.edges[d][-1] - w.edges[d][0]
+        ulps = (L + np.max(np.abs(w.edges[d]))) * 2.0 ** -52 * 4
+        dq = np.abs(periodic_diff(w, d, g["q"][d][idx][alive], qo[d][alive]))
+        assert np.all(dq <= 1e-5 * speed * metric * w.dt + ulps), d
+        dv = np.abs(g["v"][d][idx][alive] - vo[d][alive])
+        assert np.all(dv <= 1e-5 * speed), d
+    # deposit of zone layers k0 .. k0+3 of the last direction: every grain
+    # starting within two layers of them
+    n = w.n
+    k0 = n[2] // 2
+    kz = np.clip(np.searchsorted(w.edges[2], w.q[2], side="right") - 1, 0, n[2] - 1)
+    sel = np.nonzero((kz >= k0 - 2) & (kz <= k0 + 5))[0]
+    _, _, _, dep_o, _ = run_oracle(_take(w, sel), 1, feedback=0)
+    cells = np.arange(k0 * n[0] * n[1], (k0 + 4) * n[0] * n[1])
+    dep_g = g["fixed"][cells] * g["quantum"]
+    big = np.abs(dep_o[cells]).max(axis=0)
+    nz = _grains_per_zone_max(_take(w, sel)) * 27 * 2
+    p = to_momentum(w, w.q, w.v)
+    m = np.max(w.species_mass)
+    pmax = max(np.abs(x).max() for x in p)
+    tol = 16 * EPS32 * m * pmax * nz * np.array([1, 1, 1, 2.0 * pmax]) + 1e-5 * big + \
+        (0.5 * nz + 4) * g["quantum"]
+    err = np.abs(dep_g - dep_o[cells]).max(axis=0)
+    assert np.all(err <= tol), (err, tol)
