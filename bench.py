@@ -92,9 +92,9 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(ngrains):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current sources (else None)."""
+def profiled_record():
+    """The committed ncu figures of the step kernel (per grain), if they were
+    taken on the current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic_step_sbox3d.txt")
     try:
         rec = {}
@@ -103,11 +103,42 @@ def profiled_traffic(ngrains):
                 if line.strip() and not line.startswith("#"):
                     k, v = line.split(None, 1)
                     rec[k] = v.strip()
-        if rec.get("source_digest") != source_digest():
-            return None
-        return float(rec["dram_bytes_per_grain"]) * ngrains
+        return rec if rec.get("source_digest") == source_digest() else None
     except Exception:
         return None
+
+
+def profiled_traffic(ngrains):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (None when it is not for the current sources)."""
+    rec = profiled_record()
+    try:
+        return float(rec["dram_bytes_per_grain"]) * ngrains if rec else None
+    except (KeyError, ValueError):
+        return None
+
+
+# Warp-instruction issue of one GB300: 152 SMs x 4 schedulers x 2.07 GHz.
+ISSUE_PEAK_PER_S = 152 * 4 * 2.07e9
+
+
+def issue_rate(ngrains, kernel_s):
+    """The step kernel against the instruction-issue ceiling that bounds it:
+    warp instructions per grain from the committed ncu summary (same source
+    check as the traffic) times the grains of a launch, over the measured
+    launch time."""
+    rec = profiled_record()
+    try:
+        per = float(rec["warp_instructions_per_grain"]) if rec else None
+    except (KeyError, ValueError):
+        per = None
+    if per is None or kernel_s <= 0:
+        return None
+    achieved = per * ngrains / kernel_s
+    return {"bound": "instruction issue", "achieved": achieved, "peak": ISSUE_PEAK_PER_S,
+            "unit": "warp instructions/s", "frac": achieved / ISSUE_PEAK_PER_S,
+            "warp_instructions_per_grain": per,
+            "source": "profiles/traffic_step_sbox3d.txt (ncu), peak from unit counts and clock"}
 
 
 class ClockSampler:
@@ -354,6 +385,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": ab,
                          "bytes_per_grain": per_grain, "bytes_per_zone": per_zone,
                          "traffic": profiled_traffic(ngr)},
+            "issue": issue_rate(ngr, kt.step_ms / max(1, kt.step_launches) / 1e3),
             "gpu_launches": launches,
             "fp64": fp64,
             "batch": batch,
