@@ -56,6 +56,7 @@ extern "C" {
 #define DUST_ECFL (-4)      /* a grain moved more than 1.8 zones in one step (Eq. particles_dt); results are still correct */
 #define DUST_EOVERFLOW (-5) /* a fixed-point deposit piece exceeded 2^52 quanta */
 #define DUST_ENAN (-6)      /* a NaN/Inf appeared on the device                  */
+#define DUST_ETIMEOUT (-7)  /* a bounded device wait gave up; results are void  */
 #define DUST_ESTATE (-8)    /* call out of order (e.g. dust_step before data)    */
 
 /* ---- enumerations ------------------------------------------------------ */
@@ -102,6 +103,7 @@ enum { DUST_KERNEL_AUTO = 0, DUST_KERNEL_PER_GRAIN = 1, DUST_KERNEL_TILED = 2, D
 #define DUST_FLAG_OVERFLOW 2
 #define DUST_FLAG_CFL 4
 #define DUST_FLAG_WRAP 8   /* a grain moved more than one period in one step */
+#define DUST_FLAG_TIMEOUT 16 /* a bounded device wait gave up (a tile was skipped) */
 
 /* ---- descriptors -------------------------------------------------------- */
 typedef struct dust_geometry {

@@ -10,6 +10,8 @@
 #include <utility>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its enumerations (the encoder is fetched at run time)
+
 #include "dust_internal.h"
 
 using namespace dust;
@@ -55,6 +57,10 @@ struct dust_ctx {
     unsigned long long *d_pred = nullptr;
     unsigned long long *d_mass = nullptr;   // dust_get_mass_deposit (on first use)
     void *d_gas_half = nullptr;
+    // tensor maps (CUtensorMap, 64-byte aligned device memory) of d_gas [0]
+    // and d_gas_half [1] for the slab kernel's bulk gas-box copy; null: none
+    CUtensorMap *d_tmaps = nullptr;
+    bool tmap_ok[2] = {false, false};
     unsigned int *d_status = nullptr;
     unsigned int *h_status = nullptr;
 
@@ -804,10 +810,11 @@ template <typename Real, int GEOM>
 cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
                              const int32_t *key_off, int32_t *key_out, int32_t *count_out,
                              const int32_t *perm, const int32_t *perm_id, const StoreDev<Real> &dst,
-                             cudaStream_t s)
+                             const void *gas_tmap, cudaStream_t s)
 {
     TiledArgs<Real> ta;
     ta.s = a;
+    ta.gas_tmap = gas_tmap;
     ta.key_off = key_off;
     ta.tsc = weight == DUST_WEIGHT_TSC;
     const bool vol = (GEOM == GEOM_CYL || GEOM == GEOM_SPH) && weight == DUST_WEIGHT_VOLUME;
@@ -945,11 +952,15 @@ int run_step(dust_ctx *ctx, double dt)
     const StoreDev<Real> dst = store_of<Real>(ctx, 1 - ctx->cur);
     if (emit)
         CU(cudaMemsetAsync(ctx->d_count_next, 0, (ctx->g.nkeys + 2) * sizeof(int32_t), st));
+    // tensor map of the gas the step gathers from (the predicted gas or the
+    // gas at t^n)
+    const int tslot = ctx->opt.gas_predictor ? 1 : 0;
+    const void *tmap = ctx->tmap_ok[tslot] ? static_cast<const void *>(ctx->d_tmaps + tslot) : nullptr;
     switch (ctx->geom.kind) {
-    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
-    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
-    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
-    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, st); break;
+    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
+    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
+    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
+    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
     }
     delete step_timer;
     CU(e);
@@ -970,6 +981,47 @@ int run_step(dust_ctx *ctx, double dt)
 }
 
 }  // namespace
+
+// Tensor map of a mixed-precision gas array [ncell][4] float viewed as the
+// 4-D array (channel, x, y, z), with the slab kernel's box (4, B0, B1, B2)
+// (the tile plus its halo); written to device memory for the kernel.  The
+// encoder is the driver's cuTensorMapEncodeTiled, fetched at run time.
+// Returns false (no bulk copy; plain loads) if anything is unavailable.
+bool make_gas_tmap(dust_ctx *ctx, const void *gas, int slot)
+{
+    typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<EncodeTiled>(fn);
+    }
+    const GridDev &g = ctx->g;
+    cuuint64_t dims[4] = {4, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+    cuuint64_t strides[3] = {4 * sizeof(float), 4 * sizeof(float) * (cuuint64_t)g.n[0],
+                             4 * sizeof(float) * (cuuint64_t)g.n[0] * g.n[1]};
+    cuuint32_t box[4] = {4, 1, 1, 1};
+    for (int d = 0; d < 3; ++d) {
+        box[d + 1] = (cuuint32_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
+        if (box[d + 1] > 256) return false;
+    }
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMap map;
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(gas), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (!ctx->d_tmaps &&
+        cudaMalloc(reinterpret_cast<void **>(&ctx->d_tmaps), 2 * sizeof(CUtensorMap)) != cudaSuccess)
+        return false;
+    return cudaMemcpy(ctx->d_tmaps + slot, &map, sizeof map, cudaMemcpyHostToDevice) == cudaSuccess;
+}
 
 // ================================================================ C API ====
 
@@ -1115,6 +1167,10 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     }
     cudaMemset(ctx->d_gas, 0, ncell * 4 * ctx->rsz);
     cudaMemset(ctx->d_dep, 0, ncell * 4 * sizeof(unsigned long long));
+    if (ctx->mixed) {
+        ctx->tmap_ok[0] = make_gas_tmap(ctx, ctx->d_gas, 0);
+        if (ctx->d_gas_half) ctx->tmap_ok[1] = make_gas_tmap(ctx, ctx->d_gas_half, 1);
+    }
     cudaMemset(ctx->d_status, 0, ST_WORDS * sizeof(unsigned));
     if (cudaDeviceSynchronize() != cudaSuccess) {
         ctx->err = "device initialisation failed";
@@ -1399,6 +1455,8 @@ extern "C" int dust_sync(dust_ctx *ctx, dust_stats *out)
     if (load_bad)
         return fail(ctx, DUST_EINVAL,
                     "invalid grain or gas data in an asynchronous load (invalid grains were dropped)");
+    if (flags & DUST_FLAG_TIMEOUT)
+        return fail(ctx, DUST_ETIMEOUT, "a bounded device wait gave up; the step's results are void");
     if (flags & DUST_FLAG_NAN) return fail(ctx, DUST_ENAN, "NaN/Inf produced on the device");
     if (flags & DUST_FLAG_OVERFLOW)
         return fail(ctx, DUST_EOVERFLOW, "fixed-point deposit piece beyond 2^52 quanta");
@@ -1614,6 +1672,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     dfree(ctx->d_dep);
     dfree(ctx->d_pred);
     dfree(ctx->d_gas_half);
+    dfree(ctx->d_tmaps);
     dfree(ctx->d_status);
     dfree(ctx->d_count);
     dfree(ctx->d_count_next);

@@ -131,6 +131,10 @@ struct TiledArgs {
     const int32_t *perm;
     const int32_t *perm_id;
     StoreDev<Real> dst;
+    // optional: tensor map (CUtensorMap, device memory) of s.gas viewed as a
+    // 4-D array (channel, x, y, z); the slab kernel then stages its gas box
+    // with one bulk tensor copy
+    const void *gas_tmap;
 };
 
 template <typename Real>

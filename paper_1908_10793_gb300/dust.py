@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libdust.so")
 
 DUST_OK = 0
 DUST_EINVAL, DUST_ENOMEM, DUST_ECUDA, DUST_ECFL, DUST_EOVERFLOW, DUST_ENAN = -1, -2, -3, -4, -5, -6
-DUST_ESTATE = -8
+DUST_ETIMEOUT, DUST_ESTATE = -7, -8
 DUST_CARTESIAN, DUST_SHEARING_BOX, DUST_CYLINDRICAL, DUST_SPHERICAL = 0, 1, 2, 3
 DUST_BC_PERIODIC, DUST_BC_OUTFLOW = 0, 1
 DUST_WEIGHT_CIC, DUST_WEIGHT_TSC, DUST_WEIGHT_VOLUME = 0, 1, 2
@@ -25,7 +25,7 @@ DUST_FP64, DUST_MIXED = 0, 1
 DUST_PUSHER_EM, DUST_PUSHER_SEMI_IMPLICIT = 0, 1
 DUST_MEM_HOST, DUST_MEM_DEVICE = 0, 1
 DUST_KERNEL_AUTO, DUST_KERNEL_PER_GRAIN, DUST_KERNEL_TILED, DUST_KERNEL_SLAB = 0, 1, 2, 3
-DUST_FLAG_NAN, DUST_FLAG_OVERFLOW, DUST_FLAG_CFL, DUST_FLAG_WRAP = 1, 2, 4, 8
+DUST_FLAG_NAN, DUST_FLAG_OVERFLOW, DUST_FLAG_CFL, DUST_FLAG_WRAP, DUST_FLAG_TIMEOUT = 1, 2, 4, 8, 16
 
 
 class DustError(RuntimeError):
