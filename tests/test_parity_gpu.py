@@ -40,6 +40,15 @@ def compare(w, steps, precision, dt=None, feedback=None, extra_v=0.0, predictor=
     if predictor:
         kw["gas_predictor"] = 1
     g = run_gpu(w, steps, precision, dt, feedback, **kw)
+    check_against_oracle(w, g, (qo, vo, active, dep_o), steps, precision, dt, extra_v)
+    return g, (qo, vo, active, dep_o, pg_o)
+
+
+def check_against_oracle(w, g, oracle_out, steps, precision, dt, extra_v=0.0):
+    """Grain states and the last deposit of a GPU run (dict with q, v in id
+    order, fixed, quantum, rc) against the oracle's, with the tolerances of
+    the module docstring."""
+    qo, vo, active, dep_o = oracle_out
     assert g["rc"] in (0, -4), "device status %d" % g["rc"]
     alive = active.astype(bool)
     assert np.array_equal(~np.isnan(g["q"][0]), alive), "removed grains differ"
@@ -80,7 +89,6 @@ def compare(w, steps, precision, dt=None, feedback=None, extra_v=0.0, predictor=
             (0.5 * nz + 4) * g["quantum"]
     err = np.abs(dep_g - dep_o).max(axis=0)
     assert np.all(err <= tol), "deposit err %s tol %s" % (err, tol)
-    return g, (qo, vo, active, dep_o, pg_o)
 
 
 WORKLOADS = {
@@ -640,3 +648,43 @@ def test_full_size_disks_sampled_against_oracle(name):
         (0.5 * nz + 4) * g["quantum"]
     err = np.abs(dep_g - dep_o[cells]).max(axis=0)
     assert np.all(err <= tol), (err, tol)
+
+
+def test_full_size_batch_against_oracle():
+    """The 64 streaming-instability boxes at full size (36M grains) advanced
+    by one graph replay of two steps (the batch launch configuration the
+    benchmark times, mixed precision, feedback on); instances 0-4 (32^2 to
+    512^2 zones), 20 and 63 compared grain by grain, and their last deposit,
+    with the oracle run on the whole instance."""
+    from paper_1908_10793_gb300 import dust as D
+    ws = I.si2d_batch("full")
+    ctxs = []
+    try:
+        for w in ws:
+            c = D.Context(w, precision=MIXED, sort_interval=1)
+            c.set_gas(w.rho, w.vgas)
+            c.load(w.q, w.v, w.species, w.param)
+            ctxs.append(c)
+        b = D.dust_batch_create([c.handle for c in ctxs])
+        try:
+            D.dust_batch_step(b, [w.dt for w in ws], 2)
+        finally:
+            D.dust_batch_destroy(b)
+        for k in (0, 1, 2, 3, 4, 20, 63):
+            w, c = ws[k], ctxs[k]
+            q, v, ids = c.particles()
+            o = np.argsort(ids)
+            fixed, quantum = c.deposit()
+            rc, _ = c.sync(check=False)
+            g = {"q": [x[o] for x in q], "v": [x[o] for x in v], "fixed": fixed,
+                 "quantum": quantum, "rc": rc}
+            qo, vo, active, dep_o, _ = run_oracle(w, 2, feedback=1)
+            # the gas of step 2 carries step 1's fixed-point feedback
+            from test_oracle_push import _zone_volumes
+            dV = _zone_volumes(O.Problem(geom=w.geom, edges=w.edges))
+            nz = _grains_per_zone_max(w) * 9
+            dgas = (nz * 0.5 * quantum / (w.rho * dV)).max()
+            check_against_oracle(w, g, (qo, vo, active, dep_o), 2, MIXED, w.dt, extra_v=4 * dgas)
+    finally:
+        for c in ctxs:
+            c.close()
