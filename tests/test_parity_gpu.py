@@ -688,3 +688,21 @@ def test_full_size_batch_against_oracle():
     finally:
         for c in ctxs:
             c.close()
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+@pytest.mark.parametrize("n", [13, 21])
+def test_parity_ragged_tiles(n, precision):
+    """Shearing box of n^3 zones, n not a multiple of the 8^3 tile: partial
+    tiles on every axis (the slab kernel's gas box then reaches past the grid
+    at the high end as well as the low one), two steps with feedback."""
+    w = I.sbox3d(str(n))
+    compare(w, 2, precision, feedback=1, extra_v=_feedback_extra_v(w, 2))
+
+
+def _feedback_extra_v(w, steps):
+    from test_oracle_push import _zone_volumes
+    dV = _zone_volumes(O.Problem(geom=w.geom, edges=w.edges))
+    nz = _grains_per_zone_max(w) * (27 if w.n[2] > 1 else 9)
+    quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
+    return 2 * steps * (steps * nz * 0.5 * quantum / (w.rho * dV)).max()
