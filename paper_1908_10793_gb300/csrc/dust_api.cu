@@ -58,7 +58,7 @@ struct dust_ctx {
     unsigned long long *d_mass = nullptr;   // dust_get_mass_deposit (on first use)
     void *d_gas_half = nullptr;
     // tensor maps (CUtensorMap, 64-byte aligned device memory) of d_gas [0]
-    // and d_gas_half [1] for the slab kernel's bulk gas-box copy; null: none
+    // and d_gas_half [1] for the tile kernels' bulk gas-box copy; null: none
     CUtensorMap *d_tmaps = nullptr;
     bool tmap_ok[2] = {false, false};
     unsigned int *d_status = nullptr;
@@ -920,6 +920,8 @@ int run_step(dust_ctx *ctx, double dt)
                 pt.s = pa;
                 pt.key_off = ctx->d_count;
                 pt.perm = ctx->perm_pending ? ctx->d_pair_src : nullptr;
+                // the predictor gathers the gas at t^n
+                pt.gas_tmap = ctx->tmap_ok[0] ? static_cast<const void *>(ctx->d_tmaps) : nullptr;
                 pe = launch_predict<Real>(ctx->geom.kind, ctx->opt.weight, pa, &pt, ctx->stream);
             }
             CU(pe);
@@ -982,11 +984,12 @@ int run_step(dust_ctx *ctx, double dt)
 
 }  // namespace
 
-// Tensor map of a mixed-precision gas array [ncell][4] float viewed as the
-// 4-D array (channel, x, y, z), with the slab kernel's box (4, B0, B1, B2)
-// (the tile plus its halo); written to device memory for the kernel.  The
-// encoder is the driver's cuTensorMapEncodeTiled, fetched at run time.
-// Returns false (no bulk copy; plain loads) if anything is unavailable.
+// Tensor map of a gas array [ncell][4] (float in mixed precision, double in
+// FP64) viewed as the 4-D array (channel, x, y, z), with the tile kernels'
+// box (4, B0, B1, B2) (the tile plus its halo); written to device memory for
+// the kernels.  The encoder is the driver's cuTensorMapEncodeTiled, fetched
+// at run time.  Returns false (no bulk copy; plain loads) if anything is
+// unavailable.
 bool make_gas_tmap(dust_ctx *ctx, const void *gas, int slot)
 {
     typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -1003,9 +1006,9 @@ bool make_gas_tmap(dust_ctx *ctx, const void *gas, int slot)
         encode = reinterpret_cast<EncodeTiled>(fn);
     }
     const GridDev &g = ctx->g;
+    const cuuint64_t zone = 4 * (cuuint64_t)ctx->rsz;  // bytes per zone
     cuuint64_t dims[4] = {4, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
-    cuuint64_t strides[3] = {4 * sizeof(float), 4 * sizeof(float) * (cuuint64_t)g.n[0],
-                             4 * sizeof(float) * (cuuint64_t)g.n[0] * g.n[1]};
+    cuuint64_t strides[3] = {zone, zone * (cuuint64_t)g.n[0], zone * (cuuint64_t)g.n[0] * g.n[1]};
     cuuint32_t box[4] = {4, 1, 1, 1};
     for (int d = 0; d < 3; ++d) {
         box[d + 1] = (cuuint32_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
@@ -1013,7 +1016,8 @@ bool make_gas_tmap(dust_ctx *ctx, const void *gas, int slot)
     }
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUtensorMap map;
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(gas), dims, strides, box,
+    const CUtensorMapDataType type = ctx->mixed ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (encode(&map, type, 4, const_cast<void *>(gas), dims, strides, box,
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
@@ -1167,10 +1171,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     }
     cudaMemset(ctx->d_gas, 0, ncell * 4 * ctx->rsz);
     cudaMemset(ctx->d_dep, 0, ncell * 4 * sizeof(unsigned long long));
-    if (ctx->mixed) {
-        ctx->tmap_ok[0] = make_gas_tmap(ctx, ctx->d_gas, 0);
-        if (ctx->d_gas_half) ctx->tmap_ok[1] = make_gas_tmap(ctx, ctx->d_gas_half, 1);
-    }
+    ctx->tmap_ok[0] = make_gas_tmap(ctx, ctx->d_gas, 0);
+    if (ctx->d_gas_half) ctx->tmap_ok[1] = make_gas_tmap(ctx, ctx->d_gas_half, 1);
     cudaMemset(ctx->d_status, 0, ST_WORDS * sizeof(unsigned));
     if (cudaDeviceSynchronize() != cudaSuccess) {
         ctx->err = "device initialisation failed";

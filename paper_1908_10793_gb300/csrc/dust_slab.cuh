@@ -29,9 +29,6 @@
 namespace dust {
 
 constexpr int kSlabThreads = 256;
-// polls of the gas box's transaction barrier before the kernel gives up
-// (DUST_FLAG_TIMEOUT); a bulk copy of a few tens of KB takes microseconds
-constexpr unsigned kTmaPollLimit = 1u << 24;
 constexpr int kSlabCap = 128;  // grains per warp record pass
 // Record slots: a grain of zone kq (0..9 in the group) at pass position s
 // uses slot s + kq, so the owner lanes of different zones, which read their
@@ -133,49 +130,6 @@ __device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev
     return predict_key<float, GEOM>(g, ph, q, p, h);
 }
 
-// ---- bulk tensor copy (TMA) of the gas box into shared memory
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// One thread: initialise the transaction barrier and make it visible to the
-// copy engine.
-__device__ __forceinline__ void tma_barrier_init(unsigned long long *bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One thread: expect `bytes` and start the 4-D tile copy of the box at
-// coordinates (0, x, y, z) of the tensor map into dst.
-__device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int x, int y, int z,
-                                             unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                 ::"r"(smem_u32(dst)), "l"(tmap), "r"(0), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Every thread: wait for phase 0 of the barrier, at most `limit` polls.
-__device__ __forceinline__ bool tma_wait(unsigned long long *bar, unsigned limit)
-{
-    for (unsigned it = 0; it < limit; ++it) {
-        unsigned done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(smem_u32(bar)) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 template <int GEOM, int FLAT>
 __global__ void __launch_bounds__(kSlabThreads, 2)
 step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
@@ -246,11 +200,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     unsigned long long *sbar = reinterpret_cast<unsigned long long *>(
         (reinterpret_cast<uintptr_t>(szlo + g.T[1] + 1) + 7) & ~(uintptr_t)7);
     // the gas box by one bulk tensor copy, overlapping the tables below
-    const bool tma = TA.gas_tmap != nullptr;
-    if (tma && threadIdx.x == 0) {
-        tma_barrier_init(sbar);
-        tma_load_box(sgas, TA.gas_tmap, o[0], o[1], o[2], sbar, (unsigned)(bvol * 4 * sizeof(float)));
-    }
+    gas_box_begin<float>(TA.gas_tmap, sgas, o, bvol, sbar);
     for (int t = threadIdx.x; t < tsum + g.T[1] + 1; t += blockDim.x) {
         if (t < tsum) {
             const int d = t < toff[1] ? 0 : (t < toff[2] ? 1 : 2);
@@ -271,48 +221,11 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     }
 
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
-        if (!tma) {
-            const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
-            const int i = map_zone(o[0] + bx, g.n[0], g.bc[0]);
-            const int j = map_zone(o[1] + by, g.n[1], g.bc[1]);
-            const int k = map_zone(o[2] + bz, g.n[2], g.bc[2]);
-            float v[4];
-            load_gas<float>(A.gas, i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), v);
-            smem_gas_store<float>(sgas, lin, v);
-        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) sdep[c * bvol + lin] = 0ull;
     }
     __syncthreads();
-    if (tma) {
-        // bounded wait; on a timeout every thread waits once more for the copy
-        // in flight, and the block gives up with DUST_FLAG_TIMEOUT
-        const bool late = !tma_wait(sbar, kTmaPollLimit);
-        if (__syncthreads_or(late)) {
-            if (late) tma_wait(sbar, kTmaPollLimit);
-            if (threadIdx.x == 0) atomicOr(&A.status[ST_FLAGS], DUST_FLAG_TIMEOUT);
-            return;
-        }
-        // box zones outside the grid were filled with zeros: periodic images
-        // and outflow ghosts (copies of the edge zone) from global memory
-        bool edge = false;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) edge |= g.n[d] > 1 && (o[d] < 0 || o[d] + B[d] > g.n[d]);
-        if (edge) {
-            for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
-                const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
-                const int x = o[0] + bx, y = o[1] + by, z = o[2] + bz;
-                if (x >= 0 && x < g.n[0] && y >= 0 && y < g.n[1] && z >= 0 && z < g.n[2]) continue;
-                const int i = map_zone(x, g.n[0], g.bc[0]);
-                const int j = map_zone(y, g.n[1], g.bc[1]);
-                const int k = map_zone(z, g.n[2], g.bc[2]);
-                float v[4];
-                load_gas<float>(A.gas, i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), v);
-                smem_gas_store<float>(sgas, lin, v);
-            }
-            __syncthreads();
-        }
-    }
+    if (!gas_box_finish<float>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status)) return;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;

@@ -84,6 +84,106 @@ __device__ __forceinline__ void shared_add_i64(unsigned long long *p, long long 
     if (up != 0u) atomicAdd(w + 1, up);
 }
 
+// polls of the gas box's transaction barrier before the kernel gives up
+// (DUST_FLAG_TIMEOUT); a bulk copy of a few tens of KB takes microseconds
+constexpr unsigned kTmaPollLimit = 1u << 24;
+
+// ---- bulk tensor copy (TMA) of the gas box into shared memory
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// One thread: initialise the transaction barrier and make it visible to the
+// copy engine.
+__device__ __forceinline__ void tma_barrier_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One thread: expect `bytes` and start the 4-D tile copy of the box at
+// coordinates (0, x, y, z) of the tensor map into dst.
+__device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int x, int y, int z,
+                                             unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 ::"r"(smem_u32(dst)), "l"(tmap), "r"(0), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Every thread: wait for phase 0 of the barrier, at most `limit` polls.
+__device__ __forceinline__ bool tma_wait(unsigned long long *bar, unsigned limit)
+{
+    for (unsigned it = 0; it < limit; ++it) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(bar)) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Staging of a tile's gas box (the tile plus its halo: origin o, B zones per
+// direction, bvol = B0 B1 B2 zones of 4 channels) into shared memory.
+// Begin: with a tensor map of the gas, thread 0 starts one bulk copy.
+template <typename Real>
+__device__ __forceinline__ void gas_box_begin(const void *tmap, Real *sgas, const int o[3], int bvol,
+                                              unsigned long long *bar)
+{
+    if (tmap && threadIdx.x == 0) {
+        tma_barrier_init(bar);
+        tma_load_box(sgas, tmap, o[0], o[1], o[2], bar, (unsigned)(bvol * 4 * sizeof(Real)));
+    }
+}
+
+// Finish (every thread, after a __syncthreads that follows gas_box_begin):
+// without a tensor map, load the box zone by zone; with one, wait for the
+// copy (bounded: on a timeout every thread waits once more for the copy in
+// flight, DUST_FLAG_TIMEOUT is raised and false returned, and the block
+// must return) and replace the zones outside the grid, which the copy
+// zero-fills, by their periodic images or outflow ghosts.
+template <typename Real>
+__device__ bool gas_box_finish(const GridDev &g, const Real *gas, const void *tmap, Real *sgas,
+                               const int o[3], const int B[3], unsigned long long *bar,
+                               unsigned int *status)
+{
+    const int bvol = B[0] * B[1] * B[2];
+    bool edge = !tmap;
+    if (tmap) {
+        const bool late = !tma_wait(bar, kTmaPollLimit);
+        if (__syncthreads_or(late)) {
+            if (late) tma_wait(bar, kTmaPollLimit);
+            if (threadIdx.x == 0) atomicOr(&status[ST_FLAGS], DUST_FLAG_TIMEOUT);
+            return false;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) edge |= g.n[d] > 1 && (o[d] < 0 || o[d] + B[d] > g.n[d]);
+    }
+    if (edge) {
+        for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
+            const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
+            const int x = o[0] + bx, y = o[1] + by, z = o[2] + bz;
+            if (tmap && x >= 0 && x < g.n[0] && y >= 0 && y < g.n[1] && z >= 0 && z < g.n[2]) continue;
+            const int i = map_zone(x, g.n[0], g.bc[0]);
+            const int j = map_zone(y, g.n[1], g.bc[1]);
+            const int k = map_zone(z, g.n[2], g.bc[2]);
+            Real v[4];
+            load_gas<Real>(gas, i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), v);
+            smem_gas_store<Real>(sgas, lin, v);
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
 constexpr int kChunk = kTiledThreads;
 
 // Shared memory of one CTA: deposit box (channel major), run tables, gas
@@ -94,6 +194,7 @@ __host__ __device__ inline size_t tiled_smem_bytes(const GridDev &g)
     size_t bvol = 1;
     for (int d = 0; d < 3; ++d) bvol *= (size_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
     const size_t ch = kChunk;
+    // + 64: the three control words and the bulk copy's barrier (8-byte aligned)
     return bvol * (4 * sizeof(Real) + 4 * sizeof(long long)) +
            ch * (8 * sizeof(long long) + 13 * sizeof(Real) + 7 * sizeof(int)) + 64;
 }
@@ -114,7 +215,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
 {
     const StepArgs<Real> &A = TA.s;
     const GridDev &g = A.g;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int CH = kChunk;
 
     const int tile = blockIdx.x;
@@ -136,14 +237,14 @@ step_tiled_kernel(const TiledArgs<Real> TA)
     }
     const int bvol = B[0] * B[1] * B[2];
     unsigned char *ptr = smem_raw;
+    Real *sgas = reinterpret_cast<Real *>(ptr);     // first: 128-byte aligned for the bulk copy
+    ptr += (size_t)bvol * 4 * sizeof(Real);
     unsigned long long *sdep = reinterpret_cast<unsigned long long *>(ptr);
     ptr += (size_t)bvol * 4 * sizeof(long long);
     unsigned long long *run_sum = reinterpret_cast<unsigned long long *>(ptr);   // [4][CH]
     ptr += (size_t)CH * 4 * sizeof(long long);
     long long *run_q = reinterpret_cast<long long *>(ptr);                       // [4][CH]
     ptr += (size_t)CH * 4 * sizeof(long long);
-    Real *sgas = reinterpret_cast<Real *>(ptr);
-    ptr += (size_t)bvol * 4 * sizeof(Real);
     Real *rec_w = reinterpret_cast<Real *>(ptr);                                 // [9][CH]
     ptr += (size_t)CH * 9 * sizeof(Real);
     Real *rec_d = reinterpret_cast<Real *>(ptr);                                 // [4][CH]
@@ -163,20 +264,18 @@ step_tiled_kernel(const TiledArgs<Real> TA)
     int *seg_hi = reinterpret_cast<int *>(ptr);                                  // [CH]
     ptr += (size_t)CH * sizeof(int);
     int *ctl = reinterpret_cast<int *>(ptr);  // [0] runs, [1] chunk end key, [2] chunk grains
+    unsigned long long *sbar = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(ctl + 3) + 7) & ~(uintptr_t)7);
 
     // ---- stage the gas box, clear the deposit box and the run sums
+    gas_box_begin<Real>(TA.gas_tmap, sgas, o, bvol, sbar);
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
-        const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
-        const int i = map_zone(o[0] + bx, g.n[0], g.bc[0]);
-        const int j = map_zone(o[1] + by, g.n[1], g.bc[1]);
-        const int k = map_zone(o[2] + bz, g.n[2], g.bc[2]);
-        Real v[4];
-        load_gas<Real>(A.gas, i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), v);
-        smem_gas_store<Real>(sgas, lin, v);
 #pragma unroll
         for (int c = 0; c < 4; ++c) sdep[c * bvol + lin] = 0ull;
     }
     for (int k = threadIdx.x; k < 4 * CH; k += blockDim.x) run_sum[k] = 0ull;
+    __syncthreads();
+    if (!gas_box_finish<Real>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status)) return;
 
     int nremoved = 0;
     float moved = 0.f;
@@ -504,7 +603,7 @@ predict_tiled_kernel(const __grid_constant__ TiledArgs<Real> TA)
 {
     const StepArgs<Real> &A = TA.s;
     const GridDev &g = A.g;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tile = blockIdx.x;
     const int64_t kbase = (int64_t)tile * g.tvol;
     const int g0 = TA.key_off[kbase], g1 = TA.key_off[kbase + g.tvol];
@@ -520,20 +619,16 @@ predict_tiled_kernel(const __grid_constant__ TiledArgs<Real> TA)
         }
     }
     const int bvol = B[0] * B[1] * B[2];
-    unsigned long long *simp = reinterpret_cast<unsigned long long *>(smem_raw);   // [3][bvol]
-    Real *sgas = reinterpret_cast<Real *>(smem_raw + (size_t)bvol * 3 * sizeof(long long));
+    Real *sgas = reinterpret_cast<Real *>(smem_raw);   // first: 128-byte aligned for the bulk copy
+    unsigned long long *simp = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)bvol * 4 * sizeof(Real));   // [3][bvol]
+    unsigned long long *sbar = simp + (size_t)3 * bvol;
+    gas_box_begin<Real>(TA.gas_tmap, sgas, o, bvol, sbar);
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
-        const int bx = lin % B[0], by = (lin / B[0]) % B[1], bz = lin / (B[0] * B[1]);
-        const int i = map_zone(o[0] + bx, g.n[0], g.bc[0]);
-        const int j = map_zone(o[1] + by, g.n[1], g.bc[1]);
-        const int k = map_zone(o[2] + bz, g.n[2], g.bc[2]);
-        Real v[4];
-        load_gas<Real>(A.gas, i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k), v);
-        smem_gas_store<Real>(sgas, lin, v);
 #pragma unroll
         for (int c = 0; c < 3; ++c) simp[c * bvol + lin] = 0ull;
     }
     __syncthreads();
+    if (!gas_box_finish<Real>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status)) return;
     const Real dt = (Real)A.dt;
     for (int gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
         const int src = TA.perm ? TA.perm[gi] : gi;
@@ -642,7 +737,7 @@ cudaError_t launch_predict_tiled(const TiledArgs<Real> &a, cudaStream_t s)
     const int ntiles = g.nt[0] * g.nt[1] * g.nt[2];
     size_t bvol = 1;
     for (int d = 0; d < 3; ++d) bvol *= (size_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
-    const size_t smem = bvol * (3 * sizeof(long long) + 4 * sizeof(Real));
+    const size_t smem = bvol * (3 * sizeof(long long) + 4 * sizeof(Real)) + 16;  // + the barrier
     auto kern = predict_tiled_kernel<Real, GEOM, WEIGHT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
