@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=0, help="zones per side (profiling runs)")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 per-grain, 2 tiled")
     ap.add_argument("--tile", type=str, default="0,0,0")
+    ap.add_argument("--gas-predictor", action="store_true",
+                    help="main leg with the gas half-step predictor (profiling runs)")
     return ap.parse_args()
 
 
@@ -268,7 +270,7 @@ def run_ours(args):
         return ms, rc, st, kt, ck
 
     # ---- mixed path, inputs resident in HBM
-    ctx = make(D.DUST_MIXED, 1)
+    ctx = make(D.DUST_MIXED, 1, gas_predictor=int(args.gas_predictor))
     ms, rc, st, kt, clocks = timed(ctx, args.steps, args.warmup, sample_clocks=True)
     ngr = w.ngrains
     value = weak_value(world, ngr * args.steps, ms / 1e3)
@@ -375,7 +377,8 @@ def run_ours(args):
                        "precision": "mixed: f32 push/gather, f64 positions, int64 deposit",
                        "grains": ngr, "zones": w.ncell, "sort_interval": args.sort_interval or 1,
                        "l2": "inputs larger than L2 (grain store %d MB)" % (ngr * 36 // 2**20),
-                       "parallelism": "independent instance per GPU"},
+                       "parallelism": "independent instance per GPU",
+                       "gas_predictor": int(args.gas_predictor)},
             "status": rc,
             "kernel_ms_per_step": {"step": kt.step_ms / args.steps, "sort": kt.sort_ms / args.steps,
                                    "other": kt.other_ms / args.steps},
