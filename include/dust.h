@@ -172,6 +172,12 @@ typedef struct dust_options {
                               (DUST_EINVAL) instead of by the call, and invalid
                               grains are dropped as removed.  dust_get_gas stays
                               synchronous.                                    */
+    int test_wait_timeout; /* testing only (0 otherwise): 1 makes the tile
+                              kernels' bounded wait for their gas box run out
+                              after 1 ms (the barrier expects more bytes than
+                              the copy brings), so the failure path can be
+                              checked without a GPU fault: the step's blocks
+                              give up and dust_sync returns DUST_ETIMEOUT   */
 } dust_options;
 
 typedef struct dust_stats {

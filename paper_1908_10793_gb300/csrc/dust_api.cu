@@ -810,11 +810,13 @@ template <typename Real, int GEOM>
 cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
                              const int32_t *key_off, int32_t *key_out, int32_t *count_out,
                              const int32_t *perm, const int32_t *perm_id, const StoreDev<Real> &dst,
-                             const void *gas_tmap, cudaStream_t s)
+                             const void *gas_tmap, unsigned wait_extra_tx, cudaStream_t s)
 {
     TiledArgs<Real> ta;
     ta.s = a;
     ta.gas_tmap = gas_tmap;
+    ta.wait_extra_tx = wait_extra_tx;
+    ta.wait_ns = wait_extra_tx ? 1000000ull : 0ull;  // the timeout test waits 1 ms
     ta.key_off = key_off;
     ta.tsc = weight == DUST_WEIGHT_TSC;
     const bool vol = (GEOM == GEOM_CYL || GEOM == GEOM_SPH) && weight == DUST_WEIGHT_VOLUME;
@@ -922,6 +924,8 @@ int run_step(dust_ctx *ctx, double dt)
                 pt.perm = ctx->perm_pending ? ctx->d_pair_src : nullptr;
                 // the predictor gathers the gas at t^n
                 pt.gas_tmap = ctx->tmap_ok[0] ? static_cast<const void *>(ctx->d_tmaps) : nullptr;
+                pt.wait_extra_tx = ctx->opt.test_wait_timeout ? 16u : 0u;
+                pt.wait_ns = ctx->opt.test_wait_timeout ? 1000000ull : 0ull;
                 pe = launch_predict<Real>(ctx->geom.kind, ctx->opt.weight, pa, &pt, ctx->stream);
             }
             CU(pe);
@@ -958,11 +962,12 @@ int run_step(dust_ctx *ctx, double dt)
     // gas at t^n)
     const int tslot = ctx->opt.gas_predictor ? 1 : 0;
     const void *tmap = ctx->tmap_ok[tslot] ? static_cast<const void *>(ctx->d_tmaps + tslot) : nullptr;
+    const unsigned xtx = ctx->opt.test_wait_timeout ? 16u : 0u;
     switch (ctx->geom.kind) {
-    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
-    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
-    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
-    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, st); break;
+    case DUST_CARTESIAN: e = launch_step_geom<Real, GEOM_CART>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, xtx, st); break;
+    case DUST_SHEARING_BOX: e = launch_step_geom<Real, GEOM_SB>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, xtx, st); break;
+    case DUST_CYLINDRICAL: e = launch_step_geom<Real, GEOM_CYL>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, xtx, st); break;
+    default: e = launch_step_geom<Real, GEOM_SPH>(a, wt, kn, ko, kout, cout_, perm, perm_id, dst, tmap, xtx, st); break;
     }
     delete step_timer;
     CU(e);
@@ -1043,6 +1048,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         return fail(nullptr, DUST_EINVAL, "gas_predictor must be 0 or 1");
     if (opt->host_io_async != 0 && opt->host_io_async != 1)
         return fail(nullptr, DUST_EINVAL, "host_io_async must be 0 or 1");
+    if (opt->test_wait_timeout != 0 && opt->test_wait_timeout != 1)
+        return fail(nullptr, DUST_EINVAL, "test_wait_timeout must be 0 or 1");
     if (opt->pusher == DUST_PUSHER_SEMI_IMPLICIT && geom->kind != DUST_CARTESIAN &&
         geom->kind != DUST_SHEARING_BOX)
         return fail(nullptr, DUST_EINVAL,

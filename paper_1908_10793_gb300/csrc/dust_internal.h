@@ -132,9 +132,13 @@ struct TiledArgs {
     const int32_t *perm_id;
     StoreDev<Real> dst;
     // optional: tensor map (CUtensorMap, device memory) of s.gas viewed as a
-    // 4-D array (channel, x, y, z); the slab kernel then stages its gas box
-    // with one bulk tensor copy
+    // 4-D array (channel, x, y, z); the tile kernels then stage their gas
+    // box with one bulk tensor copy
     const void *gas_tmap;
+    // limit of the wait for that copy (0: one second), and bytes the
+    // barrier expects beyond the copy (0; > 0 only to test the timeout)
+    unsigned long long wait_ns;
+    unsigned int wait_extra_tx;
 };
 
 template <typename Real>

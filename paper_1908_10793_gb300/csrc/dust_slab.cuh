@@ -200,7 +200,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     unsigned long long *sbar = reinterpret_cast<unsigned long long *>(
         (reinterpret_cast<uintptr_t>(szlo + g.T[1] + 1) + 7) & ~(uintptr_t)7);
     // the gas box by one bulk tensor copy, overlapping the tables below
-    gas_box_begin<float>(TA.gas_tmap, sgas, o, bvol, sbar);
+    gas_box_begin<float>(TA.gas_tmap, sgas, o, bvol, sbar, TA.wait_extra_tx);
     for (int t = threadIdx.x; t < tsum + g.T[1] + 1; t += blockDim.x) {
         if (t < tsum) {
             const int d = t < toff[1] ? 0 : (t < toff[2] ? 1 : 2);
@@ -225,7 +225,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
         for (int c = 0; c < 4; ++c) sdep[c * bvol + lin] = 0ull;
     }
     __syncthreads();
-    if (!gas_box_finish<float>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status)) return;
+    if (!gas_box_finish<float>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status, TA.wait_ns)) return;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;

@@ -84,9 +84,10 @@ __device__ __forceinline__ void shared_add_i64(unsigned long long *p, long long 
     if (up != 0u) atomicAdd(w + 1, up);
 }
 
-// polls of the gas box's transaction barrier before the kernel gives up
-// (DUST_FLAG_TIMEOUT); a bulk copy of a few tens of KB takes microseconds
-constexpr unsigned kTmaPollLimit = 1u << 24;
+// How long a block waits for its gas box before it gives up
+// (DUST_FLAG_TIMEOUT): one second; the copy of a few tens of KB takes
+// microseconds.
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;
 
 // ---- bulk tensor copy (TMA) of the gas box into shared memory
 
@@ -117,30 +118,40 @@ __device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int x,
                  : "memory");
 }
 
-// Every thread: wait for phase 0 of the barrier, at most `limit` polls.
-__device__ __forceinline__ bool tma_wait(unsigned long long *bar, unsigned limit)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (unsigned it = 0; it < limit; ++it) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every thread: wait for phase 0 of the barrier, at most limit_ns.
+__device__ __forceinline__ bool tma_wait(unsigned long long *bar, unsigned long long limit_ns)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         unsigned done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(smem_u32(bar)) : "memory");
         if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 // Staging of a tile's gas box (the tile plus its halo: origin o, B zones per
 // direction, bvol = B0 B1 B2 zones of 4 channels) into shared memory.
 // Begin: with a tensor map of the gas, thread 0 starts one bulk copy.
+// extra_tx > 0 (testing the timeout path only) makes the barrier expect
+// more bytes than the copy delivers, so that the wait runs out.
 template <typename Real>
 __device__ __forceinline__ void gas_box_begin(const void *tmap, Real *sgas, const int o[3], int bvol,
-                                              unsigned long long *bar)
+                                              unsigned long long *bar, unsigned extra_tx)
 {
     if (tmap && threadIdx.x == 0) {
         tma_barrier_init(bar);
-        tma_load_box(sgas, tmap, o[0], o[1], o[2], bar, (unsigned)(bvol * 4 * sizeof(Real)));
+        tma_load_box(sgas, tmap, o[0], o[1], o[2], bar, (unsigned)(bvol * 4 * sizeof(Real)) + extra_tx);
     }
 }
 
@@ -153,14 +164,15 @@ __device__ __forceinline__ void gas_box_begin(const void *tmap, Real *sgas, cons
 template <typename Real>
 __device__ bool gas_box_finish(const GridDev &g, const Real *gas, const void *tmap, Real *sgas,
                                const int o[3], const int B[3], unsigned long long *bar,
-                               unsigned int *status)
+                               unsigned int *status, unsigned long long wait_ns)
 {
     const int bvol = B[0] * B[1] * B[2];
     bool edge = !tmap;
     if (tmap) {
-        const bool late = !tma_wait(bar, kTmaPollLimit);
+        const unsigned long long lim = wait_ns ? wait_ns : kTmaWaitNs;
+        const bool late = !tma_wait(bar, lim);
         if (__syncthreads_or(late)) {
-            if (late) tma_wait(bar, kTmaPollLimit);
+            if (late) tma_wait(bar, lim);
             if (threadIdx.x == 0) atomicOr(&status[ST_FLAGS], DUST_FLAG_TIMEOUT);
             return false;
         }
@@ -268,14 +280,14 @@ step_tiled_kernel(const TiledArgs<Real> TA)
         (reinterpret_cast<uintptr_t>(ctl + 3) + 7) & ~(uintptr_t)7);
 
     // ---- stage the gas box, clear the deposit box and the run sums
-    gas_box_begin<Real>(TA.gas_tmap, sgas, o, bvol, sbar);
+    gas_box_begin<Real>(TA.gas_tmap, sgas, o, bvol, sbar, TA.wait_extra_tx);
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) sdep[c * bvol + lin] = 0ull;
     }
     for (int k = threadIdx.x; k < 4 * CH; k += blockDim.x) run_sum[k] = 0ull;
     __syncthreads();
-    if (!gas_box_finish<Real>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status)) return;
+    if (!gas_box_finish<Real>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status, TA.wait_ns)) return;
 
     int nremoved = 0;
     float moved = 0.f;
@@ -622,13 +634,13 @@ predict_tiled_kernel(const __grid_constant__ TiledArgs<Real> TA)
     Real *sgas = reinterpret_cast<Real *>(smem_raw);   // first: 128-byte aligned for the bulk copy
     unsigned long long *simp = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)bvol * 4 * sizeof(Real));   // [3][bvol]
     unsigned long long *sbar = simp + (size_t)3 * bvol;
-    gas_box_begin<Real>(TA.gas_tmap, sgas, o, bvol, sbar);
+    gas_box_begin<Real>(TA.gas_tmap, sgas, o, bvol, sbar, TA.wait_extra_tx);
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) simp[c * bvol + lin] = 0ull;
     }
     __syncthreads();
-    if (!gas_box_finish<Real>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status)) return;
+    if (!gas_box_finish<Real>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status, TA.wait_ns)) return;
     const Real dt = (Real)A.dt;
     for (int gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
         const int src = TA.perm ? TA.perm[gi] : gi;

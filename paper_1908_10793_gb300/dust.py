@@ -56,7 +56,8 @@ class dust_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("sort_interval", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("device", ctypes.c_int), ("timing", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("pusher", ctypes.c_int),
-                ("gas_predictor", ctypes.c_int), ("host_io_async", ctypes.c_int)]
+                ("gas_predictor", ctypes.c_int), ("host_io_async", ctypes.c_int),
+                ("test_wait_timeout", ctypes.c_int)]
 
 
 class dust_kernel_times(ctypes.Structure):
@@ -285,7 +286,7 @@ def dust_destroy(ctx):
 # ------------------------------------------------- descriptor helpers ----
 def make_descriptors(w, precision=DUST_MIXED, feedback=None, stream=None, sort_interval=0,
                      kernel=DUST_KERNEL_AUTO, quantum=0.0, device=0, timing=0, tile=(0, 0, 0),
-                     pusher=None, gas_predictor=0, host_io_async=0):
+                     pusher=None, gas_predictor=0, host_io_async=0, test_wait_timeout=0):
     """C descriptors for a workload from paper_1908_10793_gb300.inputs.
     Returns (geometry, grid, species list, options, keepalive)."""
     geo = dust_geometry(kind=w.geom, fargo=w.fargo, omega=w.omega, q=w.qshear, gm=w.gm,
@@ -303,7 +304,8 @@ def make_descriptors(w, precision=DUST_MIXED, feedback=None, stream=None, sort_i
                        quantum=quantum, stream=stream, sort_interval=sort_interval,
                        kernel=kernel, device=device, timing=timing,
                        pusher=getattr(w, "pusher", DUST_PUSHER_EM) if pusher is None else pusher,
-                       gas_predictor=gas_predictor, host_io_async=host_io_async)
+                       gas_predictor=gas_predictor, host_io_async=host_io_async,
+                       test_wait_timeout=test_wait_timeout)
     for d in range(3):
         opt.tile[d] = int(tile[d])
     return geo, grid, sp, opt, edges

@@ -74,3 +74,13 @@ def test_host_io_async_option_validated_without_gpu(lib):
     with pytest.raises(D.DustError) as e:
         D.dust_create(geo, grid, sp, opt)
     assert e.value.code == D.DUST_EINVAL and "host_io_async" in str(e.value)
+
+
+def test_test_wait_timeout_option_validated_without_gpu(lib):
+    from paper_1908_10793_gb300 import dust as D
+    from paper_1908_10793_gb300 import inputs as I
+    w = I.box2d("small")
+    geo, grid, sp, opt, keep = D.make_descriptors(w, test_wait_timeout=3)
+    with pytest.raises(D.DustError) as e:
+        D.dust_create(geo, grid, sp, opt)
+    assert e.value.code == D.DUST_EINVAL and "test_wait_timeout" in str(e.value)
