@@ -764,29 +764,46 @@ inline int slab_flat(const GridDev &g)
     return -1;
 }
 
+// Slab kernel variant: the flat pattern, and the pusher / shearing-box frame
+// fixed at compile time where the context allows (MODE, see launch_step_slab).
+template <int GEOM, int FLAT>
+cudaError_t launch_slab_mode(const TiledArgs<float> &ta, cudaStream_t s)
+{
+    const PhysDev &ph = ta.s.ph;
+    if constexpr (GEOM == GEOM_CYL || GEOM == GEOM_SPH) {
+        return launch_step_slab<GEOM, FLAT, 1>(ta, s);  // exponential midpoint only
+    } else if constexpr (GEOM == GEOM_SB) {
+        if (ph.pusher != DUST_PUSHER_EM) return launch_step_slab<GEOM, FLAT, 0>(ta, s);
+        return ph.fargo ? launch_step_slab<GEOM, FLAT, 1>(ta, s) : launch_step_slab<GEOM, FLAT, 2>(ta, s);
+    } else {
+        return ph.pusher != DUST_PUSHER_EM ? launch_step_slab<GEOM, FLAT, 0>(ta, s)
+                                           : launch_step_slab<GEOM, FLAT, 1>(ta, s);
+    }
+}
+
 template <int GEOM>
 cudaError_t launch_slab_geom(const TiledArgs<float> &ta, int flat, cudaStream_t s);
 
 template <>
 cudaError_t launch_slab_geom<GEOM_CART>(const TiledArgs<float> &ta, int flat, cudaStream_t s)
 {
-    return flat == 0 ? launch_step_slab<GEOM_CART, 0>(ta, s) : launch_step_slab<GEOM_CART, 2>(ta, s);
+    return flat == 0 ? launch_slab_mode<GEOM_CART, 0>(ta, s) : launch_slab_mode<GEOM_CART, 2>(ta, s);
 }
 template <>
 cudaError_t launch_slab_geom<GEOM_SB>(const TiledArgs<float> &ta, int flat, cudaStream_t s)
 {
-    return flat == 0 ? launch_step_slab<GEOM_SB, 0>(ta, s)
-                     : (flat == 1 ? launch_step_slab<GEOM_SB, 1>(ta, s) : launch_step_slab<GEOM_SB, 2>(ta, s));
+    return flat == 0 ? launch_slab_mode<GEOM_SB, 0>(ta, s)
+                     : (flat == 1 ? launch_slab_mode<GEOM_SB, 1>(ta, s) : launch_slab_mode<GEOM_SB, 2>(ta, s));
 }
 template <>
 cudaError_t launch_slab_geom<GEOM_CYL>(const TiledArgs<float> &ta, int, cudaStream_t s)
 {
-    return launch_step_slab<GEOM_CYL, 0>(ta, s);
+    return launch_slab_mode<GEOM_CYL, 0>(ta, s);
 }
 template <>
 cudaError_t launch_slab_geom<GEOM_SPH>(const TiledArgs<float> &ta, int, cudaStream_t s)
 {
-    return launch_step_slab<GEOM_SPH, 0>(ta, s);
+    return launch_slab_mode<GEOM_SPH, 0>(ta, s);
 }
 
 // Whether volume weighting differs from CIC in this geometry (it has a

@@ -162,8 +162,11 @@ cudaError_t launch_step_per_grain(const StepArgs<Real> &a, cudaStream_t s);
 template <typename Real, int GEOM, int WEIGHT>
 cudaError_t launch_step_tiled(const TiledArgs<Real> &a, cudaStream_t s);
 
-// FLAT: 0 = all directions gridded, 1 = y not gridded, 2 = z not gridded
-template <int GEOM, int FLAT>
+// FLAT: 0 = all directions gridded, 1 = y not gridded, 2 = z not gridded;
+// MODE: 0 = pusher and frame at run time, 1 = exponential midpoint (and, in
+// the shearing box, the orbital-advection frame), 2 = exponential midpoint
+// in the standard shearing-box frame
+template <int GEOM, int FLAT, int MODE>
 cudaError_t launch_step_slab(const TiledArgs<float> &a, cudaStream_t s);
 
 template <typename Real, int GEOM>

@@ -130,7 +130,11 @@ __device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev
     return predict_key<float, GEOM>(g, ph, q, p, h);
 }
 
-template <int GEOM, int FLAT>
+// MODE 0: the pusher and the shearing-box frame as the context has them;
+// MODE > 0 fixes the exponential-midpoint pusher and, in the shearing box,
+// the frame (1: orbital advection, 2: standard) at compile time, which
+// drops the other branches from the hot code.
+template <int GEOM, int FLAT, int MODE>
 __global__ void __launch_bounds__(kSlabThreads, 2)
 step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
 {
@@ -138,6 +142,12 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     constexpr int NB = Sh::NB, NC = Sh::NC;
     const StepArgs<float> &A = TA.s;
     const GridDev &g = A.g;
+    // the inline push reads ph; the rare out-of-line paths read the kernel
+    // argument (the same values)
+    PhysDev ph = A.ph;
+    if (MODE > 0) ph.pusher = DUST_PUSHER_EM;
+    if (GEOM == GEOM_SB && MODE == 1) ph.fargo = 1;
+    if (GEOM == GEOM_SB && MODE == 2) ph.fargo = 0;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const unsigned FULL = 0xffffffffu;
 
@@ -231,7 +241,6 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     const int nwarps = blockDim.x >> 5;
     const int a = lane % 3, kq = lane / 3;
     const int base = lane - a;
-    const int src1 = base + (a + 1) % 3, src2 = base + (a + 2) % 3;
     const float h = (float)(0.5 * A.dt), dt = (float)A.dt;
     const int groups = (g.tvol + 9) / 10;
     int nremoved = 0;
@@ -356,7 +365,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                             inc1[2] = h * pn[2] / (r * r * st * st); u[2] += inc1[2];
                         } else if (GEOM == GEOM_SB) {
                             inc1[0] = h * pn[0]; u[0] += inc1[0];
-                            inc1[1] = A.ph.fargo ? h * (pn[1] - A.ph.q_om_f * (zc3[0] + u[0])) : h * pn[1];
+                            inc1[1] = ph.fargo ? h * (pn[1] - ph.q_om_f * (zc3[0] + u[0])) : h * pn[1];
                             u[1] += inc1[1];
                             inc1[2] = h * pn[2]; u[2] += inc1[2];
                         } else {
@@ -476,14 +485,14 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                         }
                     }
                     const float value = S.param ? S.param[src] : A.sp.tau_f[sp];
-                    const float tau = stopping_time<float, GEOM>(A.ph, A.sp.mode[sp], value, qf, G[0]);
+                    const float tau = stopping_time<float, GEOM>(ph, A.sp.mode[sp], value, qf, G[0]);
                     const float x = dt / tau;
                     const float E = expf(-x);
                     const float cg = -expm1f(-x);
                     const float h1 = (x == 0.f) ? dt : dt * cg / x;
                     const float vg[3] = {G[1], G[2], G[3]};
                     float pp[3], acc3[3], dH[3], inc2[3];
-                    kick_any<float, GEOM>(A.ph, qf, pn, vg, tau, dt, E, cg, h1, pp, acc3, dH);
+                    kick_any<float, GEOM>(ph, qf, pn, vg, tau, dt, E, cg, h1, pp, acc3, dH);
                     if (ingroup) {
                         // second half drift with the half-step metric factors, then
                         // one double-precision update by the summed increment
@@ -498,7 +507,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                             inc2[2] = h * pp[2] / (qf[0] * qf[0] * st * st);
                         } else if (GEOM == GEOM_SB) {
                             inc2[0] = h * pp[0];
-                            inc2[1] = A.ph.fargo ? h * (pp[1] - A.ph.q_om_f * qf[0]) : h * pp[1];
+                            inc2[1] = ph.fargo ? h * (pp[1] - ph.q_om_f * qf[0]) : h * pp[1];
                             inc2[2] = h * pp[2];
                         } else {
     #pragma unroll
@@ -508,10 +517,10 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                         for (int d = 0; d < 3; ++d) q[d] += f32_to_f64(inc1[d] + inc2[d]);
                     } else {
                         const double qm[3] = {q[0], q[1], q[2]};
-                        drift<float, GEOM>(A.ph, q, qm, pp, h, true, inc2);
+                        drift<float, GEOM>(ph, q, qm, pp, h, true, inc2);
                     }
                     float pnew[3] = {pp[0], pp[1], pp[2]};
-                    const bool alive = apply_bc<float, GEOM>(g, A.ph, shift_end_of(A), q, pnew);
+                    const bool alive = apply_bc<float, GEOM>(g, ph, shift_end_of(A), q, pnew);
                     const float mq = A.sp.mqf[sp];
     #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -581,7 +590,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                                 un[2] += h * pnew[2] / (r * r * st * st);
                             } else if (GEOM == GEOM_SB) {
                                 un[0] += h * pnew[0];
-                                un[1] += A.ph.fargo ? h * (pnew[1] - A.ph.q_om_f * (zc3[0] + un[0])) : h * pnew[1];
+                                un[1] += ph.fargo ? h * (pnew[1] - ph.q_om_f * (zc3[0] + un[0])) : h * pnew[1];
                                 un[2] += h * pnew[2];
                             } else {
 #pragma unroll
@@ -774,13 +783,13 @@ inline size_t slab_smem_bytes(const GridDev &g)
            16;  // the bulk copy's transaction barrier (8-byte aligned)
 }
 
-template <int GEOM, int FLAT>
+template <int GEOM, int FLAT, int MODE>
 cudaError_t launch_step_slab(const TiledArgs<float> &a, cudaStream_t s)
 {
     const GridDev &g = a.s.g;
     const int ntiles = g.nt[0] * g.nt[1] * g.nt[2];
     const size_t smem = slab_smem_bytes(g);
-    auto kern = step_slab_kernel<GEOM, FLAT>;
+    auto kern = step_slab_kernel<GEOM, FLAT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<ntiles, kSlabThreads, smem, s>>>(a);
