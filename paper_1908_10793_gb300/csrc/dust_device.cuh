@@ -25,48 +25,6 @@ __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ long long rround(float x) { return __float2ll_rn(x); }
 __device__ __forceinline__ long long rround(double x) { return __double2ll_rn(x); }
 
-// Conversions between binary64 and binary32 done on the integer pipe, from
-// the IEEE-754 field layouts (binary64: sign 1, exponent 11 with bias 1023,
-// fraction 52; binary32: sign 1, exponent 8 with bias 127, fraction 23).  The
-// double-precision unit of this GPU is narrow, so the mixed-precision push
-// keeps its conversions off it; the rare operands outside the normal range
-// fall back to the conversion instructions.
-
-// Round a double to the nearest float (ties to even).
-__device__ __forceinline__ float f64_to_f32_rn(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned ex = (hi >> 20) & 0x7ffu;
-    // a normal float result needs a binary64 exponent in [897, 1150]
-    if (ex - 897u > 253u) return __double2float_rn(x);
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 fraction bits
-    const unsigned r = lo & 0x1fffffffu;                     // the 29 dropped bits
-    unsigned f = (hi & 0x80000000u) | ((ex - 896u) << 23) | m;
-    // round to nearest even; a carry out of the fraction raises the exponent
-    f += (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;
-    return __uint_as_float(f);
-}
-
-// A float as a double (exact).
-__device__ __forceinline__ double f32_to_f64(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-    if (e == 0u) {
-        if (m != 0u) return (double)f;   // subnormal
-        return __hiloint2double((int)(b & 0x80000000u), 0);
-    }
-    const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
-    return __hiloint2double((int)((b & 0x80000000u) | (ed << 20) | (m >> 3)), (int)(m << 29));
-}
-
-// NaN test of a double on the integer pipe.
-__device__ __forceinline__ bool is_nan_f64(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu, lo = (unsigned)__double2loint(x);
-    return hi > 0x7ff00000u || (hi == 0x7ff00000u && lo != 0u);
-}
-
 // Shear-periodic shifts of the step at its half and full time: from the
 // kernel arguments, or from device memory for steps replayed from a graph.
 template <typename Real>

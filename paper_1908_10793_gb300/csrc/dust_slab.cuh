@@ -341,13 +341,13 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                 bool live = false, ingroup = false, gone = false;
                 {
                     q[0] = S.q[0][src]; q[1] = S.q[1][src]; q[2] = S.q[2][src];
-                    live = !is_nan_f64(q[0]);
+                    live = !isnan(q[0]);
                     if (live) {
                         pn[0] = S.p[0][src]; pn[1] = S.p[1][src]; pn[2] = S.p[2][src];
                         sp = S.species ? S.species[src] : 0;
     #pragma unroll
                         for (int d = 0; d < 3; ++d) {
-                            if (g.n[d] > 1) { u[d] = f64_to_f32_rn(q[d] - zcd[d]); zc3[d] = zcf[d]; }
+                            if (g.n[d] > 1) { u[d] = __double2float_rn(q[d] - zcd[d]); zc3[d] = zcf[d]; }
                             else { u[d] = 0.f; zc3[d] = (float)q[d]; }
                         }
                         // first half drift (Eq. exp_midpoint; Eq. drift1_cylindrical;
@@ -514,7 +514,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                             for (int d = 0; d < 3; ++d) inc2[d] = h * pp[d];
                         }
     #pragma unroll
-                        for (int d = 0; d < 3; ++d) q[d] += f32_to_f64(inc1[d] + inc2[d]);
+                        for (int d = 0; d < 3; ++d) q[d] += (double)(inc1[d] + inc2[d]);
                     } else {
                         const double qm[3] = {q[0], q[1], q[2]};
                         drift<float, GEOM>(ph, q, qm, pp, h, true, inc2);
