@@ -536,7 +536,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                         if (inbox) {
                             long long rest[4];
     #pragma unroll
-                            for (int ch = 0; ch < 4; ++ch) rest[ch] = rint_to_ll(D[ch]);
+                            for (int ch = 0; ch < 4; ++ch) rest[ch] = rround(D[ch]);
                             const int hl = lb[0] + B[0] * (lb[1] + B[1] * lb[2]);
     #pragma unroll 1
                             for (int nd = 0; nd < 27; ++nd) {
@@ -546,7 +546,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                                 const int lin = hl + (aa - 1) + B[0] * ((b - 1) + B[1] * (c3 - 1));
     #pragma unroll
                                 for (int ch = 0; ch < 4; ++ch) {
-                                    const long long piece = rint_to_ll(W * D[ch]);
+                                    const long long piece = rround(W * D[ch]);
                                     if (piece != 0) {
                                         shared_add_i64(&sdep[ch * bvol + lin], piece);
                                         rest[ch] -= piece;
@@ -725,7 +725,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                         for (int ch = 0; ch < 4; ++ch) {
                             const float v = (ch & 1) ? acc[b][c][ch >> 1].y : acc[b][c][ch >> 1].x;
                             big |= !(fabsf(v) < 4.5e15f);
-                            const long long piece = rint_to_ll(v);
+                            const long long piece = rround(v);
                             if (piece != 0) {
                                 shared_add_i64(&sdep[ch * bvol + lin], piece);
                                 ps[ch] += piece;
@@ -740,7 +740,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                 if (a == 1 && own) {
                     const float Sc = (ch & 1) ? S2[ch >> 1].y : S2[ch >> 1].x;
                     big |= !(fabsf(Sc) < 4.5e15f);
-                    const long long rest = rint_to_ll(Sc) - (ps[ch] + s1 + s2);
+                    const long long rest = rround(Sc) - (ps[ch] + s1 + s2);
                     if (rest != 0) shared_add_i64(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], rest);
                 }
             }

@@ -51,24 +51,6 @@ __device__ __forceinline__ void smem_gas_load<double>(const double *s, int lin, 
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
-// Round-half-even of a single-precision value to int64 without a 64-bit
-// conversion instruction (those share the narrow double-precision pipe):
-// v = hi * 2^21 + lo with hi = rint(v / 2^21) and |lo| <= 2^20 both formed by
-// the 1.5 * 2^23 magic-number addition; lo is exact, hi * 2^21 is even, so
-// the sum is exactly rint(v).  Valid for |v| < 2^43; larger values use the
-// conversion instruction.
-__device__ __forceinline__ long long rint_to_ll(float v)
-{
-    if (!(fabsf(v) < 8.796093e12f)) return __float2ll_rn(v);
-    const float magic = 12582912.0f;  // 1.5 * 2^23
-    const float th = __fadd_rn(__fmul_rn(v, 4.76837158203125e-07f), magic);  // v / 2^21
-    const int hi = __float_as_int(th) - 0x4B400000;
-    const float hf = __fsub_rn(th, magic);  // == (float)hi, exactly
-    const float lo = __fmaf_rn(-hf, 2097152.0f, v);
-    const int l = __float_as_int(__fadd_rn(lo, magic)) - 0x4B400000;
-    return ((long long)hi << 21) + (long long)l;
-}
-__device__ __forceinline__ long long rint_to_ll(double v) { return __double2ll_rn(v); }
 
 // Adds v to the 64-bit integer at p (shared memory) with two 32-bit atomics:
 // the low word's carry goes into the high word, so the sum is exact modulo
@@ -520,7 +502,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         big |= !(fabs(sum[z][c]) < Real(4.5e15));
-                        const long long piece = rint_to_ll(sum[z][c]);
+                        const long long piece = rround(sum[z][c]);
                         if (piece != 0) {
                             shared_add_i64(&sdep[c * bvol + lin], piece);
                             ps[c] += piece;
@@ -532,7 +514,7 @@ step_tiled_kernel(const TiledArgs<Real> TA)
                     if (ps[c] != 0) shared_add_i64(&run_sum[c * CH + r], ps[c]);
                     if (htask) {
                         big |= !(fabs(S[c]) < Real(4.5e15));
-                        run_q[c * CH + r] = rint_to_ll(S[c]);
+                        run_q[c * CH + r] = rround(S[c]);
                     }
                 }
             }
