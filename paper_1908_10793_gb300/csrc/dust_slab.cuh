@@ -726,10 +726,10 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                             const float v = (ch & 1) ? acc[b][c][ch >> 1].y : acc[b][c][ch >> 1].x;
                             big |= !(fabsf(v) < 4.5e15f);
                             const long long piece = rround(v);
-                            if (piece != 0) {
-                                shared_add_i64(&sdep[ch * bvol + lin], piece);
-                                ps[ch] += piece;
-                            }
+                            // no test for zero: a chunk sum is rarely exactly
+                            // zero, and the test cost more than the adds it saved
+                            shared_add_i64(&sdep[ch * bvol + lin], piece);
+                            ps[ch] += piece;
                         }
                     }
             }
