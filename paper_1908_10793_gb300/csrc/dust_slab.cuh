@@ -62,7 +62,7 @@ __device__ __forceinline__ void deposit_fixed_rolled(const GridDev &g, unsigned 
     bool big = false;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        big |= !(fabs((double)Dq[c]) < 4.5e15);
+        big |= !(fabsf(Dq[c]) < 4.5e15f);
         rest[c] = rround(Dq[c]);
     }
     if (big) atomicOr(&status[ST_FLAGS], DUST_FLAG_OVERFLOW);

@@ -22,7 +22,7 @@ __device__ __forceinline__ void deposit_fixed(const GridDev &g, unsigned long lo
     bool big = false;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        big |= !(fabs((double)Dq[c]) < 4.5e15);
+        big |= !(fabs(Dq[c]) < Real(4.5e15));  // in the working precision
         rest[c] = rround(Dq[c]);
     }
     if (big) atomicOr(&status[ST_FLAGS], DUST_FLAG_OVERFLOW);
@@ -238,7 +238,9 @@ predict_gas_kernel(const StepArgs<Real> A)
     const Real tau = stopping_time<Real, GEOM>(A.ph, A.sp.mode[sp], value, q, acc[0]);
     const Real dt = (Real)A.dt;
     const Real taup = fmax(tau, fabs(dt));
-    const Real coef = Real(0.5) * dt * (Real)(A.sp.mass[sp] * A.inv_quantum) / taup;
+    // mass / quantum, precomputed per species in both precisions
+    const Real mq = sizeof(Real) == 4 ? (Real)A.sp.mqf[sp] : (Real)A.sp.mq[sp];
+    const Real coef = Real(0.5) * dt * mq / taup;
     Real Dq[4];
 #pragma unroll
     for (int c = 0; c < 3; ++c) Dq[c] = coef * (pn[c] - acc[1 + c]);

@@ -668,7 +668,9 @@ predict_tiled_kernel(const __grid_constant__ TiledArgs<Real> TA)
         const Real value = A.s.param ? A.s.param[src] : (Real)A.sp.tau[sp];
         const Real tau = stopping_time<Real, GEOM>(A.ph, A.sp.mode[sp], value, q, acc[0]);
         const Real taup = fmax(tau, fabs(dt));
-        const Real coef = Real(0.5) * dt * (Real)(A.sp.mass[sp] * A.inv_quantum) / taup;
+        // mass / quantum, precomputed per species in both precisions
+        const Real mq = sizeof(Real) == 4 ? (Real)A.sp.mqf[sp] : (Real)A.sp.mq[sp];
+        const Real coef = Real(0.5) * dt * mq / taup;
         Real Dq[4];
 #pragma unroll
         for (int c = 0; c < 3; ++c) Dq[c] = coef * (pn[c] - acc[1 + c]);
@@ -683,7 +685,7 @@ predict_tiled_kernel(const __grid_constant__ TiledArgs<Real> TA)
         bool big = false;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            big |= !(fabs((double)Dq[c]) < 4.5e15);
+            big |= !(fabs(Dq[c]) < Real(4.5e15));  // in the working precision
             rest[c] = rround(Dq[c]);
         }
         if (big) atomicOr(&A.status[ST_FLAGS], DUST_FLAG_OVERFLOW);
