@@ -103,32 +103,48 @@ cudaError_t launch_exclusive_scan(int32_t *data, int64_t n, int32_t *block_sums,
 // Scatter of (id, source position) pairs to their key segments.  Positions
 // inside a segment come from atomics (arbitrary order); the segment sort
 // below puts every segment in grain-id order, so the sorted store is
-// reproducible.
+// reproducible.  A warp takes kScatterItems x 32 consecutive grains and
+// issues all their loads, then all their cursor atomics, before it uses a
+// result, so that the round trips overlap.
+constexpr int kScatterItems = 4;
+
 template <typename Real>
 __global__ void sort_scatter_pairs_kernel(const SortArgs<Real> A)
 {
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t w0 = gi - (threadIdx.x & 31);
-    if (w0 >= A.src.n) return;  // whole warp past the end
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int m = (int)min((int64_t)32, A.src.n - w0);  // lanes 0 .. m-1 hold grains
-    const unsigned pm = m == 32 ? 0xffffffffu : ((1u << m) - 1u);
-    if (lane >= m) return;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane)) * kScatterItems;
+    if (w0 >= A.src.n) return;  // whole warp past the end
+    int32_t key[kScatterItems], id[kScatterItems], base[kScatterItems], first[kScatterItems];
+#pragma unroll
+    for (int r = 0; r < kScatterItems; ++r) {
+        const int64_t gi = w0 + 32 * r + lane;
+        key[r] = gi < A.src.n ? A.key[gi] : -1;  // keys are >= 0
+        id[r] = gi < A.src.n ? A.src.id[gi] : 0;
+    }
     // runs of equal keys on consecutive lanes (keys arrive nearly sorted):
-    // one cursor atomic per run, positions inside the run by lane
-    const int32_t key = A.key[gi];
-    const int32_t prev = __shfl_up_sync(pm, key, 1);
-    const bool start = lane == 0 || prev != key;
-    const unsigned starts = __ballot_sync(pm, start);
-    const int first = 31 - __clz(starts & ((2u << lane) - 1u));  // this lane's run start
-    const unsigned later = starts & ~((2u << lane) - 1u);
-    const int end = later ? __ffs(later) - 1 : m;
-    int32_t base = 0;
-    if (start) base = atomicAdd(&A.cursor[key], end - lane);
-    base = __shfl_sync(pm, base, first);
-    const int32_t pos = base + (lane - first);
-    A.pair_id[pos] = A.src.id[gi];
-    A.pair_src[pos] = (int32_t)gi;
+    // one cursor atomic per run, positions inside the run by lane.  The
+    // lanes past the end form one run of key -1 that takes no atomic.
+#pragma unroll
+    for (int r = 0; r < kScatterItems; ++r) {
+        const int32_t prev = __shfl_up_sync(FULL, key[r], 1);
+        const bool start = lane == 0 || prev != key[r];
+        const unsigned starts = __ballot_sync(FULL, start);
+        first[r] = 31 - __clz(starts & ((2u << lane) - 1u));  // this lane's run start
+        const unsigned later = starts & ~((2u << lane) - 1u);
+        const int end = later ? __ffs(later) - 1 : 32;
+        base[r] = 0;
+        if (start && key[r] >= 0) base[r] = atomicAdd(&A.cursor[key[r]], end - lane);
+    }
+#pragma unroll
+    for (int r = 0; r < kScatterItems; ++r) {
+        const int32_t b = __shfl_sync(FULL, base[r], first[r]);
+        if (key[r] >= 0) {
+            const int32_t pos = b + (lane - first[r]);
+            A.pair_id[pos] = id[r];
+            A.pair_src[pos] = (int32_t)(w0 + 32 * r + lane);
+        }
+    }
 }
 
 // Insertion sort by id of the (id, source) pairs of every key.  A warp
@@ -174,10 +190,24 @@ __global__ void __launch_bounds__(kSegThreads) sort_segments_kernel(const SortAr
         return;
     }
     const unsigned FULL = 0xffffffffu;
+    // all loads first, then the shared stores: the loads' round trips overlap
+    int32_t rid[kSegStage / 32], rsrc[kSegStage / 32];
+#pragma unroll
+    for (int r = 0; r < kSegStage / 32; ++r) {
+        const int32_t u = W0 + lane + 32 * r;
+        if (u < W1) {
+            rid[r] = A.pair_id[u];
+            rsrc[r] = A.pair_src[u];
+        }
+    }
     __syncwarp(FULL);
-    for (int32_t u = W0 + lane; u < W1; u += 32) {
-        sid[warp][u - W0] = A.pair_id[u];
-        ssrc[warp][u - W0] = A.pair_src[u];
+#pragma unroll
+    for (int r = 0; r < kSegStage / 32; ++r) {
+        const int32_t u = W0 + lane + 32 * r;
+        if (u < W1) {
+            sid[warp][u - W0] = rid[r];
+            ssrc[warp][u - W0] = rsrc[r];
+        }
     }
     __syncwarp(FULL);
     if (mine) insertion_sort_pairs(sid[warp], ssrc[warp], b - W0, e - W0);
@@ -211,7 +241,8 @@ cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s, bool ga
 {
     if (a.src.n == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((a.src.n + 255) / 256);
-    sort_scatter_pairs_kernel<Real><<<nb, 256, 0, s>>>(a);
+    const unsigned nbs = (unsigned)((a.src.n + 256 * kScatterItems - 1) / (256 * kScatterItems));
+    sort_scatter_pairs_kernel<Real><<<nbs, 256, 0, s>>>(a);
     sort_segments_kernel<Real><<<(unsigned)((a.nkeys1 + kSegThreads - 1) / kSegThreads), kSegThreads, 0, s>>>(a);
     if (gather) sort_gather_kernel<Real><<<nb, 256, 0, s>>>(a);
     return cudaGetLastError();
