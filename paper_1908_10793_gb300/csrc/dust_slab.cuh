@@ -209,8 +209,6 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     float *szlo = sznu + g.T[0];        // [T1 + 1]
     unsigned long long *sbar = reinterpret_cast<unsigned long long *>(
         (reinterpret_cast<uintptr_t>(szlo + g.T[1] + 1) + 7) & ~(uintptr_t)7);
-    int *snext = reinterpret_cast<int *>(sbar + 1);  // next zone group
-    if (threadIdx.x == 0) *snext = kSlabThreads / 32;
     // the gas box by one bulk tensor copy, overlapping the tables below
     gas_box_begin<float>(TA.gas_tmap, sgas, o, bvol, sbar, TA.wait_extra_tx);
     for (int t = threadIdx.x; t < tsum + g.T[1] + 1; t += blockDim.x) {
@@ -240,6 +238,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     if (!gas_box_finish<float>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status, TA.wait_ns)) return;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     const int a = lane % 3, kq = lane / 3;
     const int base = lane - a;
     const float h = (float)(0.5 * A.dt), dt = (float)A.dt;
@@ -248,14 +247,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     float moved = 0.f;
     bool big = false;
 
-    // groups of 10 zones, the first one per warp and then from a shared
-    // counter, so that the warps finish close together at the barrier below
-    auto next_group = [&]() {
-        int v = 0;
-        if (lane == 0) v = atomicAdd(snext, 1);
-        return __shfl_sync(FULL, v, 0);
-    };
-    for (int grp = warp; grp < groups; grp = next_group()) {
+    for (int grp = warp; grp < groups; grp += nwarps) {
         const int kg0 = grp * 10;
         const int kl = kg0 + kq;
         const bool kok = lane < 30 && kl < g.tvol;
@@ -673,12 +665,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                     rb[(6 + k) * kRecStride + slot] = w[2][k];
                 }
 #pragma unroll
-                // the four channels as two pairs (fields 9-10 and 11-12 hold
-                // float2 arrays)
-                reinterpret_cast<float2 *>(rb + 9 * kRecStride)[slot] =
-                    grp_ok ? make_float2(D[0], D[1]) : make_float2(0.f, 0.f);
-                reinterpret_cast<float2 *>(rb + 11 * kRecStride)[slot] =
-                    grp_ok ? make_float2(D[2], D[3]) : make_float2(0.f, 0.f);
+                for (int ch = 0; ch < 4; ++ch) rb[(9 + ch) * kRecStride + slot] = grp_ok ? D[ch] : 0.f;
             }
             __syncwarp();
             // ---- deposit: the three owner lanes of a zone accumulate its
@@ -700,8 +687,8 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                 const float *rx = rb + a * kRecStride;
                 auto one = [&](int sl) {
                     const float wx = rx[sl];
-                    const float2 De01 = reinterpret_cast<const float2 *>(rb + 9 * kRecStride)[sl];
-                    const float2 De23 = reinterpret_cast<const float2 *>(rb + 11 * kRecStride)[sl];
+                    const float2 De01 = make_float2(rb[9 * kRecStride + sl], rb[10 * kRecStride + sl]);
+                    const float2 De23 = make_float2(rb[11 * kRecStride + sl], rb[12 * kRecStride + sl]);
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         const float wxy = wx * rb[(3 + (NB == 3 ? b : 1)) * kRecStride + sl];
@@ -793,7 +780,7 @@ inline size_t slab_smem_bytes(const GridDev &g)
            (size_t)((g.tvol + 31) & ~31) * sizeof(int) +
            (size_t)(kSlabThreads / 32) * kRecFields * kRecStride * sizeof(float) +
            tsum * (sizeof(double) + 2 * sizeof(float)) + ((size_t)g.T[0] + g.T[1] + 1) * sizeof(float) +
-           24;  // the bulk copy's transaction barrier (8-byte aligned), group counter
+           16;  // the bulk copy's transaction barrier (8-byte aligned)
 }
 
 template <int GEOM, int FLAT, int MODE>
