@@ -148,7 +148,8 @@ typedef struct dust_options {
                               (read with dust_get_kernel_times)                */
     int tile[3];           /* zones per tile of the tiled kernel and of the
                               sort order (0 = default: 8x8x8 in 3-D, 16x16 in
-                              2-D; clipped to the grid)                       */
+                              2-D; clipped to the grid); each 0..1023, else
+                              DUST_EINVAL                                     */
     int pusher;            /* DUST_PUSHER_EM (0) or DUST_PUSHER_SEMI_IMPLICIT */
     int gas_predictor;     /* 1: before each step, advance the gas by half a
                               step with the drag of the grains at x^n (Sec. 3.1,

@@ -1067,6 +1067,10 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         return fail(nullptr, DUST_EINVAL, "host_io_async must be 0 or 1");
     if (opt->test_wait_timeout != 0 && opt->test_wait_timeout != 1)
         return fail(nullptr, DUST_EINVAL, "test_wait_timeout must be 0 or 1");
+    // the slab kernel packs a zone's tile-local coordinates in 10-bit fields
+    for (int d = 0; d < 3; ++d)
+        if (opt->tile[d] < 0 || opt->tile[d] > 1023)
+            return fail(nullptr, DUST_EINVAL, "tile[%d] must be 0 (default) or 1..1023 zones", d);
     if (opt->pusher == DUST_PUSHER_SEMI_IMPLICIT && geom->kind != DUST_CARTESIAN &&
         geom->kind != DUST_SHEARING_BOX)
         return fail(nullptr, DUST_EINVAL,

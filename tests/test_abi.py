@@ -84,3 +84,14 @@ def test_test_wait_timeout_option_validated_without_gpu(lib):
     with pytest.raises(D.DustError) as e:
         D.dust_create(geo, grid, sp, opt)
     assert e.value.code == D.DUST_EINVAL and "test_wait_timeout" in str(e.value)
+
+
+@pytest.mark.parametrize("tile", [(2048, 1, 1), (8, -1, 8), (8, 8, 1024)])
+def test_tile_option_validated_without_gpu(lib, tile):
+    from paper_1908_10793_gb300 import dust as D
+    from paper_1908_10793_gb300 import inputs as I
+    w = I.box2d("small")
+    geo, grid, sp, opt, keep = D.make_descriptors(w, tile=tile)
+    with pytest.raises(D.DustError) as e:
+        D.dust_create(geo, grid, sp, opt)
+    assert e.value.code == D.DUST_EINVAL and "tile[" in str(e.value)
