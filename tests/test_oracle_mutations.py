@@ -43,6 +43,13 @@ MUTATIONS = [
     ("Stokes-number stopping time exponent", "return value * sqrt(R * R * R / P->gm);",
      "return value * sqrt(R * R / P->gm);"),
     ("energy channel with p^n", "D[3] += D[c] * dHdp[c];", "D[3] += D[c] * pn[c];"),
+    ("cylindrical energy channel with l / R", "dHdp[1] = 0.5 * (pn[1] + pp[1]) / (R * R);",
+     "dHdp[1] = 0.5 * (pn[1] + pp[1]) / R;"),
+    ("spherical energy channel without sin^2 theta",
+     "dHdp[2] = 0.5 * (pn[2] + pp[2]) / (r * r * st * st);", "dHdp[2] = 0.5 * (pn[2] + pp[2]) / (r * r);"),
+    ("cylindrical energy channel with the end-point v_R",
+     "dHdp[0] = 0.5 * (pn[0] + pp[0]);\n            dHdp[1] = 0.5 * (pn[1] + pp[1]) / (R * R);",
+     "dHdp[0] = pp[0];\n            dHdp[1] = 0.5 * (pn[1] + pp[1]) / (R * R);"),
     ("deposit sign", "D[c] = -m * ((pp[c] - pn[c]) - dt * a[c]);",
      "D[c] = m * ((pp[c] - pn[c]) - dt * a[c]);"),
     ("cylindrical zone volume", "dV = 0.5 * (a1 * a1 - a0 * a0) * (b1 - b0) * (c1 - c0);",

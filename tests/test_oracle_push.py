@@ -14,7 +14,10 @@ what the paper and the mathematics fix (none of them re-types the oracle):
 * the NSH equilibrium is a fixed point of the orbital-advection kick
   (Eq. SI_equil, Sec. 4.3);
 * momentum (and angular momentum) conservation of the feedback (Sec. 3.1,
-  Eq. dust_feedback_final) and the energy identity of the energy channel;
+  Eq. dust_feedback_final) and the energy identity of the energy channel
+  (exact in Cartesian coordinates; minus the grain's mechanical energy
+  change to third order per step in the shearing box, cylindrical and
+  spherical geometries);
 * the printed stiff-deceleration L1 errors (Sec. 4.1, tests/golden);
 * radial drift against the NSH prediction (Sec. 4.5).
 """
@@ -434,6 +437,77 @@ def test_energy_channel_equals_minus_dust_kinetic_energy_change():
     dep, _ = O.step(prob, q, p, np.ones(w.ngrains, np.uint8), 0.0, w.dt, rho, pg)
     ke1 = 0.5 * m * sum((x ** 2).sum() for x in p)
     assert abs(dep[:, 3].sum() + (ke1 - ke0)) < 1e-13 * abs(ke1 - ke0) + 1e-17
+
+
+def _mechanical_energy_case(case):
+    """One grain inside a 4^3-zone grid with non-uniform gas and drag, and its
+    specific kinetic and potential energy in physical terms: the shearing box
+    in the standard frame (Jacobi form: tidal -q Omega^2 x^2, vertical
+    Omega^2 z^2 / 2), the cylindrical and spherical disk around a point mass
+    (with or without the z part of the gravity in cylindrical coordinates)."""
+    mass, tau = 0.3, 0.1
+    if case.startswith("sbox"):
+        vg = case.endswith("vgrav")
+        prob = box_problem(n=(4, 4, 4), lo=-0.5, hi=0.5, geom=O.OG_SHEARING_BOX,
+                           species_mass=(mass,), species_tau=(tau,), omega=1.0, q=1.5,
+                           vertical_gravity=int(vg))
+        q, p = [0.07, -0.03, 0.05], [0.11, -0.08, 0.04]
+
+        def energy(q, p):
+            return 0.5 * (p[0] ** 2 + p[1] ** 2 + p[2] ** 2) - 1.5 * q[0] ** 2 + \
+                (0.5 * q[2] ** 2 if vg else 0.0)
+    elif case.startswith("cyl"):
+        vg = case.endswith("vgrav")
+        edges = [np.linspace(0.5, 1.5, 5), np.linspace(0.0, 2 * np.pi, 9), np.linspace(-0.2, 0.2, 5)]
+        prob = O.Problem(geom=O.OG_CYLINDRICAL, edges=edges, species_mass=(mass,),
+                         species_tau=(tau,), gm=1.0, vertical_gravity=int(vg))
+        q, p = [1.03, 1.1, 0.04], [0.05, 1.03 * 0.93, 0.02]   # (v_R, l = R v_phi, v_z)
+
+        def energy(q, p):
+            phi = -1.0 / np.hypot(q[0], q[2]) if vg else -1.0 / q[0]
+            return 0.5 * (p[0] ** 2 + (p[1] / q[0]) ** 2 + p[2] ** 2) + phi
+    else:
+        th = 0.5 * np.pi - 0.1
+        edges = [np.linspace(0.5, 1.5, 5), np.linspace(0.5 * np.pi - 0.3, 0.5 * np.pi + 0.3, 5),
+                 np.linspace(0.0, 2 * np.pi, 9)]
+        prob = O.Problem(geom=O.OG_SPHERICAL, edges=edges, species_mass=(mass,),
+                         species_tau=(tau,), gm=1.0)
+        # (v_r, l_theta = r v_theta, l_phi = r sin(theta) v_phi)
+        q, p = [1.02, th, 1.1], [0.05, 0.03, 1.02 * np.sin(th) * 0.95]
+
+        def energy(q, p):
+            r, st = q[0], np.sin(q[1])
+            return 0.5 * (p[0] ** 2 + (p[1] / r) ** 2 + (p[2] / (r * st)) ** 2) - 1.0 / r
+    return prob, q, p, energy
+
+
+@pytest.mark.parametrize("case", ["sbox", "sbox_vgrav", "cyl", "cyl_vgrav", "sph"])
+def test_energy_channel_equals_minus_mechanical_energy_change_at_third_order(case):
+    # Drag is the only non-conservative force on a grain, and the energy
+    # channel is minus its impulse times the midpoint dH/dp: it must equal
+    # minus the grain's change of kinetic plus potential energy, up to the
+    # local error of a second-order step, O(dt^3).  A wrong metric factor or
+    # an end-point instead of a midpoint value leaves O(dt) or O(dt^2).
+    def one(dt):
+        prob, q0, p0, energy = _mechanical_energy_case(case)
+        rng = np.random.default_rng(5)
+        rho = rng.uniform(0.8, 1.2, prob.ncell)
+        pg = [p0[d] + rng.uniform(-0.1, 0.1, prob.ncell) for d in range(3)]
+        q = [np.array([x]) for x in q0]
+        p = [np.array([x]) for x in p0]
+        m = prob.sp_mass[0]
+        e0 = m * energy([x[0] for x in q], [x[0] for x in p])
+        dep, removed = O.step(prob, q, p, np.ones(1, np.uint8), 0.0, dt, rho, pg)
+        assert removed == 0
+        e1 = m * energy([x[0] for x in q], [x[0] for x in p])
+        return dep[:, 3].sum(), dep[:, 3].sum() + (e1 - e0)
+
+    res = [one(h) for h in (0.02, 0.01, 0.005)]
+    for de, r in res:
+        assert abs(de) > 1e-5             # the drag really exchanged energy
+        assert abs(r) < 1e-3 * abs(de)
+    for k in range(2):
+        assert abs(res[k][1]) > 6.0 * abs(res[k + 1][1]), (case, res)
 
 
 # --------------------------------------------------------------------------
