@@ -33,12 +33,13 @@
  * are repeated where they are used below.
  *
  * Parity status: the energy channel of the deposit in the orbital-advection
- * frame of the shearing box, the weights on non-uniform radial grids, the
- * theta-TSC weights and the shear-periodic y-shift follow stated readings
- * (see the notes at each function); the tests pin them only by quadrature of
- * the defining integral, by algebraic identities and by special cases (parity
- * unpinned).  The energy channel in the other geometries is pinned by the
- * grain's mechanical-energy change, to third order per step.
+ * frame of the shearing box, the weights on non-uniform radial grids and the
+ * theta-TSC weights follow stated readings (see the notes at each function);
+ * the tests pin them only by quadrature of the defining integral, by
+ * algebraic identities and by special cases (parity unpinned).  The energy
+ * channel in the other geometries is pinned by the grain's mechanical-energy
+ * change, to third order per step, and the shear-periodic boundary by the
+ * sheared image of a wider box.
  */
 #include <math.h>
 #include <stdint.h>

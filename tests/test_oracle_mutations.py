@@ -50,6 +50,12 @@ MUTATIONS = [
     ("cylindrical energy channel with the end-point v_R",
      "dHdp[0] = 0.5 * (pn[0] + pp[0]);\n            dHdp[1] = 0.5 * (pn[1] + pp[1]) / (R * R);",
      "dHdp[0] = pp[0];\n            dHdp[1] = 0.5 * (pn[1] + pp[1]) / (R * R);"),
+    ("shear-periodic y shift sign at +x", "if (q[0] >= hi) {\n                q[1] += shift;",
+     "if (q[0] >= hi) {\n                q[1] -= shift;"),
+    ("standard-frame v_y jump sign at +x", "if (!P->fargo) p[1] += P->q * P->omega * Lx;",
+     "if (!P->fargo) p[1] -= P->q * P->omega * Lx;"),
+    ("shear-periodic shift at the step's start time", "int alive = apply_bc(P, qn, pnew, t + dt);",
+     "int alive = apply_bc(P, qn, pnew, t);"),
     ("deposit sign", "D[c] = -m * ((pp[c] - pn[c]) - dt * a[c]);",
      "D[c] = m * ((pp[c] - pn[c]) - dt * a[c]);"),
     ("cylindrical zone volume", "dV = 0.5 * (a1 * a1 - a0 * a0) * (b1 - b0) * (c1 - c0);",

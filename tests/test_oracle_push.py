@@ -18,6 +18,8 @@ what the paper and the mathematics fix (none of them re-types the oracle):
   (exact in Cartesian coordinates; minus the grain's mechanical energy
   change to third order per step in the shearing box, cylindrical and
   spherical geometries);
+* the shear-periodic boundary is the sheared image of the central box: a
+  grain crossing it ends where it ends in a wider box, mapped back;
 * the printed stiff-deceleration L1 errors (Sec. 4.1, tests/golden);
 * radial drift against the NSH prediction (Sec. 4.5).
 """
@@ -508,6 +510,55 @@ def test_energy_channel_equals_minus_mechanical_energy_change_at_third_order(cas
         assert abs(r) < 1e-3 * abs(de)
     for k in range(2):
         assert abs(res[k][1]) > 6.0 * abs(res[k + 1][1]), (case, res)
+
+
+@pytest.mark.parametrize("fargo", [0, 1])
+def test_shear_periodic_boundary_matches_the_sheared_image_of_a_wider_box(fargo):
+    # Shearing-sheet symmetry (Sec. 4.2 setup): the flow -q Omega x makes the
+    # box at x + L_x the central box moved by -q Omega L_x t in y, so a grain
+    # that leaves through +x is the image (x - L_x, y + q Omega L_x t,
+    # v_y + q Omega L_x in the standard frame; the residual velocity is
+    # unchanged).  Without drag, grains crossing the x boundaries of a box
+    # of width 1 must therefore end where the same grains end in a box of
+    # width 3 (no crossing there), mapped back by that image.
+    Om, qs, L = 1.0, 1.5, 1.0
+
+    def evolve(xlo, xhi, nx, q0, p0, t0, dt, steps):
+        edges = [np.linspace(xlo, xhi, nx + 1), np.linspace(-0.5, 0.5, 5), np.linspace(-0.5, 0.5, 5)]
+        prob = O.Problem(geom=O.OG_SHEARING_BOX, edges=edges, species_tau=(INF,), omega=Om, q=qs,
+                         fargo=fargo)
+        rho = np.ones(prob.ncell)
+        pg = [np.zeros(prob.ncell) for _ in range(3)]
+        q, p, active, _ = run(prob, q0, p0, dt, steps, rho, pg, t0=t0)
+        assert active.all()
+        return q, p
+
+    x0 = [0.4, -0.4, 0.45, -0.3]
+    q0 = [x0, [0.1, -0.2, -0.45, 0.3], [0.0, 0.1, 0.2, -0.1]]
+    res = [[0.5, -0.5, 0.2, -0.45], [0.2, 0.1, 0.3, -0.2], [0.0, 0.05, 0.0, 0.02]]
+    if fargo:
+        p0 = res
+    else:   # the same motion in the standard frame: v_y = v'_y - q Omega x
+        p0 = [res[0], [v - qs * Om * x for v, x in zip(res[1], x0)], res[2]]
+    t0, dt, steps = 0.3, 0.05, 30
+    T = t0 + steps * dt
+    qa, pa = evolve(-0.5 * L, 0.5 * L, 4, q0, p0, t0, dt, steps)
+    qb, pb = evolve(-1.5 * L, 1.5 * L, 12, q0, p0, t0, dt, steps)
+    k = np.floor((qb[0] + 0.5 * L) / L)
+    assert (k == 1).any() and (k == -1).any()     # both boundaries crossed
+    x = qb[0] - k * L
+    y = qb[1] + k * qs * Om * L * T
+    vy = pb[1] + (0.0 if fargo else k * qs * Om * L)
+
+    def wrapped(a):
+        return (a + 0.5) % 1.0 - 0.5
+
+    assert np.abs(qa[0] - x).max() < 1e-13
+    assert np.abs(wrapped(qa[1] - y)).max() < 1e-13
+    assert np.abs(qa[2] - qb[2]).max() < 1e-13
+    assert np.abs(pa[0] - pb[0]).max() < 1e-13
+    assert np.abs(pa[1] - vy).max() < 1e-13
+    assert np.abs(pa[2] - pb[2]).max() < 1e-13
 
 
 # --------------------------------------------------------------------------
