@@ -621,7 +621,10 @@ def run_reference(args):
     if rank != 0:
         return
     w = I.sbox3d("small" if args.small else "full")
-    n = min(w.ngrains, 1 << 21)
+    # a bounded sample per step: at most 2M grains, and about 2e8 grain-steps
+    # for the whole warm-up + timed run (a minute or two on one host core)
+    budget = 200_000_000
+    n = int(min(w.ngrains, 1 << 21, max(1 << 16, budget // max(1, args.steps + args.warmup))))
     cpu_baseline(w, steps=1, ngrains=1024)  # build + warm the library
     times = []
     for _ in range(args.warmup):
