@@ -95,3 +95,12 @@ def test_tile_option_validated_without_gpu(lib, tile):
     with pytest.raises(D.DustError) as e:
         D.dust_create(geo, grid, sp, opt)
     assert e.value.code == D.DUST_EINVAL and "tile[" in str(e.value)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    # no fallback: with libdust.so missing, the first call raises
+    from paper_1908_10793_gb300 import dust as D
+    monkeypatch.setattr(D, "LIB_PATH", str(tmp_path / "libdust.so"))
+    monkeypatch.setattr(D, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        D.load_library()
