@@ -365,7 +365,9 @@ int dust_get_mass_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double,
 
 /* Copy the stored grains (current storage order, which the zone sort
  * permutes): coordinates, physical velocities and original ids (int64).
- * Removed grains are included with NaN coordinates.  cap = capacity of the
+ * Removed grains are included with NaN coordinates, after the live ones and
+ * in no particular order (the live ones are in zone-key, then id, order
+ * after a sort).  cap = capacity of the
  * caller arrays; *n_out = grains written.  Any pointer but n_out may be
  * NULL. */
 int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,

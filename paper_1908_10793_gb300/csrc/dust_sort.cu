@@ -1,7 +1,10 @@
 // Counting sort of the grain store by zone key: exclusive scan of the key
 // counts, scatter of (id, source) pairs, an id sort inside every key and a
 // gather of the store columns (keys are computed by the geometry-specific
-// sort_keys kernel).  The sorted order is deterministic: by key, then id.
+// sort_keys kernel).  The live grains' order is deterministic: by key, then
+// id.  Removed grains (the last key) come after them in the scatter's order:
+// nothing is computed from them, and sorting that segment, which grows with
+// every removal, would make the sort's cost grow with the run's length.
 #include "dust_internal.h"
 
 namespace dust {
@@ -180,10 +183,13 @@ __global__ void __launch_bounds__(kSegThreads) sort_segments_kernel(const SortAr
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t k0 = k - lane;
-    if (k0 >= A.nkeys1) return;  // whole warp past the end
-    const int64_t klast = min(k0 + 32, A.nkeys1);  // one past the warp's last key
+    // keys 0 .. nsort - 1 are zones; key nsort (removed grains) is left as
+    // the scatter placed it
+    const int64_t nsort = A.nkeys1 - 1;
+    if (k0 >= nsort) return;  // whole warp past the zone keys
+    const int64_t klast = min(k0 + 32, nsort);  // one past the warp's last key
     const int32_t W0 = A.count[k0], W1 = A.count[klast];
-    const bool mine = k < A.nkeys1;
+    const bool mine = k < nsort;
     const int32_t b = mine ? A.count[k] : W1, e = mine ? A.count[k + 1] : W1;
     if (W1 - W0 > kSegStage) {
         if (mine) insertion_sort_pairs(A.pair_id, A.pair_src, b, e);
