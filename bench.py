@@ -15,6 +15,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -86,11 +87,29 @@ STEP_KERNEL_SOURCES = [
 ]
 
 
-def source_digest():
+# string and character literals (kept), line and block comments (dropped)
+_C_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def _code_only(text):
+    """C/C++ source without its comments, whitespace runs collapsed: edits of
+    comments or layout do not change the compiled kernel."""
+    kept = _C_TOKENS.sub(lambda m: " " if m.group(0).startswith("/") else m.group(0), text)
+    return " ".join(kept.split())
+
+
+def source_digest(root=None, read=None):
+    """Digest of the step kernel's sources (code only).  read(path) -> text
+    can supply another revision's files."""
+    root = ROOT if root is None else root
     h = hashlib.sha256()
     for f in STEP_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(os.path.basename(f).encode() + fh.read())
+        if read is None:
+            with open(os.path.join(root, f), encoding="utf-8") as fh:
+                text = fh.read()
+        else:
+            text = read(f)
+        h.update(os.path.basename(f).encode() + _code_only(text).encode())
     return h.hexdigest()[:16]
 
 
