@@ -9,6 +9,6 @@ from .oracle import (  # noqa: F401
     OP_EM, OP_SEMI_IMPLICIT,
     W1_CART_CIC, W1_CART_TSC, W1_CYL_R_CIC, W1_CYL_R_TSC, W1_SPH_R_CIC,
     W1_SPH_R_TSC, W1_SPH_TH_CIC, W1_SPH_TH_TSC, W1_CYL_R_VOL, W1_SPH_R_VOL, W1_SPH_TH_VOL,
-    build, weights_1d, weights_vol, locate, Problem, step, gas_momentum, gas_predictor,
+    build, weights_1d, weights_vol, locate, Problem, step, step_fixed, gas_momentum, gas_predictor,
     deposit_mass,
 )

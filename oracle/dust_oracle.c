@@ -32,14 +32,17 @@
  * Readings of points the paper leaves open are listed in the design notes and
  * are repeated where they are used below.
  *
- * Parity status: the energy channel of the deposit in the orbital-advection
- * frame of the shearing box, the weights on non-uniform radial grids and the
- * theta-TSC weights follow stated readings (see the notes at each function);
- * the tests pin them only by quadrature of the defining integral, by
- * algebraic identities and by special cases (parity unpinned).  The energy
- * channel in the other geometries is pinned by the grain's mechanical-energy
- * change, to third order per step, and the shear-periodic boundary by the
- * sheared image of a wider box.
+ * Parity status: every part is pinned by a reference built outside this
+ * file.  The weights on non-uniform radial grids and the theta-TSC weights,
+ * which the paper does not print, follow stated readings (see the notes at
+ * each function) and are pinned by quadrature of their defining integral.
+ * The deposit channels are pinned by the drag impulse and drag work of an
+ * independently integrated trajectory in the shearing box (both frames),
+ * and the energy channel in the curvilinear geometries by the grain's
+ * mechanical-energy change, to third order per step; the Epstein stopping
+ * time by the relaxation of a grain with the TSC-gathered density; the
+ * fixed-point rule by integer identities and a closed-form case; the
+ * shear-periodic boundary by the sheared image of a wider box.
  */
 #include <math.h>
 #include <stdint.h>
@@ -503,6 +506,51 @@ static double stopping_time(const oracle_problem *P, int mode, double value,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Fixed-point deposit rule                                                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Integer deposit of one grain's impulse D[4] (Eq. dust_feedback_final, one
+ * grain's term) with the stencil weights w[d][0..2] of host zone host[].
+ * Reading (the paper deposits in floating point; the integer form is this
+ * project's, so that the deposited grid does not depend on the order in
+ * which grains are summed): in units of the quantum, per channel c,
+ *   Q      = nearest integer to D[c] / quantum,
+ *   piece  = nearest integer to W_j D[c] / quantum   for every node j other
+ *            than the host zone (W_j the product of the three 1-D weights),
+ *   host  += Q - (sum of the pieces),
+ * so the zones receive exactly Q in total.  Ties round to even (the IEEE
+ * default rounding).  Nodes beyond an outflow boundary fold onto the edge
+ * zone, as in the dense deposit.
+ */
+static void deposit_fixed_point(const oracle_problem *P, const int host[3],
+                                double w[3][3], const double D[4], double quantum,
+                                int64_t *fixed)
+{
+    const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+    int64_t hidx = node_index(host[0], 0, n0, P->bc[0])
+        + (int64_t)n0 * (node_index(host[1], 0, n1, P->bc[1])
+        + (int64_t)n1 * node_index(host[2], 0, n2, P->bc[2]));
+    for (int ch = 0; ch < 4; ch++) {
+        int64_t rest = (int64_t)llrint(D[ch] / quantum);
+        for (int c = 0; c < 3; c++)
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    if (a == 1 && b == 1 && c == 1) continue;
+                    double W = w[0][a] * w[1][b] * w[2][c];
+                    if (W == 0.0) continue;
+                    int64_t idx = node_index(host[0], a - 1, n0, P->bc[0])
+                        + (int64_t)n0 * (node_index(host[1], b - 1, n1, P->bc[1])
+                        + (int64_t)n1 * node_index(host[2], c - 1, n2, P->bc[2]));
+                    int64_t piece = (int64_t)llrint(W * D[ch] / quantum);
+                    fixed[4 * idx + ch] += piece;
+                    rest -= piece;
+                }
+        fixed[4 * hidx + ch] += rest;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* The step                                                                    */
 /* ------------------------------------------------------------------------- */
 
@@ -526,13 +574,13 @@ static double stopping_time(const oracle_problem *P, int mode, double value,
  *                    dt, i.e. the impulse given to the gas) and energy (3)
  * Returns the number of grains removed in this step.
  */
-int64_t oracle_step(const oracle_problem *P,
-                    double *q0, double *q1, double *q2,
-                    double *p0, double *p1, double *p2,
-                    const uint8_t *species, const double *param,
-                    uint8_t *active, int64_t n, double t, double dt,
-                    const double *rho, double *pg0, double *pg1, double *pg2,
-                    double *dep)
+static int64_t step_grains(const oracle_problem *P,
+                           double *q0, double *q1, double *q2,
+                           double *p0, double *p1, double *p2,
+                           const uint8_t *species, const double *param,
+                           uint8_t *active, int64_t n, double t, double dt,
+                           const double *rho, double *pg0, double *pg1, double *pg2,
+                           double *dep, int64_t *fixed, double quantum)
 {
     const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
     const int64_t ncell = (int64_t)n0 * n1 * n2;
@@ -541,6 +589,7 @@ int64_t oracle_step(const oracle_problem *P,
     int wk[3];
     for (int d = 0; d < 3; d++) wk[d] = weight_kind(P, d);
     memset(dep, 0, sizeof(double) * 4 * ncell);
+    if (fixed) memset(fixed, 0, sizeof(int64_t) * 4 * ncell);
 
     for (int64_t g = 0; g < n; g++) {
         if (!active[g]) continue;
@@ -743,6 +792,7 @@ int64_t oracle_step(const oracle_problem *P,
                         + (int64_t)n1 * node_index(host[2], c - 1, n2, P->bc[2]));
                     for (int ch = 0; ch < 4; ch++) dep[4 * idx + ch] += W * D[ch];
                 }
+        if (fixed) deposit_fixed_point(P, host, w, D, quantum, fixed);
 
         q0[g] = qn[0]; q1[g] = qn[1]; q2[g] = qn[2];
         p0[g] = pnew[0]; p1[g] = pnew[1]; p2[g] = pnew[2];
@@ -772,6 +822,35 @@ int64_t oracle_step(const oracle_problem *P,
                 }
     }
     return removed;
+}
+
+/* One step with the deposit accumulated densely in double precision only. */
+int64_t oracle_step(const oracle_problem *P,
+                    double *q0, double *q1, double *q2,
+                    double *p0, double *p1, double *p2,
+                    const uint8_t *species, const double *param,
+                    uint8_t *active, int64_t n, double t, double dt,
+                    const double *rho, double *pg0, double *pg1, double *pg2,
+                    double *dep)
+{
+    return step_grains(P, q0, q1, q2, p0, p1, p2, species, param, active, n, t, dt,
+                       rho, pg0, pg1, pg2, dep, NULL, 0.0);
+}
+
+/* The same step, with the deposit also given in fixed point: fixed[ncell][4]
+ * receives the integers of the per-grain rule (deposit_fixed_point) in units
+ * of quantum.  The dense deposit dep and the feedback are as in
+ * oracle_step (the feedback uses the dense deposit). */
+int64_t oracle_step_fixed(const oracle_problem *P,
+                          double *q0, double *q1, double *q2,
+                          double *p0, double *p1, double *p2,
+                          const uint8_t *species, const double *param,
+                          uint8_t *active, int64_t n, double t, double dt,
+                          const double *rho, double *pg0, double *pg1, double *pg2,
+                          double *dep, int64_t *fixed, double quantum)
+{
+    return step_grains(P, q0, q1, q2, p0, p1, p2, species, param, active, n, t, dt,
+                       rho, pg0, pg1, pg2, dep, fixed, quantum);
 }
 
 /* Volume of zone (i, j, k): dR dphi dz R-weighted in cylindrical, r^2 dr

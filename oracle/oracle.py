@@ -80,6 +80,9 @@ def _load():
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                 ctypes.c_double, ctypes.c_double, dp, dp, dp, dp, dp]
             lib.oracle_step.restype = ctypes.c_int64
+            lib.oracle_step_fixed.argtypes = lib.oracle_step.argtypes + [ctypes.c_void_p,
+                                                                         ctypes.c_double]
+            lib.oracle_step_fixed.restype = ctypes.c_int64
             lib.oracle_gas_momentum.argtypes = [ctypes.POINTER(_ProblemC)] + [dp] * 6
             lib.oracle_gas_momentum.restype = None
             lib.oracle_gas_predictor.argtypes = [ctypes.POINTER(_ProblemC)] + [dp] * 6 + [
@@ -180,6 +183,31 @@ def step(prob, q, p, active, t, dt, rho, pg, species=None, param=None):
                               active.ctypes.data, n, float(t), float(dt),
                               _dp(rho), _dp(pg[0]), _dp(pg[1]), _dp(pg[2]), _dp(dep))
     return dep, removed
+
+
+def step_fixed(prob, q, p, active, t, dt, rho, pg, quantum, species=None, param=None):
+    """One step in place, like step(), with the deposit also given by the
+    fixed-point rule (per grain: the non-host nodes get the nearest integer
+    of W D / quantum, the host zone the rest of the nearest integer of
+    D / quantum).  Returns (dense deposit [ncell, 4], int64 deposit
+    [ncell, 4] in units of quantum, number removed)."""
+    lib = _load()
+    for a in list(q) + list(p) + [rho] + list(pg):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    assert active.dtype == np.uint8
+    n = len(q[0])
+    dep = np.zeros((prob.ncell, 4))
+    fixed = np.zeros((prob.ncell, 4), np.int64)
+    sp = None if species is None else np.ascontiguousarray(species, dtype=np.uint8)
+    pa = None if param is None else _f64(param)
+    removed = lib.oracle_step_fixed(ctypes.byref(prob.c), _dp(q[0]), _dp(q[1]), _dp(q[2]),
+                                    _dp(p[0]), _dp(p[1]), _dp(p[2]),
+                                    None if sp is None else sp.ctypes.data,
+                                    None if pa is None else pa.ctypes.data,
+                                    active.ctypes.data, n, float(t), float(dt),
+                                    _dp(rho), _dp(pg[0]), _dp(pg[1]), _dp(pg[2]), _dp(dep),
+                                    fixed.ctypes.data, float(quantum))
+    return dep, fixed, removed
 
 
 def gas_predictor(prob, q, p, active, dt, rho, pg, species=None, param=None):

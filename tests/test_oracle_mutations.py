@@ -14,7 +14,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "dust_oracle.c")
 PIN_SUITES = [os.path.join(ROOT, "tests", "test_oracle_weights.py"),
-              os.path.join(ROOT, "tests", "test_oracle_push.py")]
+              os.path.join(ROOT, "tests", "test_oracle_push.py"),
+              os.path.join(ROOT, "tests", "test_oracle_drag_work.py"),
+              os.path.join(ROOT, "tests", "test_oracle_fixed_point.py")]
 
 # (name, original text, planted text); the original must occur exactly once
 MUTATIONS = [
@@ -85,6 +87,30 @@ MUTATIONS = [
      "mass[idx] += m * (w[0][a] * w[1][b]);"),
     ("mass deposit with species 0 for every grain",
      "double m = P->sp_mass[species ? species[g] : 0];", "double m = P->sp_mass[0];"),
+    ("Epstein stopping time value times rho", "if (mode == OT_EPSTEIN) return value / rho_g;",
+     "if (mode == OT_EPSTEIN) return value * rho_g;"),
+    ("Epstein with the host zone's density instead of the gathered one",
+     "double tau = stopping_time(P, mode, value, qm, rg);",
+     "double tau = stopping_time(P, mode, value, qm, rho[node_index(host[0], 0, n0, P->bc[0])"
+     " + (int64_t)n0 * (node_index(host[1], 0, n1, P->bc[1])"
+     " + (int64_t)n1 * node_index(host[2], 0, n2, P->bc[2]))]);"),
+    ("orbital-advection energy channel with p^n",
+     "            a[2] = zf;\n            dHdp[0] = vh[0]; dHdp[1] = vh[1]; dHdp[2] = vh[2];",
+     "            a[2] = zf;\n            if (P->fargo) { dHdp[0] = pn[0]; dHdp[1] = pn[1]; "
+     "dHdp[2] = pn[2]; } else { dHdp[0] = vh[0]; dHdp[1] = vh[1]; dHdp[2] = vh[2]; }"),
+    ("orbital-advection energy channel with the total velocity",
+     "            a[2] = zf;\n            dHdp[0] = vh[0]; dHdp[1] = vh[1]; dHdp[2] = vh[2];",
+     "            a[2] = zf;\n            dHdp[0] = vh[0]; dHdp[1] = vh[1] - (P->fargo ? qq * Om * qm[0]"
+     " : 0.0); dHdp[2] = vh[2];"),
+    ("orbital-advection non-frictional force without the shear",
+     "                a[1] = (qq - 2.0) * Om * vh[0];\n            }\n            a[2] = zf;",
+     "                a[1] = -2.0 * Om * vh[0];\n            }\n            a[2] = zf;"),
+    ("fixed point: host rounded on its own, not the rest",
+     "        fixed[4 * hidx + ch] += rest;",
+     "        fixed[4 * hidx + ch] += (int64_t)llrint(w[0][1] * w[1][1] * w[2][1] * D[ch] / quantum);"),
+    ("fixed point: pieces truncated instead of rounded",
+     "int64_t piece = (int64_t)llrint(W * D[ch] / quantum);",
+     "int64_t piece = (int64_t)(W * D[ch] / quantum);"),
 ]
 
 
