@@ -224,23 +224,33 @@ def weak_value(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
-def algorithmic_bytes(w, precision_bytes, fused_gather=False):
-    """Bytes one step kernel launch must move at minimum: every grain's state
-    read and written once (3 FP64 coordinates + 3 momentum-like values, and
-    the species index and stopping-time value where the workload has them), each
-    zone's gas (rho + 3 velocities) read once and its 4-channel int64 deposit
-    written once."""
+def algorithmic_bytes(w, precision_bytes):
+    """Bytes one step (gather + push + deposit) must move at minimum: every
+    grain's state read and written once (3 FP64 coordinates + 3 momentum-like
+    values, and the species index and stopping-time value where the workload
+    has them), each zone's gas (rho + 3 velocities) read once and its
+    4-channel int64 deposit written once.  The zone sort is not part of it
+    (reported as sort_overhead).  Shearing box 128^3, mixed: 72 B per grain
+    + 48 B per zone at 8 grains per zone = 78 B per grain."""
     per_grain = 2 * (3 * 8 + 3 * precision_bytes)
     if w.species is not None:
         per_grain += 2 * 1
     if w.param is not None:
         per_grain += 2 * precision_bytes
-    if fused_gather:
-        # the step also finishes the zone sort: it reads the permutation and
-        # the sorted ids and writes the id column
-        per_grain += 3 * 4
     per_zone = 4 * precision_bytes + 4 * 8
     return w.ngrains * per_grain + w.ncell * per_zone, per_grain, per_zone
+
+
+def sort_overhead(w, kt, steps):
+    """The zone sort, beside the roofline: the step kernel finishes it (reads
+    each grain through the permutation, reads the sorted id and writes the
+    id column, 12 B per grain beyond the algorithmic bytes), and the sort's
+    own kernels run before the step (key counts, scan, pair scatter, id sort
+    inside each zone)."""
+    extra = 3 * 4 * w.ngrains
+    return {"step_kernel_bytes_per_grain": 12, "step_kernel_bytes_per_launch": extra,
+            "sort_kernels_ms_per_step": kt.sort_ms / max(1, steps),
+            "sort_kernel_launches_per_step": kt.sort_launches / max(1, steps)}
 
 
 def run_ours(args):
@@ -294,9 +304,10 @@ def run_ours(args):
     ngr = w.ngrains
     value = weak_value(world, ngr * args.steps, ms / 1e3)
     step_ms_avg = kt.step_ms / max(1, kt.step_launches)
-    ab, per_grain, per_zone = algorithmic_bytes(w, 4, fused_gather=True)
+    ab, per_grain, per_zone = algorithmic_bytes(w, 4)
     achieved = ab / (step_ms_avg / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
+    sort_over = sort_overhead(w, kt, args.steps)
     launches = int(kt.step_launches + kt.sort_launches + kt.other_launches)
     ctx.close()
 
@@ -383,7 +394,7 @@ def run_ours(args):
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = cpu_baseline(w, steps=2)
+        cpu = cpu_baselines(w, steps=2)
 
     if rank == 0:
         line = {
@@ -406,7 +417,9 @@ def run_ours(args):
                          "kernel": "step (gather+push+deposit)",
                          "algorithmic_bytes_per_launch": ab,
                          "bytes_per_grain": per_grain, "bytes_per_zone": per_zone,
+                         "bytes_per_grain_amortised": ab / ngr,
                          "traffic": profiled_traffic(ngr)},
+            "sort_overhead": sort_over,
             "issue": issue_rate(ngr, kt.step_ms / max(1, kt.step_launches) / 1e3),
             "gpu_launches": launches,
             "fp64": fp64,
@@ -597,7 +610,7 @@ def run_disks(args, D, torch, dev, stream):
             kt = ctx.kernel_times(reset=True)
         finally:
             ctx.close()
-        ab, per_grain, per_zone = algorithmic_bytes(w, 4, fused_gather=True)
+        ab, per_grain, per_zone = algorithmic_bytes(w, 4)
         step_ms = kt.step_ms / max(1, kt.step_launches)
         out[name] = {"value": w.ngrains * args.disk_steps / (ms / 1e3), "unit": UNIT,
                      "ms_per_step": ms / args.disk_steps, "grains": w.ngrains, "zones": w.ncell,
@@ -611,28 +624,103 @@ def run_disks(args, D, torch, dev, stream):
     return out
 
 
-def cpu_baseline(w, steps=2, ngrains=None):
-    """The FP64 oracle as it stands (single thread) on the full grid and a
-    seeded subset (default: all) of the grains, `steps` steps."""
+def _momentum_like(w, q, v):
+    """Physical grain velocities -> the momentum-like variables the oracle
+    steps (cylindrical l = R v_phi; spherical r v_theta, r sin(theta) v_phi)."""
+    p = [x.copy() for x in v]
+    if w.geom == I.CYLINDRICAL:
+        p[1] = q[0] * v[1]
+    elif w.geom == I.SPHERICAL:
+        p[1] = q[0] * v[1]
+        p[2] = q[0] * np.sin(q[1]) * v[2]
+    return p
+
+
+def _zone_volumes(w):
+    e = w.edges
+    d = [np.diff(x) for x in e]
+    if w.geom == I.CYLINDRICAL:
+        d[0] = 0.5 * np.diff(e[0] ** 2)
+    elif w.geom == I.SPHERICAL:
+        d[0] = np.diff(e[0] ** 3) / 3.0
+        d[1] = -np.diff(np.cos(e[1]))
+    Z, Y, X = np.meshgrid(d[2], d[1], d[0], indexing="ij")
+    return (X * Y * Z).ravel()
+
+
+def host_threads():
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except Exception:
+        return max(1, os.cpu_count() or 1)
+
+
+def cpu_baseline(w, steps=2, ngrains=None, threads=1, return_state=False):
+    """The FP64 oracle as it stands on the full grid and a seeded subset
+    (default: all) of the grains, `steps` steps.  threads > 1: the grains are
+    cut into that many contiguous ranges, each stepped by the oracle on its
+    own host thread into its own dense deposit (the oracle's C function runs
+    without the interpreter lock), the deposits are summed in range order and
+    the feedback is applied to the gas after the sum."""
+    import concurrent.futures as cf
+
     import oracle as O
     O.build()
     s = w if ngrains is None else I.subsample(w, ngrains)
+    fb = bool(s.feedback)
     prob = O.Problem(geom=s.geom, edges=s.edges, bc=s.bc, weight=s.weight,
                      species_mass=s.species_mass, species_tau_mode=s.species_tau_mode,
                      species_tau=s.species_tau, fargo=s.fargo, omega=s.omega, q=s.qshear,
-                     gm=s.gm, vertical_gravity=s.vertical_gravity, feedback_apply=s.feedback)
+                     gm=s.gm, vertical_gravity=s.vertical_gravity,
+                     feedback_apply=int(fb and threads == 1))
     q = [x.copy() for x in s.q]
-    p = [x.copy() for x in s.v]
+    p = _momentum_like(s, q, s.v)
     pg = O.gas_momentum(prob, s.vgas)
     rho = s.rho.copy()
     active = np.ones(s.ngrains, np.uint8)
+    bounds = np.linspace(0, s.ngrains, threads + 1).astype(np.int64)
+    sp, par = s.species, s.param
+    dV = _zone_volumes(s) if (fb and threads > 1) else None
+
+    def part(i, t):
+        r = slice(int(bounds[i]), int(bounds[i + 1]))
+        dep, _ = O.step(prob, [x[r] for x in q], [x[r] for x in p], active[r], t, s.dt, rho, pg,
+                        None if sp is None else sp[r], None if par is None else par[r])
+        return dep
+
+    ex = cf.ThreadPoolExecutor(max_workers=threads) if threads > 1 else None
     t0 = time.perf_counter()
     for k in range(steps):
-        O.step(prob, q, p, active, k * s.dt, s.dt, rho, pg, s.species, s.param)
+        if ex is None:
+            O.step(prob, q, p, active, k * s.dt, s.dt, rho, pg, sp, par)
+        else:
+            deps = list(ex.map(lambda i: part(i, k * s.dt), range(threads)))
+            dep = deps[0]
+            for d in deps[1:]:
+                dep += d
+            if fb:
+                for c in range(3):
+                    pg[c] += dep[:, c] / (rho * dV)
     el = time.perf_counter() - t0
-    return {"value": s.ngrains * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d grains x %d steps of the same workload (full grid), single thread"
-                      % (s.ngrains, steps), "seconds": el}
+    if ex is not None:
+        ex.shutdown()
+    out = {"value": s.ngrains * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "%d grains x %d steps of the same workload (full grid), %s"
+                     % (s.ngrains, steps, "single thread" if threads == 1 else
+                        "%d host threads over grain ranges" % threads), "seconds": el}
+    if return_state:
+        out["state"] = (q, p, pg, active)
+    return out
+
+
+def cpu_baselines(w, steps=2):
+    """The oracle on all host cores (the line's cpu_baseline) with the
+    single-thread figure beside it."""
+    nt = host_threads()
+    one = cpu_baseline(w, steps=steps, threads=1)
+    allc = cpu_baseline(w, steps=steps, threads=nt) if nt > 1 else dict(one)
+    allc["single_thread"] = one
+    return allc
 
 
 def run_reference(args):
@@ -640,16 +728,17 @@ def run_reference(args):
     if rank != 0:
         return
     w = I.sbox3d("small" if args.small else "full")
-    # a bounded sample per step: at most 2M grains, and about 2e8 grain-steps
-    # for the whole warm-up + timed run (a minute or two on one host core)
-    budget = 200_000_000
-    n = int(min(w.ngrains, 1 << 21, max(1 << 16, budget // max(1, args.steps + args.warmup))))
+    nt = host_threads()
+    # a bounded sample per step: about 1.5e8 grain-steps per host thread for
+    # the whole warm-up + timed run (a minute or two)
+    budget = 150_000_000 * nt
+    n = int(min(w.ngrains, max(1 << 16, budget // max(1, args.steps + args.warmup))))
     cpu_baseline(w, steps=1, ngrains=1024)  # build + warm the library
     times = []
     for _ in range(args.warmup):
-        cpu_baseline(w, steps=1, ngrains=n)
+        cpu_baseline(w, steps=1, ngrains=n, threads=nt)
     for _ in range(args.steps):
-        r = cpu_baseline(w, steps=1, ngrains=n)
+        r = cpu_baseline(w, steps=1, ngrains=n, threads=nt)
         times.append(r["seconds"])
     tot = sum(times)
     value = n * args.steps / tot
@@ -658,9 +747,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "grains_per_step": n},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d of the %d grains (full grid) per step, single thread"
-                                   % (n, w.ngrains)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                         "sample": "%d of the %d grains (full grid) per step, %d host threads "
+                                   "over grain ranges" % (n, w.ngrains, nt)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

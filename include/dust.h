@@ -104,6 +104,7 @@ enum { DUST_KERNEL_AUTO = 0, DUST_KERNEL_PER_GRAIN = 1, DUST_KERNEL_TILED = 2, D
 #define DUST_FLAG_CFL 4
 #define DUST_FLAG_WRAP 8   /* a grain moved more than one period in one step */
 #define DUST_FLAG_TIMEOUT 16 /* a bounded device wait gave up (a tile was skipped) */
+#define DUST_FLAG_SPECIES 32 /* a grain's species index was >= n_species; the grain was left unchanged */
 
 /* ---- descriptors -------------------------------------------------------- */
 typedef struct dust_geometry {
@@ -271,8 +272,10 @@ int dust_step(dust_ctx *ctx, double dt);
  *       of Sec. 2.2 (cylindrical: v_R, R v_phi, v_z; spherical: v_r,
  *       r v_theta, r sin(theta) v_phi; shearing box with fargo = 1: the
  *       residual velocity), updated in place.  species_idx: device uint8 [n]
- *       or NULL (species 0).  param: device float64 [n] stopping-time values
- *       or NULL.
+ *       or NULL (species 0); every index must be < n_species (a grain with a
+ *       larger index is left unchanged and DUST_FLAG_SPECIES is raised in
+ *       status_out).  param: device float64 [n] stopping-time values or
+ *       NULL.
  *   gas: device float64 [ncell][4]: rho, then the momentum-like gas
  *       velocity p_g0..p_g2 of each zone (zone-centre radius factors).
  *   dep: device int64 [ncell][4], overwritten with this step's deposit in
@@ -282,15 +285,21 @@ int dust_step(dust_ctx *ctx, double dt);
  *   device: CUDA device ordinal (0..63), made current by the call.
  *   stream: cudaStream_t (NULL = the legacy default stream).
  *
- * Everything is enqueued on `stream`; the call does not wait for the GPU.
- * The first call on a device looks up the scratch's address
- * (cudaGetSymbolAddress), so make it before any stream capture.  Each call
- * copies the grid tables from a host image of the library and zeroes the
- * status words and `dep` before the kernel.  The scratch and the host image
- * are shared by all calls: calls that overlap (from two host threads, or on
- * two streams without ordering between them) race.  Errors: DUST_EINVAL
- * (bad descriptor, oversize grid, NULL array), DUST_ECUDA; the message is
- * dust_last_error(NULL). */
+ * Everything is enqueued on `stream`.  Each call writes the grid tables
+ * into a static host image of the library and copies it asynchronously into
+ * the scratch, then zeroes `dep`; the scratch's status words start at zero.
+ * The image is page-locked (the first call registers it with
+ * cudaHostRegister, which locks memory the library already holds and
+ * allocates nothing), so the call does not wait for the GPU, with one
+ * exception: before it rewrites the image it waits until the previous call's
+ * copy, on whichever device, has run.  The first call on a device also
+ * looks up the scratch's address (cudaGetSymbolAddress) and creates one
+ * event; make that first call before any stream capture.  Calls from
+ * several host threads are serialised by a lock; the scratch itself is
+ * shared by all calls on a device, so calls whose kernels can overlap on the
+ * GPU (two streams without ordering between them) race.  Errors:
+ * DUST_EINVAL (bad descriptor, oversize grid, NULL array), DUST_ECUDA; the
+ * message is dust_last_error(NULL). */
 int dust_step_noalloc(const dust_geometry *geom, const dust_grid *grid,
                       const dust_species *species, int n_species, int weight,
                       double quantum, double t, double dt, int64_t n,

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -75,6 +76,8 @@ struct dust_ctx {
 
     int32_t *d_key = nullptr, *d_count = nullptr, *d_cursor = nullptr, *d_blocksums = nullptr;
     int32_t *d_pair_id = nullptr, *d_pair_src = nullptr;
+    // zone segments left to the block sort: count, then keys ([nkeys + 2])
+    int32_t *d_bigseg = nullptr;
     // key counts for the next sort (d_count holds the current key offsets)
     int32_t *d_count_next = nullptr;
     bool keys_ready = false;   // d_key / d_count_next predicted by the last step
@@ -232,6 +235,28 @@ SpeciesDev make_species(const dust_species *species, int n_species, double quant
     }
     *quantum_out = qu;
     return sp;
+}
+
+// Propagators E = exp(-dt/tau), c_g = -expm1(-dt/tau), h1 = dt c_g/(dt/tau)
+// (Eqs. phi1, h1) of every species whose stopping time does not depend on
+// the grain, for a step of length dt, rounded once to single precision.
+void species_coefficients(SpeciesDev &sp, int geom, double omega, double dt)
+{
+    sp.coef_const = 0u;
+    for (int s = 0; s < sp.n; ++s) {
+        double tau;
+        if (sp.mode[s] == DUST_TAU_CONST) tau = sp.tau[s];
+        else if (sp.mode[s] == DUST_TAU_STOKES && (geom == DUST_CARTESIAN || geom == DUST_SHEARING_BOX))
+            tau = sp.tau[s] / omega;
+        else continue;
+        const double x = dt / tau;
+        const double cg = -expm1(-x);
+        sp.tau_eff_f[s] = (float)tau;
+        sp.E_f[s] = (float)exp(-x);
+        sp.cg_f[s] = (float)cg;
+        sp.h1_f[s] = (float)(x == 0.0 ? dt : dt * cg / x);
+        sp.coef_const |= 1u << s;
+    }
 }
 
 // Scalar description of direction d of the grid (host side).
@@ -722,6 +747,11 @@ int run_sort(dust_ctx *ctx, double dt, bool fused)
     a.pair_id = ctx->d_pair_id;
     a.pair_src = ctx->d_pair_src;
     a.nkeys1 = ctx->g.nkeys + 1;
+    a.big = ctx->d_bigseg;
+    // scratch of the block sort: the key column (read by the scatter, next
+    // written by the step) and the other store's ids (written after the sort)
+    a.tmp_id = ctx->d_key;
+    a.tmp_src = ctx->d_id[1 - ctx->cur];
     // counts of the nkeys + 1 keys and a zero: the exclusive scan then also
     // gives the end of the last (removed-grain) key's segment
     const int64_t m = ctx->g.nkeys + 2;
@@ -729,7 +759,7 @@ int run_sort(dust_ctx *ctx, double dt, bool fused)
     // keys predicted by the previous step for this dt are reused; otherwise
     // the key kernel computes them
     const bool reuse = ctx->keys_ready && ctx->keys_dt == dt;
-    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += (reuse ? 6 : 7) - (fused ? 1 : 0);
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_SORT] += (reuse ? 7 : 8) - (fused ? 1 : 0);
     if (!reuse) {
         CU(cudaMemsetAsync(ctx->d_count_next, 0, m * sizeof(int32_t), ctx->stream));
         cudaError_t e = cudaSuccess;
@@ -744,6 +774,7 @@ int run_sort(dust_ctx *ctx, double dt, bool fused)
     CU(launch_exclusive_scan(ctx->d_count_next, m, ctx->d_blocksums, ctx->stream));
     CU(cudaMemcpyAsync(ctx->d_cursor, ctx->d_count_next, m * sizeof(int32_t),
                        cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_bigseg, 0, sizeof(int32_t), ctx->stream));
     CU(launch_sort_scatter<Real>(a, ctx->stream, !fused));
     // fused: the step kernel moves the grains (and then flips the store)
     if (fused) ctx->perm_pending = true;
@@ -910,6 +941,7 @@ int run_step(dust_ctx *ctx, double dt)
     a.g = ctx->g;
     a.ph = phys_of(ctx, ctx->t, dt);
     a.sp = ctx->sp;
+    species_coefficients(a.sp, ctx->geom.kind, ctx->geom.omega, dt);
     a.t = ctx->t;
     a.dt = dt;
     a.inv_quantum = 1.0 / ctx->quantum;
@@ -1191,6 +1223,7 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
         dalloc(&ctx->d_count_next, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_time, 4) != cudaSuccess ||
         dalloc(&ctx->d_cursor, nk + 2) != cudaSuccess ||
+        dalloc(&ctx->d_bigseg, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_blocksums, scan_block_sums_size(nk + 2)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void **>(&ctx->h_status), ST_WORDS * sizeof(unsigned)) !=
             cudaSuccess) {
@@ -1708,6 +1741,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     dfree(ctx->d_count_next);
     dfree(ctx->d_time);
     dfree(ctx->d_cursor);
+    dfree(ctx->d_bigseg);
     dfree(ctx->d_blocksums);
     dfree(ctx->d_stage);
     dfree(ctx->d_mass);
@@ -1811,6 +1845,9 @@ int prime_keys(dust_ctx *ctx, double dt)
     a.pair_id = ctx->d_pair_id;
     a.pair_src = ctx->d_pair_src;
     a.nkeys1 = ctx->g.nkeys + 1;
+    a.big = ctx->d_bigseg;
+    a.tmp_id = ctx->d_key;
+    a.tmp_src = ctx->d_id[1 - ctx->cur];
     CU(cudaMemsetAsync(ctx->d_count_next, 0, (ctx->g.nkeys + 2) * sizeof(int32_t), ctx->stream));
     cudaError_t e;
     switch (ctx->geom.kind) {
@@ -2079,8 +2116,15 @@ namespace {
 // Device address of g_noalloc_scratch per device ordinal (null until the
 // first call on that device looks it up).
 void *g_noalloc_addr[kNoAllocMaxDevices];
-// Host image of the scratch contents, copied to the device by each call.
-alignas(256) unsigned char g_noalloc_image[kNoAllocScratchBytes];
+// Host image of the scratch contents, copied to the device by each call.  It
+// is page-locked once (cudaHostRegister of this existing array, no
+// allocation), so the copy runs asynchronously; the next call waits for the
+// event recorded after the copy before it rewrites the image.
+alignas(4096) unsigned char g_noalloc_image[kNoAllocScratchBytes];
+bool g_noalloc_image_locked = false;
+cudaEvent_t g_noalloc_copied[kNoAllocMaxDevices];
+// one call at a time writes the image and enqueues its copy
+std::mutex g_noalloc_mutex;
 
 // Byte offsets inside the scratch: status words, then per direction the grid
 // tables, each region on a 256-byte boundary.
@@ -2161,16 +2205,27 @@ extern "C" int dust_step_noalloc(const dust_geometry *geom, const dust_grid *gri
         return fail(nullptr, DUST_EINVAL, "grid tables exceed the %zu-byte scratch",
                     kNoAllocScratchBytes);
 
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     CU(cudaSetDevice(device));
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // setup, first call on this device only: the scratch's device address
+    // setup: once per process, page-lock the host image; once per device, the
+    // scratch's device address and the event that marks the image's copy
+    if (!g_noalloc_image_locked) {
+        CU(cudaHostRegister(g_noalloc_image, sizeof(g_noalloc_image), cudaHostRegisterPortable));
+        g_noalloc_image_locked = true;
+    }
     if (!g_noalloc_addr[device]) {
         void *addr = nullptr;
         CU(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+        CU(cudaEventCreateWithFlags(&g_noalloc_copied[device], cudaEventDisableTiming));
         g_noalloc_addr[device] = addr;
     }
     unsigned char *base = static_cast<unsigned char *>(g_noalloc_addr[device]);
     unsigned char *img = g_noalloc_image;
+    // the previous call's copy (on whichever device) reads the image: wait
+    // until it has run before writing the image again
+    for (int dv = 0; dv < kNoAllocMaxDevices; ++dv)
+        if (g_noalloc_copied[dv]) CU(cudaEventSynchronize(g_noalloc_copied[dv]));
 
     StepArgs<double> a{};
     GridDev &g = a.g;
@@ -2225,6 +2280,7 @@ extern "C" int dust_step_noalloc(const dust_geometry *geom, const dust_grid *gri
 
     // tables and zeroed status words in one copy; the deposit starts at zero
     CU(cudaMemcpyAsync(base, img, L.total, cudaMemcpyHostToDevice, st));
+    CU(cudaEventRecord(g_noalloc_copied[device], st));
     CU(cudaMemsetAsync(dep, 0, (size_t)ncell * 4 * sizeof(int64_t), st));
     cudaError_t e;
     switch (geom->kind) {

@@ -88,6 +88,13 @@ struct SpeciesDev {
     double mq[kMaxSpecies];   // mass / fixed-point quantum
     float mqf[kMaxSpecies];
     float tau_f[kMaxSpecies];
+    // single-precision propagators of the step (Eqs. phi1, h1) for species
+    // whose stopping time is the same for all their grains (constant tau;
+    // constant Stokes number in Cartesian and shearing-box geometry),
+    // computed in double precision on the host for the step's dt; bit s of
+    // coef_const says species s has them
+    unsigned coef_const;
+    float tau_eff_f[kMaxSpecies], E_f[kMaxSpecies], cg_f[kMaxSpecies], h1_f[kMaxSpecies];
 };
 
 template <typename Real>
@@ -153,6 +160,12 @@ struct SortArgs {
     int32_t *pair_id;             // [n] grain id at its sorted position
     int32_t *pair_src;            // [n] source position of that grain
     int64_t nkeys1;               // nkeys + 1 (the removed-grain key included)
+    // zone segments too long for the warp's staging: [0] their count
+    // (zeroed before the segment sort), [1 ..] their keys ([nkeys + 2])
+    int32_t *big;
+    // scratch of the block sort's merge passes, [n] each (free between the
+    // scatter and the step: the key column and the other store's ids)
+    int32_t *tmp_id, *tmp_src;
 };
 
 // Launch wrappers, explicitly instantiated per geometry.

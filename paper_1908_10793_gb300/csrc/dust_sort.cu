@@ -153,10 +153,13 @@ __global__ void sort_scatter_pairs_kernel(const SortArgs<Real> A)
 // Insertion sort by id of the (id, source) pairs of every key.  A warp
 // takes 32 consecutive keys; their segments are contiguous, so the warp
 // stages them in shared memory with coalesced loads, each lane sorts its
-// key's segment there, and the warp writes them back.  Segments of more
-// than kSegStage pairs in total are sorted in place in global memory.
+// key's segment there, and the warp writes them back.  When the warp's
+// segments hold more than kSegStage pairs in total, segments of at most
+// kSmallSeg pairs are insertion-sorted in place in global memory (bounded
+// cost) and longer ones are listed for the block sort below.
 constexpr int kSegThreads = 256;
 constexpr int kSegStage = 512;  // pairs staged per warp
+constexpr int kSmallSeg = 32;
 
 __device__ __forceinline__ void insertion_sort_pairs(int32_t *id, int32_t *src, int32_t b, int32_t e)
 {
@@ -192,7 +195,8 @@ __global__ void __launch_bounds__(kSegThreads) sort_segments_kernel(const SortAr
     const bool mine = k < nsort;
     const int32_t b = mine ? A.count[k] : W1, e = mine ? A.count[k + 1] : W1;
     if (W1 - W0 > kSegStage) {
-        if (mine) insertion_sort_pairs(A.pair_id, A.pair_src, b, e);
+        if (mine && e - b <= kSmallSeg) insertion_sort_pairs(A.pair_id, A.pair_src, b, e);
+        else if (mine) A.big[1 + atomicAdd(&A.big[0], 1)] = (int32_t)k;
         return;
     }
     const unsigned FULL = 0xffffffffu;
@@ -224,6 +228,100 @@ __global__ void __launch_bounds__(kSegThreads) sort_segments_kernel(const SortAr
     }
 }
 
+// Block sort by id of the long zone segments the segment sort listed (a
+// dense clump puts thousands of grains in one zone).  One block per segment:
+// chunks of kBigChunk pairs are sorted in shared memory by a bitonic
+// network, then merge passes double the sorted runs, ping-ponging between
+// the pair arrays and the scratch.  Ids are unique, so an element's place in
+// the merged run is its index in its own run plus the number of smaller ids
+// in the other run (a binary search).  Work O(L log L) per segment of L.
+constexpr int kBigThreads = 1024;
+constexpr int kBigChunk = 4096;
+constexpr int kBigSortBlocks = 152;  // one per SM of a GB300
+
+__device__ __forceinline__ int32_t count_less(const int32_t *v, int32_t len, int32_t x)
+{
+    int32_t lo = 0, hi = len;  // first index with v[index] >= x
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (v[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kBigThreads) sort_big_segments_kernel(const SortArgs<Real> A)
+{
+    __shared__ int32_t sid[kBigChunk];
+    __shared__ int32_t ssrc[kBigChunk];
+    const int32_t nbig = A.big[0];
+    for (int32_t item = blockIdx.x; item < nbig; item += gridDim.x) {
+        const int32_t key = A.big[1 + item];
+        const int32_t b = A.count[key], L = A.count[key + 1] - b;
+        // 1. sorted chunks
+        for (int32_t c0 = 0; c0 < L; c0 += kBigChunk) {
+            const int32_t m = min(kBigChunk, L - c0);
+            int32_t P = 2;
+            while (P < m) P <<= 1;
+            for (int32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                sid[i] = i < m ? A.pair_id[b + c0 + i] : 0x7fffffff;  // pads sort last
+                ssrc[i] = i < m ? A.pair_src[b + c0 + i] : 0;
+            }
+            __syncthreads();
+            for (int32_t k = 2; k <= P; k <<= 1) {
+                for (int32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (int32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                        const int32_t l = i ^ j;
+                        if (l > i) {
+                            const int32_t x = sid[i], y = sid[l];
+                            if ((x > y) == ((i & k) == 0)) {
+                                sid[i] = y;
+                                sid[l] = x;
+                                const int32_t t = ssrc[i];
+                                ssrc[i] = ssrc[l];
+                                ssrc[l] = t;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+                A.pair_id[b + c0 + i] = sid[i];
+                A.pair_src[b + c0 + i] = ssrc[i];
+            }
+            __syncthreads();
+        }
+        // 2. merge passes
+        int32_t *fid = A.pair_id + b, *fsrc = A.pair_src + b;
+        int32_t *tid = A.tmp_id + b, *tsrc = A.tmp_src + b;
+        for (int32_t w = kBigChunk; w < L; w <<= 1) {
+            for (int32_t u = threadIdx.x; u < L; u += blockDim.x) {
+                const int32_t run = u / w;
+                const int32_t p0 = (run & ~1) * w;
+                const int32_t a1 = min(p0 + w, L), b1 = min(p0 + 2 * w, L);
+                const int32_t x = fid[u];
+                const int32_t pos = (run & 1) ? p0 + (u - a1) + count_less(fid + p0, a1 - p0, x)
+                                              : u + count_less(fid + a1, b1 - a1, x);
+                tid[pos] = x;
+                tsrc[pos] = fsrc[u];
+            }
+            __syncthreads();
+            int32_t *t0 = fid, *t1 = fsrc;
+            fid = tid; fsrc = tsrc;
+            tid = t0; tsrc = t1;
+        }
+        if (fid != A.pair_id + b) {
+            for (int32_t u = threadIdx.x; u < L; u += blockDim.x) {
+                A.pair_id[b + u] = fid[u];
+                A.pair_src[b + u] = fsrc[u];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Gather every store column into sorted order (coalesced writes; the
 // sources are nearly in order because grains move little between sorts).
 template <typename Real>
@@ -250,6 +348,8 @@ cudaError_t launch_sort_scatter(const SortArgs<Real> &a, cudaStream_t s, bool ga
     const unsigned nbs = (unsigned)((a.src.n + 256 * kScatterItems - 1) / (256 * kScatterItems));
     sort_scatter_pairs_kernel<Real><<<nbs, 256, 0, s>>>(a);
     sort_segments_kernel<Real><<<(unsigned)((a.nkeys1 + kSegThreads - 1) / kSegThreads), kSegThreads, 0, s>>>(a);
+    // long segments, if any (the kernel reads their count on the device)
+    sort_big_segments_kernel<Real><<<kBigSortBlocks, kBigThreads, 0, s>>>(a);
     if (gather) sort_gather_kernel<Real><<<nb, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -93,9 +93,13 @@ step_per_grain_kernel(const StepArgs<Real> A)
     float moved = 0.f;
     if (gi < A.s.n) {
         double q[3] = {A.s.q[0][gi], A.s.q[1][gi], A.s.q[2][gi]};
-        if (!isnan(q[0])) {
+        const int sp = A.s.species ? A.s.species[gi] : 0;
+        // a species index the species table does not hold (possible only
+        // where the caller owns the store): flagged, the grain left as it is
+        const bool sp_ok = sp < A.sp.n;
+        if (!sp_ok && !isnan(q[0])) atomicOr(&A.status[ST_FLAGS], DUST_FLAG_SPECIES);
+        if (!isnan(q[0]) && sp_ok) {
             Real pn[3] = {A.s.p[0][gi], A.s.p[1][gi], A.s.p[2][gi]};
-            const int sp = A.s.species ? A.s.species[gi] : 0;
             const Real h = (Real)(0.5 * A.dt);
             Real inc1[3], inc2[3];
             drift<Real, GEOM>(A.ph, q, q, pn, h, false, inc1);

@@ -26,6 +26,7 @@ DUST_PUSHER_EM, DUST_PUSHER_SEMI_IMPLICIT = 0, 1
 DUST_MEM_HOST, DUST_MEM_DEVICE = 0, 1
 DUST_KERNEL_AUTO, DUST_KERNEL_PER_GRAIN, DUST_KERNEL_TILED, DUST_KERNEL_SLAB = 0, 1, 2, 3
 DUST_FLAG_NAN, DUST_FLAG_OVERFLOW, DUST_FLAG_CFL, DUST_FLAG_WRAP, DUST_FLAG_TIMEOUT = 1, 2, 4, 8, 16
+DUST_FLAG_SPECIES = 32
 
 
 class DustError(RuntimeError):

@@ -32,13 +32,22 @@ def test_code_only_keeps_string_and_character_literals():
 
 
 def test_algorithmic_bytes_of_the_mixed_step():
-    # mixed precision, fused sort gather: 2 x (3 FP64 coordinates + 3 FP32
-    # momenta) + permutation, sorted id and id write = 84 B per grain; gas
-    # (4 x FP32) + int64 deposit (4 x 8) = 48 B per zone
+    # mixed precision: 2 x (3 FP64 coordinates + 3 FP32 momenta) = 72 B per
+    # grain; gas (4 x FP32) + int64 deposit (4 x 8) = 48 B per zone; at 8
+    # grains per zone 78 B per grain.  The zone sort's permutation and id
+    # traffic (12 B per grain in the step kernel) is reported apart.
     from paper_1908_10793_gb300 import inputs as I
     w = I.sbox3d("small")
-    total, per_grain, per_zone = bench.algorithmic_bytes(w, 4, fused_gather=True)
-    assert (per_grain, per_zone) == (84, 48)
-    assert total == 84 * w.ngrains + 48 * w.ncell
-    # the bench workload: 16.8M grains and 2.1M zones -> 1.51 GB per launch
-    assert 84 * 16_777_216 + 48 * 128 ** 3 == 1_509_949_440
+    total, per_grain, per_zone = bench.algorithmic_bytes(w, 4)
+    assert (per_grain, per_zone) == (72, 48)
+    assert total == 72 * w.ngrains + 48 * w.ncell
+    assert total == 78 * w.ngrains
+    # the bench workload: 16.8M grains and 2.1M zones -> 1.309 GB per launch
+    assert 72 * 16_777_216 + 48 * 128 ** 3 == 1_308_622_848
+
+    class KT:
+        sort_ms, sort_launches = 4.0, 12
+    so = bench.sort_overhead(w, KT, 2)
+    assert so["step_kernel_bytes_per_grain"] == 12
+    assert so["step_kernel_bytes_per_launch"] == 12 * w.ngrains
+    assert so["sort_kernels_ms_per_step"] == 2.0 and so["sort_kernel_launches_per_step"] == 6
