@@ -437,88 +437,57 @@ def run_ours(args):
 
 def run_batch(args, D, torch, dev, stream):
     """64 independent 2-D shearing boxes (32^2 .. 512^2 zones, 1-16 grains per
-    zone, St in {0.01, 0.1, 1}), mixed precision.  The autotuner times tile
-    shapes per grid size on one instance alone; the batch is then run through
-    one graph with those tiles and with the default tiles, and the faster
-    assignment is the batch's value (instances alone favour small tiles, many
-    instances at once already fill the GPU).  Baseline: dust_step on each
-    context in turn on one stream, with the per-instance tuned tiles."""
+    zone, St in {0.01, 0.1, 1}), mixed precision.  Each dust_batch_step call
+    is one persistent launch for all instances and steps.  The autotuner
+    times candidate configurations (a tile shape for every instance, and the
+    batch's sort interval) in the batch itself, a few steps each; the chosen
+    configuration is then timed over the leg's steps.  Beside it: the default
+    configuration, the earlier graph of per-instance kernels, and dust_step
+    on each context in turn on one stream."""
     from paper_1908_10793_gb300 import autotune
     ws = I.si2d_batch("full")
     ngr = sum(w.ngrains for w in ws)
-    dts = [w.dt for w in ws]
-    K = max(2, args.batch_steps - args.batch_steps % 2)
-
-    # tune one representative instance per grid size (the largest grains per
-    # zone of that size, so the tile is chosen under the heaviest load)
-    tiles = {}
-    for w in ws:
-        side = w.n[0]
-        if side not in tiles or w.ngrains > tiles[side][1].ngrains:
-            tiles[side] = (None, w)
-    tuned = {}
-    for side, (_, w) in sorted(tiles.items()):
-        best, times = autotune.tune_tile(w, steps=4, device=dev.index)
-        tuned[side] = {"tile": list(best), "ms": {str(list(k)): v for k, v in times.items()}}
-
-    def make(one_stream, tuned_tiles):
-        cs = []
+    K = max(2, args.batch_steps)
+    best, tried = autotune.tune_batch(ws, steps=4, device=dev.index)
+    policy, kint = best
+    ms_best = autotune.time_batch(ws, policy, kint, steps=K, device=dev.index)
+    ms_def = autotune.time_batch(ws, None, 1, steps=K, device=dev.index)
+    ms_graph = autotune.time_batch(ws, None, 1, steps=K - K % 2, device=dev.index, batch_mode=1)
+    cs = []
+    try:
         for w in ws:
-            tile = tuned[w.n[0]]["tile"] if tuned_tiles else (0, 0, 0)
             c = D.Context(w, precision=D.DUST_MIXED, sort_interval=1, device=dev.index,
-                          stream=stream.cuda_stream if one_stream else None, tile=tile)
+                          stream=stream.cuda_stream)
             c.set_gas(w.rho, w.vgas)
             c.load(w.q, w.v)
             cs.append(c)
-        return cs
-
-    def timed(cs, run):
-        run()  # warm-up (and capture)
-        run()
-        for c in cs:
-            c.sync()
+        for _ in range(2):
+            for c, w in zip(cs, ws):
+                c.step(w.dt)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        run()
+        for c, w in zip(cs, ws):
+            for _ in range(K):
+                c.step(w.dt)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1)
-
-    def batched(tuned_tiles):
-        cs = make(False, tuned_tiles)
-        opt = D.dust_options(stream=stream.cuda_stream)
-        b = D.dust_batch_create([c.handle for c in cs], opt)
-        try:
-            ms = timed(cs, lambda: D.dust_batch_step(b, dts, K))
-            rcs = [c.sync(check=False)[0] for c in cs]
-        finally:
-            D.dust_batch_destroy(b)
-            for c in cs:
-                c.close()
-        return ms, min(rcs)
-
-    ms_b, rc = batched(True)
-    ms_d, _ = batched(False)
-    cs = make(True, True)
-    try:
-        def serial():
-            for c, x in zip(cs, dts):
-                for _ in range(K):
-                    c.step(x)
-        ms_s = timed(cs, serial)
+        ms_s = e0.elapsed_time(e1) / K
+        rc = min(c.sync(check=False)[0] for c in cs)
     finally:
         for c in cs:
             c.close()
-    best = min(ms_b, ms_d)
-    return {"value": ngr * K / (best / 1e3), "unit": UNIT, "ms_per_step": best / K,
-            "tiles_chosen": "tuned per grid size" if ms_b <= ms_d else "default",
-            "instances": len(ws), "grains": ngr, "zones": sum(w.ncell for w in ws),
-            "steps": K, "graph_launches": K // 2,
-            "tiles": {str(k): v for k, v in tuned.items()},
-            "tuned_tiles": {"value": ngr * K / (ms_b / 1e3), "ms_per_step": ms_b / K},
-            "default_tiles": {"value": ngr * K / (ms_d / 1e3), "ms_per_step": ms_d / K},
-            "one_at_a_time": {"value": ngr * K / (ms_s / 1e3), "ms_per_step": ms_s / K},
+    label = lambda cfg: "%s, sort every %d" % ("default tiles" if cfg[0] is None else  # noqa: E731
+                                             "tile %s" % list(cfg[0]), cfg[1])
+    return {"value": ngr / (ms_best / 1e3), "unit": UNIT, "ms_per_step": ms_best,
+            "config_chosen": label(best), "instances": len(ws), "grains": ngr,
+            "zones": sum(w.ncell for w in ws), "steps": K,
+            "launches_per_call": 1, "path": "one persistent cooperative launch per call",
+            "tuner": {label(k): v for k, v in tried.items()},
+            "default_config": {"value": ngr / (ms_def / 1e3), "ms_per_step": ms_def},
+            "graph_of_per_instance_kernels": {"value": ngr / (ms_graph / 1e3),
+                                              "ms_per_step": ms_graph},
+            "one_at_a_time": {"value": ngr / (ms_s / 1e3), "ms_per_step": ms_s},
             "status": rc,
             "workload": "64 2-D (x,z) orbital-advection shearing boxes, 32^2..512^2 zones, "
                         "1-16 grains/zone, St 0.01/0.1/1, dust/gas 0.01/0.02/0.1, TSC, "

@@ -180,6 +180,17 @@ typedef struct dust_options {
                               the copy brings), so the failure path can be
                               checked without a GPU fault: the step's blocks
                               give up and dust_sync returns DUST_ETIMEOUT   */
+    int batch_mode;        /* dust_batch_create only.  0: where every instance
+                              allows it (mixed precision on the slab kernel,
+                              exponential midpoint, no gas predictor, one
+                              geometry: x-z shearing boxes in the orbital-
+                              advection frame, or x-y Cartesian boxes),
+                              each dust_batch_step call is one persistent
+                              launch for all instances and steps; otherwise,
+                              and with 1, a graph of per-instance kernels.
+                              The batch's sort_interval k (0 = 1): the steps
+                              s = 0, k, 2k, ... of a call sort first (the
+                              graph sorts every step)                        */
 } dust_options;
 
 typedef struct dust_stats {

@@ -1,4 +1,5 @@
-"""Tile-shape autotuner for the dust contexts.
+"""Autotuner for the dust contexts and batches: tile shape, and for a batch
+the sort interval, each candidate timed in the configuration it is for.
 
 The zone sort groups grains by tiles of zones and the step kernels stage one
 tile's gas and deposit box per thread block, so the tile shape sets the
@@ -67,5 +68,76 @@ def tune_tile(w, precision=D.DUST_MIXED, steps=4, candidates=None, **kw):
             times[tile] = time_tile(w, tile, precision, steps, **kw)
         except D.DustError:
             continue  # e.g. a tile whose boxes do not fit in shared memory
+    best = min(times, key=times.get)
+    return best, times
+
+
+# ---- batches -------------------------------------------------------------
+
+def batch_candidates(ws, sort_intervals=(1, 2)):
+    """Configurations of a batch to try: a tile policy (None = the library's
+    default for every instance, or one shape applied to every instance,
+    clipped to its grid) and the batch's sort interval.  The default policy
+    with a sort every step comes first."""
+    shapes = candidate_tiles(max(ws, key=lambda w: w.ncell))
+    policies = [None] + [s for s in shapes if s != shapes[0]]
+    return [(p, k) for k in sort_intervals for p in policies]
+
+
+def _tile_for(w, policy):
+    if policy is None:
+        return (0, 0, 0)
+    return tuple(min(policy[d], w.n[d]) if w.n[d] > 1 else 1 for d in range(3))
+
+
+def time_batch(ws, policy=None, sort_interval=1, steps=4, warmup=2, device=0, batch_mode=0):
+    """Device time per step (ms, CUDA events on the batch's stream) of a
+    batch of the workloads ws in one configuration: every instance a mixed
+    precision context with the policy's tile, one dust_batch_step call of
+    `steps` steps after `warmup` steps."""
+    import torch
+    stream = torch.cuda.Stream(device)
+    ctxs = []
+    b = None
+    try:
+        for w in ws:
+            c = D.Context(w, precision=D.DUST_MIXED, sort_interval=sort_interval, device=device,
+                          tile=_tile_for(w, policy))
+            c.set_gas(w.rho, w.vgas)
+            c.load(w.q, w.v, w.species, w.param)
+            ctxs.append(c)
+        opt = D.dust_options(stream=stream.cuda_stream, sort_interval=sort_interval,
+                             batch_mode=batch_mode)
+        b = D.dust_batch_create([c.handle for c in ctxs], opt)
+        dts = [w.dt for w in ws]
+        D.dust_batch_step(b, dts, warmup)
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        D.dust_batch_step(b, dts, steps)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        bad = [rc for rc in (c.sync(check=False)[0] for c in ctxs) if rc not in (0, D.DUST_ECFL)]
+        if bad:
+            raise D.DustError(bad[0], "batch status %d" % bad[0])
+        return e0.elapsed_time(e1) / steps
+    finally:
+        if b is not None:
+            D.dust_batch_destroy(b)
+        for c in ctxs:
+            c.close()
+
+
+def tune_batch(ws, steps=4, candidates=None, device=0):
+    """Times every candidate configuration in the batch (not instance by
+    instance) and returns (best (policy, sort interval), {config: ms per
+    step}).  Candidates that do not fit are skipped."""
+    cands = candidates or batch_candidates(ws)
+    times = {}
+    for cfg in cands:
+        try:
+            times[cfg] = time_batch(ws, cfg[0], cfg[1], steps=steps, device=device)
+        except D.DustError:
+            continue
     best = min(times, key=times.get)
     return best, times

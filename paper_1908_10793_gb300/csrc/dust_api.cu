@@ -1,5 +1,6 @@
 // Host side of the C interface declared in include/dust.h: context
 // management, data movement, unit conversion, step sequencing.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdarg>
@@ -461,24 +462,7 @@ __global__ void apply_feedback_kernel(GridDev g, double quantum, Real *gas,
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.ncell) return;
-    const int i = (int)(c % g.n[0]);
-    const int j = (int)((c / g.n[0]) % g.n[1]);
-    const int k = (int)(c / ((int64_t)g.n[0] * g.n[1]));
-    const long long d0 = (long long)dep[4 * c + 0], d1 = (long long)dep[4 * c + 1],
-                    d2 = (long long)dep[4 * c + 2];
-    if ((d0 | d1 | d2) == 0) return;
-    if (sizeof(Real) == 4) {
-        const float s = (float)quantum /
-                        ((float)gas[4 * c] * g.dvol_f[0][i] * g.dvol_f[1][j] * g.dvol_f[2][k]);
-        gas[4 * c + 1] += (Real)((float)d0 * s);
-        gas[4 * c + 2] += (Real)((float)d1 * s);
-        gas[4 * c + 3] += (Real)((float)d2 * s);
-    } else {
-        const double s = quantum / ((double)gas[4 * c] * g.dvol[0][i] * g.dvol[1][j] * g.dvol[2][k]);
-        gas[4 * c + 1] += (Real)((double)d0 * s);
-        gas[4 * c + 2] += (Real)((double)d1 * s);
-        gas[4 * c + 3] += (Real)((double)d2 * s);
-    }
+    apply_feedback_zone<Real>(g, quantum, gas, dep, c);
 }
 
 __global__ void dep_to_double_kernel(const unsigned long long *dep, int64_t n, double quantum,
@@ -1784,6 +1768,23 @@ struct dust_batch {
     std::vector<int32_t *> count;
     std::vector<std::array<int64_t, dust_ctx::N_GROUPS>> period_launches;
     std::string err;
+    // one persistent launch for all instances (batch_persistent_kernel):
+    // the instances' descriptors (page-locked host copy, device copy),
+    // the work items' prefix sums, the grid barrier, and a graph of the
+    // call (descriptor copy, barrier reset, the launch) per step count
+    int mode = 0;               // 0: persistent where the instances allow it; 1: graph
+    int sort_interval = 1;
+    int test_timeout = 0;
+    BatchInst *h_inst = nullptr, *d_inst = nullptr;
+    int *d_pre = nullptr;
+    unsigned *d_bar = nullptr;
+    cudaEvent_t inst_copied = nullptr;
+    cudaGraph_t pgraph = nullptr;
+    cudaGraphExec_t pexec = nullptr;
+    int pgraph_steps = -1;
+    int pvariant = -1;
+    size_t psmem = 0;
+    int pgrid = 0;
 };
 
 namespace {
@@ -1820,12 +1821,7 @@ __global__ void set_time_kernel(double *tm, double t, double shift_mid, double s
 // same operations as make_phys: fmod(((q Omega) Lx) (t + dt/2), Ly).
 __global__ void time_advance_kernel(double *tm, double dt, double q_om_lx, double ly, int sb)
 {
-    const double t = __dadd_rn(tm[0], dt);
-    tm[0] = t;
-    if (sb) {
-        tm[1] = fmod(__dmul_rn(q_om_lx, __dadd_rn(t, __dmul_rn(0.5, dt))), ly);
-        tm[2] = fmod(__dmul_rn(q_om_lx, __dadd_rn(t, dt)), ly);
-    }
+    advance_time(tm, dt, q_om_lx, ly, sb);
 }
 
 // Keys of the first sort of a captured period, computed now for the current
@@ -1958,6 +1954,214 @@ int capture(dust_batch *b, const double *dt)
     return DUST_OK;
 }
 
+// ---- the persistent path
+
+// Kernel variant of the persistent launch for these instances, -1 if they
+// cannot share it: all mixed precision on the slab kernel (which predicts
+// the next sort's keys), the exponential-midpoint pusher, no gas predictor,
+// and one of the two instantiated geometries: x-z shearing boxes in the
+// orbital-advection frame (variant 0) or x-y Cartesian boxes (variant 1).
+int persistent_variant(const dust_batch *b)
+{
+    int v = -1;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const dust_ctx *c = b->ctx[i];
+        if (!step_emits_keys(c) || c->opt.gas_predictor || c->opt.pusher != DUST_PUSHER_EM) return -1;
+        const int flat = slab_flat(c->g);
+        int vi = -1;
+        if (c->geom.kind == DUST_SHEARING_BOX && c->geom.fargo && flat == 1) vi = 0;
+        else if (c->geom.kind == DUST_CARTESIAN && flat == 2) vi = 1;
+        if (vi < 0 || (v >= 0 && vi != v)) return -1;
+        v = vi;
+    }
+    return v;
+}
+
+int grid_of(int variant, size_t smem)
+{
+    return variant == 0 ? batch_persistent_grid<GEOM_SB, 1, 1>(smem)
+                        : batch_persistent_grid<GEOM_CART, 2, 1>(smem);
+}
+
+cudaError_t launch_variant(int variant, const BatchDev &d, size_t smem, int grid, cudaStream_t st)
+{
+    return variant == 0 ? launch_batch_persistent<GEOM_SB, 1, 1>(d, smem, grid, st)
+                        : launch_batch_persistent<GEOM_CART, 2, 1>(d, smem, grid, st);
+}
+
+// Descriptor of instance c for a launch of steps of length dt starting at
+// its current time.
+BatchInst batch_inst_of(dust_ctx *c, double dt, int test_timeout)
+{
+    BatchInst I{};
+    TiledArgs<float> &ta = I.ta;
+    StepArgs<float> &a = ta.s;
+    a.g = c->g;
+    a.ph = phys_of(c, c->t, dt);
+    a.sp = c->sp;
+    species_coefficients(a.sp, c->geom.kind, c->geom.omega, dt);
+    a.t = c->t;
+    a.dt = dt;
+    a.inv_quantum = 1.0 / c->quantum;
+    a.s = store_of<float>(c, c->cur);
+    a.gas = static_cast<const float *>(c->d_gas);
+    a.dep = c->d_dep;
+    a.status = c->d_status;
+    a.tdev = c->d_time;
+    ta.tsc = c->opt.weight == DUST_WEIGHT_TSC;
+    ta.gas_tmap = c->tmap_ok[0] ? static_cast<const void *>(c->d_tmaps) : nullptr;
+    ta.wait_extra_tx = (c->opt.test_wait_timeout || test_timeout) ? 16u : 0u;
+    ta.wait_ns = (c->opt.test_wait_timeout || test_timeout) ? 1000000ull : 0ull;
+    for (int w = 0; w < 2; ++w) I.store[w] = store_of<float>(c, w);
+    I.count[0] = c->d_count;
+    I.count[1] = c->d_count_next;
+    I.key = c->d_key;
+    I.cursor = c->d_cursor;
+    I.pair_id = c->d_pair_id;
+    I.pair_src = c->d_pair_src;
+    I.bigseg = c->d_bigseg;
+    I.blocksums = c->d_blocksums;
+    I.time = c->d_time;
+    I.dt = dt;
+    I.q_om_lx = c->geom.q * c->geom.omega * (c->g.hi[0] - c->g.lo[0]);
+    I.ly = c->g.hi[1] - c->g.lo[1];
+    I.sb = c->geom.kind == DUST_SHEARING_BOX;
+    I.quantum = c->quantum;
+    I.cur = c->cur;
+    I.feedback = c->opt.feedback_apply;
+    I.ntiles = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
+    I.n = c->n_grains;
+    I.nkeys = c->g.nkeys;
+    I.ncell = c->ncell;
+    return I;
+}
+
+void drop_persistent(dust_batch *b)
+{
+    if (b->pexec) cudaGraphExecDestroy(b->pexec);
+    if (b->pgraph) cudaGraphDestroy(b->pgraph);
+    b->pexec = nullptr;
+    b->pgraph = nullptr;
+    b->pgraph_steps = -1;
+}
+
+// nsteps steps of every instance as one persistent launch (see
+// dust_batch.cu).  Steps s with s % sort_interval == 0 of the call sort
+// first; the step before a sort predicts its keys.
+int step_persistent(dust_batch *b, const double *dt, int nsteps)
+{
+    const size_t n = b->ctx.size();
+    const int K = b->sort_interval;
+    // keys for the first sort (the previous call's last step, or now)
+    for (size_t i = 0; i < n; ++i) {
+        dust_ctx *c = b->ctx[i];
+        if (c->n_grains > 0 && !(c->keys_ready && c->keys_dt == dt[i]) && !c->perm_pending) {
+            const int r = prime_keys<float>(c, dt[i]);
+            if (r) return bfail(b, r, "context %zu: %s", i, c->err.c_str());
+        }
+        if (c->perm_pending) return bfail(b, DUST_ESTATE, "context %zu: a sort is pending", i);
+    }
+    // descriptors and work items
+    if (b->inst_copied) BCU(cudaEventSynchronize(b->inst_copied));
+    std::vector<int> pre((size_t)BPH_N * (n + 1), 0);
+    size_t slab = 0;
+    for (size_t i = 0; i < n; ++i) {
+        dust_ctx *c = b->ctx[i];
+        b->h_inst[i] = batch_inst_of(c, dt[i], b->test_timeout);
+        slab = std::max(slab, batch_tile_smem(c->g));
+        const BatchInst &I = b->h_inst[i];
+        const int64_t items[BPH_N] = {
+            (I.nkeys + 2 + kBatchScanChunk - 1) / kBatchScanChunk,
+            (I.n + kBatchScatterChunk - 1) / kBatchScatterChunk,
+            (I.nkeys + 1 + 255) / 256,
+            (std::max(I.ncell * 4, I.nkeys + 2) + kBatchZeroChunk - 1) / kBatchZeroChunk,
+            I.ntiles,
+            (I.ncell + 255) / 256,
+            1};
+        for (int ph = 0; ph < BPH_N; ++ph) {
+            const int64_t v = pre[(size_t)ph * (n + 1) + i] + items[ph];
+            if (v >= ((int64_t)1 << 31)) return bfail(b, DUST_EINVAL, "too many work items");
+            pre[(size_t)ph * (n + 1) + i + 1] = (int)v;
+        }
+    }
+    // shared memory: the largest tile layout (or the sort's staging), then
+    // the block's copy of the step arguments
+    const size_t ta_off = (std::max(slab, batch_sort_smem()) + 15) & ~(size_t)15;
+    const size_t smem = ta_off + sizeof(TiledArgs<float>);
+    if (smem != b->psmem) {
+        b->psmem = smem;
+        b->pgrid = grid_of(b->pvariant, smem);
+        drop_persistent(b);
+    }
+    if (b->pgrid <= 0) return bfail(b, DUST_ECUDA, "the persistent kernel does not fit on the device");
+    if (!b->d_pre) BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_pre), pre.size() * sizeof(int)));
+    BCU(cudaMemcpyAsync(b->d_pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, b->root));
+    // each instance's time of this call, after its pending work
+    for (size_t i = 0; i < n; ++i) {
+        dust_ctx *c = b->ctx[i];
+        const PhysDev ph = phys_of(c, c->t, dt[i]);
+        set_time_kernel<<<1, 1, 0, c->stream>>>(c->d_time, c->t, ph.shift_mid, ph.shift_end);
+        BCU(cudaGetLastError());
+        BCU(cudaEventRecord(b->join[i], c->stream));
+        BCU(cudaStreamWaitEvent(b->root, b->join[i], 0));
+    }
+    if (b->pgraph_steps != nsteps || !b->pexec) {
+        drop_persistent(b);
+        BatchDev d{};
+        d.inst = b->d_inst;
+        d.ninst = (int)n;
+        d.pre = b->d_pre;
+        d.bar = b->d_bar;
+        d.nsteps = nsteps;
+        d.sort_interval = K;
+        d.bar_extra = b->test_timeout ? 1 : 0;
+        d.wait_ns = b->test_timeout ? 1000000ull : 1000000000ull;
+        d.ta_offset = ta_off;
+        cudaStream_t cs = nullptr;
+        BCU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_inst, b->h_inst, n * sizeof(BatchInst),
+                                                  cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), cs);
+        if (e == cudaSuccess) e = launch_variant(b->pvariant, d, smem, b->pgrid, cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bfail(b, DUST_ECUDA, "persistent launch capture: %s",
+                         cudaGetErrorString(e != cudaSuccess ? e : ee));
+        }
+        b->pgraph = g;
+        BCU(cudaGraphInstantiate(&b->pexec, g, 0));
+        b->pgraph_steps = nsteps;
+    }
+    BCU(cudaGraphLaunch(b->pexec, b->root));
+    BCU(cudaEventRecord(b->inst_copied, b->root));
+    BCU(cudaEventRecord(b->done, b->root));
+    // host state of every context after the call
+    const int sorts = (nsteps + K - 1) / K;
+    for (size_t i = 0; i < n; ++i) {
+        dust_ctx *c = b->ctx[i];
+        BCU(cudaStreamWaitEvent(c->stream, b->done, 0));
+        if (sorts & 1) {
+            c->cur = 1 - c->cur;
+            std::swap(c->d_count, c->d_count_next);
+        }
+        c->keys_ready = (nsteps % K) == 0 && c->n_grains > 0;
+        c->keys_dt = dt[i];
+        c->perm_pending = false;
+        for (int s = 0; s < nsteps; ++s) c->t += dt[i];
+        c->last_dt = dt[i];
+        c->steps += nsteps;
+        c->timed_steps += nsteps;
+        c->have_deposit = true;
+        c->need_sort = false;
+    }
+    b->ctx[0]->launches[dust_ctx::GROUP_STEP] += 1;
+    return DUST_OK;
+}
+
 }  // namespace
 
 extern "C" int dust_batch_create(dust_batch **out, dust_ctx *const *insts, int n,
@@ -2002,6 +2206,19 @@ extern "C" int dust_batch_create(dust_batch **out, dust_ctx *const *insts, int n
     for (int i = 0; i < n; ++i)
         if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
             return bail("event creation failed");
+    if (opt) {
+        b->mode = opt->batch_mode;
+        b->sort_interval = opt->sort_interval > 0 ? opt->sort_interval : 1;
+        b->test_timeout = opt->test_wait_timeout;
+    }
+    b->pvariant = b->mode == 0 ? persistent_variant(b) : -1;
+    if (b->pvariant >= 0) {
+        if (cudaMallocHost(reinterpret_cast<void **>(&b->h_inst), n * sizeof(BatchInst)) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void **>(&b->d_inst), n * sizeof(BatchInst)) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void **>(&b->d_bar), 2 * sizeof(unsigned)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->inst_copied, cudaEventDisableTiming) != cudaSuccess)
+            return bail("allocation for the persistent launch failed");
+    }
     *out = b;
     return DUST_OK;
 }
@@ -2018,6 +2235,7 @@ extern "C" int dust_batch_step(dust_batch *b, const double *dt, int nsteps)
     }
     if (nsteps == 0) return DUST_OK;
     BCU(cudaSetDevice(b->device));
+    if (b->pvariant >= 0 && persistent_variant(b) == b->pvariant) return step_persistent(b, dt, nsteps);
     const int pairs = nsteps / 2;
     if (pairs > 0) {
         // keys for the first captured sort
@@ -2082,6 +2300,12 @@ extern "C" void dust_batch_destroy(dust_batch *b)
     cudaSetDevice(b->device);
     if (b->root) cudaStreamSynchronize(b->root);
     drop_graph(b);
+    drop_persistent(b);
+    if (b->h_inst) cudaFreeHost(b->h_inst);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_pre) cudaFree(b->d_pre);
+    if (b->d_bar) cudaFree(b->d_bar);
+    if (b->inst_copied) cudaEventDestroy(b->inst_copied);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->done) cudaEventDestroy(b->done);
     for (cudaEvent_t e : b->join)

@@ -1,5 +1,5 @@
 // Instantiations of the step and sort kernels for one geometry.
-#include "dust_slab.cuh"
+#include "dust_batch.cuh"
 
 namespace dust {
 
@@ -34,5 +34,9 @@ template cudaError_t launch_predict_gas<double, GEOM_SB, 1>(const StepArgs<doubl
 template cudaError_t launch_deposit_mass<GEOM_SB>(const GridDev &, const SpeciesDev &, int, int64_t,
                                                    const double *const[3], const uint8_t *,
                                                    unsigned long long *, unsigned int *, cudaStream_t);
+
+// the batched persistent kernel of this geometry's shared variant
+template int batch_persistent_grid<GEOM_SB, 1, 1>(size_t);
+template cudaError_t launch_batch_persistent<GEOM_SB, 1, 1>(const BatchDev &, size_t, int, cudaStream_t);
 
 }  // namespace dust

@@ -168,6 +168,100 @@ struct SortArgs {
     int32_t *tmp_id, *tmp_src;
 };
 
+#ifdef __CUDACC__
+// Feedback of zone c (a8): the deposited momentum-like impulse over rho dV
+// added to the gas (the corrector term of the RK2 step, Sec. 3.1).
+template <typename Real>
+__device__ __forceinline__ void apply_feedback_zone(const GridDev &g, double quantum, Real *gas,
+                                                    const unsigned long long *dep, int64_t c)
+{
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((int64_t)g.n[0] * g.n[1]));
+    const long long d0 = (long long)dep[4 * c + 0], d1 = (long long)dep[4 * c + 1],
+                    d2 = (long long)dep[4 * c + 2];
+    if ((d0 | d1 | d2) == 0) return;
+    if (sizeof(Real) == 4) {
+        const float s = (float)quantum /
+                        ((float)gas[4 * c] * g.dvol_f[0][i] * g.dvol_f[1][j] * g.dvol_f[2][k]);
+        gas[4 * c + 1] += (Real)((float)d0 * s);
+        gas[4 * c + 2] += (Real)((float)d1 * s);
+        gas[4 * c + 3] += (Real)((float)d2 * s);
+    } else {
+        const double s = quantum / ((double)gas[4 * c] * g.dvol[0][i] * g.dvol[1][j] * g.dvol[2][k]);
+        gas[4 * c + 1] += (Real)((double)d0 * s);
+        gas[4 * c + 2] += (Real)((double)d1 * s);
+        gas[4 * c + 3] += (Real)((double)d2 * s);
+    }
+}
+
+// Time of the next step of a context stepped from the device: t += dt, then
+// the shear-periodic shifts of the step that starts at the new t, with the
+// same operations as on the host: fmod(((q Omega) Lx) (t + dt/2), Ly).
+__device__ __forceinline__ void advance_time(double *tm, double dt, double q_om_lx, double ly, int sb)
+{
+    const double t = __dadd_rn(tm[0], dt);
+    tm[0] = t;
+    if (sb) {
+        tm[1] = fmod(__dmul_rn(q_om_lx, __dadd_rn(t, __dmul_rn(0.5, dt))), ly);
+        tm[2] = fmod(__dmul_rn(q_om_lx, __dadd_rn(t, dt)), ly);
+    }
+}
+#endif  // __CUDACC__
+
+// ---- batched persistent step (dust_batch_step) ---------------------------
+// One instance of a batch as the persistent kernel sees it: the step's
+// arguments with the fields that change from step to step set per step from
+// the buffers below.
+struct BatchInst {
+    TiledArgs<float> ta;         // the step's arguments (store, sort and count fields set per step)
+    StoreDev<float> store[2];    // the two grain stores
+    int32_t *count[2];           // [0]: offsets of the last sort, [1]: counts for the next sort (at the launch)
+    int32_t *key, *cursor, *pair_id, *pair_src, *bigseg, *blocksums;
+    double *time;                // [t, shift_mid, shift_end] of the step (the steps' tdev)
+    double dt, q_om_lx, ly;
+    double quantum;
+    int sb;                      // shearing box: the shifts advance with t
+    int cur;                     // current store at the launch
+    int feedback;                // apply the deposit to the gas after each step
+    int ntiles;
+    int64_t n, nkeys, ncell;
+};
+
+// Work items of one phase, over the instances: item w belongs to instance
+// i with pre[i] <= w < pre[i + 1].
+enum { BPH_SCAN = 0, BPH_SCATTER, BPH_SEG, BPH_ZERO, BPH_TILE, BPH_FB, BPH_INST, BPH_N };
+
+struct BatchDev {
+    const BatchInst *inst;
+    int ninst;
+    const int *pre;              // [BPH_N][ninst + 1]
+    unsigned *bar;               // grid barrier: arrivals, generation (zero at launch)
+    int nsteps;
+    int sort_interval;           // steps s with s % sort_interval == 0 sort first
+    int bar_extra;               // > 0 only to test the barrier's timeout
+    unsigned long long wait_ns;  // limit of one barrier wait
+    size_t ta_offset;            // where the block's copy of the step arguments sits in shared memory
+};
+
+// Work items per phase of one instance (the batched kernel's decomposition).
+constexpr int kBatchScanChunk = 256 * 4;     // counts per scan chunk (256 threads x 4)
+constexpr int kBatchScatterChunk = 256 * 4;  // grains per scatter item
+constexpr int kBatchZeroChunk = 256 * 8;     // 8-byte words zeroed per item
+constexpr int kBatchBigItems = 8;            // items of the block sort per instance
+
+template <int GEOM, int FLAT, int MODE>
+cudaError_t launch_batch_persistent(const BatchDev &b, size_t smem, int grid, cudaStream_t s);
+
+// Shared memory of one slab tile of this grid, and of the sort's staging.
+size_t batch_tile_smem(const GridDev &g);
+size_t batch_sort_smem();
+
+// Grid size of the persistent kernel for this shared memory (all blocks
+// resident at once), 0 if it cannot run.
+template <int GEOM, int FLAT, int MODE>
+int batch_persistent_grid(size_t smem);
+
 // Launch wrappers, explicitly instantiated per geometry.
 template <typename Real, int GEOM, int WEIGHT>
 cudaError_t launch_step_per_grain(const StepArgs<Real> &a, cudaStream_t s);

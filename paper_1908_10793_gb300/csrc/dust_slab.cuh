@@ -134,9 +134,18 @@ __device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev
 // MODE > 0 fixes the exponential-midpoint pusher and, in the shearing box,
 // the frame (1: orbital advection, 2: standard) at compile time, which
 // drops the other branches from the hot code.
+//
+// One tile (tile index `tile` of `ntile` tiles; blocks of kSlabThreads
+// threads, smem_raw the dynamic shared memory of slab_smem_bytes) as a
+// device function: the step kernel below runs one tile per block, the
+// batched persistent kernel runs tiles of many instances in turn.
+// reuse: the block processes further tiles after this one (the batched
+// persistent kernel): the tile ends with a block barrier and invalidates its
+// copy barrier, so that the shared memory can be reused.
+// Returns false when the wait for the gas box ran out (DUST_FLAG_TIMEOUT).
 template <int GEOM, int FLAT, int MODE>
-__global__ void __launch_bounds__(kSlabThreads, 2)
-step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
+__device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int tile, const int ntile,
+                                          unsigned char *smem_raw, const bool reuse)
 {
     using Sh = SlabShape<FLAT>;
     constexpr int NB = Sh::NB, NC = Sh::NC;
@@ -148,10 +157,8 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     if (MODE > 0) ph.pusher = DUST_PUSHER_EM;
     if (GEOM == GEOM_SB && MODE == 1) ph.fargo = 1;
     if (GEOM == GEOM_SB && MODE == 2) ph.fargo = 0;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     const unsigned FULL = 0xffffffffu;
 
-    const int tile = blockIdx.x;
     // grains are read from S and written to O (the other store when the
     // sort's gather is fused into this kernel)
     const StoreDev<float> &S = A.s;
@@ -160,7 +167,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
         // grains removed before the last sort sit after every zone's group:
         // they keep the removed-grain key and are moved as they are
         const int D0 = TA.key_off[g.nkeys], D1 = (int)A.s.n;
-        for (int gi = D0 + blockIdx.x * blockDim.x + threadIdx.x; gi < D1; gi += gridDim.x * blockDim.x) {
+        for (int gi = D0 + tile * blockDim.x + threadIdx.x; gi < D1; gi += ntile * blockDim.x) {
             if (TA.emit_keys) TA.key_out[gi] = (int32_t)g.nkeys;
             if (TA.perm) {
                 const int src = TA.perm[gi];
@@ -174,11 +181,11 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
                 if (S.param) O.param[gi] = S.param[src];
             }
         }
-        if (TA.emit_keys && blockIdx.x == 0 && threadIdx.x == 0 && D1 > D0)
+        if (TA.emit_keys && tile == 0 && threadIdx.x == 0 && D1 > D0)
             atomicAdd(&TA.count_out[g.nkeys], (int32_t)(D1 - D0));
     }
     const int64_t kbase = (int64_t)tile * g.tvol;
-    if (TA.key_off[kbase + g.tvol] <= TA.key_off[kbase]) return;
+    if (TA.key_off[kbase + g.tvol] <= TA.key_off[kbase]) return true;
 
     int B[3], o[3], tc[3];
     tc[0] = tile % g.nt[0];
@@ -235,7 +242,7 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
         for (int c = 0; c < 4; ++c) sdep[c * bvol + lin] = 0ull;
     }
     __syncthreads();
-    if (!gas_box_finish<float>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status, TA.wait_ns)) return;
+    if (!gas_box_finish<float>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status, TA.wait_ns)) return false;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -799,6 +806,41 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
         if (nr) atomicAdd(reinterpret_cast<unsigned long long *>(&A.status[ST_REMOVED_LO]),
                           (unsigned long long)nr);
     }
+    if (reuse) {
+        __syncthreads();
+        if (threadIdx.x == 0 && TA.gas_tmap) tma_barrier_inval(sbar);
+    }
+    return true;
+}
+
+// Variants that a batch of instances can also run in one persistent launch
+// (dust_batch.cuh): x-z shearing boxes in the orbital-advection frame and
+// x-y Cartesian boxes.  For these, the step kernel and the persistent kernel
+// call one out-of-line copy of the tile function, compiled once in the same
+// translation unit, so that the compiler's contraction of multiplies and
+// adds into fused multiply-adds is the same in both, and a batch gives the
+// results of its instances stepped alone bit for bit.
+template <int GEOM, int FLAT, int MODE>
+struct SlabShared {
+    static constexpr bool value = MODE == 1 && ((GEOM == GEOM_SB && FLAT == 1) || (GEOM == GEOM_CART && FLAT == 2));
+};
+
+template <int GEOM, int FLAT, int MODE>
+__device__ __noinline__ bool slab_tile_shared(const TiledArgs<float> &TA, const int tile, const int ntile,
+                                              unsigned char *smem_raw, const bool reuse)
+{
+    return slab_tile<GEOM, FLAT, MODE>(TA, tile, ntile, smem_raw, reuse);
+}
+
+template <int GEOM, int FLAT, int MODE>
+__global__ void __launch_bounds__(kSlabThreads, 2)
+step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    if constexpr (SlabShared<GEOM, FLAT, MODE>::value)
+        slab_tile_shared<GEOM, FLAT, MODE>(TA, blockIdx.x, gridDim.x, smem_raw, false);
+    else
+        slab_tile<GEOM, FLAT, MODE>(TA, blockIdx.x, gridDim.x, smem_raw, false);
 }
 
 inline size_t slab_smem_bytes(const GridDev &g)

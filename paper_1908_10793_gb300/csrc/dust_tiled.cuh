@@ -87,6 +87,14 @@ __device__ __forceinline__ void tma_barrier_init(unsigned long long *bar)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// One thread, after every thread's wait on it has returned: invalidate the
+// barrier, so that the same shared memory can hold the next tile's barrier
+// (a block that processes several tiles in turn).
+__device__ __forceinline__ void tma_barrier_inval(unsigned long long *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // One thread: expect `bytes` and start the 4-D tile copy of the box at
 // coordinates (0, x, y, z) of the tensor map into dst.
 __device__ __forceinline__ void tma_load_box(void *dst, const void *tmap, int x, int y, int z,

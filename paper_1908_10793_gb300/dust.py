@@ -58,7 +58,7 @@ class dust_options(ctypes.Structure):
                 ("kernel", ctypes.c_int), ("device", ctypes.c_int), ("timing", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("pusher", ctypes.c_int),
                 ("gas_predictor", ctypes.c_int), ("host_io_async", ctypes.c_int),
-                ("test_wait_timeout", ctypes.c_int)]
+                ("test_wait_timeout", ctypes.c_int), ("batch_mode", ctypes.c_int)]
 
 
 class dust_kernel_times(ctypes.Structure):
