@@ -449,8 +449,9 @@ def run_batch(args, D, torch, dev, stream):
     ngr = sum(w.ngrains for w in ws)
     K = max(2, args.batch_steps)
     best, tried = autotune.tune_batch(ws, steps=4, device=dev.index)
-    policy, kint = best
-    ms_best = autotune.time_batch(ws, policy, kint, steps=K, device=dev.index)
+    policy, kint, mode = best
+    Kb = K - K % 2 if mode else K
+    ms_best = autotune.time_batch(ws, policy, kint, steps=Kb, device=dev.index, batch_mode=mode)
     ms_def = autotune.time_batch(ws, None, 1, steps=K, device=dev.index)
     ms_graph = autotune.time_batch(ws, None, 1, steps=K - K % 2, device=dev.index, batch_mode=1)
     cs = []
@@ -477,14 +478,17 @@ def run_batch(args, D, torch, dev, stream):
     finally:
         for c in cs:
             c.close()
-    label = lambda cfg: "%s, sort every %d" % ("default tiles" if cfg[0] is None else  # noqa: E731
-                                             "tile %s" % list(cfg[0]), cfg[1])
+    label = lambda cfg: "%s, sort every %d, %s" % (  # noqa: E731
+        "default tiles" if cfg[0] is None else "tile %s" % list(cfg[0]), cfg[1],
+        "graph of per-instance kernels" if cfg[2] else "one persistent launch")
     return {"value": ngr / (ms_best / 1e3), "unit": UNIT, "ms_per_step": ms_best,
             "config_chosen": label(best), "instances": len(ws), "grains": ngr,
-            "zones": sum(w.ncell for w in ws), "steps": K,
-            "launches_per_call": 1, "path": "one persistent cooperative launch per call",
+            "zones": sum(w.ncell for w in ws), "steps": Kb,
+            "path": "graph of per-instance kernels" if mode else
+                    "one persistent cooperative launch per call",
             "tuner": {label(k): v for k, v in tried.items()},
-            "default_config": {"value": ngr / (ms_def / 1e3), "ms_per_step": ms_def},
+            "default_config": {"value": ngr / (ms_def / 1e3), "ms_per_step": ms_def,
+                               "config": "default tiles, sort every 1, one persistent launch"},
             "graph_of_per_instance_kernels": {"value": ngr / (ms_graph / 1e3),
                                               "ms_per_step": ms_graph},
             "one_at_a_time": {"value": ngr / (ms_s / 1e3), "ms_per_step": ms_s},

@@ -74,14 +74,22 @@ def tune_tile(w, precision=D.DUST_MIXED, steps=4, candidates=None, **kw):
 
 # ---- batches -------------------------------------------------------------
 
-def batch_candidates(ws, sort_intervals=(1, 2)):
+def batch_candidates(ws, sort_intervals=(1, 2), modes=(0, 1)):
     """Configurations of a batch to try: a tile policy (None = the library's
     default for every instance, or one shape applied to every instance,
-    clipped to its grid) and the batch's sort interval.  The default policy
-    with a sort every step comes first."""
+    clipped to its grid), the batch's sort interval, and the execution mode
+    (dust_options.batch_mode: 0 one persistent launch, 1 a graph of
+    per-instance kernels, which sorts every step).  The default
+    configuration comes first."""
     shapes = candidate_tiles(max(ws, key=lambda w: w.ncell))
     policies = [None] + [s for s in shapes if s != shapes[0]]
-    return [(p, k) for k in sort_intervals for p in policies]
+    out = []
+    for m in modes:
+        for k in sort_intervals:
+            if m == 1 and k != 1:
+                continue
+            out += [(p, k, m) for p in policies]
+    return out
 
 
 def _tile_for(w, policy):
@@ -130,13 +138,14 @@ def time_batch(ws, policy=None, sort_interval=1, steps=4, warmup=2, device=0, ba
 
 def tune_batch(ws, steps=4, candidates=None, device=0):
     """Times every candidate configuration in the batch (not instance by
-    instance) and returns (best (policy, sort interval), {config: ms per
-    step}).  Candidates that do not fit are skipped."""
+    instance) and returns (best (policy, sort interval, mode), {config: ms
+    per step}).  Candidates that do not fit are skipped."""
     cands = candidates or batch_candidates(ws)
     times = {}
     for cfg in cands:
         try:
-            times[cfg] = time_batch(ws, cfg[0], cfg[1], steps=steps, device=device)
+            times[cfg] = time_batch(ws, cfg[0], cfg[1], steps=steps - steps % 2 if cfg[2] else steps,
+                                    device=device, batch_mode=cfg[2])
         except D.DustError:
             continue
     best = min(times, key=times.get)

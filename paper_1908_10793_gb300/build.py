@@ -20,6 +20,9 @@ LIB = os.path.join(LIBDIR, "libdust.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
               "-I", INCLUDE, "-I", CSRC] + ARCH
+# per-unit flags: the unit holding both the batched persistent kernels and the
+# step kernels they must agree with rounds every multiply and add on its own
+UNIT_FLAGS = {"dust_slab_batch.cu": ["-fmad=false"]}
 
 
 def _nvcc():
@@ -56,7 +59,8 @@ def build_library(force=False, verbose=False, extra_flags=()):
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nvcc, "-c", src, "-o", obj] + NVCC_FLAGS + list(extra_flags)
+        cmd = [nvcc, "-c", src, "-o", obj] + NVCC_FLAGS + UNIT_FLAGS.get(os.path.basename(src), []) + \
+            list(extra_flags)
         jobs.append(cmd)
 
     def run(cmd):

@@ -1777,6 +1777,9 @@ struct dust_batch {
     int test_timeout = 0;
     BatchInst *h_inst = nullptr, *d_inst = nullptr;
     int *d_pre = nullptr;
+    int *d_order = nullptr;     // tile phase: instances, most grains per tile first
+    int *d_ctr = nullptr;       // tile counters, one per step of the captured launch
+    int ctr_cap = 0;
     unsigned *d_bar = nullptr;
     cudaEvent_t inst_copied = nullptr;
     cudaGraph_t pgraph = nullptr;
@@ -2065,6 +2068,16 @@ int step_persistent(dust_batch *b, const double *dt, int nsteps)
     if (b->inst_copied) BCU(cudaEventSynchronize(b->inst_copied));
     std::vector<int> pre((size_t)BPH_N * (n + 1), 0);
     size_t slab = 0;
+    // the tile phase takes the instances with the most grains per tile
+    // first, so that the phase does not end on a heavy tile
+    std::vector<int> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const dust_ctx *a = b->ctx[x], *c = b->ctx[y];
+        const double ga = (double)a->n_grains / std::max(1, a->g.nt[0] * a->g.nt[1] * a->g.nt[2]);
+        const double gc = (double)c->n_grains / std::max(1, c->g.nt[0] * c->g.nt[1] * c->g.nt[2]);
+        return ga > gc;
+    });
     for (size_t i = 0; i < n; ++i) {
         dust_ctx *c = b->ctx[i];
         b->h_inst[i] = batch_inst_of(c, dt[i], b->test_timeout);
@@ -2079,23 +2092,42 @@ int step_persistent(dust_batch *b, const double *dt, int nsteps)
             (I.ncell + 255) / 256,
             1};
         for (int ph = 0; ph < BPH_N; ++ph) {
+            if (ph == BPH_TILE) continue;
             const int64_t v = pre[(size_t)ph * (n + 1) + i] + items[ph];
             if (v >= ((int64_t)1 << 31)) return bfail(b, DUST_EINVAL, "too many work items");
             pre[(size_t)ph * (n + 1) + i + 1] = (int)v;
         }
     }
+    for (size_t j = 0; j < n; ++j) {
+        const int64_t v = pre[(size_t)BPH_TILE * (n + 1) + j] + b->h_inst[order[j]].ntiles;
+        if (v >= ((int64_t)1 << 31)) return bfail(b, DUST_EINVAL, "too many work items");
+        pre[(size_t)BPH_TILE * (n + 1) + j + 1] = (int)v;
+    }
     // shared memory: the largest tile layout (or the sort's staging), then
     // the block's copy of the step arguments
     const size_t ta_off = (std::max(slab, batch_sort_smem()) + 15) & ~(size_t)15;
-    const size_t smem = ta_off + sizeof(TiledArgs<float>);
+    const size_t smem = ta_off + sizeof(TiledArgs<float>) + 16;  // + the tile counter's broadcast
     if (smem != b->psmem) {
         b->psmem = smem;
         b->pgrid = grid_of(b->pvariant, smem);
         drop_persistent(b);
     }
     if (b->pgrid <= 0) return bfail(b, DUST_ECUDA, "the persistent kernel does not fit on the device");
-    if (!b->d_pre) BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_pre), pre.size() * sizeof(int)));
+    if (!b->d_pre) {
+        BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_pre), pre.size() * sizeof(int)));
+        BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_order), n * sizeof(int)));
+    }
+    if (b->ctr_cap < nsteps) {
+        // the captured graph names the counters: capture again
+        drop_persistent(b);
+        if (b->d_ctr) BCU(cudaFree(b->d_ctr));
+        b->d_ctr = nullptr;
+        b->ctr_cap = 0;
+        BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_ctr), (size_t)nsteps * sizeof(int)));
+        b->ctr_cap = nsteps;
+    }
     BCU(cudaMemcpyAsync(b->d_pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, b->root));
+    BCU(cudaMemcpyAsync(b->d_order, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->root));
     // each instance's time of this call, after its pending work
     for (size_t i = 0; i < n; ++i) {
         dust_ctx *c = b->ctx[i];
@@ -2111,6 +2143,8 @@ int step_persistent(dust_batch *b, const double *dt, int nsteps)
         d.inst = b->d_inst;
         d.ninst = (int)n;
         d.pre = b->d_pre;
+        d.tile_order = b->d_order;
+        d.ctr = b->d_ctr;
         d.bar = b->d_bar;
         d.nsteps = nsteps;
         d.sort_interval = K;
@@ -2123,6 +2157,7 @@ int step_persistent(dust_batch *b, const double *dt, int nsteps)
         if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_inst, b->h_inst, n * sizeof(BatchInst),
                                                   cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, (size_t)nsteps * sizeof(int), cs);
         if (e == cudaSuccess) e = launch_variant(b->pvariant, d, smem, b->pgrid, cs);
         cudaGraph_t g = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(cs, &g);
@@ -2304,6 +2339,8 @@ extern "C" void dust_batch_destroy(dust_batch *b)
     if (b->h_inst) cudaFreeHost(b->h_inst);
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_pre) cudaFree(b->d_pre);
+    if (b->d_order) cudaFree(b->d_order);
+    if (b->d_ctr) cudaFree(b->d_ctr);
     if (b->d_bar) cudaFree(b->d_bar);
     if (b->inst_copied) cudaEventDestroy(b->inst_copied);
     if (b->fork) cudaEventDestroy(b->fork);

@@ -1,6 +1,6 @@
 // Batched step of many independent instances as one persistent launch
-// (instantiated in the geometry units beside the step kernels whose tile
-// function it shares, see SlabShared).
+// (instantiated in dust_slab_batch.cu, beside the step kernels of the same
+// geometries).
 //
 // One cooperative launch (every block resident at once) runs all steps of a
 // dust_batch_step call for all instances of a batch.  Each step is a
@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
     };
     int32_t *ws = reinterpret_cast<int32_t *>(smem_raw);  // scan: 32 words
     TiledArgs<float> *sTA = reinterpret_cast<TiledArgs<float> *>(smem_raw + B.ta_offset);
+    int *s_item = reinterpret_cast<int *>(smem_raw + B.ta_offset + sizeof(TiledArgs<float>));
 
     for (int s = 0; s < B.nsteps && ok; ++s) {
         const bool sorted = (s % K) == 0;
@@ -241,9 +242,17 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
             }
         }
         if (!barrier()) break;
-        // ---- step: the tiles of every instance
-        for (int w = blockIdx.x; w < items_of(B, BPH_TILE); w += nblk) {
-            const int i = item_instance(B, BPH_TILE, w);
+        // ---- step: the tiles of every instance, the heaviest instances'
+        // tiles first, each block taking the next tile from a counter
+        const int ntile_items = items_of(B, BPH_TILE);
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) *s_item = atomicAdd(&B.ctr[s], 1);
+            __syncthreads();
+            const int w = *s_item;
+            if (w >= ntile_items) break;
+            const int j = item_instance(B, BPH_TILE, w);
+            const int i = B.tile_order[j];
             const BatchInst &I = B.inst[i];
             const StepState st = state_of(I, s, K);
             // the step's arguments, with this step's store, permutation and
@@ -273,8 +282,8 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
                 T.count_out = emit ? I.count[st.coff ^ 1] : nullptr;
             }
             __syncthreads();
-            const bool in_time = slab_tile_shared<GEOM, FLAT, MODE>(*sTA, w - item_first(B, BPH_TILE, i),
-                                                                    I.ntiles, smem_raw, true);
+            const bool in_time = slab_tile<GEOM, FLAT, MODE>(*sTA, w - item_first(B, BPH_TILE, j), I.ntiles,
+                                                             smem_raw, true);
             // every thread is done with the arguments before the next copy
             __syncthreads();
             if (!in_time) {

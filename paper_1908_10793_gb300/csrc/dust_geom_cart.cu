@@ -1,5 +1,5 @@
 // Instantiations of the step and sort kernels for one geometry.
-#include "dust_batch.cuh"
+#include "dust_slab.cuh"
 
 namespace dust {
 
@@ -14,7 +14,6 @@ template cudaError_t launch_step_tiled<double, GEOM_CART, 1>(const TiledArgs<dou
 template cudaError_t launch_step_slab<GEOM_CART, 0, 0>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_CART, 0, 1>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_CART, 2, 0>(const TiledArgs<float> &, cudaStream_t);
-template cudaError_t launch_step_slab<GEOM_CART, 2, 1>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_CART>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_CART>(const SortArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_tiled<float, GEOM_CART, 0>(const TiledArgs<float> &, cudaStream_t);
@@ -29,9 +28,5 @@ template cudaError_t launch_predict_gas<double, GEOM_CART, 1>(const StepArgs<dou
 template cudaError_t launch_deposit_mass<GEOM_CART>(const GridDev &, const SpeciesDev &, int, int64_t,
                                                    const double *const[3], const uint8_t *,
                                                    unsigned long long *, unsigned int *, cudaStream_t);
-
-// the batched persistent kernel of this geometry's shared variant
-template int batch_persistent_grid<GEOM_CART, 2, 1>(size_t);
-template cudaError_t launch_batch_persistent<GEOM_CART, 2, 1>(const BatchDev &, size_t, int, cudaStream_t);
 
 }  // namespace dust

@@ -1,5 +1,5 @@
 // Instantiations of the step and sort kernels for one geometry.
-#include "dust_batch.cuh"
+#include "dust_slab.cuh"
 
 namespace dust {
 
@@ -15,7 +15,6 @@ template cudaError_t launch_step_slab<GEOM_SB, 0, 0>(const TiledArgs<float> &, c
 template cudaError_t launch_step_slab<GEOM_SB, 0, 1>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_SB, 0, 2>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_SB, 1, 0>(const TiledArgs<float> &, cudaStream_t);
-template cudaError_t launch_step_slab<GEOM_SB, 1, 1>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_SB, 1, 2>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_SB, 2, 0>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_SB, 2, 1>(const TiledArgs<float> &, cudaStream_t);
@@ -34,9 +33,5 @@ template cudaError_t launch_predict_gas<double, GEOM_SB, 1>(const StepArgs<doubl
 template cudaError_t launch_deposit_mass<GEOM_SB>(const GridDev &, const SpeciesDev &, int, int64_t,
                                                    const double *const[3], const uint8_t *,
                                                    unsigned long long *, unsigned int *, cudaStream_t);
-
-// the batched persistent kernel of this geometry's shared variant
-template int batch_persistent_grid<GEOM_SB, 1, 1>(size_t);
-template cudaError_t launch_batch_persistent<GEOM_SB, 1, 1>(const BatchDev &, size_t, int, cudaStream_t);
 
 }  // namespace dust

@@ -181,17 +181,19 @@ __device__ __forceinline__ void apply_feedback_zone(const GridDev &g, double qua
     const long long d0 = (long long)dep[4 * c + 0], d1 = (long long)dep[4 * c + 1],
                     d2 = (long long)dep[4 * c + 2];
     if ((d0 | d1 | d2) == 0) return;
+    // each product and sum rounded on its own (no fused multiply-add), so
+    // that every kernel that applies the feedback gives the same bits
     if (sizeof(Real) == 4) {
         const float s = (float)quantum /
                         ((float)gas[4 * c] * g.dvol_f[0][i] * g.dvol_f[1][j] * g.dvol_f[2][k]);
-        gas[4 * c + 1] += (Real)((float)d0 * s);
-        gas[4 * c + 2] += (Real)((float)d1 * s);
-        gas[4 * c + 3] += (Real)((float)d2 * s);
+        gas[4 * c + 1] = (Real)__fadd_rn((float)gas[4 * c + 1], __fmul_rn((float)d0, s));
+        gas[4 * c + 2] = (Real)__fadd_rn((float)gas[4 * c + 2], __fmul_rn((float)d1, s));
+        gas[4 * c + 3] = (Real)__fadd_rn((float)gas[4 * c + 3], __fmul_rn((float)d2, s));
     } else {
         const double s = quantum / ((double)gas[4 * c] * g.dvol[0][i] * g.dvol[1][j] * g.dvol[2][k]);
-        gas[4 * c + 1] += (Real)((double)d0 * s);
-        gas[4 * c + 2] += (Real)((double)d1 * s);
-        gas[4 * c + 3] += (Real)((double)d2 * s);
+        gas[4 * c + 1] = (Real)__dadd_rn((double)gas[4 * c + 1], __dmul_rn((double)d0, s));
+        gas[4 * c + 2] = (Real)__dadd_rn((double)gas[4 * c + 2], __dmul_rn((double)d1, s));
+        gas[4 * c + 3] = (Real)__dadd_rn((double)gas[4 * c + 3], __dmul_rn((double)d2, s));
     }
 }
 
@@ -236,6 +238,11 @@ struct BatchDev {
     const BatchInst *inst;
     int ninst;
     const int *pre;              // [BPH_N][ninst + 1]
+    // the tile phase: its prefix sums run over the instances in the order
+    // tile_order (most grains per tile first), and blocks take tiles in
+    // turn from a counter per step (ctr[nsteps], zero at launch)
+    const int *tile_order;
+    int *ctr;
     unsigned *bar;               // grid barrier: arrivals, generation (zero at launch)
     int nsteps;
     int sort_interval;           // steps s with s % sort_interval == 0 sort first

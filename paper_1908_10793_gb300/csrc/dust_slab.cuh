@@ -813,34 +813,12 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     return true;
 }
 
-// Variants that a batch of instances can also run in one persistent launch
-// (dust_batch.cuh): x-z shearing boxes in the orbital-advection frame and
-// x-y Cartesian boxes.  For these, the step kernel and the persistent kernel
-// call one out-of-line copy of the tile function, compiled once in the same
-// translation unit, so that the compiler's contraction of multiplies and
-// adds into fused multiply-adds is the same in both, and a batch gives the
-// results of its instances stepped alone bit for bit.
-template <int GEOM, int FLAT, int MODE>
-struct SlabShared {
-    static constexpr bool value = MODE == 1 && ((GEOM == GEOM_SB && FLAT == 1) || (GEOM == GEOM_CART && FLAT == 2));
-};
-
-template <int GEOM, int FLAT, int MODE>
-__device__ __noinline__ bool slab_tile_shared(const TiledArgs<float> &TA, const int tile, const int ntile,
-                                              unsigned char *smem_raw, const bool reuse)
-{
-    return slab_tile<GEOM, FLAT, MODE>(TA, tile, ntile, smem_raw, reuse);
-}
-
 template <int GEOM, int FLAT, int MODE>
 __global__ void __launch_bounds__(kSlabThreads, 2)
 step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    if constexpr (SlabShared<GEOM, FLAT, MODE>::value)
-        slab_tile_shared<GEOM, FLAT, MODE>(TA, blockIdx.x, gridDim.x, smem_raw, false);
-    else
-        slab_tile<GEOM, FLAT, MODE>(TA, blockIdx.x, gridDim.x, smem_raw, false);
+    slab_tile<GEOM, FLAT, MODE>(TA, blockIdx.x, gridDim.x, smem_raw, false);
 }
 
 inline size_t slab_smem_bytes(const GridDev &g)

@@ -25,3 +25,15 @@ def test_tuning_returns_a_timed_candidate():
     best, times = autotune.tune_tile(w, steps=2)
     assert best in autotune.candidate_tiles(w)
     assert times[best] == min(times.values()) and all(t > 0 for t in times.values())
+
+
+def test_batch_candidates_start_with_the_default_and_cover_modes():
+    from paper_1908_10793_gb300 import autotune
+    ws = [I.si2d_instance(k, "small") for k in range(3)]
+    cands = autotune.batch_candidates(ws)
+    assert cands[0] == (None, 1, 0)
+    assert len(set(cands)) == len(cands)
+    assert {m for _, _, m in cands} == {0, 1}
+    # the graph path sorts every step
+    assert all(k == 1 for _, k, m in cands if m == 1)
+    assert {k for _, k, m in cands if m == 0} == {1, 2}
