@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-disks", action="store_true")
     ap.add_argument("--disk-steps", type=int, default=10)
+    ap.add_argument("--disk-scale", default="full", choices=["full", "mid"],
+                    help="mid: the cylindrical disk at an eighth of its size (profiling runs)")
+    ap.add_argument("--disk-legs", default="cyldisk,sphdisk,cyldisk_gas_predictor,cyldisk_volume_weighting")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--small", action="store_true", help="16^3 grid (profiling runs)")
     ap.add_argument("--grid", type=int, default=0, help="zones per side (profiling runs)")
@@ -558,8 +561,11 @@ def run_disks(args, D, torch, dev, stream):
             ("sphdisk", I.sphdisk, 0, {}, None),
             ("cyldisk_gas_predictor", I.cyldisk, 1, {"gas_predictor": 1}, None),
             ("cyldisk_volume_weighting", I.cyldisk, 1, {}, I.VOLUME))
+    wanted = args.disk_legs.split(",")
     for name, make, feedback, extra, weight in legs:
-        w = make("full")
+        if name not in wanted or (args.disk_scale == "mid" and make is not I.cyldisk):
+            continue
+        w = make(args.disk_scale)
         if weight is not None:
             w.weight = weight
         ctx = D.Context(w, precision=D.DUST_MIXED, stream=stream.cuda_stream, timing=1,

@@ -170,6 +170,9 @@ def cyldisk(scale="full", seed=BASE_SEED + 2):
     r = _rng(seed)
     if scale == "full":
         nR, nphi, nz, ng = 384, 1024, 64, 50_000_000
+    elif scale == "mid":
+        # an eighth of the zones and grains (profiling size, same structure)
+        nR, nphi, nz, ng = 192, 512, 32, 6_250_000
     else:
         nR, nphi, nz, ng = 24, 32, 8, 24_000
     R0, R1, zh = 0.4, 2.5, 0.15
