@@ -1769,22 +1769,23 @@ struct dust_batch {
     std::vector<std::array<int64_t, dust_ctx::N_GROUPS>> period_launches;
     std::string err;
     // one persistent launch for all instances (batch_persistent_kernel):
-    // the instances' descriptors (page-locked host copy, device copy),
-    // the work items' prefix sums, the grid barrier, and a graph of the
-    // call (descriptor copy, barrier reset, the launch) per step count
+    // the instances' descriptors (page-locked host copy, device copy), the
+    // work list, and a graph of the call (descriptor copy, counter reset,
+    // the launch) per work list
     int mode = 0;               // 0: persistent where the instances allow it; 1: graph
     int sort_interval = 1;
     int test_timeout = 0;
     BatchInst *h_inst = nullptr, *d_inst = nullptr;
-    int *d_pre = nullptr;
-    int *d_order = nullptr;     // tile phase: instances, most grains per tile first
-    int *d_ctr = nullptr;       // tile counters, one per step of the captured launch
-    int ctr_cap = 0;
-    unsigned *d_bar = nullptr;
+    // the work list of the captured launch (tasks, groups, item prefix
+    // sums; then the completion counts and the item counter, zeroed by the
+    // graph) and its shape
+    int *d_tab = nullptr;
+    size_t tab_cap = 0;
+    std::vector<int> tab;
+    BatchDev pdev{};
     cudaEvent_t inst_copied = nullptr;
     cudaGraph_t pgraph = nullptr;
     cudaGraphExec_t pexec = nullptr;
-    int pgraph_steps = -1;
     int pvariant = -1;
     size_t psmem = 0;
     int pgrid = 0;
@@ -2045,7 +2046,100 @@ void drop_persistent(dust_batch *b)
     if (b->pgraph) cudaGraphDestroy(b->pgraph);
     b->pexec = nullptr;
     b->pgraph = nullptr;
-    b->pgraph_steps = -1;
+    b->tab.clear();
+}
+
+// Work items of phase p of a step of instance I (sorted: the step sorts
+// first).
+int64_t phase_items(const BatchInst &I, int p, bool sorted)
+{
+    auto items = [](int64_t chunks) { return (chunks + kBatchChunks - 1) / kBatchChunks; };
+    const int64_t nscan = (I.nkeys + 2 + kBatchScanChunk - 1) / kBatchScanChunk;
+    switch (p) {
+    case BPH_SCANA: return sorted ? items(nscan) : 0;
+    case BPH_SCANB: return sorted ? 1 : 0;
+    case BPH_SCANC: return sorted ? items(nscan) : 0;
+    case BPH_SCATTER: return sorted ? items((I.n + kBatchScatterChunk - 1) / kBatchScatterChunk) : 0;
+    case BPH_SEG: return sorted ? items((I.nkeys + 1 + kBatchSegChunk - 1) / kBatchSegChunk) : 0;
+    case BPH_ZERO:
+        return items((std::max(I.ncell * 4, I.nkeys + 2) + kBatchZeroChunk - 1) / kBatchZeroChunk) +
+               (sorted ? kBatchBigItems : 0);
+    case BPH_TILE: return I.ntiles;
+    default: return items((I.ncell + kBatchFbChunk - 1) / kBatchFbChunk);
+    }
+}
+
+// The work list of nsteps steps of the n instances (batch_persistent_kernel):
+// the instances dealt, most grains first, into groups of about equal work;
+// group g's phase p of step s in round s * period + g + p, so that the
+// groups run different phases side by side; inside a round by phase; tasks
+// without items left out, each task depending on its group's previous one.
+// Fills the table and the shape fields of d; false if the items overflow.
+bool work_list(const BatchInst *inst, size_t n, int nsteps, int K, std::vector<int> &tab, BatchDev &d)
+{
+    const int G = (int)std::min<size_t>(n, BPH_N);
+    const int W = std::max(G, (int)BPH_N);
+    std::vector<int> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return inst[x].n > inst[y].n; });
+    std::vector<std::vector<int>> members(G);
+    for (size_t j = 0; j < n; ++j) members[j % G].push_back(order[j]);
+    int gmax = 0;
+    for (auto &m : members) gmax = std::max(gmax, (int)m.size());
+    // prefix sums of the members' items per (sorted, phase, group)
+    std::vector<int64_t> gpre((size_t)2 * BPH_N * G * (gmax + 1), 0);
+    for (int so = 0; so < 2; ++so)
+        for (int p = 0; p < BPH_N; ++p)
+            for (int g = 0; g < G; ++g) {
+                int64_t *q = &gpre[((size_t)(so * BPH_N + p) * G + g) * (gmax + 1)];
+                for (size_t k = 0; k < members[g].size(); ++k)
+                    q[k + 1] = q[k] + phase_items(inst[members[g][k]], p, so != 0);
+                for (int k = (int)members[g].size(); k < gmax; ++k) q[k + 1] = q[k];
+            }
+    struct Slot {
+        int64_t round;
+        int p, s, g;
+    };
+    std::vector<Slot> slots;
+    slots.reserve((size_t)nsteps * G * BPH_N);
+    for (int s = 0; s < nsteps; ++s)
+        for (int g = 0; g < G; ++g)
+            for (int p = 0; p < BPH_N; ++p) slots.push_back({(int64_t)s * W + g + p, p, s, g});
+    std::stable_sort(slots.begin(), slots.end(), [](const Slot &x, const Slot &y) {
+        return x.round != y.round ? x.round < y.round : x.p < y.p;
+    });
+    std::vector<BatchTask> tasks;
+    std::vector<int> last(G, -1);
+    int64_t begin = 0;
+    for (const Slot &sl : slots) {
+        const int so = (sl.s % K) == 0 ? 1 : 0;
+        const int64_t items = gpre[((size_t)(so * BPH_N + sl.p) * G + sl.g) * (gmax + 1) + members[sl.g].size()];
+        if (items == 0) continue;
+        if (begin + items >= ((int64_t)1 << 31)) return false;
+        tasks.push_back({sl.s, sl.g, sl.p, (int)begin, (int)items, last[sl.g]});
+        last[sl.g] = (int)tasks.size() - 1;
+        begin += items;
+    }
+    static_assert(sizeof(BatchTask) == 6 * sizeof(int), "task layout");
+    d.off_tasks = 0;
+    d.off_members = (int)(tasks.size() * 6);
+    d.off_gcount = d.off_members + G * gmax;
+    d.off_gpre = d.off_gcount + G;
+    d.nstatic = d.off_gpre + (int)gpre.size();
+    tab.assign((size_t)d.nstatic, 0);
+    std::memcpy(tab.data(), tasks.data(), tasks.size() * sizeof(BatchTask));
+    for (int g = 0; g < G; ++g) {
+        for (size_t k = 0; k < members[g].size(); ++k) tab[d.off_members + g * gmax + k] = members[g][k];
+        tab[d.off_gcount + g] = (int)members[g].size();
+    }
+    for (size_t k = 0; k < gpre.size(); ++k) tab[d.off_gpre + k] = (int)gpre[k];
+    d.ntasks = (int)tasks.size();
+    d.nitems = (int)begin;
+    d.ngroups = G;
+    d.gmax = gmax;
+    d.nsteps = nsteps;
+    d.sort_interval = K;
+    return true;
 }
 
 // nsteps steps of every instance as one persistent launch (see
@@ -2064,70 +2158,27 @@ int step_persistent(dust_batch *b, const double *dt, int nsteps)
         }
         if (c->perm_pending) return bfail(b, DUST_ESTATE, "context %zu: a sort is pending", i);
     }
-    // descriptors and work items
+    // descriptors and work list
     if (b->inst_copied) BCU(cudaEventSynchronize(b->inst_copied));
-    std::vector<int> pre((size_t)BPH_N * (n + 1), 0);
     size_t slab = 0;
-    // the tile phase takes the instances with the most grains per tile
-    // first, so that the phase does not end on a heavy tile
-    std::vector<int> order(n);
-    for (size_t i = 0; i < n; ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        const dust_ctx *a = b->ctx[x], *c = b->ctx[y];
-        const double ga = (double)a->n_grains / std::max(1, a->g.nt[0] * a->g.nt[1] * a->g.nt[2]);
-        const double gc = (double)c->n_grains / std::max(1, c->g.nt[0] * c->g.nt[1] * c->g.nt[2]);
-        return ga > gc;
-    });
     for (size_t i = 0; i < n; ++i) {
         dust_ctx *c = b->ctx[i];
         b->h_inst[i] = batch_inst_of(c, dt[i], b->test_timeout);
         slab = std::max(slab, batch_tile_smem(c->g));
-        const BatchInst &I = b->h_inst[i];
-        const int64_t items[BPH_N] = {
-            (I.nkeys + 2 + kBatchScanChunk - 1) / kBatchScanChunk,
-            (I.n + kBatchScatterChunk - 1) / kBatchScatterChunk,
-            (I.nkeys + 1 + 255) / 256,
-            (std::max(I.ncell * 4, I.nkeys + 2) + kBatchZeroChunk - 1) / kBatchZeroChunk,
-            I.ntiles,
-            (I.ncell + 255) / 256,
-            1};
-        for (int ph = 0; ph < BPH_N; ++ph) {
-            if (ph == BPH_TILE) continue;
-            const int64_t v = pre[(size_t)ph * (n + 1) + i] + items[ph];
-            if (v >= ((int64_t)1 << 31)) return bfail(b, DUST_EINVAL, "too many work items");
-            pre[(size_t)ph * (n + 1) + i + 1] = (int)v;
-        }
     }
-    for (size_t j = 0; j < n; ++j) {
-        const int64_t v = pre[(size_t)BPH_TILE * (n + 1) + j] + b->h_inst[order[j]].ntiles;
-        if (v >= ((int64_t)1 << 31)) return bfail(b, DUST_EINVAL, "too many work items");
-        pre[(size_t)BPH_TILE * (n + 1) + j + 1] = (int)v;
-    }
+    std::vector<int> tab;
+    BatchDev d{};
+    if (!work_list(b->h_inst, n, nsteps, K, tab, d)) return bfail(b, DUST_EINVAL, "too many work items");
     // shared memory: the largest tile layout (or the sort's staging), then
     // the block's copy of the step arguments
     const size_t ta_off = (std::max(slab, batch_sort_smem()) + 15) & ~(size_t)15;
-    const size_t smem = ta_off + sizeof(TiledArgs<float>) + 16;  // + the tile counter's broadcast
+    const size_t smem = ta_off + sizeof(TiledArgs<float>) + 16;  // + the item counter's broadcast
     if (smem != b->psmem) {
         b->psmem = smem;
         b->pgrid = grid_of(b->pvariant, smem);
         drop_persistent(b);
     }
-    if (b->pgrid <= 0) return bfail(b, DUST_ECUDA, "the persistent kernel does not fit on the device");
-    if (!b->d_pre) {
-        BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_pre), pre.size() * sizeof(int)));
-        BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_order), n * sizeof(int)));
-    }
-    if (b->ctr_cap < nsteps) {
-        // the captured graph names the counters: capture again
-        drop_persistent(b);
-        if (b->d_ctr) BCU(cudaFree(b->d_ctr));
-        b->d_ctr = nullptr;
-        b->ctr_cap = 0;
-        BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_ctr), (size_t)nsteps * sizeof(int)));
-        b->ctr_cap = nsteps;
-    }
-    BCU(cudaMemcpyAsync(b->d_pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, b->root));
-    BCU(cudaMemcpyAsync(b->d_order, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->root));
+    if (b->pgrid <= 0) return bfail(b, DUST_EINVAL, "the persistent kernel does not fit on the device");
     // each instance's time of this call, after its pending work
     for (size_t i = 0; i < n; ++i) {
         dust_ctx *c = b->ctx[i];
@@ -2137,27 +2188,36 @@ int step_persistent(dust_batch *b, const double *dt, int nsteps)
         BCU(cudaEventRecord(b->join[i], c->stream));
         BCU(cudaStreamWaitEvent(b->root, b->join[i], 0));
     }
-    if (b->pgraph_steps != nsteps || !b->pexec) {
+    if (!b->pexec || tab != b->tab || d.nsteps != b->pdev.nsteps || d.sort_interval != b->pdev.sort_interval) {
+        // a new work list: its static part copied once, a new graph
         drop_persistent(b);
-        BatchDev d{};
+        const size_t nstatic = (size_t)d.nstatic, ntotal = tab.size() + (size_t)d.ntasks + 1;
+        if (ntotal > b->tab_cap) {
+            if (b->d_tab) BCU(cudaFree(b->d_tab));
+            b->d_tab = nullptr;
+            b->tab_cap = 0;
+            BCU(cudaMalloc(reinterpret_cast<void **>(&b->d_tab), ntotal * sizeof(int)));
+            b->tab_cap = ntotal;
+        }
+        BCU(cudaMemcpyAsync(b->d_tab, tab.data(), nstatic * sizeof(int), cudaMemcpyHostToDevice, b->root));
+        BCU(cudaStreamSynchronize(b->root));
         d.inst = b->d_inst;
         d.ninst = (int)n;
-        d.pre = b->d_pre;
-        d.tile_order = b->d_order;
-        d.ctr = b->d_ctr;
-        d.bar = b->d_bar;
-        d.nsteps = nsteps;
-        d.sort_interval = K;
-        d.bar_extra = b->test_timeout ? 1 : 0;
-        d.wait_ns = b->test_timeout ? 1000000ull : 1000000000ull;
+        d.tasks = reinterpret_cast<const BatchTask *>(b->d_tab + d.off_tasks);
+        d.members = b->d_tab + d.off_members;
+        d.gcount = b->d_tab + d.off_gcount;
+        d.gpre = b->d_tab + d.off_gpre;
+        d.done = b->d_tab + nstatic;
+        d.grab = d.done + d.ntasks;
+        d.wait_extra = b->test_timeout ? 1 : 0;
+        d.wait_ns = b->test_timeout ? 1000000ull : 4000000000ull;
         d.ta_offset = ta_off;
         cudaStream_t cs = nullptr;
         BCU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_inst, b->h_inst, n * sizeof(BatchInst),
                                                   cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, (size_t)nsteps * sizeof(int), cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.done, 0, ((size_t)d.ntasks + 1) * sizeof(int), cs);
         if (e == cudaSuccess) e = launch_variant(b->pvariant, d, smem, b->pgrid, cs);
         cudaGraph_t g = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(cs, &g);
@@ -2169,7 +2229,8 @@ int step_persistent(dust_batch *b, const double *dt, int nsteps)
         }
         b->pgraph = g;
         BCU(cudaGraphInstantiate(&b->pexec, g, 0));
-        b->pgraph_steps = nsteps;
+        b->tab.swap(tab);
+        b->pdev = d;
     }
     BCU(cudaGraphLaunch(b->pexec, b->root));
     BCU(cudaEventRecord(b->inst_copied, b->root));
@@ -2250,7 +2311,6 @@ extern "C" int dust_batch_create(dust_batch **out, dust_ctx *const *insts, int n
     if (b->pvariant >= 0) {
         if (cudaMallocHost(reinterpret_cast<void **>(&b->h_inst), n * sizeof(BatchInst)) != cudaSuccess ||
             cudaMalloc(reinterpret_cast<void **>(&b->d_inst), n * sizeof(BatchInst)) != cudaSuccess ||
-            cudaMalloc(reinterpret_cast<void **>(&b->d_bar), 2 * sizeof(unsigned)) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->inst_copied, cudaEventDisableTiming) != cudaSuccess)
             return bail("allocation for the persistent launch failed");
     }
@@ -2338,10 +2398,7 @@ extern "C" void dust_batch_destroy(dust_batch *b)
     drop_persistent(b);
     if (b->h_inst) cudaFreeHost(b->h_inst);
     if (b->d_inst) cudaFree(b->d_inst);
-    if (b->d_pre) cudaFree(b->d_pre);
-    if (b->d_order) cudaFree(b->d_order);
-    if (b->d_ctr) cudaFree(b->d_ctr);
-    if (b->d_bar) cudaFree(b->d_bar);
+    if (b->d_tab) cudaFree(b->d_tab);
     if (b->inst_copied) cudaEventDestroy(b->inst_copied);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->done) cudaEventDestroy(b->done);

@@ -3,15 +3,12 @@
 // geometries).
 //
 // One cooperative launch (every block resident at once) runs all steps of a
-// dust_batch_step call for all instances of a batch.  Each step is a
-// sequence of phases; a phase is a list of work items over the instances
-// (a chunk of one instance's key counts, grains, keys or zones, or one of its
-// tiles) that the blocks take in turn, and a grid barrier separates the
-// phases:
+// dust_batch_step call for all instances of a batch.  The instances are
+// dealt into groups; one step of a group is a chain of phases:
 //
 //   sort (steps s with s % sort_interval == 0):
 //     scan A   chunk sums of the key counts the previous step predicted
-//     scan B   exclusive scan of the chunk sums, one block per instance
+//     scan B   exclusive scan of the chunk sums, one item per instance
 //     scan C   offsets inside each chunk, copied to the scatter's cursors
 //     scatter  (id, source) pairs to their key segments
 //     segments id sort inside each key (warp-staged)
@@ -21,12 +18,21 @@
 //              next keys, and the sort's gather through the permutation)
 //   feedback   the deposit applied to the gas; time advanced
 //
-// Every phase runs the same device functions as the per-context kernels, on
+// A task is one phase of one step of one group, cut into work items (chunks
+// of the per-context kernels' blocks, or tiles).  The host lays the tasks out
+// in rounds, group g's phase p of step s in round s * period + g + p, so that
+// at any time the groups are in different phases (the sort of one group runs
+// beside the tiles of others), and the blocks take work items in that order
+// from one counter.  A task waits, bounded in time, until the group's
+// previous task has counted all its items done; since items are taken in
+// order and every task waits only for earlier ones, the wait always ends
+// unless a block stopped.  When a wait runs out the kernel raises
+// DUST_FLAG_TIMEOUT in every instance's status words and returns.
+//
+// Every item runs the same device functions as the per-context kernels, on
 // the same buffers, in the same order per instance, so a batch gives the
 // grains, gas and deposit of its instances stepped one at a time, bit for
-// bit.  The grid barrier waits a bounded time (wait_ns); when it runs out the
-// kernel raises DUST_FLAG_TIMEOUT in every instance's status words and
-// returns.
+// bit.
 #pragma once
 
 #include <algorithm>
@@ -35,6 +41,10 @@
 #include "dust_sort.cuh"
 
 namespace dust {
+
+static_assert(kBatchSegChunk == kSegThreads && kBatchScanChunk == kSlabThreads * kScanItems &&
+                  kBatchFbChunk == kSlabThreads,
+              "batch chunks are the per-context kernels' blocks");
 
 namespace {
 
@@ -49,27 +59,18 @@ struct BatchSort {
     int64_t nkeys1;
 };
 
-// Grid barrier over all blocks of the launch, bounded in time.  Thread 0 of
-// each block arrives; the last arrival resets the count and bumps the
-// generation, the others wait for the generation to change.  Returns false
-// (in every thread) when the wait ran out.
-__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned long long limit_ns)
+// Thread 0 waits until *count reaches target, at most limit_ns; the result
+// is broadcast to the block.  Writes that the counted items made before
+// signalling (generic proxy) are then visible to this block's bulk tensor
+// copies (async proxy).
+__device__ bool wait_count(const int *count, int target, unsigned long long limit_ns)
 {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        const volatile int *c = count;
+        if (*c < target) {
             const unsigned long long t0 = global_ns();
-            while (*gen == g0) {
+            while (*c < target) {
                 if (global_ns() - t0 > limit_ns) {
                     ok = 0;
                     break;
@@ -80,33 +81,31 @@ __device__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned long long
         __threadfence();
     }
     ok = __syncthreads_and(ok);
-    // writes of the previous phase (generic proxy) become visible to the
-    // next phase's bulk tensor copies (async proxy)
     asm volatile("fence.proxy.async.global;" ::: "memory");
     return ok != 0;
 }
 
-// Instance of work item w of phase ph (binary search of the prefix sums).
-__device__ __forceinline__ int item_instance(const BatchDev &B, int ph, int w)
+// After a work item: every thread's writes, then one count.
+__device__ __forceinline__ void signal_done(int *count)
 {
-    const int *pre = B.pre + (size_t)ph * (B.ninst + 1);
-    int lo = 0, hi = B.ninst;  // pre[lo] <= w < pre[hi]
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1);
+    }
+}
+
+// Task of work item w (largest t with tasks[t].begin <= w).
+__device__ __forceinline__ int task_of(const BatchDev &B, int w)
+{
+    int lo = 0, hi = B.ntasks;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (pre[mid] <= w) lo = mid;
+        if (B.tasks[mid].begin <= w) lo = mid;
         else hi = mid;
     }
     return lo;
-}
-
-__device__ __forceinline__ int items_of(const BatchDev &B, int ph)
-{
-    return B.pre[(size_t)ph * (B.ninst + 1) + B.ninst];
-}
-
-__device__ __forceinline__ int item_first(const BatchDev &B, int ph, int i)
-{
-    return B.pre[(size_t)ph * (B.ninst + 1) + i];
 }
 
 // Per-instance state of step s: which store is current, which count buffer
@@ -154,107 +153,89 @@ template <int GEOM, int FLAT, int MODE>
 __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const BatchDev B)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const unsigned nblk = gridDim.x;
-    const unsigned long long lim = B.wait_ns;
     const int K = B.sort_interval;
-    unsigned *bar = B.bar;
-    bool ok = true;
-    auto barrier = [&]() {
-        if (ok) ok = grid_barrier(bar, nblk + (unsigned)B.bar_extra, lim);
-        return ok;
-    };
     int32_t *ws = reinterpret_cast<int32_t *>(smem_raw);  // scan: 32 words
     TiledArgs<float> *sTA = reinterpret_cast<TiledArgs<float> *>(smem_raw + B.ta_offset);
     int *s_item = reinterpret_cast<int *>(smem_raw + B.ta_offset + sizeof(TiledArgs<float>));
+    bool ok = true;
 
-    for (int s = 0; s < B.nsteps && ok; ++s) {
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) *s_item = atomicAdd(B.grab, 1);
+        __syncthreads();
+        const int w = *s_item;
+        if (w >= B.nitems) break;
+        const int t = task_of(B, w);
+        const BatchTask T = B.tasks[t];
+        // the group's previous task must be complete
+        if (T.dep >= 0 && !wait_count(B.done + T.dep, B.tasks[T.dep].items + B.wait_extra, B.wait_ns)) {
+            ok = false;
+            break;
+        }
+        const int s = T.s, p = T.p;
         const bool sorted = (s % K) == 0;
         const bool emit = ((s + 1) % K) == 0;
-        if (sorted) {
-            // ---- scan A: chunk sums of the counts
-            for (int w = blockIdx.x; w < items_of(B, BPH_SCAN); w += nblk) {
-                const int i = item_instance(B, BPH_SCAN, w);
-                const BatchInst &I = B.inst[i];
-                const StepState st = state_of(I, s, K);
-                scan_reduce_block(I.count[st.coff], I.nkeys + 2, I.blocksums, w - item_first(B, BPH_SCAN, i),
-                                  ws);
+        // the instance of the group and its item
+        const int l = w - T.begin;
+        const int *pre = B.gpre + ((size_t)((sorted ? 1 : 0) * BPH_N + p) * B.ngroups + T.g) * (B.gmax + 1);
+        int lo = 0, hi = B.gcount[T.g];  // pre[lo] <= l < pre[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pre[mid] <= l) lo = mid;
+            else hi = mid;
+        }
+        const int i = B.members[T.g * B.gmax + lo];
+        const int li = l - pre[lo];
+        const BatchInst &I = B.inst[i];
+        const StepState st = state_of(I, s, K);
+        const int64_t c0 = (int64_t)li * kBatchChunks;  // first chunk of a chunked item
+
+        if (p == BPH_SCANA) {
+            const int64_t nscan = (I.nkeys + 2 + kBatchScanChunk - 1) / kBatchScanChunk;
+            for (int64_t c = c0; c < min(c0 + kBatchChunks, nscan); ++c) {
+                scan_reduce_block(I.count[st.coff], I.nkeys + 2, I.blocksums, c, ws);
                 __syncthreads();
             }
-            if (!barrier()) break;
-            // ---- scan B: the chunk sums of each instance
-            for (int w = blockIdx.x; w < items_of(B, BPH_INST); w += nblk) {
-                const BatchInst &I = B.inst[w];
-                scan_sums_block(I.blocksums, (I.nkeys + 2 + kBatchScanChunk - 1) / kBatchScanChunk, ws);
-                __syncthreads();
-            }
-            if (!barrier()) break;
-            // ---- scan C: offsets and cursors; the block sort's list emptied
-            for (int w = blockIdx.x; w < items_of(B, BPH_SCAN); w += nblk) {
-                const int i = item_instance(B, BPH_SCAN, w);
-                const BatchInst &I = B.inst[i];
-                const StepState st = state_of(I, s, K);
-                const int c = w - item_first(B, BPH_SCAN, i);
+        } else if (p == BPH_SCANB) {
+            scan_sums_block(I.blocksums, (I.nkeys + 2 + kBatchScanChunk - 1) / kBatchScanChunk, ws);
+        } else if (p == BPH_SCANC) {
+            // offsets and cursors; the block sort's list emptied
+            const int64_t nscan = (I.nkeys + 2 + kBatchScanChunk - 1) / kBatchScanChunk;
+            for (int64_t c = c0; c < min(c0 + kBatchChunks, nscan); ++c) {
                 scan_apply_block(I.count[st.coff], I.nkeys + 2, I.blocksums, c, ws, I.cursor);
-                if (c == 0 && threadIdx.x == 0) I.bigseg[0] = 0;
                 __syncthreads();
             }
-            if (!barrier()) break;
-            // ---- scatter of (id, source) pairs
-            for (int w = blockIdx.x; w < items_of(B, BPH_SCATTER); w += nblk) {
-                const int i = item_instance(B, BPH_SCATTER, w);
-                const BatchInst &I = B.inst[i];
-                const BatchSort a = sort_of(I, state_of(I, s, K));
-                scatter_pairs_block(a, w - item_first(B, BPH_SCATTER, i));
-            }
-            if (!barrier()) break;
-            // ---- id sort inside each key
-            for (int w = blockIdx.x; w < items_of(B, BPH_SEG); w += nblk) {
-                const int i = item_instance(B, BPH_SEG, w);
-                const BatchInst &I = B.inst[i];
-                const BatchSort a = sort_of(I, state_of(I, s, K));
-                segments_block(a, w - item_first(B, BPH_SEG, i),
-                               reinterpret_cast<int32_t(*)[kSegStage]>(smem_raw),
+            if (li == 0 && threadIdx.x == 0) I.bigseg[0] = 0;
+        } else if (p == BPH_SCATTER) {
+            const BatchSort a = sort_of(I, st);
+            const int64_t nc = (I.n + kBatchScatterChunk - 1) / kBatchScatterChunk;
+            for (int64_t c = c0; c < min(c0 + kBatchChunks, nc); ++c) scatter_pairs_block(a, c);
+        } else if (p == BPH_SEG) {
+            const BatchSort a = sort_of(I, st);
+            const int64_t nc = (I.nkeys + 1 + kBatchSegChunk - 1) / kBatchSegChunk;
+            for (int64_t c = c0; c < min(c0 + kBatchChunks, nc); ++c) {
+                segments_block(a, c, reinterpret_cast<int32_t(*)[kSegStage]>(smem_raw),
                                reinterpret_cast<int32_t(*)[kSegStage]>(smem_raw + kSegThreads / 32 * kSegStage * 4));
                 __syncwarp();
             }
-            if (!barrier()) break;
-        }
-        // ---- zero the deposit and the next sort's counts; long segments
-        for (int w = blockIdx.x; w < items_of(B, BPH_ZERO); w += nblk) {
-            const int i = item_instance(B, BPH_ZERO, w);
-            const BatchInst &I = B.inst[i];
-            const StepState st = state_of(I, s, K);
-            const int64_t c = w - item_first(B, BPH_ZERO, i);
+        } else if (p == BPH_ZERO) {
+            // the deposit and the next sort's counts zeroed; then (sorted
+            // steps) the block sort of long segments
             const int64_t ndep = I.ncell * 4, ncnt = I.nkeys + 2;
-            for (int64_t k = c * kBatchZeroChunk + threadIdx.x; k < (c + 1) * kBatchZeroChunk; k += blockDim.x) {
-                if (k < ndep) I.ta.s.dep[k] = 0ull;
-                if (emit && k < ncnt) I.count[st.coff ^ 1][k] = 0;
-            }
-        }
-        if (sorted) {
-            for (int w = blockIdx.x; w < B.ninst * kBatchBigItems; w += nblk) {
-                const int i = w / kBatchBigItems;
-                const BatchInst &I = B.inst[i];
-                const BatchSort a = sort_of(I, state_of(I, s, K));
-                big_segments_block(a, w % kBatchBigItems, kBatchBigItems, reinterpret_cast<int32_t *>(smem_raw),
+            const int64_t nz = (max(ndep, ncnt) + kBatchZeroChunk - 1) / kBatchZeroChunk;
+            const int64_t nzi = (nz + kBatchChunks - 1) / kBatchChunks;
+            if (li < nzi) {
+                const int64_t k1 = min((c0 + kBatchChunks) * kBatchZeroChunk, max(ndep, ncnt));
+                for (int64_t k = c0 * kBatchZeroChunk + threadIdx.x; k < k1; k += blockDim.x) {
+                    if (k < ndep) I.ta.s.dep[k] = 0ull;
+                    if (emit && k < ncnt) I.count[st.coff ^ 1][k] = 0;
+                }
+            } else {
+                const BatchSort a = sort_of(I, st);
+                big_segments_block(a, (int32_t)(li - nzi), kBatchBigItems, reinterpret_cast<int32_t *>(smem_raw),
                                    reinterpret_cast<int32_t *>(smem_raw + kBigChunk * 4));
-                __syncthreads();
             }
-        }
-        if (!barrier()) break;
-        // ---- step: the tiles of every instance, the heaviest instances'
-        // tiles first, each block taking the next tile from a counter
-        const int ntile_items = items_of(B, BPH_TILE);
-        for (;;) {
-            __syncthreads();
-            if (threadIdx.x == 0) *s_item = atomicAdd(&B.ctr[s], 1);
-            __syncthreads();
-            const int w = *s_item;
-            if (w >= ntile_items) break;
-            const int j = item_instance(B, BPH_TILE, w);
-            const int i = B.tile_order[j];
-            const BatchInst &I = B.inst[i];
-            const StepState st = state_of(I, s, K);
+        } else if (p == BPH_TILE) {
             // the step's arguments, with this step's store, permutation and
             // count fields, in shared memory
             {
@@ -264,49 +245,44 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
             }
             __syncthreads();
             if (threadIdx.x == 0) {
-                TiledArgs<float> &T = *sTA;
+                TiledArgs<float> &A = *sTA;
                 if (sorted) {
-                    T.s.s = I.store[st.cur ^ 1];   // read through the permutation
-                    T.dst = I.store[st.cur];
-                    T.perm = I.pair_src;
-                    T.perm_id = I.pair_id;
+                    A.s.s = I.store[st.cur ^ 1];   // read through the permutation
+                    A.dst = I.store[st.cur];
+                    A.perm = I.pair_src;
+                    A.perm_id = I.pair_id;
                 } else {
-                    T.s.s = I.store[st.cur];
-                    T.dst = I.store[st.cur];
-                    T.perm = nullptr;
-                    T.perm_id = nullptr;
+                    A.s.s = I.store[st.cur];
+                    A.dst = I.store[st.cur];
+                    A.perm = nullptr;
+                    A.perm_id = nullptr;
                 }
-                T.key_off = I.count[st.coff];
-                T.emit_keys = emit ? 1 : 0;
-                T.key_out = emit ? I.key : nullptr;
-                T.count_out = emit ? I.count[st.coff ^ 1] : nullptr;
+                A.key_off = I.count[st.coff];
+                A.emit_keys = emit ? 1 : 0;
+                A.key_out = emit ? I.key : nullptr;
+                A.count_out = emit ? I.count[st.coff ^ 1] : nullptr;
             }
             __syncthreads();
-            const bool in_time = slab_tile<GEOM, FLAT, MODE>(*sTA, w - item_first(B, BPH_TILE, j), I.ntiles,
-                                                             smem_raw, true);
-            // every thread is done with the arguments before the next copy
-            __syncthreads();
+            const bool in_time = slab_tile<GEOM, FLAT, MODE>(*sTA, li, I.ntiles, smem_raw, true);
             if (!in_time) {
-                // the gas box did not arrive in time: stop this block (the
-                // others run out at the next barrier)
+                // the gas box did not arrive in time: stop this block; tasks
+                // that wait for this one run out of time too
                 ok = false;
                 break;
             }
-        }
-        if (!barrier()) break;
-        // ---- feedback on the gas, and the time of the next step
-        for (int w = blockIdx.x; w < items_of(B, BPH_FB); w += nblk) {
-            const int i = item_instance(B, BPH_FB, w);
-            const BatchInst &I = B.inst[i];
-            const int c0 = w - item_first(B, BPH_FB, i);
+        } else {
+            // feedback on the gas, and the time of the next step
             if (I.feedback) {
-                const int64_t c = (int64_t)c0 * blockDim.x + threadIdx.x;
-                if (c < I.ncell) apply_feedback_zone<float>(I.ta.s.g, I.quantum, const_cast<float *>(I.ta.s.gas),
-                                                            I.ta.s.dep, c);
+                const int64_t nc = (I.ncell + kBatchFbChunk - 1) / kBatchFbChunk;
+                for (int64_t c = c0; c < min(c0 + kBatchChunks, nc); ++c) {
+                    const int64_t z = c * kBatchFbChunk + threadIdx.x;
+                    if (z < I.ncell)
+                        apply_feedback_zone<float>(I.ta.s.g, I.quantum, const_cast<float *>(I.ta.s.gas), I.ta.s.dep, z);
+                }
             }
-            if (c0 == 0 && threadIdx.x == 0) advance_time(I.time, I.dt, I.q_om_lx, I.ly, I.sb);
+            if (li == 0 && threadIdx.x == 0) advance_time(I.time, I.dt, I.q_om_lx, I.ly, I.sb);
         }
-        if (!barrier()) break;
+        signal_done(B.done + t);
     }
     if (!ok && threadIdx.x == 0)
         for (int i = 0; i < B.ninst; ++i) atomicOr(&B.inst[i].ta.s.status[ST_FLAGS], DUST_FLAG_TIMEOUT);

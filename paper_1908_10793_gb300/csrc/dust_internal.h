@@ -230,31 +230,51 @@ struct BatchInst {
     int64_t n, nkeys, ncell;
 };
 
-// Work items of one phase, over the instances: item w belongs to instance
-// i with pre[i] <= w < pre[i + 1].
-enum { BPH_SCAN = 0, BPH_SCATTER, BPH_SEG, BPH_ZERO, BPH_TILE, BPH_FB, BPH_INST, BPH_N };
+// Phases of one step of one instance in the persistent kernel.
+enum { BPH_SCANA = 0, BPH_SCANB, BPH_SCANC, BPH_SCATTER, BPH_SEG, BPH_ZERO, BPH_TILE, BPH_FB, BPH_N };
+
+// One task of the persistent kernel's work list: phase p of step s for the
+// instances of group g, as `items` consecutive work items from `begin`.  It
+// starts once task `dep` (the group's previous task with items, or -1) has
+// completed all its items.
+struct BatchTask {
+    int s, g, p;
+    int begin, items;
+    int dep;
+};
 
 struct BatchDev {
     const BatchInst *inst;
     int ninst;
-    const int *pre;              // [BPH_N][ninst + 1]
-    // the tile phase: its prefix sums run over the instances in the order
-    // tile_order (most grains per tile first), and blocks take tiles in
-    // turn from a counter per step (ctr[nsteps], zero at launch)
-    const int *tile_order;
-    int *ctr;
-    unsigned *bar;               // grid barrier: arrivals, generation (zero at launch)
+    // the work list: tasks in round order (a group's phase p of step s in
+    // round s * period + g + p; inside a round by phase), nitems work items
+    // in all, taken by the blocks in turn from *grab
+    const BatchTask *tasks;
+    int ntasks, nitems;
+    int *grab;                   // zero at launch
+    int *done;                   // [ntasks] items completed, zero at launch
+    // instances of group g: members[g * gmax + k], k < gcount[g]; their work
+    // items per phase: prefix sums gpre[((sorted * BPH_N + p) * ngroups + g) * (gmax + 1) + k]
+    const int *members, *gcount, *gpre;
+    int ngroups, gmax;
     int nsteps;
     int sort_interval;           // steps s with s % sort_interval == 0 sort first
-    int bar_extra;               // > 0 only to test the barrier's timeout
-    unsigned long long wait_ns;  // limit of one barrier wait
+    int wait_extra;              // > 0 only to test the bounded wait
+    unsigned long long wait_ns;  // limit of one wait for a task
     size_t ta_offset;            // where the block's copy of the step arguments sits in shared memory
+    // the host's layout of the work list in one int table: tasks, members,
+    // gcount, gpre (nstatic ints), then done and grab
+    int off_tasks, off_members, off_gcount, off_gpre, nstatic;
 };
 
-// Work items per phase of one instance (the batched kernel's decomposition).
+// Work items per phase of one instance: chunks of the per-context kernels'
+// blocks, kBatchChunks of them per item.
 constexpr int kBatchScanChunk = 256 * 4;     // counts per scan chunk (256 threads x 4)
-constexpr int kBatchScatterChunk = 256 * 4;  // grains per scatter item
-constexpr int kBatchZeroChunk = 256 * 8;     // 8-byte words zeroed per item
+constexpr int kBatchScatterChunk = 256 * 4;  // grains per scatter chunk
+constexpr int kBatchSegChunk = 256;          // keys per segment-sort chunk
+constexpr int kBatchZeroChunk = 256 * 8;     // 8-byte words zeroed per chunk
+constexpr int kBatchFbChunk = 256;           // zones per feedback chunk
+constexpr int kBatchChunks = 8;              // chunks per work item
 constexpr int kBatchBigItems = 8;            // items of the block sort per instance
 
 template <int GEOM, int FLAT, int MODE>

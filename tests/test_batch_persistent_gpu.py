@@ -1,14 +1,14 @@
 """Batched stepping as one persistent launch: a batch of streaming-instability
 boxes (2-D x-z shearing boxes in the orbital-advection frame, mixed
 precision) runs each dust_batch_step call as a single cooperative kernel
-that walks every instance's sort, step and feedback work items, with grid
-barriers between the phases.  The grains, gas, deposit and counters must
-equal, bit for bit, those of the same contexts stepped one at a time with
-dust_step, across calls with even and odd step counts, a new step length,
-eager steps in between, and a sort every second step.  The barriers' bounded
-wait is checked without a GPU fault: a testing option makes every barrier
-expect one block more than the launch has, the wait runs out, and every
-instance reports DUST_ETIMEOUT."""
+that takes every instance's sort, step and feedback work items from one
+work list, each task waiting for its group's previous task to complete.
+The grains, gas, deposit and counters must equal, bit for bit, those of the
+same contexts stepped one at a time with dust_step, across calls with even
+and odd step counts, a new step length, eager steps in between, and a sort
+every second step.  The tasks' bounded wait is checked without a GPU fault:
+a testing option makes every wait expect one item more than its task has,
+the wait runs out, and every instance reports DUST_ETIMEOUT."""
 import numpy as np
 import pytest
 
@@ -70,7 +70,7 @@ def test_persistent_batch_equals_one_context_at_a_time(sort_interval):
             c.close()
 
 
-def test_persistent_batch_barrier_wait_runs_out_and_is_reported():
+def test_persistent_batch_task_wait_runs_out_and_is_reported():
     from paper_1908_10793_gb300 import dust as D
     ws = _instances()[:4]
     bat = [_make(D, w) for w in ws]
