@@ -92,6 +92,13 @@ __device__ __forceinline__ void deposit_fixed_rolled(const GridDev &g, unsigned 
         if (rest[c] != 0) atomicAdd(&dep[4 * hidx + c], (unsigned long long)rest[c]);
 }
 
+// Tile-local key -> zone offsets (x | y << 10 | z << 20) of a TS^3 tile.
+template <int TS>
+__device__ __forceinline__ int kdec_cube(int k)
+{
+    return (k % TS) | (((k / TS) % TS) << 10) | ((k / (TS * TS)) << 20);
+}
+
 // Out-of-line rare paths.  They work on copies (their addresses are taken
 // here, not the hot loop's registers); the kernel argument is a grid
 // constant, so the geometry structures are passed by reference to it.
@@ -143,7 +150,7 @@ __device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev
 // persistent kernel): the tile ends with a block barrier and invalidates its
 // copy barrier, so that the shared memory can be reused.
 // Returns false when the wait for the gas box ran out (DUST_FLAG_TIMEOUT).
-template <int GEOM, int FLAT, int MODE>
+template <int GEOM, int FLAT, int MODE, int TS = 0>
 __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int tile, const int ntile,
                                           unsigned char *smem_raw, const bool reuse)
 {
@@ -151,6 +158,14 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     constexpr int NB = Sh::NB, NC = Sh::NC;
     const StepArgs<float> &A = TA.s;
     const GridDev &g = A.g;
+    // tile extents: compile-time constants for the specialised cubic tile
+    // (TS > 0: TS^3 zones, every direction gridded), else the grid's
+    const int T0 = TS ? TS : g.T[0], T1 = TS ? TS : g.T[1], T2 = TS ? TS : g.T[2];
+    const int tvol = TS ? TS * TS * TS : g.tvol;
+    auto Td = [&](int d) { return d == 0 ? T0 : (d == 1 ? T1 : T2); };
+    // gridded directions, and the weights (the specialised tile runs TSC)
+    auto gd = [&](int d) { return TS ? true : g.n[d] > 1; };
+    const int tsc = TS ? 1 : TA.tsc;
     // the inline push reads ph; the rare out-of-line paths read the kernel
     // argument (the same values)
     PhysDev ph = A.ph;
@@ -184,8 +199,8 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
         if (TA.emit_keys && tile == 0 && threadIdx.x == 0 && D1 > D0)
             atomicAdd(&TA.count_out[g.nkeys], (int32_t)(D1 - D0));
     }
-    const int64_t kbase = (int64_t)tile * g.tvol;
-    if (TA.key_off[kbase + g.tvol] <= TA.key_off[kbase]) return true;
+    const int64_t kbase = (int64_t)tile * tvol;
+    if (TA.key_off[kbase + tvol] <= TA.key_off[kbase]) return true;
 
     int B[3], o[3], tc[3];
     tc[0] = tile % g.nt[0];
@@ -193,9 +208,9 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     tc[2] = tile / (g.nt[0] * g.nt[1]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const int H = g.n[d] > 1 ? 1 : 0;
-        B[d] = g.T[d] + 2 * H;
-        o[d] = tc[d] * g.T[d] - H;
+        const int H = gd(d) ? 1 : 0;
+        B[d] = Td(d) + 2 * H;
+        o[d] = tc[d] * Td(d) - H;
     }
     const int bvol = B[0] * B[1] * B[2];
     // gas box first (128-byte aligned for the bulk tensor copy), then the
@@ -204,36 +219,36 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     unsigned long long *sdep = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)bvol * 4 * sizeof(float));
     // tile-local key -> zone offsets (x | y << 10 | z << 20), no runtime division
     int *kdec = reinterpret_cast<int *>(sdep + (size_t)bvol * 4);
-    float *srec = reinterpret_cast<float *>(kdec + ((g.tvol + 31) & ~31));  // [warps][13][kRecStride]
+    float *srec = reinterpret_cast<float *>(kdec + ((tvol + 31) & ~31));  // [warps][13][kRecStride]
     // the tile's zone geometry, per direction d at toff[d]: centre (double and
     // float) and inverse width; radial centre / width; polar lower edges
-    const int toff[3] = {0, g.T[0], g.T[0] + g.T[1]};
-    const int tsum = g.T[0] + g.T[1] + g.T[2];
+    const int toff[3] = {0, T0, T0 + T1};
+    const int tsum = T0 + T1 + T2;
     double *szcd = reinterpret_cast<double *>(srec + (kSlabThreads / 32) * kRecFields * kRecStride);
     float *szcf = reinterpret_cast<float *>(szcd + tsum);
     float *szif = szcf + tsum;
     float *sznu = szif + tsum;          // [T0]
-    float *szlo = sznu + g.T[0];        // [T1 + 1]
+    float *szlo = sznu + T0;        // [T1 + 1]
     unsigned long long *sbar = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(szlo + g.T[1] + 1) + 7) & ~(uintptr_t)7);
+        (reinterpret_cast<uintptr_t>(szlo + T1 + 1) + 7) & ~(uintptr_t)7);
     // the gas box by one bulk tensor copy, overlapping the tables below
     gas_box_begin<float>(TA.gas_tmap, sgas, o, bvol, sbar, TA.wait_extra_tx);
-    for (int t = threadIdx.x; t < tsum + g.T[1] + 1; t += blockDim.x) {
+    for (int t = threadIdx.x; t < tsum + T1 + 1; t += blockDim.x) {
         if (t < tsum) {
             const int d = t < toff[1] ? 0 : (t < toff[2] ? 1 : 2);
-            const int z = tc[d] * g.T[d] + (t - toff[d]);
-            const bool ok = g.n[d] > 1 && z < g.n[d];
+            const int z = tc[d] * Td(d) + (t - toff[d]);
+            const bool ok = gd(d) && z < g.n[d];
             szcd[t] = ok ? g.zc[d][z] : 0.0;
             szcf[t] = ok ? g.zc_f[d][z] : 0.f;
             szif[t] = ok ? g.ziw_f[d][z] : 0.f;
             if (d == 0 && (GEOM == GEOM_CYL || GEOM == GEOM_SPH)) sznu[t] = ok ? g.znu_f[0][z] : 0.f;
         } else if (GEOM == GEOM_SPH) {
-            const int z = tc[1] * g.T[1] + (t - tsum);
+            const int z = tc[1] * T1 + (t - tsum);
             szlo[t - tsum] = (g.n[1] > 1 && z <= g.n[1]) ? g.zlo_f[1][z] : 0.f;
         }
     }
-    for (int k = threadIdx.x; k < g.tvol; k += blockDim.x) {
-        const int kx = k % g.T[0], ky = (k / g.T[0]) % g.T[1], kz = k / (g.T[0] * g.T[1]);
+    for (int k = threadIdx.x; k < tvol; k += blockDim.x) {
+        const int kx = k % T0, ky = (k / T0) % T1, kz = k / (T0 * T1);
         kdec[k] = kx | (ky << 10) | (kz << 20);
     }
 
@@ -249,7 +264,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     const int a = lane % 3, kq = lane / 3;
     const int base = lane - a;
     const float h = (float)(0.5 * A.dt), dt = (float)A.dt;
-    const int groups = (g.tvol + 9) / 10;
+    const int groups = (tvol + 9) / 10;
     int nremoved = 0;
     float moved = 0.f;
     bool big = false;
@@ -257,10 +272,10 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     for (int grp = warp; grp < groups; grp += nwarps) {
         const int kg0 = grp * 10;
         const int kl = kg0 + kq;
-        const bool kok = lane < 30 && kl < g.tvol;
+        const bool kok = lane < 30 && kl < tvol;
         // the group's 10 keys: grain range [koff[0], koff[10]) in the store
         // store positions fit in 32 bits (fewer than 2^31 grains)
-        const int offl = lane <= 10 ? TA.key_off[kbase + min(kg0 + lane, g.tvol)] : 0;
+        const int offl = lane <= 10 ? TA.key_off[kbase + min(kg0 + lane, tvol)] : 0;
         int koff[11];
 #pragma unroll
         for (int j = 0; j <= 10; ++j) koff[j] = __shfl_sync(FULL, offl, j);
@@ -280,7 +295,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
             cnt = off1 - off0;
         }
         // owner zone's position in the tile box
-        const int okd = kok ? kdec[kl] : 0;
+        const int okd = kok ? (TS ? kdec_cube<TS>(kl) : kdec[kl]) : 0;
         const int ohx = (okd & 1023) + 1, ohy = ((okd >> 10) & 1023) + (NB == 3 ? 1 : 0),
                   ohz = (okd >> 20) + (NC == 3 ? 1 : 0);
         // Passes of at most kSlabCap grains that end on chunk boundaries
@@ -313,9 +328,9 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 int kq2 = 0;
 #pragma unroll
                 for (int j = 1; j < 10; ++j) kq2 += gi >= koff[j] ? 1 : 0;
-                const int kd = kdec[kg0 + kq2];
+                const int kd = TS ? kdec_cube<TS>(kg0 + kq2) : kdec[kg0 + kq2];
                 const int lx = kd & 1023, ly = (kd >> 10) & 1023, lz = kd >> 20;
-                const int zx = tc[0] * g.T[0] + lx, zy = tc[1] * g.T[1] + ly, zz = tc[2] * g.T[2] + lz;
+                const int zx = tc[0] * T0 + lx, zy = tc[1] * T1 + ly, zz = tc[2] * T2 + lz;
                 const int hx = lx + 1, hy = ly + (NB == 3 ? 1 : 0), hz = lz + (NC == 3 ? 1 : 0);
                 const int lid[3] = {toff[0] + lx, toff[1] + ly, toff[2] + lz};
                 double zcd[3];
@@ -354,7 +369,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         sp = S.species ? S.species[src] : 0;
     #pragma unroll
                         for (int d = 0; d < 3; ++d) {
-                            if (g.n[d] > 1) { u[d] = __double2float_rn(q[d] - zcd[d]); zc3[d] = zcf[d]; }
+                            if (gd(d)) { u[d] = __double2float_rn(q[d] - zcd[d]); zc3[d] = zcf[d]; }
                             else { u[d] = 0.f; zc3[d] = (float)q[d]; }
                         }
                         // first half drift (Eq. exp_midpoint; Eq. drift1_cylindrical;
@@ -385,21 +400,21 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         for (int d = 0; d < 3; ++d) {
                             qf[d] = zc3[d] + u[d];
                             dl[d] = u[d] * zif[d];
-                            if (g.n[d] > 1) ingroup &= fabsf(dl[d]) <= 0.50001f;
+                            if (gd(d)) ingroup &= fabsf(dl[d]) <= 0.50001f;
                         }
                         if (ingroup) {
                             host[0] = zx; host[1] = zy; host[2] = zz;
     #pragma unroll
                             for (int d = 0; d < 3; ++d) {
                                 iw[d] = zif[d];
-                                if (g.n[d] <= 1) continue;
+                                if (!gd(d)) continue;
                                 if ((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && d == 0) {
-                                    if (GEOM == GEOM_CYL) w_cyl<float>(TA.tsc, dl[0], znu, w[0]);
-                                    else w_sphr<float>(TA.tsc, dl[0], znu, w[0]);
+                                    if (GEOM == GEOM_CYL) w_cyl<float>(tsc, dl[0], znu, w[0]);
+                                    else w_sphr<float>(tsc, dl[0], znu, w[0]);
                                 } else if (GEOM == GEOM_SPH && d == 1) {
-                                    w_theta<float>(TA.tsc, qf[1], zlo, zhi, u[1], zhw, w[1]);
+                                    w_theta<float>(tsc, qf[1], zlo, zhi, u[1], zhw, w[1]);
                                 } else {
-                                    w_cart<float>(TA.tsc, dl[d], w[d]);
+                                    w_cart<float>(tsc, dl[d], w[d]);
                                 }
                             }
                         } else {
@@ -408,7 +423,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             SlabExact ex;
 #pragma unroll
                             for (int d = 0; d < 3; ++d) { ex.q[d] = q[d]; ex.p[d] = pn[d]; }
-                            const bool in = slab_exact_first_half<GEOM>(g, A.ph, shift_mid_of(A), TA.tsc, h, ex);
+                            const bool in = slab_exact_first_half<GEOM>(g, A.ph, shift_mid_of(A), tsc, h, ex);
 #pragma unroll
                             for (int d = 0; d < 3; ++d) { q[d] = ex.q[d]; pn[d] = ex.p[d]; inc1[d] = ex.inc[d]; }
                             if (!in) {
@@ -441,12 +456,12 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     #pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             int l = host[d] - o[d];
-                            if (g.n[d] > 1 && g.bc[d] == DUST_BC_PERIODIC) {
+                            if (gd(d) && g.bc[d] == DUST_BC_PERIODIC) {
                                 if (l < 0) l += g.n[d];
                                 else if (l >= B[d]) l -= g.n[d];
                             }
                             lb[d] = l;
-                            if (g.n[d] > 1) inbox &= (l >= 1) && (l <= B[d] - 2);
+                            if (gd(d)) inbox &= (l >= 1) && (l <= B[d] - 2);
                         }
                     }
                     // 27-node gather (Eq. Delta_vp) from the staged gas box; the
@@ -547,7 +562,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         const int zk[3] = {zx, zy, zz};
 #pragma unroll
                         for (int d = 0; d < 3; ++d) {
-                            if (g.n[d] > 1) {
+                            if (gd(d)) {
                                 const float te = fabsf((u[d] + inc2[d]) * zif[d]);
                                 inner &= te < 0.499f ||
                                          (g.edge_kind[d] == EDGE_UNIFORM && te < 1.999f && zk[d] >= 2 &&
@@ -635,7 +650,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             }
 #pragma unroll
                             for (int d = 0; d < 3; ++d) {
-                                if (g.n[d] <= 1) continue;
+                                if (!gd(d)) continue;
                                 // zone offset floor(t + 1/2) for |t| < 3/2, by comparisons
                                 const float t = un[d] * zif[d];
                                 const int k = (t >= 0.5f ? 1 : 0) - (t < -0.5f ? 1 : 0);
@@ -652,13 +667,13 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
 #pragma unroll
                             for (int d = 0; d < 3; ++d) {
                                 int l = lloc[d] + kk[d], t = tc[d];
-                                if (l < 0) { l += g.T[d]; --t; }
-                                else if (l >= g.T[d]) { l -= g.T[d]; ++t; }
+                                if (l < 0) { l += Td(d); --t; }
+                                else if (l >= Td(d)) { l -= Td(d); ++t; }
                                 ll[d] = l;
                                 tt[d] = t;
                             }
-                            nkey = (tt[0] + g.nt[0] * (tt[1] + g.nt[1] * tt[2])) * g.tvol +
-                                   ll[0] + g.T[0] * (ll[1] + g.T[1] * ll[2]);
+                            nkey = (tt[0] + g.nt[0] * (tt[1] + g.nt[1] * tt[2])) * tvol +
+                                   ll[0] + T0 * (ll[1] + T1 * ll[2]);
                         } else {
                             double qk[3] = {q[0], q[1], q[2]};
                             const float pk[3] = {pnew[0], pnew[1], pnew[2]};
@@ -765,7 +780,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             const long long piece = rround(v);
                             // no test for zero: a chunk sum is rarely exactly
                             // zero, and the test cost more than the adds it saved
-                            shared_add_i64(&sdep[ch * bvol + lin], piece);
+                            shared_add_i64_always(&sdep[ch * bvol + lin], piece);
                             ps[ch] += piece;
                         }
                     }
@@ -813,12 +828,12 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     return true;
 }
 
-template <int GEOM, int FLAT, int MODE>
+template <int GEOM, int FLAT, int MODE, int TS = 0>
 __global__ void __launch_bounds__(kSlabThreads, 2)
 step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    slab_tile<GEOM, FLAT, MODE>(TA, blockIdx.x, gridDim.x, smem_raw, false);
+    slab_tile<GEOM, FLAT, MODE, TS>(TA, blockIdx.x, gridDim.x, smem_raw, false);
 }
 
 inline size_t slab_smem_bytes(const GridDev &g)
@@ -839,7 +854,12 @@ cudaError_t launch_step_slab(const TiledArgs<float> &a, cudaStream_t s)
     const GridDev &g = a.s.g;
     const int ntiles = g.nt[0] * g.nt[1] * g.nt[2];
     const size_t smem = slab_smem_bytes(g);
-    auto kern = step_slab_kernel<GEOM, FLAT, MODE>;
+    // the default 8^3 tile of a 3-D grid with the exponential-midpoint
+    // pusher and TSC weights runs a copy compiled for that case
+    constexpr bool kCube = FLAT == 0 && MODE == 1;
+    const bool cube = kCube && g.T[0] == 8 && g.T[1] == 8 && g.T[2] == 8 && g.n[0] > 1 && g.n[1] > 1 &&
+                      g.n[2] > 1 && a.tsc == 1;
+    auto kern = cube ? step_slab_kernel<GEOM, FLAT, MODE, kCube ? 8 : 0> : step_slab_kernel<GEOM, FLAT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<ntiles, kSlabThreads, smem, s>>>(a);

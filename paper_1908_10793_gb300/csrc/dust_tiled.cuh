@@ -66,6 +66,18 @@ __device__ __forceinline__ void shared_add_i64(unsigned long long *p, long long 
     if (up != 0u) atomicAdd(w + 1, up);
 }
 
+// The same, with the high word's add issued unconditionally (no branch on
+// the carried value): for the many pieces of a chunk, where the branch costs
+// more than the adds of zero it saves.
+__device__ __forceinline__ void shared_add_i64_always(unsigned long long *p, long long v)
+{
+    unsigned *w = reinterpret_cast<unsigned *>(p);
+    const unsigned lo = (unsigned)(unsigned long long)v;
+    const unsigned hi = (unsigned)((unsigned long long)v >> 32);
+    const unsigned old = atomicAdd(w, lo);
+    atomicAdd(w + 1, hi + ((old + lo < old) ? 1u : 0u));
+}
+
 // How long a block waits for its gas box before it gives up
 // (DUST_FLAG_TIMEOUT): one second; the copy of a few tens of KB takes
 // microseconds.
