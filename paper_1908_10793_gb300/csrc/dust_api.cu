@@ -77,6 +77,9 @@ struct dust_ctx {
 
     int32_t *d_key = nullptr, *d_count = nullptr, *d_cursor = nullptr, *d_blocksums = nullptr;
     int32_t *d_pair_id = nullptr, *d_pair_src = nullptr;
+    // the gas predictor's own sort of the store by the zone at x^n (mixed
+    // precision on the slab layout): keys, key offsets, (id, source) pairs
+    int32_t *d_pkey = nullptr, *d_pcount = nullptr, *d_ppair_id = nullptr, *d_ppair_src = nullptr;
     // zone segments left to the block sort: count, then keys ([nkeys + 2])
     int32_t *d_bigseg = nullptr;
     // key counts for the next sort (d_count holds the current key offsets)
@@ -691,9 +694,15 @@ void free_store(dust_ctx *c)
     dfree(c->d_key);
     dfree(c->d_pair_id);
     dfree(c->d_pair_src);
+    dfree(c->d_pkey);
+    dfree(c->d_ppair_id);
+    dfree(c->d_ppair_src);
     c->d_pair_id = nullptr;
     c->d_pair_src = nullptr;
     c->d_key = nullptr;
+    c->d_pkey = nullptr;
+    c->d_ppair_id = nullptr;
+    c->d_ppair_src = nullptr;
     c->cap = 0;
 }
 
@@ -712,6 +721,11 @@ int alloc_store(dust_ctx *ctx, int64_t n)
     CU(dalloc(&ctx->d_key, n));
     CU(dalloc(&ctx->d_pair_id, n));
     CU(dalloc(&ctx->d_pair_src, n));
+    if (ctx->d_pcount) {
+        CU(dalloc(&ctx->d_pkey, n));
+        CU(dalloc(&ctx->d_ppair_id, n));
+        CU(dalloc(&ctx->d_ppair_src, n));
+    }
     ctx->cap = n;
     return DUST_OK;
 }
@@ -918,6 +932,60 @@ cudaError_t launch_predict(int geom, int weight, const StepArgs<Real> &pa, const
     }
 }
 
+// The gas predictor's sort: the live store (the current store, before any
+// pending gather) ordered by the key of the zone at x^n (the key kernel with
+// no drift), grains in id order inside a zone, as the pairs d_ppair_id /
+// d_ppair_src with the zone offsets d_pcount.  The scratch of its block sort
+// is the other store's id column, which the step writes afterwards.
+int run_predictor_sort(dust_ctx *ctx)
+{
+    SortArgs<float> a;
+    a.g = ctx->g;
+    a.ph = phys_of(ctx, ctx->t, 0.0);
+    a.dt = 0.0;
+    a.src = store_of<float>(ctx, ctx->cur);
+    a.dst = store_of<float>(ctx, 1 - ctx->cur);
+    a.key = ctx->d_pkey;
+    a.count = ctx->d_pcount;
+    a.cursor = ctx->d_cursor;
+    a.pair_id = ctx->d_ppair_id;
+    a.pair_src = ctx->d_ppair_src;
+    a.nkeys1 = ctx->g.nkeys + 1;
+    a.big = ctx->d_bigseg;
+    a.tmp_id = ctx->d_pkey;
+    a.tmp_src = ctx->d_id[1 - ctx->cur];
+    const int64_t m = ctx->g.nkeys + 2;
+    CU(cudaMemsetAsync(ctx->d_pcount, 0, m * sizeof(int32_t), ctx->stream));
+    cudaError_t e = cudaSuccess;
+    switch (ctx->geom.kind) {
+    case DUST_CARTESIAN: e = launch_sort_keys<float, GEOM_CART>(a, ctx->stream); break;
+    case DUST_SHEARING_BOX: e = launch_sort_keys<float, GEOM_SB>(a, ctx->stream); break;
+    case DUST_CYLINDRICAL: e = launch_sort_keys<float, GEOM_CYL>(a, ctx->stream); break;
+    default: e = launch_sort_keys<float, GEOM_SPH>(a, ctx->stream); break;
+    }
+    CU(e);
+    CU(launch_exclusive_scan(ctx->d_pcount, m, ctx->d_blocksums, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->d_cursor, ctx->d_pcount, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_bigseg, 0, sizeof(int32_t), ctx->stream));
+    CU(launch_sort_scatter<float>(a, ctx->stream, false));
+    if (ctx->n_grains > 0) ctx->launches[dust_ctx::GROUP_OTHER] += 7;
+    return DUST_OK;
+}
+
+// Gas predictor on the slab layout, for the flat patterns the slab kernel has.
+cudaError_t launch_predict_slab_any(int geom, const TiledArgs<float> &pt, int flat, cudaStream_t s)
+{
+    switch (geom) {
+    case DUST_CARTESIAN:
+        return flat == 0 ? launch_predict_slab<GEOM_CART, 0>(pt, s) : launch_predict_slab<GEOM_CART, 2>(pt, s);
+    case DUST_SHEARING_BOX:
+        return flat == 0 ? launch_predict_slab<GEOM_SB, 0>(pt, s)
+                         : (flat == 1 ? launch_predict_slab<GEOM_SB, 1>(pt, s) : launch_predict_slab<GEOM_SB, 2>(pt, s));
+    case DUST_CYLINDRICAL: return launch_predict_slab<GEOM_CYL, 0>(pt, s);
+    default: return launch_predict_slab<GEOM_SPH, 0>(pt, s);
+    }
+}
+
 template <typename Real>
 int run_step(dust_ctx *ctx, double dt)
 {
@@ -959,7 +1027,21 @@ int run_step(dust_ctx *ctx, double dt)
                 pt.gas_tmap = ctx->tmap_ok[0] ? static_cast<const void *>(ctx->d_tmaps) : nullptr;
                 pt.wait_extra_tx = ctx->opt.test_wait_timeout ? 16u : 0u;
                 pt.wait_ns = ctx->opt.test_wait_timeout ? 1000000ull : 0ull;
-                pe = launch_predict<Real>(ctx->geom.kind, ctx->opt.weight, pa, &pt, ctx->stream);
+                pt.tsc = ctx->opt.weight == DUST_WEIGHT_TSC;
+                if constexpr (sizeof(Real) == 4) {
+                    // on the slab layout where the step runs the slab kernel,
+                    // over the store sorted by the zone at x^n
+                    if (step_emits_keys(ctx) && ctx->n_grains > 0) {
+                        const int r = run_predictor_sort(ctx);
+                        if (r) return r;
+                        pt.key_off = ctx->d_pcount;
+                        pt.perm = ctx->d_ppair_src;
+                        pe = launch_predict_slab_any(ctx->geom.kind, pt, slab_flat(ctx->g), ctx->stream);
+                    } else
+                        pe = launch_predict<Real>(ctx->geom.kind, ctx->opt.weight, pa, &pt, ctx->stream);
+                } else {
+                    pe = launch_predict<Real>(ctx->geom.kind, ctx->opt.weight, pa, &pt, ctx->stream);
+                }
             }
             CU(pe);
             predict_apply_kernel<Real><<<blocks_for(ctx->ncell), 256, 0, ctx->stream>>>(
@@ -1201,7 +1283,8 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     if (cudaMalloc(&ctx->d_gas, ncell * 4 * ctx->rsz) != cudaSuccess ||
         dalloc(&ctx->d_dep, ncell * 4) != cudaSuccess ||
         (opt->gas_predictor && (dalloc(&ctx->d_pred, ncell * 4) != cudaSuccess ||
-                                cudaMalloc(&ctx->d_gas_half, ncell * 4 * ctx->rsz) != cudaSuccess)) ||
+                                cudaMalloc(&ctx->d_gas_half, ncell * 4 * ctx->rsz) != cudaSuccess ||
+                                (ctx->mixed && dalloc(&ctx->d_pcount, nk + 2) != cudaSuccess))) ||
         dalloc(&ctx->d_status, ST_WORDS) != cudaSuccess ||
         dalloc(&ctx->d_count, nk + 2) != cudaSuccess ||
         dalloc(&ctx->d_count_next, nk + 2) != cudaSuccess ||
@@ -1718,6 +1801,7 @@ extern "C" void dust_destroy(dust_ctx *ctx)
     dfree(ctx->d_gas);
     dfree(ctx->d_dep);
     dfree(ctx->d_pred);
+    dfree(ctx->d_pcount);
     dfree(ctx->d_gas_half);
     dfree(ctx->d_tmaps);
     dfree(ctx->d_status);

@@ -14,6 +14,8 @@ template cudaError_t launch_step_tiled<double, GEOM_CART, 1>(const TiledArgs<dou
 template cudaError_t launch_step_slab<GEOM_CART, 0, 0>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_CART, 0, 1>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_CART, 2, 0>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_slab<GEOM_CART, 0>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_predict_slab<GEOM_CART, 2>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_CART>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_CART>(const SortArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_tiled<float, GEOM_CART, 0>(const TiledArgs<float> &, cudaStream_t);

@@ -303,6 +303,10 @@ cudaError_t launch_step_tiled(const TiledArgs<Real> &a, cudaStream_t s);
 template <int GEOM, int FLAT, int MODE>
 cudaError_t launch_step_slab(const TiledArgs<float> &a, cudaStream_t s);
 
+// Gas predictor on the slab layout (mixed precision), one per flat pattern.
+template <int GEOM, int FLAT>
+cudaError_t launch_predict_slab(const TiledArgs<float> &a, cudaStream_t s);
+
 template <typename Real, int GEOM>
 cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s);
 

@@ -99,6 +99,91 @@ __device__ __forceinline__ int kdec_cube(int k)
     return (k % TS) | (((k / TS) % TS) << 10) | ((k / (TS * TS)) << 20);
 }
 
+// 27-node gather (Eq. Delta_vp) from the staged gas box around box
+// position lb, channels in pairs on the packed single-precision FMA (each
+// lane rounded once, as a scalar FMA), nodes x fastest.
+template <int NB, int NC>
+__device__ __forceinline__ void gather_box(const float *sgas, const int lb[3], int B0, int B1,
+                                           const float w[3][3], float G[4])
+{
+    float2 G01 = make_float2(0.f, 0.f), G23 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) {
+        if (NC == 1 && c3 != 1) continue;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (NB == 1 && b != 1) continue;
+#pragma unroll
+            for (int aa = 0; aa < 3; ++aa) {
+                const float W = w[0][aa] * (w[1][b] * w[2][c3]);
+                const float4 fv = reinterpret_cast<const float4 *>(sgas)[
+                    (lb[0] + aa - 1) + B0 * ((lb[1] + b - 1) + B1 * (lb[2] + c3 - 1))];
+                const float2 W2 = make_float2(W, W);
+                G01 = __ffma2_rn(W2, make_float2(fv.x, fv.y), G01);
+                G23 = __ffma2_rn(W2, make_float2(fv.z, fv.w), G23);
+            }
+        }
+    }
+    G[0] = G01.x; G[1] = G01.y; G[2] = G23.x; G[3] = G23.y;
+}
+
+// The same nodes in the same order from global memory, for a grain whose
+// stencil leaves the staged box (rolled loop: a rare path).
+template <int NB, int NC>
+__device__ __forceinline__ void gather_global(const GridDev &g, const float *gas, const int host[3],
+                                              const float w[3][3], float G[4])
+{
+#pragma unroll 1
+    for (int nd = 0; nd < 27; ++nd) {
+        const int aa = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
+        if ((NB == 1 && b != 1) || (NC == 1 && c3 != 1)) continue;
+        const float W = sel3(w[0], aa) * (sel3(w[1], b) * sel3(w[2], c3));
+        const int ix = node_of(host[0], aa - 1, g.n[0], g.bc[0]);
+        const int iy = node_of(host[1], b - 1, g.n[1], g.bc[1]);
+        const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
+        float fv[4];
+        load_gas<float>(gas, ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz), fv);
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) G[ch] += W * fv[ch];
+    }
+}
+
+// The per-grain fixed-point rule into the shared deposit box (stencil
+// inside the box around lb): rint(W D) for the other nodes, the host the
+// remainder of rint(D).  Returns whether a channel was out of range.
+template <int NB, int NC>
+__device__ __forceinline__ bool deposit_box_per_grain(unsigned long long *sdep, int bvol, const int lb[3],
+                                                      int B0, int B1, const float w[3][3], const float D[4])
+{
+    long long rest[4];
+    bool big = false;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        big |= !(fabsf(D[ch]) < 4.5e15f);
+        rest[ch] = rround(D[ch]);
+    }
+    const int hl = lb[0] + B0 * (lb[1] + B1 * lb[2]);
+#pragma unroll 1
+    for (int nd = 0; nd < 27; ++nd) {
+        const int aa = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
+        if ((NB == 1 && b != 1) || (NC == 1 && c3 != 1) || nd == 13) continue;
+        const float W = sel3(w[0], aa) * (sel3(w[1], b) * sel3(w[2], c3));
+        const int lin = hl + (aa - 1) + B0 * ((b - 1) + B1 * (c3 - 1));
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            const long long piece = rround(W * D[ch]);
+            if (piece != 0) {
+                shared_add_i64(&sdep[ch * bvol + lin], piece);
+                rest[ch] -= piece;
+            }
+        }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch)
+        if (rest[ch] != 0) shared_add_i64(&sdep[ch * bvol + hl], rest[ch]);
+    return big;
+}
+
 // Out-of-line rare paths.  They work on copies (their addresses are taken
 // here, not the hot loop's registers); the kernel argument is a grid
 // constant, so the geometry structures are passed by reference to it.
@@ -149,8 +234,11 @@ __device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev
 // reuse: the block processes further tiles after this one (the batched
 // persistent kernel): the tile ends with a block barrier and invalidates its
 // copy barrier, so that the shared memory can be reused.
+// TS > 0: the copy compiled for a TS^3 tile with TSC weights.  PRED: the gas
+// predictor instead of the step: the same groups, chunks and deposit into
+// TA.s.dep, from the grains' drag impulse at x^n (nothing is moved).
 // Returns false when the wait for the gas box ran out (DUST_FLAG_TIMEOUT).
-template <int GEOM, int FLAT, int MODE, int TS = 0>
+template <int GEOM, int FLAT, int MODE, int TS = 0, bool PRED = false>
 __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int tile, const int ntile,
                                           unsigned char *smem_raw, const bool reuse)
 {
@@ -178,7 +266,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     // sort's gather is fused into this kernel)
     const StoreDev<float> &S = A.s;
     const StoreDev<float> &O = TA.perm ? TA.dst : A.s;
-    if (TA.emit_keys || TA.perm) {
+    if (!PRED && (TA.emit_keys || TA.perm)) {
         // grains removed before the last sort sit after every zone's group:
         // they keep the removed-grain key and are moved as they are
         const int D0 = TA.key_off[g.nkeys], D1 = (int)A.s.n;
@@ -348,11 +436,89 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     zhi = szlo[ly + 1];
                     zhw = 0.5f / zif[1];
                 }
+                // the grain's weights and deposit impulse for the zone's
+                // owners (zero impulse: the grain deposits by itself)
+                float w[3][3] = {{0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}};
+                float D[4] = {0.f, 0.f, 0.f, 0.f};
+                bool grp_ok = false;
+                if constexpr (PRED) {
+                    // ---- gas predictor (Sec. 3.1): the drag impulse over half
+                    // a step, dt/2 m (v - v_g) / max(tau, dt), of the grain at
+                    // x^n, gathered and deposited at x^n.  Grains whose x^n
+                    // lies in their key zone go to the zone's chunks; the
+                    // others take the exact zone search and the per-grain rule.
+                    const double q[3] = {S.q[0][src], S.q[1][src], S.q[2][src]};
+                    if ((__double_as_longlong(q[0]) & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) {
+                        const float pn[3] = {S.p[0][src], S.p[1][src], S.p[2][src]};
+                        const int sp = S.species ? S.species[src] : 0;
+                        float u[3] = {0.f, 0.f, 0.f}, qf[3], dl[3];
+                        bool here = true;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            float zc3 = (float)q[d];
+                            if (gd(d)) {
+                                u[d] = __double2float_rn(q[d] - zcd[d]);
+                                zc3 = zcf[d];
+                            }
+                            qf[d] = zc3 + u[d];
+                            dl[d] = u[d] * zif[d];
+                            if (gd(d)) here &= fabsf(dl[d]) <= 0.50001f;
+                        }
+                        int host[3] = {zx, zy, zz};
+                        int lb[3] = {hx, hy, hz};
+                        bool inbox = true;
+                        if (here) {
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                if (!gd(d)) continue;
+                                if ((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && d == 0) {
+                                    if (GEOM == GEOM_CYL) w_cyl<float>(tsc, dl[0], znu, w[0]);
+                                    else w_sphr<float>(tsc, dl[0], znu, w[0]);
+                                } else if (GEOM == GEOM_SPH && d == 1) {
+                                    w_theta<float>(tsc, qf[1], zlo, zhi, u[1], zhw, w[1]);
+                                } else {
+                                    w_cart<float>(tsc, dl[d], w[d]);
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                float iwd;
+                                zone_weights<float, GEOM>(g, d, tsc & 1, q[d], host[d], w[d], iwd);
+                                qf[d] = (float)q[d];
+                                int l = host[d] - o[d];
+                                if (gd(d) && g.bc[d] == DUST_BC_PERIODIC) {
+                                    if (l < 0) l += g.n[d];
+                                    else if (l >= B[d]) l -= g.n[d];
+                                }
+                                lb[d] = l;
+                                if (gd(d)) inbox &= (l >= 1) && (l <= B[d] - 2);
+                            }
+                        }
+                        float G[4] = {0.f, 0.f, 0.f, 0.f};
+                        if (inbox) gather_box<NB, NC>(sgas, lb, B[0], B[1], w, G);
+                        else gather_global<NB, NC>(g, A.gas, host, w, G);
+                        const float value = S.param ? S.param[src] : A.sp.tau_f[sp];
+                        const float tau = stopping_time<float, GEOM>(ph, A.sp.mode[sp], value, qf, G[0]);
+                        const float taup = fmaxf(tau, fabsf(dt));
+                        const float coef = 0.5f * dt * A.sp.mqf[sp] / taup;
+                        const float Dq[4] = {coef * (pn[0] - G[1]), coef * (pn[1] - G[2]), coef * (pn[2] - G[3]),
+                                             0.f};
+                        if (here) {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) D[c] = Dq[c];
+                            grp_ok = true;
+                        } else if (inbox) {
+                            big |= deposit_box_per_grain<NB, NC>(sdep, bvol, lb, B[0], B[1], w, Dq);
+                        } else {
+                            deposit_fixed_rolled<NB, NC>(g, A.dep, host, w, Dq, A.status);
+                        }
+                    }
+                } else {
                 // ---- own grain: first half drift and weights, relative to the
                 // key zone (fast); grains that left it take the exact path
                 double q[3] = {0.0, 0.0, 0.0};
                 float pn[3] = {0.f, 0.f, 0.f};
-                float w[3][3] = {{0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 1.f, 0.f}};
                 float iw[3] = {0.f, 0.f, 0.f};
                 float inc1[3] = {0.f, 0.f, 0.f};
                 float qf[3] = {0.f, 0.f, 0.f};  // half-step coordinates
@@ -445,10 +611,9 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         }
                     }
                 }
-                const bool grp_ok = live && ingroup;
+                grp_ok = live && ingroup;
                 float G[4] = {0.f, 0.f, 0.f, 0.f};
                 // ---- own grain: kick, second half drift, deposit impulse
-                float D[4] = {0.f, 0.f, 0.f, 0.f};
                 if (live) {
                     int lb[3] = {hx, hy, hz};
                     bool inbox = true;
@@ -707,6 +872,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         atomicAdd(&TA.count_out[nkey], end - lane);
                     }
                 }
+                }  // step
                 // record for the zone's deposit owners (grains outside their
                 // key zone, and removed ones, carry a zero impulse)
                 const int slot = gi - P0 + kq2;
@@ -836,6 +1002,17 @@ step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
     slab_tile<GEOM, FLAT, MODE, TS>(TA, blockIdx.x, gridDim.x, smem_raw, false);
 }
 
+// Gas predictor on the slab layout (Sec. 3.1): one tile per block, the
+// chunk rule for grains whose x^n lies in their key zone, the per-grain rule
+// for the others.
+template <int GEOM, int FLAT, int TS = 0>
+__global__ void __launch_bounds__(kSlabThreads, 2)
+predict_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    slab_tile<GEOM, FLAT, 1, TS, true>(TA, blockIdx.x, gridDim.x, smem_raw, false);
+}
+
 inline size_t slab_smem_bytes(const GridDev &g)
 {
     size_t bvol = 1;
@@ -860,6 +1037,21 @@ cudaError_t launch_step_slab(const TiledArgs<float> &a, cudaStream_t s)
     const bool cube = kCube && g.T[0] == 8 && g.T[1] == 8 && g.T[2] == 8 && g.n[0] > 1 && g.n[1] > 1 &&
                       g.n[2] > 1 && a.tsc == 1;
     auto kern = cube ? step_slab_kernel<GEOM, FLAT, MODE, kCube ? 8 : 0> : step_slab_kernel<GEOM, FLAT, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ntiles, kSlabThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int GEOM, int FLAT>
+cudaError_t launch_predict_slab(const TiledArgs<float> &a, cudaStream_t s)
+{
+    const GridDev &g = a.s.g;
+    const int ntiles = g.nt[0] * g.nt[1] * g.nt[2];
+    const size_t smem = slab_smem_bytes(g);
+    const bool cube = FLAT == 0 && g.T[0] == 8 && g.T[1] == 8 && g.T[2] == 8 && g.n[0] > 1 && g.n[1] > 1 &&
+                      g.n[2] > 1 && a.tsc == 1;
+    auto kern = cube ? predict_slab_kernel<GEOM, FLAT, FLAT == 0 ? 8 : 0> : predict_slab_kernel<GEOM, FLAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<ntiles, kSlabThreads, smem, s>>>(a);
