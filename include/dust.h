@@ -158,7 +158,11 @@ typedef struct dust_options {
                               the step gathers from that prediction, and with
                               feedback_apply the deposit corrects the gas at
                               t^n, as the paper's predictor-corrector does for
-                              the drag term (no hydrodynamic fluxes here)    */
+                              the drag term (no hydrodynamic fluxes here).
+                              In mixed precision on the slab kernel the
+                              predictor sorts the grains by their zone at x^n
+                              first (12 more bytes per grain of device
+                              memory, 4 per sort key)                        */
     int host_io_async;     /* 0: calls with host memory (dust_load_particles,
                               dust_set_gas, dust_get_particles, dust_get_deposit
                               with DUST_MEM_HOST) return when their copies are
