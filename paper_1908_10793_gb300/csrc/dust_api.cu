@@ -2048,10 +2048,12 @@ int capture(dust_batch *b, const double *dt)
 // cannot share it: all mixed precision on the slab kernel (which predicts
 // the next sort's keys), the exponential-midpoint pusher, no gas predictor,
 // and one of the two instantiated geometries: x-z shearing boxes in the
-// orbital-advection frame (variant 0) or x-y Cartesian boxes (variant 1).
+// orbital-advection frame (variant 0; 2 and 3 when every instance has the
+// 32 x 16 or the 16 x 16 tile with TSC weights, which have compiled copies)
+// or x-y Cartesian boxes (variant 1).
 int persistent_variant(const dust_batch *b)
 {
-    int v = -1;
+    int v = -1, shape = -1;
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         const dust_ctx *c = b->ctx[i];
         if (!step_emits_keys(c) || c->opt.gas_predictor || c->opt.pusher != DUST_PUSHER_EM) return -1;
@@ -2061,20 +2063,32 @@ int persistent_variant(const dust_batch *b)
         else if (c->geom.kind == DUST_CARTESIAN && flat == 2) vi = 1;
         if (vi < 0 || (v >= 0 && vi != v)) return -1;
         v = vi;
+        const int si = slab_shape_id(c->g, flat, c->opt.weight == DUST_WEIGHT_TSC, 1);
+        shape = (shape < 0 || shape == si) ? si : SHAPE_ANY;
     }
+    if (v == 0 && shape == SHAPE_32X16) return 2;
+    if (v == 0 && shape == SHAPE_16X16) return 3;
     return v;
 }
 
 int grid_of(int variant, size_t smem)
 {
-    return variant == 0 ? batch_persistent_grid<GEOM_SB, 1, 1>(smem)
-                        : batch_persistent_grid<GEOM_CART, 2, 1>(smem);
+    switch (variant) {
+    case 0: return batch_persistent_grid<GEOM_SB, 1, 1>(smem);
+    case 2: return batch_persistent_grid<GEOM_SB, 1, 1, 32, 1, 16>(smem);
+    case 3: return batch_persistent_grid<GEOM_SB, 1, 1, 16, 1, 16>(smem);
+    default: return batch_persistent_grid<GEOM_CART, 2, 1>(smem);
+    }
 }
 
 cudaError_t launch_variant(int variant, const BatchDev &d, size_t smem, int grid, cudaStream_t st)
 {
-    return variant == 0 ? launch_batch_persistent<GEOM_SB, 1, 1>(d, smem, grid, st)
-                        : launch_batch_persistent<GEOM_CART, 2, 1>(d, smem, grid, st);
+    switch (variant) {
+    case 0: return launch_batch_persistent<GEOM_SB, 1, 1>(d, smem, grid, st);
+    case 2: return launch_batch_persistent<GEOM_SB, 1, 1, 32, 1, 16>(d, smem, grid, st);
+    case 3: return launch_batch_persistent<GEOM_SB, 1, 1, 16, 1, 16>(d, smem, grid, st);
+    default: return launch_batch_persistent<GEOM_CART, 2, 1>(d, smem, grid, st);
+    }
 }
 
 // Descriptor of instance c for a launch of steps of length dt starting at

@@ -149,7 +149,7 @@ __device__ __forceinline__ BatchSort sort_of(const BatchInst &I, const StepState
 
 }  // namespace
 
-template <int GEOM, int FLAT, int MODE>
+template <int GEOM, int FLAT, int MODE, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const BatchDev B)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
                 A.count_out = emit ? I.count[st.coff ^ 1] : nullptr;
             }
             __syncthreads();
-            const bool in_time = slab_tile<GEOM, FLAT, MODE>(*sTA, li, I.ntiles, smem_raw, true);
+            const bool in_time = slab_tile<GEOM, FLAT, MODE, TX, TY, TZ>(*sTA, li, I.ntiles, smem_raw, true);
             if (!in_time) {
                 // the gas box did not arrive in time: stop this block; tasks
                 // that wait for this one run out of time too
@@ -288,10 +288,10 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
         for (int i = 0; i < B.ninst; ++i) atomicOr(&B.inst[i].ta.s.status[ST_FLAGS], DUST_FLAG_TIMEOUT);
 }
 
-template <int GEOM, int FLAT, int MODE>
+template <int GEOM, int FLAT, int MODE, int TX, int TY, int TZ>
 int batch_persistent_grid(size_t smem)
 {
-    auto kern = batch_persistent_kernel<GEOM, FLAT, MODE>;
+    auto kern = batch_persistent_kernel<GEOM, FLAT, MODE, TX, TY, TZ>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int per_sm = 0, dev = 0, sms = 0;
@@ -303,10 +303,10 @@ int batch_persistent_grid(size_t smem)
     return per_sm * sms;
 }
 
-template <int GEOM, int FLAT, int MODE>
+template <int GEOM, int FLAT, int MODE, int TX, int TY, int TZ>
 cudaError_t launch_batch_persistent(const BatchDev &b, size_t smem, int grid, cudaStream_t s)
 {
-    auto kern = batch_persistent_kernel<GEOM, FLAT, MODE>;
+    auto kern = batch_persistent_kernel<GEOM, FLAT, MODE, TX, TY, TZ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

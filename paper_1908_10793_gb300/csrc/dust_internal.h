@@ -230,6 +230,19 @@ struct BatchInst {
     int64_t n, nkeys, ncell;
 };
 
+// The tile shapes with a compiled copy of the slab tile function (TSC weights,
+// exponential midpoint): 8^3 in 3-D, 32 x 16 and 16 x 16 zones in x-z.
+enum SlabShapeId { SHAPE_ANY = 0, SHAPE_8C = 1, SHAPE_32X16 = 2, SHAPE_16X16 = 3 };
+
+inline int slab_shape_id(const GridDev &g, int flat, int tsc, int mode)
+{
+    if (!tsc || mode != 1) return SHAPE_ANY;
+    if (flat == 0 && g.T[0] == 8 && g.T[1] == 8 && g.T[2] == 8) return SHAPE_8C;
+    if (flat == 1 && g.T[0] == 32 && g.T[1] == 1 && g.T[2] == 16) return SHAPE_32X16;
+    if (flat == 1 && g.T[0] == 16 && g.T[1] == 1 && g.T[2] == 16) return SHAPE_16X16;
+    return SHAPE_ANY;
+}
+
 // Phases of one step of one instance in the persistent kernel.
 enum { BPH_SCANA = 0, BPH_SCANB, BPH_SCANC, BPH_SCATTER, BPH_SEG, BPH_ZERO, BPH_TILE, BPH_FB, BPH_N };
 
@@ -277,7 +290,8 @@ constexpr int kBatchFbChunk = 256;           // zones per feedback chunk
 constexpr int kBatchChunks = 8;              // chunks per work item
 constexpr int kBatchBigItems = 8;            // items of the block sort per instance
 
-template <int GEOM, int FLAT, int MODE>
+// TX > 0: the copy for a TX x TY x TZ tile (every instance's, TSC weights).
+template <int GEOM, int FLAT, int MODE, int TX = 0, int TY = 0, int TZ = 0>
 cudaError_t launch_batch_persistent(const BatchDev &b, size_t smem, int grid, cudaStream_t s);
 
 // Shared memory of one slab tile of this grid, and of the sort's staging.
@@ -286,7 +300,7 @@ size_t batch_sort_smem();
 
 // Grid size of the persistent kernel for this shared memory (all blocks
 // resident at once), 0 if it cannot run.
-template <int GEOM, int FLAT, int MODE>
+template <int GEOM, int FLAT, int MODE, int TX = 0, int TY = 0, int TZ = 0>
 int batch_persistent_grid(size_t smem);
 
 // Launch wrappers, explicitly instantiated per geometry.

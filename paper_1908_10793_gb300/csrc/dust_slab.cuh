@@ -92,11 +92,15 @@ __device__ __forceinline__ void deposit_fixed_rolled(const GridDev &g, unsigned 
         if (rest[c] != 0) atomicAdd(&dep[4 * hidx + c], (unsigned long long)rest[c]);
 }
 
-// Tile-local key -> zone offsets (x | y << 10 | z << 20) of a TS^3 tile.
-template <int TS>
-__device__ __forceinline__ int kdec_cube(int k)
+// Tile-local key -> zone offsets (x | y << 10 | z << 20) of a TX x TY x TZ
+// tile.
+template <int TX, int TY>
+__device__ __forceinline__ int kdec_shape(int k)
 {
-    return (k % TS) | (((k / TS) % TS) << 10) | ((k / (TS * TS)) << 20);
+    if constexpr (TX > 0 && TY > 0)
+        return (k % TX) | (((k / TX) % TY) << 10) | ((k / (TX * TY)) << 20);
+    else
+        return 0;
 }
 
 // 27-node gather (Eq. Delta_vp) from the staged gas box around box
@@ -234,11 +238,11 @@ __device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev
 // reuse: the block processes further tiles after this one (the batched
 // persistent kernel): the tile ends with a block barrier and invalidates its
 // copy barrier, so that the shared memory can be reused.
-// TS > 0: the copy compiled for a TS^3 tile with TSC weights.  PRED: the gas
+// TX > 0: the copy compiled for a TX x TY x TZ tile with TSC weights.  PRED: the gas
 // predictor instead of the step: the same groups, chunks and deposit into
 // TA.s.dep, from the grains' drag impulse at x^n (nothing is moved).
 // Returns false when the wait for the gas box ran out (DUST_FLAG_TIMEOUT).
-template <int GEOM, int FLAT, int MODE, int TS = 0, bool PRED = false>
+template <int GEOM, int FLAT, int MODE, int TX = 0, int TY = 0, int TZ = 0, bool PRED = false>
 __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int tile, const int ntile,
                                           unsigned char *smem_raw, const bool reuse)
 {
@@ -246,14 +250,15 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     constexpr int NB = Sh::NB, NC = Sh::NC;
     const StepArgs<float> &A = TA.s;
     const GridDev &g = A.g;
-    // tile extents: compile-time constants for the specialised cubic tile
-    // (TS > 0: TS^3 zones, every direction gridded), else the grid's
-    const int T0 = TS ? TS : g.T[0], T1 = TS ? TS : g.T[1], T2 = TS ? TS : g.T[2];
-    const int tvol = TS ? TS * TS * TS : g.tvol;
+    // tile extents: compile-time constants in a copy for one tile shape
+    // (TX > 0; the flat pattern fixes the gridded directions), else the grid's
+    constexpr bool FIX = TX > 0;
+    const int T0 = FIX ? TX : g.T[0], T1 = FIX ? TY : g.T[1], T2 = FIX ? TZ : g.T[2];
+    const int tvol = FIX ? TX * TY * TZ : g.tvol;
     auto Td = [&](int d) { return d == 0 ? T0 : (d == 1 ? T1 : T2); };
-    // gridded directions, and the weights (the specialised tile runs TSC)
-    auto gd = [&](int d) { return TS ? true : g.n[d] > 1; };
-    const int tsc = TS ? 1 : TA.tsc;
+    // gridded directions, and the weights (the shape copies run TSC)
+    auto gd = [&](int d) { return FIX ? (d == 0 || (d == 1 ? FLAT != 1 : FLAT != 2)) : g.n[d] > 1; };
+    const int tsc = FIX ? 1 : TA.tsc;
     // the inline push reads ph; the rare out-of-line paths read the kernel
     // argument (the same values)
     PhysDev ph = A.ph;
@@ -383,7 +388,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
             cnt = off1 - off0;
         }
         // owner zone's position in the tile box
-        const int okd = kok ? (TS ? kdec_cube<TS>(kl) : kdec[kl]) : 0;
+        const int okd = kok ? (FIX ? kdec_shape<TX, TY>(kl) : kdec[kl]) : 0;
         const int ohx = (okd & 1023) + 1, ohy = ((okd >> 10) & 1023) + (NB == 3 ? 1 : 0),
                   ohz = (okd >> 20) + (NC == 3 ? 1 : 0);
         // Passes of at most kSlabCap grains that end on chunk boundaries
@@ -416,7 +421,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 int kq2 = 0;
 #pragma unroll
                 for (int j = 1; j < 10; ++j) kq2 += gi >= koff[j] ? 1 : 0;
-                const int kd = TS ? kdec_cube<TS>(kg0 + kq2) : kdec[kg0 + kq2];
+                const int kd = FIX ? kdec_shape<TX, TY>(kg0 + kq2) : kdec[kg0 + kq2];
                 const int lx = kd & 1023, ly = (kd >> 10) & 1023, lz = kd >> 20;
                 const int zx = tc[0] * T0 + lx, zy = tc[1] * T1 + ly, zz = tc[2] * T2 + lz;
                 const int hx = lx + 1, hy = ly + (NB == 3 ? 1 : 0), hz = lz + (NC == 3 ? 1 : 0);
@@ -994,23 +999,38 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     return true;
 }
 
-template <int GEOM, int FLAT, int MODE, int TS = 0>
+template <int GEOM, int FLAT, int MODE, int TX = 0, int TY = 0, int TZ = 0>
 __global__ void __launch_bounds__(kSlabThreads, 2)
 step_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    slab_tile<GEOM, FLAT, MODE, TS>(TA, blockIdx.x, gridDim.x, smem_raw, false);
+    slab_tile<GEOM, FLAT, MODE, TX, TY, TZ>(TA, blockIdx.x, gridDim.x, smem_raw, false);
 }
 
 // Gas predictor on the slab layout (Sec. 3.1): one tile per block, the
 // chunk rule for grains whose x^n lies in their key zone, the per-grain rule
 // for the others.
-template <int GEOM, int FLAT, int TS = 0>
+template <int GEOM, int FLAT, int TX = 0, int TY = 0, int TZ = 0>
 __global__ void __launch_bounds__(kSlabThreads, 2)
 predict_slab_kernel(const __grid_constant__ TiledArgs<float> TA)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    slab_tile<GEOM, FLAT, 1, TS, true>(TA, blockIdx.x, gridDim.x, smem_raw, false);
+    slab_tile<GEOM, FLAT, 1, TX, TY, TZ, true>(TA, blockIdx.x, gridDim.x, smem_raw, false);
+}
+
+using SlabKernel = void (*)(TiledArgs<float>);
+
+// The step kernel's copy for this tile shape (slab_shape_id).
+template <int GEOM, int FLAT, int MODE>
+SlabKernel step_slab_pick(int shape)
+{
+    if constexpr (MODE == 1 && FLAT == 0) {
+        if (shape == SHAPE_8C) return step_slab_kernel<GEOM, FLAT, MODE, 8, 8, 8>;
+    } else if constexpr (MODE == 1 && FLAT == 1) {
+        if (shape == SHAPE_32X16) return step_slab_kernel<GEOM, FLAT, MODE, 32, 1, 16>;
+        if (shape == SHAPE_16X16) return step_slab_kernel<GEOM, FLAT, MODE, 16, 1, 16>;
+    }
+    return step_slab_kernel<GEOM, FLAT, MODE>;
 }
 
 inline size_t slab_smem_bytes(const GridDev &g)
@@ -1031,12 +1051,9 @@ cudaError_t launch_step_slab(const TiledArgs<float> &a, cudaStream_t s)
     const GridDev &g = a.s.g;
     const int ntiles = g.nt[0] * g.nt[1] * g.nt[2];
     const size_t smem = slab_smem_bytes(g);
-    // the default 8^3 tile of a 3-D grid with the exponential-midpoint
-    // pusher and TSC weights runs a copy compiled for that case
-    constexpr bool kCube = FLAT == 0 && MODE == 1;
-    const bool cube = kCube && g.T[0] == 8 && g.T[1] == 8 && g.T[2] == 8 && g.n[0] > 1 && g.n[1] > 1 &&
-                      g.n[2] > 1 && a.tsc == 1;
-    auto kern = cube ? step_slab_kernel<GEOM, FLAT, MODE, kCube ? 8 : 0> : step_slab_kernel<GEOM, FLAT, MODE>;
+    // the default tiles (TSC, exponential midpoint) run copies compiled for
+    // their shape
+    const SlabKernel kern = step_slab_pick<GEOM, FLAT, MODE>(slab_shape_id(g, FLAT, a.tsc, MODE));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<ntiles, kSlabThreads, smem, s>>>(a);
@@ -1049,9 +1066,9 @@ cudaError_t launch_predict_slab(const TiledArgs<float> &a, cudaStream_t s)
     const GridDev &g = a.s.g;
     const int ntiles = g.nt[0] * g.nt[1] * g.nt[2];
     const size_t smem = slab_smem_bytes(g);
-    const bool cube = FLAT == 0 && g.T[0] == 8 && g.T[1] == 8 && g.T[2] == 8 && g.n[0] > 1 && g.n[1] > 1 &&
-                      g.n[2] > 1 && a.tsc == 1;
-    auto kern = cube ? predict_slab_kernel<GEOM, FLAT, FLAT == 0 ? 8 : 0> : predict_slab_kernel<GEOM, FLAT>;
+    SlabKernel kern = predict_slab_kernel<GEOM, FLAT>;
+    if constexpr (FLAT == 0)
+        if (slab_shape_id(g, FLAT, a.tsc, 1) == SHAPE_8C) kern = predict_slab_kernel<GEOM, FLAT, 8, 8, 8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<ntiles, kSlabThreads, smem, s>>>(a);

@@ -16,6 +16,10 @@ template cudaError_t launch_step_slab<GEOM_CART, 2, 1>(const TiledArgs<float> &,
 
 template int batch_persistent_grid<GEOM_SB, 1, 1>(size_t);
 template cudaError_t launch_batch_persistent<GEOM_SB, 1, 1>(const BatchDev &, size_t, int, cudaStream_t);
+template int batch_persistent_grid<GEOM_SB, 1, 1, 32, 1, 16>(size_t);
+template cudaError_t launch_batch_persistent<GEOM_SB, 1, 1, 32, 1, 16>(const BatchDev &, size_t, int, cudaStream_t);
+template int batch_persistent_grid<GEOM_SB, 1, 1, 16, 1, 16>(size_t);
+template cudaError_t launch_batch_persistent<GEOM_SB, 1, 1, 16, 1, 16>(const BatchDev &, size_t, int, cudaStream_t);
 template int batch_persistent_grid<GEOM_CART, 2, 1>(size_t);
 template cudaError_t launch_batch_persistent<GEOM_CART, 2, 1>(const BatchDev &, size_t, int, cudaStream_t);
 

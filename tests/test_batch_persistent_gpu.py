@@ -18,8 +18,9 @@ from test_batch_gpu import _assert_same, _state
 pytestmark = pytest.mark.gpu
 
 
-def _make(D, w, sort_interval=1):
-    ctx = D.Context(w, precision=D.DUST_MIXED, sort_interval=sort_interval)
+def _make(D, w, sort_interval=1, tile=None):
+    kw = {} if tile is None else {"tile": tile}
+    ctx = D.Context(w, precision=D.DUST_MIXED, sort_interval=sort_interval, **kw)
     ctx.set_gas(w.rho, w.vgas)
     ctx.load(w.q, w.v, w.species, w.param)
     return ctx
@@ -64,6 +65,34 @@ def test_persistent_batch_equals_one_context_at_a_time(sort_interval):
             _assert_same(_state(c0), _state(c1), ("after eager", i))
             rc, _ = c1.sync(check=False)
             assert rc in (0, D.DUST_ECFL)
+    finally:
+        D.dust_batch_destroy(b)
+        for c in ref + bat:
+            c.close()
+
+
+@pytest.mark.parametrize("tile", [(16, 1, 16), (32, 1, 16)])
+def test_persistent_batch_with_a_compiled_tile_shape(tile):
+    """Every instance with the same 16 x 16 or 32 x 16 tile: the persistent
+    launch runs the copy compiled for that shape, and still gives the
+    one-at-a-time results bit for bit."""
+    from paper_1908_10793_gb300 import dust as D
+    if tile[0] == 16:
+        ws = [I.si2d_instance(k, "small") for k in (1, 2, 4, 5, 7, 8)]   # 16^2 and 24^2
+    else:
+        ws = [I.si2d_instance(k) for k in (0, 5, 10, 15)]               # 32^2, 1-16 per zone
+    ref = [_make(D, w, tile=tile) for w in ws]
+    bat = [_make(D, w, tile=tile) for w in ws]
+    b = D.dust_batch_create([c.handle for c in bat])
+    try:
+        dts = [w.dt for w in ws]
+        for nsteps in (3, 2):
+            D.dust_batch_step(b, dts, nsteps)
+            for c, x in zip(ref, dts):
+                for _ in range(nsteps):
+                    c.step(x)
+            for i, (c0, c1) in enumerate(zip(ref, bat)):
+                _assert_same(_state(c0), _state(c1), (tile, nsteps, i))
     finally:
         D.dust_batch_destroy(b)
         for c in ref + bat:
