@@ -866,6 +866,7 @@ cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
     ta.key_off = key_off;
     ta.tsc = weight == DUST_WEIGHT_TSC;
     const bool vol = (GEOM == GEOM_CYL || GEOM == GEOM_SPH) && weight == DUST_WEIGHT_VOLUME;
+    ta.vol = vol ? 1 : 0;
     ta.emit_keys = key_out != nullptr;
     ta.key_out = key_out;
     ta.count_out = count_out;
@@ -881,8 +882,7 @@ cudaError_t launch_step_geom(const StepArgs<Real> &a, int weight, int kernel,
     }
     if constexpr (sizeof(Real) == 4) {
         const int flat = slab_flat(a.g);
-        if ((kernel == DUST_KERNEL_AUTO || kernel == DUST_KERNEL_SLAB) && !vol &&
-            slab_available(GEOM, flat))
+        if ((kernel == DUST_KERNEL_AUTO || kernel == DUST_KERNEL_SLAB) && slab_available(GEOM, flat))
             return launch_slab_geom<GEOM>(ta, flat, s);
     }
     ta.emit_keys = 0;
@@ -899,7 +899,6 @@ inline bool step_emits_keys(const dust_ctx *ctx)
 {
     const int kn = ctx->opt.kernel;
     return ctx->mixed && (kn == DUST_KERNEL_AUTO || kn == DUST_KERNEL_SLAB) &&
-           !uses_volume_weights(ctx->geom.kind, ctx->opt.weight) &&
            slab_available(ctx->geom.kind, slab_flat(ctx->g));
 }
 
@@ -1028,6 +1027,7 @@ int run_step(dust_ctx *ctx, double dt)
                 pt.wait_extra_tx = ctx->opt.test_wait_timeout ? 16u : 0u;
                 pt.wait_ns = ctx->opt.test_wait_timeout ? 1000000ull : 0ull;
                 pt.tsc = ctx->opt.weight == DUST_WEIGHT_TSC;
+                pt.vol = uses_volume_weights(ctx->geom.kind, ctx->opt.weight) ? 1 : 0;
                 if constexpr (sizeof(Real) == 4) {
                     // on the slab layout where the step runs the slab kernel,
                     // over the store sorted by the zone at x^n
@@ -2111,6 +2111,7 @@ BatchInst batch_inst_of(dust_ctx *c, double dt, int test_timeout)
     a.status = c->d_status;
     a.tdev = c->d_time;
     ta.tsc = c->opt.weight == DUST_WEIGHT_TSC;
+    ta.vol = uses_volume_weights(c->geom.kind, c->opt.weight) ? 1 : 0;
     ta.gas_tmap = c->tmap_ok[0] ? static_cast<const void *>(c->d_tmaps) : nullptr;
     ta.wait_extra_tx = (c->opt.test_wait_timeout || test_timeout) ? 16u : 0u;
     ta.wait_ns = (c->opt.test_wait_timeout || test_timeout) ? 1000000ull : 0ull;

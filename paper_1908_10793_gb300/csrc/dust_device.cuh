@@ -251,6 +251,24 @@ __device__ __forceinline__ void w_volume(const GridDev &g, int d, double x, int 
     w[1] = (R)(1.0 - lo - hi);
 }
 
+// Eq. CIC_vol in single precision relative to the host zone's centre c, for
+// a coordinate x = c + u inside the zone: the shell volume between c and x
+// (written so that it stays accurate for small u) times the inverse shell
+// volume between c and the neighbouring node on that side (ivl, ivh, from
+// vol_shell and vol_node in double precision).  d = 0: the radius
+// (cylindrical R^2, spherical r^3); d = 1: the spherical polar angle.
+template <int GEOM>
+__device__ __forceinline__ void w_vol_f(int d, float u, float c, float ivl, float ivh, float w[3])
+{
+    float num;
+    if (GEOM == GEOM_SPH && d == 1) num = 2.f * sinf(c + 0.5f * u) * sinf(0.5f * fabsf(u));
+    else if (GEOM == GEOM_SPH) num = fabsf(u) * (3.f * c * c + 3.f * c * u + u * u);
+    else num = fabsf(u) * (2.f * c + u);
+    w[0] = u < 0.f ? num * ivl : 0.f;
+    w[2] = u > 0.f ? num * ivh : 0.f;
+    w[1] = 1.f - w[0] - w[2];
+}
+
 // Host zone and weights of direction d for coordinate x.  wk: 0 CIC, 1 TSC,
 // 2 volume weighting (plain CIC in the directions whose volume coordinate
 // is the coordinate itself).

@@ -128,6 +128,8 @@ struct TiledArgs {
     StepArgs<Real> s;
     const int32_t *key_off;       // [nkeys + 1] start of each key in the sorted store
     int tsc;                      // 1: TSC weights, 0: CIC
+    int vol;                      // 1: volume weighting (Eq. CIC_vol) in the
+                                  // curvilinear directions, CIC elsewhere (tsc 0)
     // optional: the step kernel predicts every grain's key for the next sort
     int emit_keys;
     int32_t *key_out;             // [n]

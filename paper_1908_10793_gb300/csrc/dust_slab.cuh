@@ -200,9 +200,10 @@ struct SlabExact {
     int host[3];
 };
 
+// wk: the weighting (0 CIC, 1 TSC, 2 volume weighting).
 template <int GEOM>
 __device__ __noinline__ bool slab_exact_first_half(const GridDev &g, const PhysDev &ph, double shift,
-                                                   int tsc, float h, SlabExact &e)
+                                                   int wk, float h, SlabExact &e)
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d) e.inc[d] = 0.f;
@@ -210,9 +211,7 @@ __device__ __noinline__ bool slab_exact_first_half(const GridDev &g, const PhysD
     if (!apply_bc<float, GEOM>(g, ph, shift, e.q, e.p)) return false;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        // CIC or TSC only (the slab kernel does not run volume weighting):
-        // the mask lets the compiler drop the volume branch
-        zone_weights<float, GEOM>(g, d, tsc & 1, e.q[d], e.host[d], e.w[d], e.iw[d]);
+        zone_weights<float, GEOM>(g, d, wk, e.q[d], e.host[d], e.w[d], e.iw[d]);
         e.qf[d] = (float)e.q[d];
     }
     return true;
@@ -259,6 +258,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     // gridded directions, and the weights (the shape copies run TSC)
     auto gd = [&](int d) { return FIX ? (d == 0 || (d == 1 ? FLAT != 1 : FLAT != 2)) : g.n[d] > 1; };
     const int tsc = FIX ? 1 : TA.tsc;
+    const bool vol = FIX ? false : TA.vol != 0;
     // the inline push reads ph; the rare out-of-line paths read the kernel
     // argument (the same values)
     PhysDev ph = A.ph;
@@ -322,8 +322,11 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     float *szif = szcf + tsum;
     float *sznu = szif + tsum;          // [T0]
     float *szlo = sznu + T0;        // [T1 + 1]
+    // volume weighting: inverse shell volumes to the lower and upper
+    // neighbouring nodes, radial zones then polar zones ([2 (T0 + T1)])
+    float *szvl = szlo + T1 + 1, *szvh = szvl + T0 + T1;
     unsigned long long *sbar = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(szlo + T1 + 1) + 7) & ~(uintptr_t)7);
+        (reinterpret_cast<uintptr_t>(szvh + T0 + T1) + 7) & ~(uintptr_t)7);
     // the gas box by one bulk tensor copy, overlapping the tables below
     gas_box_begin<float>(TA.gas_tmap, sgas, o, bvol, sbar, TA.wait_extra_tx);
     for (int t = threadIdx.x; t < tsum + T1 + 1; t += blockDim.x) {
@@ -338,6 +341,20 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
         } else if (GEOM == GEOM_SPH) {
             const int z = tc[1] * T1 + (t - tsum);
             szlo[t - tsum] = (g.n[1] > 1 && z <= g.n[1]) ? g.zlo_f[1][z] : 0.f;
+        }
+    }
+    if ((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && vol) {
+        for (int t = threadIdx.x; t < T0 + (GEOM == GEOM_SPH ? T1 : 0); t += blockDim.x) {
+            const int d = t < T0 ? 0 : 1;
+            const int z = d == 0 ? tc[0] * T0 + t : tc[1] * T1 + (t - T0);
+            float vl = 0.f, vh = 0.f;
+            if (z < g.n[d]) {
+                const double c = g.zc[d][z];
+                vl = (float)(1.0 / vol_shell<GEOM>(d, vol_node(g, d, z - 1), c));
+                vh = (float)(1.0 / vol_shell<GEOM>(d, c, vol_node(g, d, z + 1)));
+            }
+            szvl[t] = vl;
+            szvh[t] = vh;
         }
     }
     for (int k = threadIdx.x; k < tvol; k += blockDim.x) {
@@ -435,7 +452,18 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     zcf[d] = szcf[lid[d]];
                     zif[d] = szif[lid[d]];
                 }
-                if (GEOM == GEOM_CYL || GEOM == GEOM_SPH) znu = sznu[lx];
+                float zvl[2] = {0.f, 0.f}, zvh[2] = {0.f, 0.f};
+                if (GEOM == GEOM_CYL || GEOM == GEOM_SPH) {
+                    znu = sznu[lx];
+                    if (vol) {
+                        zvl[0] = szvl[lx];
+                        zvh[0] = szvh[lx];
+                        if (GEOM == GEOM_SPH) {
+                            zvl[1] = szvl[T0 + ly];
+                            zvh[1] = szvh[T0 + ly];
+                        }
+                    }
+                }
                 if (GEOM == GEOM_SPH) {
                     zlo = szlo[ly];
                     zhi = szlo[ly + 1];
@@ -477,10 +505,12 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             for (int d = 0; d < 3; ++d) {
                                 if (!gd(d)) continue;
                                 if ((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && d == 0) {
-                                    if (GEOM == GEOM_CYL) w_cyl<float>(tsc, dl[0], znu, w[0]);
+                                    if (vol) w_vol_f<GEOM>(0, u[0], zcf[0], zvl[0], zvh[0], w[0]);
+                                    else if (GEOM == GEOM_CYL) w_cyl<float>(tsc, dl[0], znu, w[0]);
                                     else w_sphr<float>(tsc, dl[0], znu, w[0]);
                                 } else if (GEOM == GEOM_SPH && d == 1) {
-                                    w_theta<float>(tsc, qf[1], zlo, zhi, u[1], zhw, w[1]);
+                                    if (vol) w_vol_f<GEOM>(1, u[1], zcf[1], zvl[1], zvh[1], w[1]);
+                                    else w_theta<float>(tsc, qf[1], zlo, zhi, u[1], zhw, w[1]);
                                 } else {
                                     w_cart<float>(tsc, dl[d], w[d]);
                                 }
@@ -489,7 +519,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
 #pragma unroll
                             for (int d = 0; d < 3; ++d) {
                                 float iwd;
-                                zone_weights<float, GEOM>(g, d, tsc & 1, q[d], host[d], w[d], iwd);
+                                zone_weights<float, GEOM>(g, d, vol ? 2 : (tsc & 1), q[d], host[d], w[d], iwd);
                                 qf[d] = (float)q[d];
                                 int l = host[d] - o[d];
                                 if (gd(d) && g.bc[d] == DUST_BC_PERIODIC) {
@@ -580,10 +610,12 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                                 iw[d] = zif[d];
                                 if (!gd(d)) continue;
                                 if ((GEOM == GEOM_CYL || GEOM == GEOM_SPH) && d == 0) {
-                                    if (GEOM == GEOM_CYL) w_cyl<float>(tsc, dl[0], znu, w[0]);
+                                    if (vol) w_vol_f<GEOM>(0, u[0], zcf[0], zvl[0], zvh[0], w[0]);
+                                    else if (GEOM == GEOM_CYL) w_cyl<float>(tsc, dl[0], znu, w[0]);
                                     else w_sphr<float>(tsc, dl[0], znu, w[0]);
                                 } else if (GEOM == GEOM_SPH && d == 1) {
-                                    w_theta<float>(tsc, qf[1], zlo, zhi, u[1], zhw, w[1]);
+                                    if (vol) w_vol_f<GEOM>(1, u[1], zcf[1], zvl[1], zvh[1], w[1]);
+                                    else w_theta<float>(tsc, qf[1], zlo, zhi, u[1], zhw, w[1]);
                                 } else {
                                     w_cart<float>(tsc, dl[d], w[d]);
                                 }
@@ -594,7 +626,8 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             SlabExact ex;
 #pragma unroll
                             for (int d = 0; d < 3; ++d) { ex.q[d] = q[d]; ex.p[d] = pn[d]; }
-                            const bool in = slab_exact_first_half<GEOM>(g, A.ph, shift_mid_of(A), tsc, h, ex);
+                            const bool in = slab_exact_first_half<GEOM>(g, A.ph, shift_mid_of(A), vol ? 2 : (tsc & 1),
+                                                                        h, ex);
 #pragma unroll
                             for (int d = 0; d < 3; ++d) { q[d] = ex.q[d]; pn[d] = ex.p[d]; inc1[d] = ex.inc[d]; }
                             if (!in) {
@@ -1042,6 +1075,7 @@ inline size_t slab_smem_bytes(const GridDev &g)
            (size_t)((g.tvol + 31) & ~31) * sizeof(int) +
            (size_t)(kSlabThreads / 32) * kRecFields * kRecStride * sizeof(float) +
            tsum * (sizeof(double) + 2 * sizeof(float)) + ((size_t)g.T[0] + g.T[1] + 1) * sizeof(float) +
+           2 * ((size_t)g.T[0] + g.T[1]) * sizeof(float) +
            16;  // the bulk copy's transaction barrier (8-byte aligned)
 }
 

@@ -518,9 +518,10 @@ VOLUME_WORKLOADS = {
 @pytest.mark.parametrize("name", list(VOLUME_WORKLOADS))
 @pytest.mark.parametrize("precision", [FP64, MIXED])
 def test_parity_volume_weighting(name, precision):
-    """Traditional volume weighting (Eq. CIC_vol) on the tiled kernel (two
-    steps) and the one-thread-per-grain kernel (one step) against the
-    oracle's."""
+    """Traditional volume weighting (Eq. CIC_vol) against the oracle's: the
+    default kernel (two steps; the slab kernel with single-precision volume
+    weights in mixed precision, the tiled kernel in FP64) and the
+    one-thread-per-grain kernel (one step)."""
     from paper_1908_10793_gb300 import dust as D
     w = VOLUME_WORKLOADS[name]()
     w.weight = I.VOLUME
@@ -528,7 +529,8 @@ def test_parity_volume_weighting(name, precision):
     compare(w, 1, precision, kernel=D.DUST_KERNEL_PER_GRAIN)
 
 
-def test_parity_volume_weighting_with_gas_predictor():
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_parity_volume_weighting_with_gas_predictor(precision):
     from parity_util import zone_volumes
     w = WORKLOADS["cyldisk"]()
     w.weight = I.VOLUME
@@ -536,7 +538,7 @@ def test_parity_volume_weighting_with_gas_predictor():
     nz = _grains_per_zone_max(w) * 27
     quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
     dgas = (nz * 0.5 * quantum / (w.rho * zone_volumes(w))).max()
-    compare(w, steps, FP64, feedback=1, predictor=True, extra_v=4 * steps * dgas)
+    compare(w, steps, precision, feedback=1, predictor=True, extra_v=4 * steps * dgas)
 
 
 @pytest.mark.parametrize("precision", [FP64, MIXED])
