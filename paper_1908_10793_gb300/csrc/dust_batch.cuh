@@ -147,6 +147,14 @@ __device__ __forceinline__ BatchSort sort_of(const BatchInst &I, const StepState
     return a;
 }
 
+// One tile of the persistent kernel, out of line: the tile function then
+// gets its own register allocation instead of sharing the persistent loop's.
+template <int GEOM, int FLAT, int MODE, int TX, int TY, int TZ>
+__device__ __noinline__ bool batch_tile(const TiledArgs<float> &TA, int tile, int ntile, unsigned char *smem_raw)
+{
+    return slab_tile<GEOM, FLAT, MODE, TX, TY, TZ>(TA, tile, ntile, smem_raw, true);
+}
+
 }  // namespace
 
 template <int GEOM, int FLAT, int MODE, int TX, int TY, int TZ>
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
                 A.count_out = emit ? I.count[st.coff ^ 1] : nullptr;
             }
             __syncthreads();
-            const bool in_time = slab_tile<GEOM, FLAT, MODE, TX, TY, TZ>(*sTA, li, I.ntiles, smem_raw, true);
+            const bool in_time = batch_tile<GEOM, FLAT, MODE, TX, TY, TZ>(*sTA, li, I.ntiles, smem_raw);
             if (!in_time) {
                 // the gas box did not arrive in time: stop this block; tasks
                 // that wait for this one run out of time too
