@@ -933,8 +933,8 @@ cudaError_t launch_predict(int geom, int weight, const StepArgs<Real> &pa, const
 }
 
 // The gas predictor's sort: the live store (the current store, before any
-// pending gather) ordered by the key of the zone at x^n (the key kernel with
-// no drift), grains in id order inside a zone, as the pairs d_ppair_id /
+// pending gather) ordered by the key of the zone at x^n (zone_keys_kernel:
+// the key kernel's keys with no drift), grains in id order inside a zone, as the pairs d_ppair_id /
 // d_ppair_src with the zone offsets d_pcount.  The scratch of its block sort
 // is the other store's id column, which the step writes afterwards.
 int run_predictor_sort(dust_ctx *ctx)
@@ -958,10 +958,10 @@ int run_predictor_sort(dust_ctx *ctx)
     CU(cudaMemsetAsync(ctx->d_pcount, 0, m * sizeof(int32_t), ctx->stream));
     cudaError_t e = cudaSuccess;
     switch (ctx->geom.kind) {
-    case DUST_CARTESIAN: e = launch_sort_keys<float, GEOM_CART>(a, ctx->stream); break;
-    case DUST_SHEARING_BOX: e = launch_sort_keys<float, GEOM_SB>(a, ctx->stream); break;
-    case DUST_CYLINDRICAL: e = launch_sort_keys<float, GEOM_CYL>(a, ctx->stream); break;
-    default: e = launch_sort_keys<float, GEOM_SPH>(a, ctx->stream); break;
+    case DUST_CARTESIAN: e = launch_zone_keys<GEOM_CART>(a, ctx->stream); break;
+    case DUST_SHEARING_BOX: e = launch_zone_keys<GEOM_SB>(a, ctx->stream); break;
+    case DUST_CYLINDRICAL: e = launch_zone_keys<GEOM_CYL>(a, ctx->stream); break;
+    default: e = launch_zone_keys<GEOM_SPH>(a, ctx->stream); break;
     }
     CU(e);
     CU(launch_exclusive_scan(ctx->d_pcount, m, ctx->d_blocksums, ctx->stream));

@@ -16,6 +16,7 @@ template cudaError_t launch_step_slab<GEOM_CART, 0, 1>(const TiledArgs<float> &,
 template cudaError_t launch_step_slab<GEOM_CART, 2, 0>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_slab<GEOM_CART, 0>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_slab<GEOM_CART, 2>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_zone_keys<GEOM_CART>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_CART>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_CART>(const SortArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_tiled<float, GEOM_CART, 0>(const TiledArgs<float> &, cudaStream_t);

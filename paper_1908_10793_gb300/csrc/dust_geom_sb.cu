@@ -22,6 +22,7 @@ template cudaError_t launch_step_slab<GEOM_SB, 2, 2>(const TiledArgs<float> &, c
 template cudaError_t launch_predict_slab<GEOM_SB, 0>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_slab<GEOM_SB, 1>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_slab<GEOM_SB, 2>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_zone_keys<GEOM_SB>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_SB>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_SB>(const SortArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_tiled<float, GEOM_SB, 0>(const TiledArgs<float> &, cudaStream_t);

@@ -13,6 +13,7 @@ template cudaError_t launch_step_tiled<double, GEOM_SPH, 0>(const TiledArgs<doub
 template cudaError_t launch_step_tiled<double, GEOM_SPH, 1>(const TiledArgs<double> &, cudaStream_t);
 template cudaError_t launch_step_slab<GEOM_SPH, 0, 1>(const TiledArgs<float> &, cudaStream_t);
 template cudaError_t launch_predict_slab<GEOM_SPH, 0>(const TiledArgs<float> &, cudaStream_t);
+template cudaError_t launch_zone_keys<GEOM_SPH>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<float, GEOM_SPH>(const SortArgs<float> &, cudaStream_t);
 template cudaError_t launch_sort_keys<double, GEOM_SPH>(const SortArgs<double> &, cudaStream_t);
 template cudaError_t launch_predict_tiled<float, GEOM_SPH, 0>(const TiledArgs<float> &, cudaStream_t);

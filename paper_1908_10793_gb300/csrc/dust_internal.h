@@ -326,6 +326,10 @@ cudaError_t launch_predict_slab(const TiledArgs<float> &a, cudaStream_t s);
 template <typename Real, int GEOM>
 cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s);
 
+// Keys of the zones at x^n (the gas predictor's sort), one per geometry.
+template <int GEOM>
+cudaError_t launch_zone_keys(const SortArgs<float> &a, cudaStream_t s);
+
 template <typename Real, int GEOM, int WEIGHT>
 cudaError_t launch_predict_gas(const StepArgs<Real> &a, cudaStream_t s);
 

@@ -564,7 +564,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 bool live = false, ingroup = false, gone = false;
                 {
                     q[0] = S.q[0][src]; q[1] = S.q[1][src]; q[2] = S.q[2][src];
-                    live = (__double_as_longlong(q[0]) & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll;  // not NaN
+                    live = !isnan(q[0]);
                     if (live) {
                         pn[0] = S.p[0][src]; pn[1] = S.p[1][src]; pn[2] = S.p[2][src];
                         sp = S.species ? S.species[src] : 0;

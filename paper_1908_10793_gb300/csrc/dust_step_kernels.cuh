@@ -360,6 +360,93 @@ cudaError_t launch_deposit_mass(const GridDev &g, const SpeciesDev &sp, int wk, 
     return cudaGetLastError();
 }
 
+// Single-precision estimate of a double from its bit fields (the mantissa
+// truncated; magnitudes outside the single range clamped): no
+// double-precision instruction.  Only an estimate: zone_at corrects it with
+// exact comparisons of integer order keys.
+__device__ __forceinline__ float float_estimate(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned hi = (unsigned)((unsigned long long)b >> 32);
+    const int e = (int)((hi >> 20) & 0x7ff) - 1023 + 127;
+    const unsigned sign = hi & 0x80000000u;
+    if (e <= 0) return __int_as_float((int)sign);
+    if (e >= 255) return __int_as_float((int)(sign | 0x7f7fffffu));
+    const unsigned m = (unsigned)((unsigned long long)b >> 29) & 0x7fffffu;
+    return __int_as_float((int)(sign | ((unsigned)e << 23) | m));
+}
+
+// Zone of x in direction d, exactly as locate() finds it, with the estimate
+// taken from float_estimate.
+__device__ __forceinline__ int zone_at(const GridDev &g, int d, double x)
+{
+    const int n = g.n[d];
+    if (n <= 1) return 0;
+    const long long *ek = g.ekey[d];
+    const long long kx = order_key(x);
+    int i;
+    if (g.edge_kind[d] == EDGE_UNIFORM) {
+        i = (int)floorf((float_estimate(x) - (float)g.lo[d]) * g.inv_df[d]);
+    } else if (g.edge_kind[d] == EDGE_LOG) {
+        i = (int)floorf((logf(float_estimate(x)) - g.log_lo_f[d]) * g.inv_df[d]);
+    } else {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (ek[mid] <= kx) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+    i = i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+    for (int it = 0; it < 8 && i > 0 && kx < ek[i]; ++it) --i;
+    for (int it = 0; it < 8 && i < n - 1 && kx >= ek[i + 1]; ++it) ++i;
+    // the bounded walk could stop short only for an estimate far off, which
+    // the truncation does not produce for a coordinate inside the grid;
+    // fall back to the exact search if it did
+    if ((i > 0 && kx < ek[i]) || (i < n - 1 && kx >= ek[i + 1])) return locate(g, d, x);
+    return i;
+}
+
+// Keys of the zones at x^n (the gas predictor's sort): the key kernel with
+// no drift, without double-precision arithmetic for grains inside the grid.
+// Grains outside the grid take predict_key with no drift (the same clamping
+// and wrapping); the keys equal predict_key's for every grain.
+template <int GEOM>
+__global__ void zone_keys_kernel(const SortArgs<float> A)
+{
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = gi < A.src.n;
+    int32_t key = valid ? (int32_t)A.g.nkeys : -1;
+    double q[3] = {0.0, 0.0, 0.0};
+    if (valid) {
+        q[0] = A.src.q[0][gi]; q[1] = A.src.q[1][gi]; q[2] = A.src.q[2][gi];
+    }
+    if (valid && (__double_as_longlong(q[0]) & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll) {
+        // -0 as +0, as the no-drift update q + 0 leaves it in predict_key
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (__double_as_longlong(q[d]) == (long long)0x8000000000000000ull) q[d] = 0.0;
+        if (inside(A.g, 0, q[0]) && inside(A.g, 1, q[1]) && inside(A.g, 2, q[2])) {
+            key = (int32_t)zone_key(A.g, zone_at(A.g, 0, q[0]), zone_at(A.g, 1, q[1]), zone_at(A.g, 2, q[2]));
+        } else {
+            const float p[3] = {0.f, 0.f, 0.f};
+            key = predict_key<float, GEOM>(A.g, A.ph, q, p, 0.f);
+        }
+    }
+    if (valid) A.key[gi] = key;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&A.count[key], __popc(peers));
+}
+
+template <int GEOM>
+cudaError_t launch_zone_keys(const SortArgs<float> &a, cudaStream_t s)
+{
+    if (a.src.n == 0) return cudaSuccess;
+    const int64_t blocks = (a.src.n + 255) / 256;
+    zone_keys_kernel<GEOM><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename Real, int GEOM>
 cudaError_t launch_sort_keys(const SortArgs<Real> &a, cudaStream_t s)
 {
