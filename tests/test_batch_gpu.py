@@ -21,8 +21,8 @@ def _instances():
     return ws
 
 
-def _make(D, w, precision):
-    ctx = D.Context(w, precision=precision, sort_interval=1)
+def _make(D, w, precision, **kw):
+    ctx = D.Context(w, precision=precision, sort_interval=1, **kw)
     ctx.set_gas(w.rho, w.vgas)
     ctx.load(w.q, w.v, w.species, w.param)
     return ctx
@@ -78,6 +78,41 @@ def test_batch_equals_one_context_at_a_time(precision):
         for i, (c0, c1) in enumerate(zip(ref, bat)):
             _assert_same(_state(c0), _state(c1), ("after eager", i))
         assert _state(bat[5])[4].n_removed >= 50
+    finally:
+        D.dust_batch_destroy(b)
+        for c in ref + bat:
+            c.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_with_the_gas_predictor_equals_one_context_at_a_time(precision):
+    """The gas predictor inside the captured graph (in mixed precision with its
+    own sort by the zone at x^n): grains, gas and deposit bit for bit as the
+    contexts stepped one at a time, across replays, an odd step count and
+    eager steps in between."""
+    from paper_1908_10793_gb300 import dust as D
+    ws = [I.si2d_instance(k, "small") for k in range(4)] + [I.subsample(I.cyldisk("small"), 3000)]
+    ref = [_make(D, w, precision, gas_predictor=1) for w in ws]
+    bat = [_make(D, w, precision, gas_predictor=1) for w in ws]
+    b = D.dust_batch_create([c.handle for c in bat])
+    try:
+        dts = [w.dt for w in ws]
+        for nsteps in (4, 3):
+            D.dust_batch_step(b, dts, nsteps)
+            for c, x in zip(ref, dts):
+                for _ in range(nsteps):
+                    c.step(x)
+            for i, (c0, c1) in enumerate(zip(ref, bat)):
+                _assert_same(_state(c0), _state(c1), (nsteps, i))
+        for c0, c1, x in zip(ref, bat, dts):
+            c0.step(x)
+            c1.step(x)
+        D.dust_batch_step(b, dts, 2)
+        for c, x in zip(ref, dts):
+            c.step(x)
+            c.step(x)
+        for i, (c0, c1) in enumerate(zip(ref, bat)):
+            _assert_same(_state(c0), _state(c1), ("after eager", i))
     finally:
         D.dust_batch_destroy(b)
         for c in ref + bat:
