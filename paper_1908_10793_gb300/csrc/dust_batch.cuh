@@ -96,18 +96,6 @@ __device__ __forceinline__ void signal_done(int *count)
     }
 }
 
-// Task of work item w (largest t with tasks[t].begin <= w).
-__device__ __forceinline__ int task_of(const BatchDev &B, int w)
-{
-    int lo = 0, hi = B.ntasks;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (B.tasks[mid].begin <= w) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // Per-instance state of step s: which store is current, which count buffer
 // holds the offsets of the last sort (and which the next sort's counts).
 struct StepState {
@@ -167,18 +155,46 @@ __global__ void __launch_bounds__(kSlabThreads, 2) batch_persistent_kernel(const
     int *s_item = reinterpret_cast<int *>(smem_raw + B.ta_offset + sizeof(TiledArgs<float>));
     bool ok = true;
 
+    // the block takes items in increasing order, so the task of its next item
+    // is at or after the task of its last one; and a task the block has
+    // already waited for needs no second wait
+    int tcache = 0, verified = -1;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) *s_item = atomicAdd(B.grab, 1);
+        if (threadIdx.x < 32) {
+            const unsigned FULL = 0xffffffffu;
+            const int lane = threadIdx.x;
+            int w = lane == 0 ? atomicAdd(B.grab, 1) : 0;
+            w = __shfl_sync(FULL, w, 0);
+            int t = tcache;
+            if (w < B.nitems) {
+                // tasks start in increasing order: the tasks after t that
+                // start at or before w form a prefix, 32 looked at at once
+                for (;;) {
+                    const int j = t + 1 + lane;
+                    const unsigned m = __ballot_sync(FULL, j < B.ntasks && B.tasks[j].begin <= w);
+                    t += __popc(m);
+                    if (m != FULL) break;
+                }
+            }
+            if (lane == 0) {
+                s_item[0] = w;
+                s_item[1] = t;
+            }
+        }
         __syncthreads();
-        const int w = *s_item;
+        const int w = s_item[0];
         if (w >= B.nitems) break;
-        const int t = task_of(B, w);
+        const int t = s_item[1];
+        tcache = t;
         const BatchTask T = B.tasks[t];
         // the group's previous task must be complete
-        if (T.dep >= 0 && !wait_count(B.done + T.dep, B.tasks[T.dep].items + B.wait_extra, B.wait_ns)) {
-            ok = false;
-            break;
+        if (T.dep >= 0 && T.dep != verified) {
+            if (!wait_count(B.done + T.dep, B.tasks[T.dep].items + B.wait_extra, B.wait_ns)) {
+                ok = false;
+                break;
+            }
+            verified = T.dep;
         }
         const int s = T.s, p = T.p;
         const bool sorted = (s % K) == 0;
