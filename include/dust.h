@@ -327,22 +327,31 @@ int dust_step_noalloc(const dust_geometry *geom, const dust_grid *grid,
 /* ---- batched stepping ---------------------------------------------------
  * Many independent contexts (instances with their own grids, sizes, species
  * and step lengths, e.g. a set of streaming-instability shearing boxes,
- * Sec. 4.3) advanced together.  dust_batch_step captures, once, one period of
- * two steps of every instance into a CUDA graph (each instance a branch on
- * its own stream: sort, deposit clear, step kernel, feedback, time advance)
- * and replays it nsteps / 2 times with one launch each; an odd last step is
- * taken with dust_step.  Results equal those of calling dust_step on each
- * context with the same dt (captured steps sort before every step and read
- * their time from the device).  The graph is captured again when a dt
- * changes, particles are reloaded, or a context was stepped on its own in
- * between.  Per-group timing (dust_options.timing) is not recorded for
- * captured steps.  Contexts must be on one device and on streams that can
- * be captured (not the legacy default stream); the batch does not own them
- * and must be destroyed before them. */
+ * Sec. 4.3) advanced together, in one of two ways (dust_options.batch_mode):
+ *  - one persistent launch per dust_batch_step call (the default where
+ *    every instance allows it, see batch_mode): a cooperative kernel takes
+ *    the sort, step and feedback work items of all instances and steps from
+ *    one work list, each waiting (bounded in time) only for the work its
+ *    instance's previous phase did; a wait that runs out makes every
+ *    instance report DUST_ETIMEOUT at its next dust_sync;
+ *  - a CUDA graph: dust_batch_step captures, once, one period of two steps
+ *    of every instance (each instance a branch on its own stream: sort,
+ *    deposit clear, step kernel, feedback, time advance) and replays it
+ *    nsteps / 2 times with one launch each; an odd last step is taken with
+ *    dust_step.  The graph is captured again when a dt changes, particles
+ *    are reloaded, or a context was stepped on its own in between.
+ * Results equal, bit for bit, those of calling dust_step on each context
+ * with the same dt (the graph sorts before every step; the persistent launch
+ * at the batch's sort interval, as contexts with that sort_interval do).
+ * Per-group timing (dust_options.timing) is not recorded for batched steps.
+ * Contexts must be on one device and on streams that can be captured (not
+ * the legacy default stream); the batch does not own them and must be
+ * destroyed before them. */
 typedef struct dust_batch dust_batch;
 
 /* insts: n (1..4096) distinct contexts.  opt may be NULL; opt->stream, if
- * set, is the stream the graph is launched on (else the batch creates one).
+ * set, is the stream the batch's work is launched on (else the batch creates
+ * one); opt->batch_mode and opt->sort_interval choose the way (above).
  * Errors: DUST_EINVAL, DUST_ECUDA, DUST_ENOMEM (message:
  * dust_batch_last_error(NULL)). */
 int dust_batch_create(dust_batch **out, dust_ctx *const *insts, int n, const dust_options *opt);
