@@ -968,7 +968,9 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
             }
             __syncwarp();
 
-            // ---- quantise the chunk and add it to the deposit box
+            // ---- quantise the chunk and add it to the deposit box (the
+            // predictor's impulse has no energy channel)
+            constexpr int NCH = PRED ? 3 : 4;
             long long ps[4] = {0, 0, 0, 0};
             if (own) {
 #pragma unroll
@@ -978,7 +980,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         if (a == 1 && b == Sh::BC && c == Sh::CC) continue;  // host: remainder
                         const int lin = (ohx + a - 1) + B[0] * ((ohy + b - Sh::BC) + B[1] * (ohz + c - Sh::CC));
 #pragma unroll
-                        for (int ch = 0; ch < 4; ++ch) {
+                        for (int ch = 0; ch < NCH; ++ch) {
                             const float v = (ch & 1) ? acc[b][c][ch >> 1].y : acc[b][c][ch >> 1].x;
                             big |= !(fabsf(v) < 4.5e15f);
                             const long long piece = rround(v);
@@ -990,7 +992,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     }
             }
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
+            for (int ch = 0; ch < NCH; ++ch) {
                 const long long s1 = __shfl_sync(FULL, ps[ch], base + 0);
                 const long long s2 = __shfl_sync(FULL, ps[ch], base + 2);
                 if (a == 1 && own) {
