@@ -137,10 +137,13 @@ typedef struct dust_options {
     int weight;            /* DUST_WEIGHT_CIC, DUST_WEIGHT_TSC or DUST_WEIGHT_VOLUME */
     int feedback_apply;    /* 1: add the deposit to the gas momentum each step  */
     double quantum;        /* fixed-point quantum of the deposit (momentum
-                              units); 0 = 2^-44 * (largest species mass): a
-                              grain's velocity change of up to 256 code units
-                              per step stays below 2^52 quanta, and zone sums
-                              of a few thousand pieces fit int64              */
+                              units); 0 = the default: 2^-44 * (largest
+                              species mass) with DUST_FP64 (a grain's velocity
+                              change of up to 256 code units per step stays
+                              below 2^52 quanta, and zone sums of a few
+                              thousand pieces fit int64), 2^-40 * (largest
+                              species mass) with DUST_MIXED (still finer than
+                              the single-precision sums it rounds)          */
     void *stream;          /* cudaStream_t to enqueue on; NULL = own stream     */
     int sort_interval;     /* re-sort grains by zone every k steps (0 = 1)      */
     int kernel;            /* DUST_KERNEL_*                                     */

@@ -219,9 +219,10 @@ int validate_descriptors(const dust_geometry *geom, const dust_grid *grid,
     return DUST_OK;
 }
 
-// Species constants; quantum <= 0 selects the default 2^-44 * largest mass.
+// Species constants; quantum <= 0 selects the default: 2^-44 * largest mass
+// (FP64), 2^-40 * largest mass (mixed precision, default_exp -40).
 SpeciesDev make_species(const dust_species *species, int n_species, double quantum,
-                        double *quantum_out)
+                        double *quantum_out, int default_exp = -44)
 {
     SpeciesDev sp{};
     double mmax = 0.0;
@@ -232,7 +233,7 @@ SpeciesDev make_species(const dust_species *species, int n_species, double quant
         sp.mode[s] = species[s].tau_mode;
         mmax = fmax(mmax, fabs(species[s].mass));
     }
-    const double qu = quantum > 0.0 ? quantum : ldexp(mmax > 0 ? mmax : 1.0, -44);
+    const double qu = quantum > 0.0 ? quantum : ldexp(mmax > 0 ? mmax : 1.0, default_exp);
     for (int s = 0; s < n_species; ++s) {
         sp.mq[s] = species[s].mass / qu;
         sp.mqf[s] = (float)sp.mq[s];
@@ -1187,7 +1188,7 @@ extern "C" int dust_create(dust_ctx **out, const dust_geometry *geom, const dust
     ctx->device = opt->device;
     ctx->ncell = ncell;
     ctx->sort_interval = opt->sort_interval > 0 ? opt->sort_interval : 1;
-    ctx->sp = make_species(species, n_species, opt->quantum, &ctx->quantum);
+    ctx->sp = make_species(species, n_species, opt->quantum, &ctx->quantum, ctx->mixed ? -40 : -44);
 
     auto bail = [&](int code) {
         std::string msg = ctx->err;

@@ -932,6 +932,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
             // FMA and add (each lane rounded once, as the scalar operations)
             float2 acc[NB][NC][2];
             float2 S2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float Sabs = 0.f;  // sum over the chunk of the largest |channel| of each grain
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -958,6 +959,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     }
                     S2[0] = __fadd2_rn(S2[0], De01);
                     S2[1] = __fadd2_rn(S2[1], De23);
+                    Sabs += fmaxf(fmaxf(fabsf(De01.x), fabsf(De01.y)), fmaxf(fabsf(De23.x), fabsf(De23.y)));
                 };
                 int sl = s0;
                 for (; sl + 1 < s1; sl += 2) {
@@ -972,7 +974,14 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
             // predictor's impulse has no energy channel)
             constexpr int NCH = PRED ? 3 : 4;
             long long ps[4] = {0, 0, 0, 0};
-            if (own) {
+            // every chunk sum of a channel is at most the sum of the grains'
+            // |impulse| in it (the weights lie in [0, 1]); below 2^31 (with a
+            // margin for the sums' rounding) the 32-bit rounding instruction
+            // gives the same integer as the 64-bit one, at a fraction of its
+            // cost on this GPU.  Decided for the whole warp, so that its
+            // lanes never run both forms.
+            const bool narrow = __all_sync(FULL, !own || Sabs < 2147000000.f);
+            auto quantise = [&](auto round_piece) {
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -982,14 +991,23 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
 #pragma unroll
                         for (int ch = 0; ch < NCH; ++ch) {
                             const float v = (ch & 1) ? acc[b][c][ch >> 1].y : acc[b][c][ch >> 1].x;
-                            big |= !(fabsf(v) < 4.5e15f);
-                            const long long piece = rround(v);
+                            const long long piece = round_piece(v);
                             // no test for zero: a chunk sum is rarely exactly
                             // zero, and the test cost more than the adds it saved
                             shared_add_i64_always(&sdep[ch * bvol + lin], piece);
                             ps[ch] += piece;
                         }
                     }
+            };
+            if (own) {
+                if (narrow) {
+                    quantise([](float v) { return (long long)__float2int_rn(v); });
+                } else {
+                    quantise([&](float v) {
+                        big |= !(fabsf(v) < 4.5e15f);
+                        return rround(v);
+                    });
+                }
             }
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) {
@@ -998,7 +1016,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 if (a == 1 && own) {
                     const float Sc = (ch & 1) ? S2[ch >> 1].y : S2[ch >> 1].x;
                     big |= !(fabsf(Sc) < 4.5e15f);
-                    const long long rest = rround(Sc) - (ps[ch] + s1 + s2);
+                    const long long rest = (narrow ? (long long)__float2int_rn(Sc) : rround(Sc)) - (ps[ch] + s1 + s2);
                     if (rest != 0) shared_add_i64(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], rest);
                 }
             }

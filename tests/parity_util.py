@@ -5,6 +5,12 @@ import numpy as np
 import oracle as O
 
 
+def default_quantum(w, precision):
+    """The library's default fixed-point quantum: 2^-44 (FP64, precision 0) or
+    2^-40 (mixed, precision 1) times the largest species mass."""
+    return np.ldexp(max(abs(m) for m in w.species_mass), -44 if precision == 0 else -40)
+
+
 def oracle_problem(w, feedback=None):
     return O.Problem(geom=w.geom, edges=w.edges, bc=w.bc, weight=w.weight,
                      species_mass=w.species_mass, species_tau_mode=w.species_tau_mode,

@@ -23,7 +23,7 @@ import pytest
 
 import oracle as O
 from paper_1908_10793_gb300 import inputs as I
-from parity_util import periodic_diff, run_gpu, run_oracle
+from parity_util import default_quantum, periodic_diff, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -249,7 +249,7 @@ def test_gas_predictor_dense_zones_and_tile_independent():
         w.q[1][sel] = w.edges[1][cy] + dx * rng.uniform(0.05, 0.95, k)
     steps = 2
     nz = _grains_per_zone_max(w) * 9
-    quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
+    quantum = default_quantum(w, MIXED)
     dgas = (nz * 0.5 * quantum / (w.rho * zone_volumes(w))).max()
     compare(w, steps, MIXED, feedback=1, predictor=True, extra_v=4 * steps * dgas,
             kernel=D.DUST_KERNEL_SLAB, sort_interval=1)
@@ -302,7 +302,7 @@ def test_parity_gas_predictor(name, precision):
     w = WORKLOADS[name]()
     steps = 2
     nz = _grains_per_zone_max(w) * (27 if w.n[2] > 1 else 9)
-    quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
+    quantum = default_quantum(w, precision)
     dgas = (nz * 0.5 * quantum / (w.rho * zone_volumes(w))).max()
     compare(w, steps, precision, feedback=1, predictor=True, extra_v=4 * steps * dgas)
 
@@ -536,7 +536,7 @@ def test_parity_volume_weighting_with_gas_predictor(precision):
     w.weight = I.VOLUME
     steps = 2
     nz = _grains_per_zone_max(w) * 27
-    quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
+    quantum = default_quantum(w, precision)
     dgas = (nz * 0.5 * quantum / (w.rho * zone_volumes(w))).max()
     compare(w, steps, precision, feedback=1, predictor=True, extra_v=4 * steps * dgas)
 
@@ -704,12 +704,12 @@ def test_parity_ragged_tiles(n, precision):
     tiles on every axis (the slab kernel's gas box then reaches past the grid
     at the high end as well as the low one), two steps with feedback."""
     w = I.sbox3d(str(n))
-    compare(w, 2, precision, feedback=1, extra_v=_feedback_extra_v(w, 2))
+    compare(w, 2, precision, feedback=1, extra_v=_feedback_extra_v(w, 2, precision))
 
 
-def _feedback_extra_v(w, steps):
+def _feedback_extra_v(w, steps, precision):
     from test_oracle_push import _zone_volumes
     dV = _zone_volumes(O.Problem(geom=w.geom, edges=w.edges))
     nz = _grains_per_zone_max(w) * (27 if w.n[2] > 1 else 9)
-    quantum = np.ldexp(max(abs(m) for m in w.species_mass), -44)
+    quantum = default_quantum(w, precision)
     return 2 * steps * (steps * nz * 0.5 * quantum / (w.rho * dV)).max()
