@@ -45,6 +45,26 @@ struct SlabShape {
     static constexpr int CC = NC == 3 ? 1 : 0;   // index of the host node in z
 };
 
+// Hint: move the line holding p into L2 (no register result, no wait).
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// The grain columns a push reads at store position src, prefetched into L2
+// one push iteration (or one zone group) before they are read.
+template <typename Store>
+__device__ __forceinline__ void prefetch_grain(const Store &S, int src)
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        prefetch_l2(S.q[d] + src);
+        prefetch_l2(S.p[d] + src);
+    }
+    if (S.species) prefetch_l2(S.species + src);
+}
+
 __device__ __forceinline__ float sel3(const float v[3], int i)
 {
     return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
@@ -312,7 +332,9 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     unsigned long long *sdep = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)bvol * 4 * sizeof(float));
     // tile-local key -> zone offsets (x | y << 10 | z << 20), no runtime division
     int *kdec = reinterpret_cast<int *>(sdep + (size_t)bvol * 4);
-    float *srec = reinterpret_cast<float *>(kdec + ((tvol + 31) & ~31));  // [warps][13][kRecStride]
+    // the tile's zone offsets in the store, key_off[kbase .. kbase + tvol]
+    int *skoff = kdec + ((tvol + 31) & ~31);
+    float *srec = reinterpret_cast<float *>(skoff + ((tvol + 32) & ~31));  // [warps][13][kRecStride]
     // the tile's zone geometry, per direction d at toff[d]: centre (double and
     // float) and inverse width; radial centre / width; polar lower edges
     const int toff[3] = {0, T0, T0 + T1};
@@ -361,6 +383,8 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
         const int kx = k % T0, ky = (k / T0) % T1, kz = k / (T0 * T1);
         kdec[k] = kx | (ky << 10) | (kz << 20);
     }
+    // store positions fit in 32 bits (fewer than 2^31 grains)
+    for (int k = threadIdx.x; k <= tvol; k += blockDim.x) skoff[k] = TA.key_off[kbase + k];
 
     for (int lin = threadIdx.x; lin < bvol; lin += blockDim.x) {
 #pragma unroll
@@ -384,8 +408,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
         const int kl = kg0 + kq;
         const bool kok = lane < 30 && kl < tvol;
         // the group's 10 keys: grain range [koff[0], koff[10]) in the store
-        // store positions fit in 32 bits (fewer than 2^31 grains)
-        const int offl = lane <= 10 ? TA.key_off[kbase + min(kg0 + lane, tvol)] : 0;
+        const int offl = lane <= 10 ? skoff[min(kg0 + lane, tvol)] : 0;
         int koff[11];
 #pragma unroll
         for (int j = 0; j <= 10; ++j) koff[j] = __shfl_sync(FULL, offl, j);
@@ -427,14 +450,31 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 }
             }
             float *rb = srec + warp * (kRecFields * kRecStride);
+            // the last pass of the group looks up the source positions of the
+            // first grains of the warp's next group; their columns are
+            // prefetched after the push, ahead of that group's first loads
+            int src_g = -1;
+            if (P1 == G1) {
+                const int kn = kg0 + 10 * nwarps;
+                if (kn < tvol) {
+                    const int n0 = skoff[kn] + lane;
+                    if (n0 < skoff[min(kn + 10, tvol)]) src_g = TA.perm ? TA.perm[n0] : n0;
+                }
+            }
             // ---- push: one grain per lane, consecutive grains on consecutive
-            // lanes (coalesced), each relative to its own key zone
-            // source positions one iteration ahead (the permutation load is
-            // off the grain loads' dependency chain)
+            // lanes (coalesced), each relative to its own key zone.  Source
+            // positions two iterations ahead: the next iteration's grain
+            // columns are prefetched into L2 while this one runs, and the
+            // permutation load is off the grain loads' dependency chain
             int src_next = (TA.perm && P0 + lane < P1) ? TA.perm[P0 + lane] : 0;
+            int src_nx2 = (TA.perm && P0 + lane + 32 < P1) ? TA.perm[P0 + lane + 32] : 0;
             for (int gi = P0 + lane; gi < P1; gi += 32) {
                 const int src = TA.perm ? src_next : gi;
-                if (TA.perm && gi + 32 < P1) src_next = TA.perm[gi + 32];
+                if (gi + 32 < P1) prefetch_grain(S, TA.perm ? src_nx2 : gi + 32);
+                if (TA.perm) {
+                    src_next = src_nx2;
+                    if (gi + 64 < P1) src_nx2 = TA.perm[gi + 64];
+                }
                 int kq2 = 0;
 #pragma unroll
                 for (int j = 1; j < 10; ++j) kq2 += gi >= koff[j] ? 1 : 0;
@@ -923,6 +963,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) rb[(9 + ch) * kRecStride + slot] = grp_ok ? D[ch] : 0.f;
             }
+            if (src_g >= 0) prefetch_grain(S, src_g);
             __syncwarp();
             // ---- deposit: the three owner lanes of a zone accumulate its
             // chunk in this pass (id order) into their x slabs
@@ -1092,7 +1133,7 @@ inline size_t slab_smem_bytes(const GridDev &g)
     for (int d = 0; d < 3; ++d) bvol *= (size_t)(g.T[d] + (g.n[d] > 1 ? 2 : 0));
     const size_t tsum = (size_t)g.T[0] + g.T[1] + g.T[2];
     return bvol * (4 * sizeof(float) + 4 * sizeof(long long)) +
-           (size_t)((g.tvol + 31) & ~31) * sizeof(int) +
+           (size_t)((g.tvol + 31) & ~31) * sizeof(int) + (size_t)((g.tvol + 32) & ~31) * sizeof(int) +
            (size_t)(kSlabThreads / 32) * kRecFields * kRecStride * sizeof(float) +
            tsum * (sizeof(double) + 2 * sizeof(float)) + ((size_t)g.T[0] + g.T[1] + 1) * sizeof(float) +
            2 * ((size_t)g.T[0] + g.T[1]) * sizeof(float) +
