@@ -1,10 +1,12 @@
 // Slab-group step kernel (mixed precision).  One CTA per tile of zones, the
-// tile's gas stencil staged in shared memory.  A warp takes groups of ten
-// consecutive sort keys (zones), whose grains are contiguous in the store.
-// Push: one grain per lane over the whole group (coalesced loads and stores,
+// tile's gas stencil staged in shared memory.  A warp takes an equal range of
+// the tile's sort keys (zones), whose grains are contiguous in the store, and
+// walks it in passes of up to kSlabCap grains.
+// Push: one grain per lane over the whole pass (coalesced loads and stores,
 // no per-zone imbalance); the 27-node gather reads the staged gas box (grains
 // of one zone read the same nodes, so the loads broadcast); each grain leaves
-// a record (weights, deposit impulse) in the warp's shared buffer.  Deposit:
+// a record (weights, deposit impulse) in the warp's shared buffer.  Deposit,
+// ten zones of the pass at a time:
 // three lanes own one zone; lane a keeps, in registers, the accumulators of
 // the nine stencil nodes at x-offset a - 1 and sums the zone's records into
 // them.  A zone's deposit (its run: the grains sorted into it whose half-step
@@ -30,9 +32,11 @@ namespace dust {
 
 constexpr int kSlabThreads = 256;
 constexpr int kSlabCap = 128;  // grains per warp record pass
-// Record slots: a grain of zone kq (0..9 in the group) at pass position s
-// uses slot s + kq, so the owner lanes of different zones, which read their
-// zones' grains in step, fall on different shared-memory banks.
+// Record slots: a grain of the pass's zone zp (counted from the pass's first
+// zone) at pass position s uses slot s + min(zp, 15), so the owner lanes of
+// neighbouring zones, which read their zones' grains in step, fall on
+// different shared-memory banks; the stagger never decreases along the pass,
+// so slots are unique.
 constexpr int kRecStride = kSlabCap + 16;
 constexpr int kRecFields = 13;  // 3 x 3 weights, 4 deposit channels
 
@@ -334,7 +338,9 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     int *kdec = reinterpret_cast<int *>(sdep + (size_t)bvol * 4);
     // the tile's zone offsets in the store, key_off[kbase .. kbase + tvol]
     int *skoff = kdec + ((tvol + 31) & ~31);
-    float *srec = reinterpret_cast<float *>(skoff + ((tvol + 32) & ~31));  // [warps][13][kRecStride]
+    // per warp: the zone (offset from the pass's first zone) of each grain of a pass
+    unsigned short *sztab = reinterpret_cast<unsigned short *>(skoff + ((tvol + 32) & ~31));
+    float *srec = reinterpret_cast<float *>(sztab + (kSlabThreads / 32) * kSlabCap);  // [warps][13][kRecStride]
     // the tile's zone geometry, per direction d at toff[d]: centre (double and
     // float) and inverse width; radial centre / width; polar lower edges
     const int toff[3] = {0, T0, T0 + T1};
@@ -398,69 +404,59 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     const int a = lane % 3, kq = lane / 3;
     const int base = lane - a;
     const float h = (float)(0.5 * A.dt), dt = (float)A.dt;
-    const int groups = (tvol + 9) / 10;
     int nremoved = 0;
     float moved = 0.f;
     bool big = false;
 
-    for (int grp = warp; grp < groups; grp += nwarps) {
-        const int kg0 = grp * 10;
-        const int kl = kg0 + kq;
-        const bool kok = lane < 30 && kl < tvol;
-        // the group's 10 keys: grain range [koff[0], koff[10]) in the store
-        const int offl = lane <= 10 ? skoff[min(kg0 + lane, tvol)] : 0;
-        int koff[11];
-#pragma unroll
-        for (int j = 0; j <= 10; ++j) koff[j] = __shfl_sync(FULL, offl, j);
-        const int G0 = koff[0], G1 = koff[10];
-        if (G1 == G0) continue;
-        int off0 = 0;
-        int cnt = 0;
-        if (kok) {
-            off0 = koff[0];
-#pragma unroll
-            for (int j = 1; j < 10; ++j)
-                if (kq == j) off0 = koff[j];
-            int off1 = koff[1];
-#pragma unroll
-            for (int j = 1; j < 10; ++j)
-                if (kq == j) off1 = koff[j + 1];
-            cnt = off1 - off0;
+    // Each warp takes an equal range [zw0, zw1) of the tile's zones (keys)
+    // and walks its grains, contiguous in the store, in passes of at most
+    // kSlabCap grains that end on chunk boundaries (a zone's end, or its
+    // start plus a multiple of kSlabCap), so each zone's part of a pass is
+    // one whole chunk of its run and is quantised in that pass: nothing is
+    // carried between passes.  A pass spans as many zones as its grains
+    // fill; its owner phase takes them ten at a time.
+    const int zw0 = (warp * tvol) / nwarps, zw1 = ((warp + 1) * tvol) / nwarps;
+    const int Gend = skoff[zw1];
+    float *rb = srec + warp * (kRecFields * kRecStride);
+    unsigned short *zt = sztab + warp * kSlabCap;
+    int zc = zw0;  // the zone holding grain P0: skoff[zc] <= P0 < skoff[zc + 1]
+    for (int P0 = skoff[zw0], P1; P0 < Gend; P0 = P1) {
+        // skip the zones that end at or before P0 (32 at a time; offsets are
+        // nondecreasing, so the ballot is a prefix)
+        for (;;) {
+            const int z = zc + 1 + lane;
+            const int c = __popc(__ballot_sync(FULL, z <= zw1 && skoff[z] <= P0));
+            zc += c;
+            if (c < 32) break;
         }
-        // owner zone's position in the tile box
-        const int okd = kok ? (FIX ? kdec_shape<TX, TY>(kl) : kdec[kl]) : 0;
-        const int ohx = (okd & 1023) + 1, ohy = ((okd >> 10) & 1023) + (NB == 3 ? 1 : 0),
-                  ohz = (okd >> 20) + (NC == 3 ? 1 : 0);
-        // Passes of at most kSlabCap grains that end on chunk boundaries
-        // (a zone's end, or its start plus a multiple of kSlabCap), so each
-        // zone's part of a pass is one whole chunk of its run and is
-        // quantised at the end of the pass: nothing is carried between passes.
-        for (int P0 = G0, P1; P0 < G1; P0 = P1) {
-            {
-                const int lim = min(G1, P0 + kSlabCap);
-                P1 = P0;
-#pragma unroll
-                for (int j = 0; j < 10; ++j) {
-                    const int zs = koff[j], ze = koff[j + 1];
-                    if (ze <= lim) {
-                        P1 = max(P1, ze);
-                    } else if (zs < lim) {
-                        P1 = max(P1, zs + ((lim - zs) / kSlabCap) * kSlabCap);
-                    }
-                }
+        // the pass [P0, P1) over the zones [zc, zc + nz)
+        int nz = 1;
+        if (skoff[zc + 1] > P0 + kSlabCap) {
+            P1 = P0 + kSlabCap;  // one chunk of a dense zone
+        } else {
+            // the last zone boundary at most kSlabCap grains from P0
+            const int lim = P0 + kSlabCap;
+            int zb = zc + 1;
+            for (;;) {
+                const int z = zb + 1 + lane;
+                const int c = __popc(__ballot_sync(FULL, z <= zw1 && skoff[z] <= lim));
+                zb += c;
+                if (c < 32) break;
             }
-            float *rb = srec + warp * (kRecFields * kRecStride);
-            // the last pass of the group looks up the source positions of the
-            // first grains of the warp's next group; their columns are
-            // prefetched after the push, ahead of that group's first loads
-            int src_g = -1;
-            if (P1 == G1) {
-                const int kn = kg0 + 10 * nwarps;
-                if (kn < tvol) {
-                    const int n0 = skoff[kn] + lane;
-                    if (n0 < skoff[min(kn + 10, tvol)]) src_g = TA.perm ? TA.perm[n0] : n0;
-                }
-            }
+            P1 = skoff[zb];
+            nz = zb - zc;
+        }
+        // zone of each grain of the pass, as its offset from zc
+        for (int zp = lane; zp < nz; zp += 32) {
+            const int s0 = max(skoff[zc + zp], P0) - P0, s1 = min(skoff[zc + zp + 1], P1) - P0;
+            for (int t = s0; t < s1; ++t) zt[t] = (unsigned short)zp;
+        }
+        __syncwarp();
+        // the source positions of the first grains of the next pass; their
+        // columns are prefetched after the push, ahead of that pass's loads
+        int src_g = -1;
+        if (P1 + lane < Gend) src_g = TA.perm ? TA.perm[P1 + lane] : P1 + lane;
+        {
             // ---- push: one grain per lane, consecutive grains on consecutive
             // lanes (coalesced), each relative to its own key zone.  Source
             // positions two iterations ahead: the next iteration's grain
@@ -475,10 +471,13 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     src_next = src_nx2;
                     if (gi + 64 < P1) src_nx2 = TA.perm[gi + 64];
                 }
-                int kq2 = 0;
-#pragma unroll
-                for (int j = 1; j < 10; ++j) kq2 += gi >= koff[j] ? 1 : 0;
-                const int kd = FIX ? kdec_shape<TX, TY>(kg0 + kq2) : kdec[kg0 + kq2];
+                const int zp = zt[gi - P0];
+                // the records of a zone start min(zp, 15) slots after its
+                // grains' positions in the pass (staggers the owner lanes of
+                // neighbouring zones across banks); never decreasing with zp,
+                // so no two grains of a pass share a slot
+                const int kq2 = min(zp, 15);
+                const int kd = FIX ? kdec_shape<TX, TY>(zc + zp) : kdec[zc + zp];
                 const int lx = kd & 1023, ly = (kd >> 10) & 1023, lz = kd >> 20;
                 const int zx = tc[0] * T0 + lx, zy = tc[1] * T1 + ly, zz = tc[2] * T2 + lz;
                 const int hx = lx + 1, hy = ly + (NB == 3 ? 1 : 0), hz = lz + (NC == 3 ? 1 : 0);
@@ -608,7 +607,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     if (live) {
                         pn[0] = S.p[0][src]; pn[1] = S.p[1][src]; pn[2] = S.p[2][src];
                         sp = S.species ? S.species[src] : 0;
-    #pragma unroll
+#pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             if (gd(d)) { u[d] = __double2float_rn(q[d] - zcd[d]); zc3[d] = zcf[d]; }
                             else { u[d] = 0.f; zc3[d] = (float)q[d]; }
@@ -632,12 +631,12 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             u[1] += inc1[1];
                             inc1[2] = h * pn[2]; u[2] += inc1[2];
                         } else {
-    #pragma unroll
+#pragma unroll
                             for (int d = 0; d < 3; ++d) { inc1[d] = h * pn[d]; u[d] += inc1[d]; }
                         }
                         float dl[3];
                         ingroup = true;
-    #pragma unroll
+#pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             qf[d] = zc3[d] + u[d];
                             dl[d] = u[d] * zif[d];
@@ -645,7 +644,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         }
                         if (ingroup) {
                             host[0] = zx; host[1] = zy; host[2] = zz;
-    #pragma unroll
+#pragma unroll
                             for (int d = 0; d < 3; ++d) {
                                 iw[d] = zif[d];
                                 if (!gd(d)) continue;
@@ -696,7 +695,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     int lb[3] = {hx, hy, hz};
                     bool inbox = true;
                     if (!ingroup) {
-    #pragma unroll
+#pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             int l = host[d] - o[d];
                             if (gd(d) && g.bc[d] == DUST_BC_PERIODIC) {
@@ -713,13 +712,13 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         // channels in pairs on the packed single-precision
                         // FMA (each lane rounded once, as a scalar FMA)
                         float2 G01 = make_float2(0.f, 0.f), G23 = make_float2(0.f, 0.f);
-    #pragma unroll
+#pragma unroll
                         for (int c3 = 0; c3 < 3; ++c3) {
                             if (NC == 1 && c3 != 1) continue;
-    #pragma unroll
+#pragma unroll
                             for (int b = 0; b < 3; ++b) {
                                 if (NB == 1 && b != 1) continue;
-    #pragma unroll
+#pragma unroll
                                 for (int aa = 0; aa < 3; ++aa) {
                                     const float W = w[0][aa] * (w[1][b] * w[2][c3]);
                                     const float4 fv = reinterpret_cast<const float4 *>(sgas)[
@@ -735,7 +734,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         // rare: the stencil leaves the staged box; the same
                         // nodes in the same order from global memory, in a
                         // rolled loop (keeps the hot code small)
-    #pragma unroll 1
+#pragma unroll 1
                         for (int nd = 0; nd < 27; ++nd) {
                             const int aa = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
                             if ((NB == 1 && b != 1) || (NC == 1 && c3 != 1)) continue;
@@ -745,7 +744,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             const int iz = node_of(host[2], c3 - 1, g.n[2], g.bc[2]);
                             float fv[4];
                             load_gas<float>(A.gas, ix + (int64_t)g.n[0] * (iy + (int64_t)g.n[1] * iz), fv);
-    #pragma unroll
+#pragma unroll
                             for (int ch = 0; ch < 4; ++ch) G[ch] += W * fv[ch];
                         }
                     }
@@ -784,10 +783,10 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             inc2[1] = ph.fargo ? h * (pp[1] - ph.q_om_f * qf[0]) : h * pp[1];
                             inc2[2] = h * pp[2];
                         } else {
-    #pragma unroll
+#pragma unroll
                             for (int d = 0; d < 3; ++d) inc2[d] = h * pp[d];
                         }
-    #pragma unroll
+#pragma unroll
                         for (int d = 0; d < 3; ++d) q[d] += (double)(inc1[d] + inc2[d]);
                     } else {
                         const double qm[3] = {q[0], q[1], q[2]};
@@ -817,29 +816,29 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     }
                     const bool alive = inner || apply_bc<float, GEOM>(g, ph, shift_end_of(A), q, pnew);
                     const float mq = A.sp.mqf[sp];
-    #pragma unroll
+#pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         D[c] = -mq * ((pp[c] - pn[c]) - dt * acc3[c]);
                         D[3] += D[c] * dH[c];
                     }
                     if (!(isfinite(pp[0]) && isfinite(pp[1]) && isfinite(pp[2])))
                         atomicOr(&A.status[ST_FLAGS], DUST_FLAG_NAN);
-    #pragma unroll
+#pragma unroll
                     for (int d = 0; d < 3; ++d) moved = fmaxf(moved, fabsf(inc1[d] + inc2[d]) * iw[d]);
                     if (!ingroup) {
                         // per-grain fixed-point rule for a grain outside its key zone
                         if (inbox) {
                             long long rest[4];
-    #pragma unroll
+#pragma unroll
                             for (int ch = 0; ch < 4; ++ch) rest[ch] = rround(D[ch]);
                             const int hl = lb[0] + B[0] * (lb[1] + B[1] * lb[2]);
-    #pragma unroll 1
+#pragma unroll 1
                             for (int nd = 0; nd < 27; ++nd) {
                                 const int aa = nd % 3, b = (nd / 3) % 3, c3 = nd / 9;
                                 if ((NB == 1 && b != 1) || (NC == 1 && c3 != 1) || nd == 13) continue;
                                 const float W = sel3(w[0], aa) * (sel3(w[1], b) * sel3(w[2], c3));
                                 const int lin = hl + (aa - 1) + B[0] * ((b - 1) + B[1] * (c3 - 1));
-    #pragma unroll
+#pragma unroll
                                 for (int ch = 0; ch < 4; ++ch) {
                                     const long long piece = rround(W * D[ch]);
                                     if (piece != 0) {
@@ -848,7 +847,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                                     }
                                 }
                             }
-    #pragma unroll
+#pragma unroll
                             for (int ch = 0; ch < 4; ++ch)
                                 if (rest[ch] != 0) shared_add_i64(&sdep[ch * bvol + hl], rest[ch]);
                         } else {
@@ -965,100 +964,115 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
             }
             if (src_g >= 0) prefetch_grain(S, src_g);
             __syncwarp();
-            // ---- deposit: the three owner lanes of a zone accumulate its
-            // chunk in this pass (id order) into their x slabs
-            const int za = max(off0, P0), zb = min(off0 + cnt, P1);
-            const bool own = kok && zb > za;
-            // channels in pairs (0, 1) and (2, 3) on the packed single-precision
-            // FMA and add (each lane rounded once, as the scalar operations)
-            float2 acc[NB][NC][2];
-            float2 S2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-            float Sabs = 0.f;  // sum over the chunk of the largest |channel| of each grain
-#pragma unroll
-            for (int b = 0; b < NB; ++b)
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-#pragma unroll
-                    for (int hc = 0; hc < 2; ++hc) acc[b][c][hc] = make_float2(0.f, 0.f);
-            if (own) {
-                const int s0 = za - P0 + kq, s1 = zb - P0 + kq;
-                const float *rx = rb + a * kRecStride;
-                auto one = [&](int sl) {
-                    const float wx = rx[sl];
-                    const float2 De01 = make_float2(rb[9 * kRecStride + sl], rb[10 * kRecStride + sl]);
-                    const float2 De23 = make_float2(rb[11 * kRecStride + sl], rb[12 * kRecStride + sl]);
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const float wxy = wx * rb[(3 + (NB == 3 ? b : 1)) * kRecStride + sl];
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) {
-                            const float W = wxy * rb[(6 + (NC == 3 ? c : 1)) * kRecStride + sl];
-                            const float2 W2 = make_float2(W, W);
-                            acc[b][c][0] = __ffma2_rn(W2, De01, acc[b][c][0]);
-                            acc[b][c][1] = __ffma2_rn(W2, De23, acc[b][c][1]);
-                        }
-                    }
-                    S2[0] = __fadd2_rn(S2[0], De01);
-                    S2[1] = __fadd2_rn(S2[1], De23);
-                    Sabs += fmaxf(fmaxf(fabsf(De01.x), fabsf(De01.y)), fmaxf(fabsf(De23.x), fabsf(De23.y)));
-                };
-                int sl = s0;
-                for (; sl + 1 < s1; sl += 2) {
-                    one(sl);
-                    one(sl + 1);
+            // ---- deposit, ten zones of the pass at a time: the three owner
+            // lanes of a zone accumulate its chunk in this pass (id order)
+            // into their x slabs
+            for (int z0 = zc; z0 < zc + nz; z0 += 10) {
+                const int zl = z0 + kq;
+                const bool kok = lane < 30 && zl < zc + nz;
+                int za = 0, zb = 0;
+                if (kok) {
+                    za = max(skoff[zl], P0);
+                    zb = min(skoff[zl + 1], P1);
                 }
-                if (sl < s1) one(sl);
-            }
-            __syncwarp();
-
-            // ---- quantise the chunk and add it to the deposit box (the
-            // predictor's impulse has no energy channel)
-            constexpr int NCH = PRED ? 3 : 4;
-            long long ps[4] = {0, 0, 0, 0};
-            // every chunk sum of a channel is at most the sum of the grains'
-            // |impulse| in it (the weights lie in [0, 1]); below 2^31 (with a
-            // margin for the sums' rounding) the 32-bit rounding instruction
-            // gives the same integer as the 64-bit one, at a fraction of its
-            // cost on this GPU.  Decided for the whole warp, so that its
-            // lanes never run both forms.
-            const bool narrow = __all_sync(FULL, !own || Sabs < 2147000000.f);
-            auto quantise = [&](auto round_piece) {
+                const bool own = kok && zb > za;
+                if (!__any_sync(FULL, own)) continue;
+                // owner zone's position in the tile box
+                const int okd = own ? (FIX ? kdec_shape<TX, TY>(zl) : kdec[zl]) : 0;
+                const int ohx = (okd & 1023) + 1, ohy = ((okd >> 10) & 1023) + (NB == 3 ? 1 : 0),
+                          ohz = (okd >> 20) + (NC == 3 ? 1 : 0);
+                // channels in pairs (0, 1) and (2, 3) on the packed single-precision
+                // FMA and add (each lane rounded once, as the scalar operations)
+                float2 acc[NB][NC][2];
+                float2 S2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                float Sabs = 0.f;  // sum over the chunk of the largest |channel| of each grain
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        if (a == 1 && b == Sh::BC && c == Sh::CC) continue;  // host: remainder
-                        const int lin = (ohx + a - 1) + B[0] * ((ohy + b - Sh::BC) + B[1] * (ohz + c - Sh::CC));
+                    for (int c = 0; c < NC; ++c)
 #pragma unroll
-                        for (int ch = 0; ch < NCH; ++ch) {
-                            const float v = (ch & 1) ? acc[b][c][ch >> 1].y : acc[b][c][ch >> 1].x;
-                            const long long piece = round_piece(v);
-                            // no test for zero: a chunk sum is rarely exactly
-                            // zero, and the test cost more than the adds it saved
-                            shared_add_i64_always(&sdep[ch * bvol + lin], piece);
-                            ps[ch] += piece;
+                        for (int hc = 0; hc < 2; ++hc) acc[b][c][hc] = make_float2(0.f, 0.f);
+                if (own) {
+                    const int sk = min(zl - zc, 15);
+                    const int s0 = za - P0 + sk, s1 = zb - P0 + sk;
+                    const float *rx = rb + a * kRecStride;
+                    auto one = [&](int sl) {
+                        const float wx = rx[sl];
+                        const float2 De01 = make_float2(rb[9 * kRecStride + sl], rb[10 * kRecStride + sl]);
+                        const float2 De23 = make_float2(rb[11 * kRecStride + sl], rb[12 * kRecStride + sl]);
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) {
+                            const float wxy = wx * rb[(3 + (NB == 3 ? b : 1)) * kRecStride + sl];
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) {
+                                const float W = wxy * rb[(6 + (NC == 3 ? c : 1)) * kRecStride + sl];
+                                const float2 W2 = make_float2(W, W);
+                                acc[b][c][0] = __ffma2_rn(W2, De01, acc[b][c][0]);
+                                acc[b][c][1] = __ffma2_rn(W2, De23, acc[b][c][1]);
+                            }
                         }
+                        S2[0] = __fadd2_rn(S2[0], De01);
+                        S2[1] = __fadd2_rn(S2[1], De23);
+                        Sabs += fmaxf(fmaxf(fabsf(De01.x), fabsf(De01.y)), fmaxf(fabsf(De23.x), fabsf(De23.y)));
+                    };
+                    int sl = s0;
+                    for (; sl + 1 < s1; sl += 2) {
+                        one(sl);
+                        one(sl + 1);
                     }
-            };
-            if (own) {
-                if (narrow) {
-                    quantise([](float v) { return (long long)__float2int_rn(v); });
-                } else {
-                    quantise([&](float v) {
-                        big |= !(fabsf(v) < 4.5e15f);
-                        return rround(v);
-                    });
+                    if (sl < s1) one(sl);
                 }
-            }
+                __syncwarp();
+
+                // ---- quantise the chunk and add it to the deposit box (the
+                // predictor's impulse has no energy channel)
+                constexpr int NCH = PRED ? 3 : 4;
+                long long ps[4] = {0, 0, 0, 0};
+                // every chunk sum of a channel is at most the sum of the grains'
+                // |impulse| in it (the weights lie in [0, 1]); below 2^31 (with a
+                // margin for the sums' rounding) the 32-bit rounding instruction
+                // gives the same integer as the 64-bit one, at a fraction of its
+                // cost on this GPU.  Decided for the whole warp, so that its
+                // lanes never run both forms.
+                const bool narrow = __all_sync(FULL, !own || Sabs < 2147000000.f);
+                auto quantise = [&](auto round_piece) {
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                const long long s1 = __shfl_sync(FULL, ps[ch], base + 0);
-                const long long s2 = __shfl_sync(FULL, ps[ch], base + 2);
-                if (a == 1 && own) {
-                    const float Sc = (ch & 1) ? S2[ch >> 1].y : S2[ch >> 1].x;
-                    big |= !(fabsf(Sc) < 4.5e15f);
-                    const long long rest = (narrow ? (long long)__float2int_rn(Sc) : rround(Sc)) - (ps[ch] + s1 + s2);
-                    if (rest != 0) shared_add_i64(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], rest);
+                    for (int b = 0; b < NB; ++b)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            if (a == 1 && b == Sh::BC && c == Sh::CC) continue;  // host: remainder
+                            const int lin = (ohx + a - 1) + B[0] * ((ohy + b - Sh::BC) + B[1] * (ohz + c - Sh::CC));
+#pragma unroll
+                            for (int ch = 0; ch < NCH; ++ch) {
+                                const float v = (ch & 1) ? acc[b][c][ch >> 1].y : acc[b][c][ch >> 1].x;
+                                const long long piece = round_piece(v);
+                                // no test for zero: a chunk sum is rarely exactly
+                                // zero, and the test cost more than the adds it saved
+                                shared_add_i64_always(&sdep[ch * bvol + lin], piece);
+                                ps[ch] += piece;
+                            }
+                        }
+                };
+                if (own) {
+                    if (narrow) {
+                        quantise([](float v) { return (long long)__float2int_rn(v); });
+                    } else {
+                        quantise([&](float v) {
+                            big |= !(fabsf(v) < 4.5e15f);
+                            return rround(v);
+                        });
+                    }
+                }
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const long long s1 = __shfl_sync(FULL, ps[ch], base + 0);
+                    const long long s2 = __shfl_sync(FULL, ps[ch], base + 2);
+                    if (a == 1 && own) {
+                        const float Sc = (ch & 1) ? S2[ch >> 1].y : S2[ch >> 1].x;
+                        big |= !(fabsf(Sc) < 4.5e15f);
+                        const long long rest = (narrow ? (long long)__float2int_rn(Sc) : rround(Sc)) - (ps[ch] + s1 + s2);
+                        if (rest != 0) shared_add_i64(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], rest);
+                    }
                 }
             }
         }
@@ -1134,6 +1148,7 @@ inline size_t slab_smem_bytes(const GridDev &g)
     const size_t tsum = (size_t)g.T[0] + g.T[1] + g.T[2];
     return bvol * (4 * sizeof(float) + 4 * sizeof(long long)) +
            (size_t)((g.tvol + 31) & ~31) * sizeof(int) + (size_t)((g.tvol + 32) & ~31) * sizeof(int) +
+           (size_t)(kSlabThreads / 32) * kSlabCap * sizeof(unsigned short) +
            (size_t)(kSlabThreads / 32) * kRecFields * kRecStride * sizeof(float) +
            tsum * (sizeof(double) + 2 * sizeof(float)) + ((size_t)g.T[0] + g.T[1] + 1) * sizeof(float) +
            2 * ((size_t)g.T[0] + g.T[1]) * sizeof(float) +
