@@ -146,10 +146,10 @@ __device__ __forceinline__ void scatter_pairs_block(const SA &A, int64_t vb)
     }
 }
 
-// Insertion sort by id of the (id, source) pairs of every key.  A warp
-// takes 32 consecutive keys; their segments are contiguous, so the warp
-// stages them in shared memory with coalesced loads, each lane sorts its
-// key's segment there, and the warp writes them back.  When the warp's
+// Sort by id of the (id, source) pairs of every key.  A warp takes 32
+// consecutive keys; their segments are contiguous, so the warp stages them
+// in shared memory with coalesced loads, places each pair by its rank in its
+// key's segment there, and writes them back.  When the warp's
 // segments hold more than kSegStage pairs in total, segments of at most
 // kSmallSeg pairs are insertion-sorted in place in global memory (bounded
 // cost) and longer ones are listed for the block sort below.
@@ -216,11 +216,31 @@ __device__ __forceinline__ void segments_block(const SA &A, int64_t vb, int32_t 
         }
     }
     __syncwarp(FULL);
-    if (mine) insertion_sort_pairs(sid[warp], ssrc[warp], b - W0, e - W0);
-    __syncwarp(FULL);
-    for (int32_t u = W0 + lane; u < W1; u += 32) {
-        A.pair_id[u] = sid[warp][u - W0];
-        A.pair_src[u] = ssrc[warp][u - W0];
+    // each staged pair goes straight to its place in its key's segment: the
+    // segment is found by a binary search over the lanes' segment starts
+    // (nondecreasing; lanes past the zone keys hold the end), and the place
+    // is the segment start plus the number of smaller ids in the segment (ids
+    // are unique); the loads of the count are independent, unlike an
+    // insertion sort's
+    const int32_t n = W1 - W0;
+    const int32_t st = (mine ? b : W1) - W0, en = (mine ? e : W1) - W0;
+    for (int32_t r0 = 0; r0 < n; r0 += 32) {
+        const int32_t u = r0 + lane;
+        int lo = 0, hi = 32;  // the last lane whose segment starts at or before u
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+            const int mid = (lo + hi) >> 1;
+            if (__shfl_sync(FULL, st, mid) <= u) lo = mid;
+            else hi = mid;
+        }
+        const int32_t sb = __shfl_sync(FULL, st, lo), se = __shfl_sync(FULL, en, lo);
+        if (u < n) {
+            const int32_t x = sid[warp][u];
+            int32_t rank = 0;
+            for (int32_t v = sb; v < se; ++v) rank += sid[warp][v] < x ? 1 : 0;
+            A.pair_id[W0 + sb + rank] = x;
+            A.pair_src[W0 + sb + rank] = ssrc[warp][u];
+        }
     }
 }
 
