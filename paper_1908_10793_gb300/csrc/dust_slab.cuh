@@ -69,6 +69,19 @@ __device__ __forceinline__ void prefetch_grain(const Store &S, int src)
     if (S.species) prefetch_l2(S.species + src);
 }
 
+// A deposit piece too large for the split form of the shared deposit box
+// (below), or from a tile too dense for it: added to the global deposit at
+// the zone of box position lin (x fastest, box of B0 x B1 x ..., origin o).
+static __device__ __noinline__ void box_piece_to_global(const GridDev &g, unsigned long long *dep, int o0, int o1,
+                                                 int o2, int B0, int B1, int lin, int ch, long long v)
+{
+    const int bx = lin % B0, by = (lin / B0) % B1, bz = lin / (B0 * B1);
+    const int i = map_zone(o0 + bx, g.n[0], g.bc[0]);
+    const int j = map_zone(o1 + by, g.n[1], g.bc[1]);
+    const int k = map_zone(o2 + bz, g.n[2], g.bc[2]);
+    atomicAdd(&dep[4 * (i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k)) + ch], (unsigned long long)v);
+}
+
 __device__ __forceinline__ float sel3(const float v[3], int i)
 {
     return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
@@ -179,9 +192,9 @@ __device__ __forceinline__ void gather_global(const GridDev &g, const float *gas
 // The per-grain fixed-point rule into the shared deposit box (stencil
 // inside the box around lb): rint(W D) for the other nodes, the host the
 // remainder of rint(D).  Returns whether a channel was out of range.
-template <int NB, int NC>
-__device__ __forceinline__ bool deposit_box_per_grain(unsigned long long *sdep, int bvol, const int lb[3],
-                                                      int B0, int B1, const float w[3][3], const float D[4])
+template <int NB, int NC, class Add>
+__device__ __forceinline__ bool deposit_box_per_grain(Add box_add, const int lb[3], int B0, int B1,
+                                                      const float w[3][3], const float D[4])
 {
     long long rest[4];
     bool big = false;
@@ -201,14 +214,14 @@ __device__ __forceinline__ bool deposit_box_per_grain(unsigned long long *sdep, 
         for (int ch = 0; ch < 4; ++ch) {
             const long long piece = rround(W * D[ch]);
             if (piece != 0) {
-                shared_add_i64(&sdep[ch * bvol + lin], piece);
+                box_add(ch, lin, piece);
                 rest[ch] -= piece;
             }
         }
     }
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch)
-        if (rest[ch] != 0) shared_add_i64(&sdep[ch * bvol + hl], rest[ch]);
+        if (rest[ch] != 0) box_add(ch, hl, rest[ch]);
     return big;
 }
 
@@ -399,6 +412,31 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     __syncthreads();
     if (!gas_box_finish<float>(g, A.gas, TA.gas_tmap, sgas, o, B, sbar, A.status, TA.wait_ns)) return false;
 
+    // The deposit box.  In a tile of at most 65535 grains each word of the box
+    // takes at most one piece per grain, so a piece v with |v| < 2^31 is
+    // added exactly as two 32-bit counters that need no carry: the sum of
+    // the pieces' low 16 bits (unsigned, below 2^32) and of v >> 16 (signed,
+    // below 2^31 in size); the word is 65536 * high + low.  Both adds return
+    // nothing, so no lane waits for the shared-memory round trip.  Larger
+    // pieces go to the global deposit directly.  A denser tile keeps the box
+    // as int64 words added as two 32-bit atomics with the carry.
+    unsigned *blo = reinterpret_cast<unsigned *>(sdep);
+    int *bhi = reinterpret_cast<int *>(blo + 4 * bvol);
+    const bool split = skoff[tvol] - skoff[0] <= 65535;
+    auto box_add_split = [&](int ch, int lin, int v) {
+        atomicAdd(&blo[ch * bvol + lin], (unsigned)v & 0xffffu);
+        atomicAdd(&bhi[ch * bvol + lin], v >> 16);
+    };
+    auto box_add = [&](int ch, int lin, long long v) {
+        if (!split) {
+            shared_add_i64(&sdep[ch * bvol + lin], v);
+        } else if (v >= -2147483647LL && v <= 2147483647LL) {
+            box_add_split(ch, lin, (int)v);
+        } else {
+            box_piece_to_global(g, A.dep, o[0], o[1], o[2], B[0], B[1], lin, ch, v);
+        }
+    };
+
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int a = lane % 3, kq = lane / 3;
@@ -583,7 +621,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             for (int c = 0; c < 4; ++c) D[c] = Dq[c];
                             grp_ok = true;
                         } else if (inbox) {
-                            big |= deposit_box_per_grain<NB, NC>(sdep, bvol, lb, B[0], B[1], w, Dq);
+                            big |= deposit_box_per_grain<NB, NC>(box_add, lb, B[0], B[1], w, Dq);
                         } else {
                             deposit_fixed_rolled<NB, NC>(g, A.dep, host, w, Dq, A.status);
                         }
@@ -842,14 +880,14 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                                 for (int ch = 0; ch < 4; ++ch) {
                                     const long long piece = rround(W * D[ch]);
                                     if (piece != 0) {
-                                        shared_add_i64(&sdep[ch * bvol + lin], piece);
+                                        box_add(ch, lin, piece);
                                         rest[ch] -= piece;
                                     }
                                 }
                             }
 #pragma unroll
                             for (int ch = 0; ch < 4; ++ch)
-                                if (rest[ch] != 0) shared_add_i64(&sdep[ch * bvol + hl], rest[ch]);
+                                if (rest[ch] != 0) box_add(ch, hl, rest[ch]);
                         } else {
                             deposit_fixed_rolled<NB, NC>(g, A.dep, host, w, D, A.status);
                         }
@@ -1035,7 +1073,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 // cost on this GPU.  Decided for the whole warp, so that its
                 // lanes never run both forms.
                 const bool narrow = __all_sync(FULL, !own || Sabs < 2147000000.f);
-                auto quantise = [&](auto round_piece) {
+                auto quantise = [&](auto round_piece, auto add_piece) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -1048,19 +1086,26 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                                 const long long piece = round_piece(v);
                                 // no test for zero: a chunk sum is rarely exactly
                                 // zero, and the test cost more than the adds it saved
-                                shared_add_i64_always(&sdep[ch * bvol + lin], piece);
+                                add_piece(ch, lin, piece);
                                 ps[ch] += piece;
                             }
                         }
                 };
                 if (own) {
-                    if (narrow) {
-                        quantise([](float v) { return (long long)__float2int_rn(v); });
+                    if (narrow && split) {
+                        // the common form: 32-bit roundings, carry-free adds
+                        quantise([](float v) { return (long long)__float2int_rn(v); },
+                                 [&](int ch, int lin, long long v) { box_add_split(ch, lin, (int)v); });
+                    } else if (narrow) {
+                        quantise([](float v) { return (long long)__float2int_rn(v); },
+                                 [&](int ch, int lin, long long v) {
+                                     shared_add_i64_always(&sdep[ch * bvol + lin], v);
+                                 });
                     } else {
                         quantise([&](float v) {
                             big |= !(fabsf(v) < 4.5e15f);
                             return rround(v);
-                        });
+                        }, box_add);
                     }
                 }
 #pragma unroll
@@ -1071,7 +1116,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         const float Sc = (ch & 1) ? S2[ch >> 1].y : S2[ch >> 1].x;
                         big |= !(fabsf(Sc) < 4.5e15f);
                         const long long rest = (narrow ? (long long)__float2int_rn(Sc) : rround(Sc)) - (ps[ch] + s1 + s2);
-                        if (rest != 0) shared_add_i64(&sdep[ch * bvol + ohx + B[0] * (ohy + B[1] * ohz)], rest);
+                        if (rest != 0) box_add(ch, ohx + B[0] * (ohy + B[1] * ohz), rest);
                     }
                 }
             }
@@ -1089,8 +1134,9 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
         const int64_t gz = i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const unsigned long long v = sdep[c * bvol + lin];
-            if (v != 0ull) atomicAdd(&A.dep[4 * gz + c], v);
+            const long long v = split ? (long long)bhi[c * bvol + lin] * 65536 + (long long)blo[c * bvol + lin]
+                                      : (long long)sdep[c * bvol + lin];
+            if (v != 0) atomicAdd(&A.dep[4 * gz + c], (unsigned long long)v);
         }
     }
     const unsigned mv = __reduce_max_sync(FULL, __float_as_uint(moved));

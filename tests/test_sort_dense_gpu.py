@@ -3,7 +3,10 @@ a few hundred to a few thousand in others, as the clumps of the streaming
 instability produce (Sec. 4.3 setups).  Segments longer than the warp's
 staging go to the block sort (bitonic chunks and merge passes); the order
 must still be exactly (zone key, id) against the host computation, and the
-step must still match the oracle.  The sort's time on the clump is printed."""
+step must still match the oracle.  The sort's time on the clump is printed.  A
+second case puts 70,000 grains in one zone: its tile then holds more than
+65535 grains, so the step kernel keeps that tile's deposit box as int64 words
+(the form for dense tiles) instead of the two carry-free 32-bit counters."""
 import numpy as np
 import pytest
 
@@ -14,9 +17,10 @@ pytestmark = pytest.mark.gpu
 
 CLUMPS = (((7, 7, 7), 50_000), ((3, 9, 12), 3_000), ((12, 2, 5), 600), ((1, 14, 3), 100),
           ((10, 10, 1), 40))
+DENSE_TILE = (((7, 7, 7), 70_000),)
 
 
-def _clumped_box(seed=5):
+def _clumped_box(seed=5, clumps=CLUMPS):
     import copy
     w = copy.copy(I.sbox3d("small"))
     r = np.random.Generator(np.random.Philox(seed))
@@ -24,7 +28,7 @@ def _clumped_box(seed=5):
     v = [np.asarray(x) for x in w.v]
     add_q = [[], [], []]
     add_v = [[], [], []]
-    for (i, j, k), m in CLUMPS:
+    for (i, j, k), m in clumps:
         for d, c in enumerate((i, j, k)):
             lo, hi = w.edges[d][c], w.edges[d][c + 1]
             # inside the zone, away from its edges, slow: the half step keeps
@@ -40,12 +44,13 @@ def _clumped_box(seed=5):
     return w
 
 
+@pytest.mark.parametrize("clumps", [CLUMPS, DENSE_TILE], ids=["clumps", "dense_tile"])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_dense_zones_sort_in_key_and_id_order_and_match_the_oracle(precision):
+def test_dense_zones_sort_in_key_and_id_order_and_match_the_oracle(precision, clumps):
     from paper_1908_10793_gb300 import dust as D
     from test_parity_gpu import check_against_oracle
     from parity_util import run_oracle
-    w = _clumped_box()
+    w = _clumped_box(clumps=clumps)
     T = (8, 8, 8)
     ctx = D.Context(w, precision=precision, tile=T, timing=1, feedback=0)
     try:
