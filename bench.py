@@ -330,29 +330,40 @@ def run_ours(args):
     # the grains (with ids) and the deposit back.  Headline: a context with
     # dust_options.host_io_async, where one step's read-back, the next
     # step's load and the steps overlap (dust_sync at the end waits for the
-    # last copies); beside it the same calls with synchronous copies.
+    # last copies), with the velocities as float32 host arrays (the mixed
+    # store's own precision: dust_load_particles_v32 / _get_particles_v32);
+    # beside it the same calls with synchronous copies, and the float64
+    # velocity calls.
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
         hq = [pin(x) for x in w.q]
         hv = [pin(x) for x in w.v]
+        hv32 = [pin(np.asarray(x, dtype=np.float32)) for x in w.v]
         hrho = pin(w.rho)
         hg = [pin(x) for x in w.vgas]
         outs = [([pin(np.empty(ngr)) for _ in range(6)],
                  torch.empty(ngr, dtype=torch.int64).pin_memory().numpy(),
-                 torch.empty((w.ncell, 4), dtype=torch.int64).pin_memory().numpy())
+                 torch.empty((w.ncell, 4), dtype=torch.int64).pin_memory().numpy(),
+                 [pin(np.empty(ngr, np.float32)) for _ in range(3)])
                 for _ in range(2)]
         ke = max(2, min(args.steps, 20))
 
-        def run_e2e(async_io):
+        def run_e2e(async_io, v32=True):
             ctx = make(D.DUST_MIXED, 0, host_io_async=async_io)
 
             def one(k):
-                o, oid, odep = outs[k % 2]
-                D.dust_load_particles(ctx.handle, *hq, *hv)
+                o, oid, odep, o32 = outs[k % 2]
+                if v32:
+                    D.dust_load_particles_v32(ctx.handle, *hq, *hv32)
+                else:
+                    D.dust_load_particles(ctx.handle, *hq, *hv)
                 D.dust_set_gas(ctx.handle, hrho, *hg)
                 D.dust_step(ctx.handle, w.dt)
-                D.dust_get_particles(ctx.handle, ngr, *o, ids=oid)
+                if v32:
+                    D.dust_get_particles_v32(ctx.handle, ngr, *o[:3], *o32, ids=oid)
+                else:
+                    D.dust_get_particles(ctx.handle, ngr, *o, ids=oid)
                 D.dust_get_deposit(ctx.handle, fixed=odep)
 
             one(0)
@@ -368,19 +379,27 @@ def run_ours(args):
             te = max_over_ranks(time.perf_counter() - t0, dev)
             return ctx, te
 
+        ctx, te_f64 = run_e2e(1, v32=False)
+        ctx.close()
         ctx, te_async = run_e2e(1)
         ctx.close()
         ctx, te_sync = run_e2e(0)
-        h2d = ngr * 6 * 8 + w.ncell * 4 * 8
-        d2h = ngr * (6 * 8 + 8) + w.ncell * 4 * 8
+        h2d = ngr * (3 * 8 + 3 * 4) + w.ncell * 4 * 8
+        d2h = ngr * (3 * 8 + 3 * 4 + 8) + w.ncell * 4 * 8
         e2e = {"value": weak_value(world, ngr * ke, te_async), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ke,
-               "host_io": "asynchronous (dust_options.host_io_async = 1), pinned buffers",
+               "host_io": "asynchronous (dust_options.host_io_async = 1), pinned buffers; "
+                          "coordinates float64, velocities float32 (dust_load_particles_v32, "
+                          "dust_get_particles_v32)",
                "synchronous_calls": {"value": weak_value(world, ngr * ke, te_sync),
                                      "ms_per_step": te_sync / ke * 1e3},
+               "float64_velocities": {"value": weak_value(world, ngr * ke, te_f64),
+                                      "ms_per_step": te_f64 / ke * 1e3,
+                                      "h2d_bytes_per_step": ngr * 6 * 8 + w.ncell * 4 * 8,
+                                      "d2h_bytes_per_step": ngr * (6 * 8 + 8) + w.ncell * 4 * 8},
                "ms_per_step": te_async / ke * 1e3,
-               "breakdown": e2e_breakdown(ctx, D, torch, dev, w, hq, hv, hrho, hg, outs[0][0][:3],
-                                          outs[0][0][3:], outs[0][1], outs[0][2])}
+               "breakdown": e2e_breakdown(ctx, D, torch, dev, w, hq, hv32, hrho, hg, outs[0][0][:3],
+                                          outs[0][3], outs[0][1], outs[0][2])}
         ctx.close()
 
     # ---- batched instances (64 streaming-instability boxes, one graph launch
@@ -502,8 +521,9 @@ def run_batch(args, D, torch, dev, stream):
 
 
 def e2e_breakdown(ctx, D, torch, dev, w, hq, hv, hrho, hg, oq, ov, oid, odep):
-    """Untimed by the headline: one more end-to-end step with a device
-    synchronise around every call (ms per call), and the bandwidth of plain
+    """Untimed by the headline: two more end-to-end steps of the headline's
+    calls (float32 velocities) with a device synchronise around every call
+    (ms per call, the faster of the two), and the bandwidth of plain
     pinned-memory copies of the grains' size in each direction and in both
     at once, which bound the end-to-end figure."""
     ngr = w.ngrains
@@ -515,13 +535,16 @@ def e2e_breakdown(ctx, D, torch, dev, w, hq, hv, hrho, hg, oq, ov, oid, odep):
         torch.cuda.synchronize(dev)
         return (time.perf_counter() - t0) * 1e3
 
-    calls = {
-        "load_particles": timed(lambda: D.dust_load_particles(ctx.handle, *hq, *hv)),
-        "set_gas": timed(lambda: D.dust_set_gas(ctx.handle, hrho, *hg)),
-        "step": timed(lambda: D.dust_step(ctx.handle, w.dt)),
-        "get_particles": timed(lambda: D.dust_get_particles(ctx.handle, ngr, *oq, *ov, ids=oid)),
-        "get_deposit": timed(lambda: D.dust_get_deposit(ctx.handle, fixed=odep)),
-    }
+    calls = {}
+    for _ in range(2):
+        one = {
+            "load_particles_v32": timed(lambda: D.dust_load_particles_v32(ctx.handle, *hq, *hv)),
+            "set_gas": timed(lambda: D.dust_set_gas(ctx.handle, hrho, *hg)),
+            "step": timed(lambda: D.dust_step(ctx.handle, w.dt)),
+            "get_particles_v32": timed(lambda: D.dust_get_particles_v32(ctx.handle, ngr, *oq, *ov, ids=oid)),
+            "get_deposit": timed(lambda: D.dust_get_deposit(ctx.handle, fixed=odep)),
+        }
+        calls = {k: min(v, calls.get(k, v)) for k, v in one.items()}
     nb = ngr * 6
     host = torch.empty(nb, dtype=torch.float64).pin_memory()
     host2 = torch.empty(nb, dtype=torch.float64).pin_memory()

@@ -261,6 +261,19 @@ int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, const double
                         const double *v2, const uint8_t *species, const double *param,
                         int mem);
 
+/* dust_load_particles with float32 velocity arrays v0..v2 (coordinates stay
+ * float64): the grain state of Sec. 2 with velocities at the precision a
+ * DUST_MIXED context stores them in, so a host that keeps them as float32
+ * moves 12 bytes per grain fewer over the host link.  In a Cartesian or
+ * shearing-box DUST_MIXED context the stored grains equal those of
+ * dust_load_particles given the same velocities in float64; in curvilinear
+ * geometry the momentum-like variables are formed from the float32 value.
+ * Same layout, ownership, memory kinds and errors as dust_load_particles. */
+int dust_load_particles_v32(dust_ctx *ctx, int64_t n, const double *q0, const double *q1,
+                            const double *q2, const float *v0, const float *v1,
+                            const float *v2, const uint8_t *species, const double *param,
+                            int mem);
+
 /* Advance every grain by one step of size dt (dt may be negative: the
  * scheme is time reversible, Sec. 3.2.2) and deposit the back-reaction of
  * that step; with feedback_apply the deposit is then added to the gas
@@ -409,6 +422,15 @@ int dust_get_mass_deposit(dust_ctx *ctx, int64_t *fixed, double *as_double,
 int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
                        double *v0, double *v1, double *v2, int64_t *ids, int64_t *n_out,
                        int mem);
+
+/* dust_get_particles with float32 velocity arrays v0..v2 (coordinates stay
+ * float64): each velocity is the float64 value dust_get_particles returns,
+ * rounded to float32 (exact for the stored velocities of a Cartesian or
+ * shearing-box DUST_MIXED context).  Same order, arguments and errors as
+ * dust_get_particles. */
+int dust_get_particles_v32(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
+                           float *v0, float *v1, float *v2, int64_t *ids, int64_t *n_out,
+                           int mem);
 
 /* Wait for the context stream and return the per-group device times and
  * launch counts accumulated since the last reset; reset != 0 clears them. */

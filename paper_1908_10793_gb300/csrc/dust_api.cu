@@ -370,18 +370,20 @@ __global__ void get_gas_kernel(GridDev g, int geom, const Real *gas, double *rho
     if (v2) v2[c] = p2;
 }
 
-// Physical grain velocity -> momentum-like variables (Sec. 2.2).
-template <typename Real>
+// Physical grain velocity -> momentum-like variables (Sec. 2.2).  VT: the
+// type of the host's velocity arrays (double, or float for the store's own
+// precision in mixed contexts).
+template <typename Real, typename VT>
 __global__ void load_kernel(GridDev g, int geom, int64_t n, const double *q0, const double *q1,
-                            const double *q2, const double *v0, const double *v1,
-                            const double *v2, const uint8_t *species_in, int n_species,
+                            const double *q2, const VT *v0, const VT *v1,
+                            const VT *v2, const uint8_t *species_in, int n_species,
                             const double *param_in, StoreDev<Real> s, unsigned int *st,
                             int drop_bad)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const double x0 = q0[k], x1 = q1[k], x2 = q2[k];
-    double p0 = v0[k], p1 = v1[k], p2 = v2[k];
+    double p0 = (double)v0[k], p1 = (double)v1[k], p2 = (double)v2[k];
     bool bad = !(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(p0) &&
                  isfinite(p1) && isfinite(p2));
     bad |= !(x0 >= g.lo[0] && x0 < g.hi[0] && x1 >= g.lo[1] && x1 < g.hi[1] &&
@@ -417,10 +419,9 @@ __global__ void load_kernel(GridDev g, int geom, int64_t n, const double *q0, co
     }
 }
 
-template <typename Real>
+template <typename Real, typename VT>
 __global__ void get_particles_kernel(int geom, StoreDev<Real> s, double *q0, double *q1,
-                                     double *q2, double *v0, double *v1, double *v2,
-                                     int64_t *ids)
+                                     double *q2, VT *v0, VT *v1, VT *v2, int64_t *ids)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= s.n) return;
@@ -434,9 +435,9 @@ __global__ void get_particles_kernel(int geom, StoreDev<Real> s, double *q0, dou
     if (q0) q0[k] = x0;
     if (q1) q1[k] = x1;
     if (q2) q2[k] = x2;
-    if (v0) v0[k] = p0;
-    if (v1) v1[k] = p1;
-    if (v2) v2[k] = p2;
+    if (v0) v0[k] = (VT)p0;
+    if (v1) v1[k] = (VT)p1;
+    if (v2) v2[k] = (VT)p2;
     if (ids) ids[k] = s.id[k];
 }
 
@@ -573,12 +574,15 @@ struct GroupTimer {
 };
 
 // Copy `count` doubles from caller memory into staging slot `slot` (device).
-const double *stage_in(dust_ctx *ctx, const double *src, int64_t count, int slot, int mem)
+// Host array -> slot `slot` of the staging area (slots of count doubles; a
+// float array uses the first half of its slot).
+template <typename T>
+const T *stage_in(dust_ctx *ctx, const T *src, int64_t count, int slot, int mem)
 {
     if (!src) return nullptr;
     if (mem == DUST_MEM_DEVICE) return src;
-    double *dst = ctx->d_stage + (size_t)slot * count;
-    cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    T *dst = reinterpret_cast<T *>(ctx->d_stage + (size_t)slot * count);
+    cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
     return dst;
 }
 
@@ -1394,10 +1398,12 @@ extern "C" int dust_get_gas(dust_ctx *ctx, double *rho, double *v0, double *v1, 
     return DUST_OK;
 }
 
-extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, const double *q1,
-                                   const double *q2, const double *v0, const double *v1,
-                                   const double *v2, const uint8_t *species, const double *param,
-                                   int mem)
+// dust_load_particles and dust_load_particles_v32: VT is the type of the
+// velocity arrays.
+template <typename VT>
+int load_particles_impl(dust_ctx *ctx, int64_t n, const double *q0, const double *q1, const double *q2,
+                        const VT *v0, const VT *v1, const VT *v2, const uint8_t *species,
+                        const double *param, int mem)
 {
     if (!ctx) return DUST_EINVAL;
     if (n < 0 || n >= ((int64_t)1 << 31) - 1) return fail(ctx, DUST_EINVAL, "bad grain count");
@@ -1422,24 +1428,25 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
     ctx->gen += 1;
     if (n > 0) {
         const uint8_t *sp_dev = species;
-        const double *a, *b, *c, *d, *e, *f, *pp;
+        const double *a, *b, *c, *pp;
+        const VT *d, *e, *f;
         if (async) {
             // enqueue only: copies on the input stream; invalid grains are
             // dropped and reported by dust_sync
             int r = io_streams(ctx);
             if (r) return r;
-            const size_t nb = n * sizeof(double);
+            const size_t nb = n * sizeof(double), nv = n * sizeof(VT);
             const void *src[8] = {q0, q1, q2, v0, v1, v2, param, species};
-            const size_t by[8] = {nb, nb, nb, nb, nb, nb, nb, (size_t)n};
+            const size_t by[8] = {nb, nb, nb, nv, nv, nv, nb, (size_t)n};
             const void *dv[8];
             r = io_stage_in(ctx, ctx->in_grains, 8, src, by, dv);
             if (r) return r;
             a = static_cast<const double *>(dv[0]);
             b = static_cast<const double *>(dv[1]);
             c = static_cast<const double *>(dv[2]);
-            d = static_cast<const double *>(dv[3]);
-            e = static_cast<const double *>(dv[4]);
-            f = static_cast<const double *>(dv[5]);
+            d = static_cast<const VT *>(dv[3]);
+            e = static_cast<const VT *>(dv[4]);
+            f = static_cast<const VT *>(dv[5]);
             pp = static_cast<const double *>(dv[6]);
             sp_dev = static_cast<const uint8_t *>(dv[7]);
         } else {
@@ -1463,11 +1470,11 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
             CU(cudaMemsetAsync(ctx->d_status + ST_LOAD_BAD, 0, sizeof(unsigned), ctx->stream));
         }
         if (ctx->mixed)
-            load_kernel<float><<<blocks_for(n), 256, 0, ctx->stream>>>(
+            load_kernel<float, VT><<<blocks_for(n), 256, 0, ctx->stream>>>(
                 ctx->g, ctx->geom.kind, n, a, b, c, d, e, f, sp_dev, ctx->sp.n, pp,
                 store_of<float>(ctx, 0), ctx->d_status, async ? 1 : 0);
         else
-            load_kernel<double><<<blocks_for(n), 256, 0, ctx->stream>>>(
+            load_kernel<double, VT><<<blocks_for(n), 256, 0, ctx->stream>>>(
                 ctx->g, ctx->geom.kind, n, a, b, c, d, e, f, sp_dev, ctx->sp.n, pp,
                 store_of<double>(ctx, 0), ctx->d_status, async ? 1 : 0);
         CU(cudaGetLastError());
@@ -1489,6 +1496,22 @@ extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, c
     }
     ctx->particles_set = true;
     return DUST_OK;
+}
+
+extern "C" int dust_load_particles(dust_ctx *ctx, int64_t n, const double *q0, const double *q1,
+                                   const double *q2, const double *v0, const double *v1,
+                                   const double *v2, const uint8_t *species, const double *param,
+                                   int mem)
+{
+    return load_particles_impl<double>(ctx, n, q0, q1, q2, v0, v1, v2, species, param, mem);
+}
+
+extern "C" int dust_load_particles_v32(dust_ctx *ctx, int64_t n, const double *q0, const double *q1,
+                                       const double *q2, const float *v0, const float *v1,
+                                       const float *v2, const uint8_t *species, const double *param,
+                                       int mem)
+{
+    return load_particles_impl<float>(ctx, n, q0, q1, q2, v0, v1, v2, species, param, mem);
 }
 
 extern "C" int dust_step(dust_ctx *ctx, double dt)
@@ -1696,9 +1719,27 @@ extern "C" int dust_get_mass_deposit(dust_ctx *ctx, int64_t *fixed, double *as_d
     return DUST_OK;
 }
 
-extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
-                                  double *v0, double *v1, double *v2, int64_t *ids,
-                                  int64_t *n_out, int mem)
+// The read-back kernel into dev[0..5] (positions, then velocities of type VT)
+// and ids.
+template <typename VT>
+void launch_get_particles(dust_ctx *ctx, void *const dev[6], int64_t *dids)
+{
+    const int64_t n = ctx->n_grains;
+    double *q[3] = {static_cast<double *>(dev[0]), static_cast<double *>(dev[1]), static_cast<double *>(dev[2])};
+    VT *v[3] = {static_cast<VT *>(dev[3]), static_cast<VT *>(dev[4]), static_cast<VT *>(dev[5])};
+    if (ctx->mixed)
+        get_particles_kernel<float, VT><<<blocks_for(n), 256, 0, ctx->stream>>>(
+            ctx->geom.kind, store_of<float>(ctx, ctx->cur), q[0], q[1], q[2], v[0], v[1], v[2], dids);
+    else
+        get_particles_kernel<double, VT><<<blocks_for(n), 256, 0, ctx->stream>>>(
+            ctx->geom.kind, store_of<double>(ctx, ctx->cur), q[0], q[1], q[2], v[0], v[1], v[2], dids);
+}
+
+// dust_get_particles and dust_get_particles_v32: VT is the type of the
+// velocity arrays.
+template <typename VT>
+int get_particles_impl(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2, VT *v0, VT *v1,
+                       VT *v2, int64_t *ids, int64_t *n_out, int mem)
 {
     if (!ctx || !n_out) return DUST_EINVAL;
     *n_out = 0;
@@ -1706,8 +1747,11 @@ extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double
     if (cap < n) return fail(ctx, DUST_EINVAL, "capacity %lld < %lld grains", (long long)cap, (long long)n);
     if (n == 0) return DUST_OK;
     CU(cudaSetDevice(ctx->device));
-    double *outs[6] = {q0, q1, q2, v0, v1, v2};
-    double *dev[6] = {q0, q1, q2, v0, v1, v2};
+    // the velocity columns use the first half of their double-sized slots
+    // when VT is float
+    void *outs[6] = {q0, q1, q2, v0, v1, v2};
+    void *dev[6] = {q0, q1, q2, v0, v1, v2};
+    const size_t esz[6] = {sizeof(double), sizeof(double), sizeof(double), sizeof(VT), sizeof(VT), sizeof(VT)};
     int64_t *dids = ids;
     if (io_async(ctx, mem)) {
         // enqueue only: convert into one of two staging areas, read back on
@@ -1719,21 +1763,15 @@ extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double
         r = io_out_acquire(ctx, b, 7 * n * sizeof(double));
         if (r) return r;
         double *base = static_cast<double *>(b.d);
-        for (int k = 0; k < 6; ++k) dev[k] = outs[k] ? base + k * n : nullptr;
+        for (int k = 0; k < 6; ++k) dev[k] = outs[k] ? static_cast<void *>(base + k * n) : nullptr;
         dids = ids ? reinterpret_cast<int64_t *>(base + 6 * n) : nullptr;
-        if (ctx->mixed)
-            get_particles_kernel<float><<<blocks_for(n), 256, 0, ctx->stream>>>(
-                ctx->geom.kind, store_of<float>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3],
-                dev[4], dev[5], dids);
-        else
-            get_particles_kernel<double><<<blocks_for(n), 256, 0, ctx->stream>>>(
-                ctx->geom.kind, store_of<double>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3],
-                dev[4], dev[5], dids);
+        launch_get_particles<VT>(ctx, dev, dids);
         CU(cudaGetLastError());
         void *dst[7] = {q0, q1, q2, v0, v1, v2, ids};
         const void *src[7] = {dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dids};
-        const size_t nb = n * sizeof(double);
-        const size_t by[7] = {nb, nb, nb, nb, nb, nb, nb};
+        size_t by[7];
+        for (int k = 0; k < 6; ++k) by[k] = n * esz[k];
+        by[6] = n * sizeof(int64_t);
         r = io_stage_out(ctx, b, 7, dst, src, by);
         if (r) return r;
         *n_out = n;
@@ -1742,28 +1780,34 @@ extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double
     if (mem == DUST_MEM_HOST) {
         int r = ensure_stage(ctx, 7 * n * sizeof(double));
         if (r) return r;
-        for (int k = 0; k < 6; ++k) dev[k] = outs[k] ? ctx->d_stage + k * n : nullptr;
+        for (int k = 0; k < 6; ++k) dev[k] = outs[k] ? static_cast<void *>(ctx->d_stage + k * n) : nullptr;
         dids = ids ? reinterpret_cast<int64_t *>(ctx->d_stage + 6 * n) : nullptr;
     }
-    if (ctx->mixed)
-        get_particles_kernel<float><<<blocks_for(n), 256, 0, ctx->stream>>>(
-            ctx->geom.kind, store_of<float>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3], dev[4],
-            dev[5], dids);
-    else
-        get_particles_kernel<double><<<blocks_for(n), 256, 0, ctx->stream>>>(
-            ctx->geom.kind, store_of<double>(ctx, ctx->cur), dev[0], dev[1], dev[2], dev[3], dev[4],
-            dev[5], dids);
+    launch_get_particles<VT>(ctx, dev, dids);
     CU(cudaGetLastError());
     if (mem == DUST_MEM_HOST) {
         for (int k = 0; k < 6; ++k)
             if (outs[k])
-                CU(cudaMemcpyAsync(outs[k], dev[k], n * sizeof(double), cudaMemcpyDeviceToHost,
-                                   ctx->stream));
+                CU(cudaMemcpyAsync(outs[k], dev[k], n * esz[k], cudaMemcpyDeviceToHost, ctx->stream));
         if (ids) CU(cudaMemcpyAsync(ids, dids, n * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
     }
     CU(cudaStreamSynchronize(ctx->stream));
     *n_out = n;
     return DUST_OK;
+}
+
+extern "C" int dust_get_particles(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
+                                  double *v0, double *v1, double *v2, int64_t *ids,
+                                  int64_t *n_out, int mem)
+{
+    return get_particles_impl<double>(ctx, cap, q0, q1, q2, v0, v1, v2, ids, n_out, mem);
+}
+
+extern "C" int dust_get_particles_v32(dust_ctx *ctx, int64_t cap, double *q0, double *q1, double *q2,
+                                      float *v0, float *v1, float *v2, int64_t *ids,
+                                      int64_t *n_out, int mem)
+{
+    return get_particles_impl<float>(ctx, cap, q0, q1, q2, v0, v1, v2, ids, n_out, mem);
 }
 
 extern "C" const char *dust_last_error(const dust_ctx *ctx)

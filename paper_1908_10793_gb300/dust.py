@@ -94,11 +94,13 @@ def load_library():
         "dust_set_gas": (I, [P, P, P, P, P, I]),
         "dust_get_gas": (I, [P, P, P, P, P, I]),
         "dust_load_particles": (I, [P, I64, P, P, P, P, P, P, P, P, I]),
+        "dust_load_particles_v32": (I, [P, I64, P, P, P, P, P, P, P, P, I]),
         "dust_step": (I, [P, D]),
         "dust_sync": (I, [P, ctypes.POINTER(dust_stats)]),
         "dust_get_deposit": (I, [P, P, P, ctypes.POINTER(D), I]),
         "dust_get_mass_deposit": (I, [P, P, P, ctypes.POINTER(D), I]),
         "dust_get_particles": (I, [P, I64, P, P, P, P, P, P, P, ctypes.POINTER(I64), I]),
+        "dust_get_particles_v32": (I, [P, I64, P, P, P, P, P, P, P, ctypes.POINTER(I64), I]),
         "dust_get_kernel_times": (I, [P, ctypes.POINTER(dust_kernel_times), I]),
         "dust_step_noalloc": (I, [ctypes.POINTER(dust_geometry), ctypes.POINTER(dust_grid),
                                   ctypes.POINTER(dust_species), I, I, D, D, D, I64,
@@ -179,6 +181,15 @@ def dust_load_particles(ctx, q0, q1, q2, v0, v1, v2, species=None, param=None):
         _ptr(species)[0], _ptr(param)[0], mem))
 
 
+def dust_load_particles_v32(ctx, q0, q1, q2, v0, v1, v2, species=None, param=None):
+    """Velocities as float32 arrays (coordinates float64)."""
+    mem = _mem_of(q0, q1, q2, v0, v1, v2, species, param)
+    n = len(q0)
+    return _check(ctx, load_library().dust_load_particles_v32(
+        ctx, n, _ptr(q0)[0], _ptr(q1)[0], _ptr(q2)[0], _ptr(v0)[0], _ptr(v1)[0], _ptr(v2)[0],
+        _ptr(species)[0], _ptr(param)[0], mem))
+
+
 def dust_step(ctx, dt):
     return _check(ctx, load_library().dust_step(ctx, float(dt)))
 
@@ -211,6 +222,16 @@ def dust_get_particles(ctx, cap, q0=None, q1=None, q2=None, v0=None, v1=None, v2
     mem = _mem_of(q0, q1, q2, v0, v1, v2, ids)
     n = ctypes.c_int64()
     _check(ctx, load_library().dust_get_particles(
+        ctx, int(cap), _ptr(q0)[0], _ptr(q1)[0], _ptr(q2)[0], _ptr(v0)[0], _ptr(v1)[0],
+        _ptr(v2)[0], _ptr(ids)[0], ctypes.byref(n), mem))
+    return n.value
+
+
+def dust_get_particles_v32(ctx, cap, q0=None, q1=None, q2=None, v0=None, v1=None, v2=None, ids=None):
+    """Velocities into float32 arrays (coordinates float64)."""
+    mem = _mem_of(q0, q1, q2, v0, v1, v2, ids)
+    n = ctypes.c_int64()
+    _check(ctx, load_library().dust_get_particles_v32(
         ctx, int(cap), _ptr(q0)[0], _ptr(q1)[0], _ptr(q2)[0], _ptr(v0)[0], _ptr(v1)[0],
         _ptr(v2)[0], _ptr(ids)[0], ctypes.byref(n), mem))
     return n.value
