@@ -493,7 +493,6 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
         // the source positions of the first grains of the next pass; their
         // columns are prefetched after the push, ahead of that pass's loads
         int src_g = -1;
-        float dmax = 0.f;  // the largest |impulse channel| of this lane's grains in the pass
         if (P1 + lane < Gend) src_g = TA.perm ? TA.perm[P1 + lane] : P1 + lane;
         {
             // ---- push: one grain per lane, consecutive grains on consecutive
@@ -1000,15 +999,12 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 }
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) rb[(9 + ch) * kRecStride + slot] = grp_ok ? D[ch] : 0.f;
-                if (grp_ok)
-                    dmax = fmaxf(dmax, fmaxf(fmaxf(fabsf(D[0]), fabsf(D[1])), fmaxf(fabsf(D[2]), fabsf(D[3]))));
             }
             if (src_g >= 0) prefetch_grain(S, src_g);
             __syncwarp();
             // ---- deposit, ten zones of the pass at a time: the three owner
             // lanes of a zone accumulate its chunk in this pass (id order)
             // into their x slabs
-            const float dmaxw = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(dmax)));
             for (int z0 = zc; z0 < zc + nz; z0 += 10) {
                 const int zl = z0 + kq;
                 const bool kok = lane < 30 && zl < zc + nz;
@@ -1033,6 +1029,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                     for (int c = 0; c < NC; ++c)
 #pragma unroll
                         for (int hc = 0; hc < 2; ++hc) acc[b][c][hc] = make_float2(0.f, 0.f);
+                float Sabs = 0.f;  // sum over the chunk of the largest |channel| of each grain
                 if (own) {
                     const int sk = min(zl - zc, 15);
                     const int s0 = za - P0 + sk, s1 = zb - P0 + sk;
@@ -1054,6 +1051,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                         }
                         S2[0] = __fadd2_rn(S2[0], De01);
                         S2[1] = __fadd2_rn(S2[1], De23);
+                        Sabs += fmaxf(fmaxf(fabsf(De01.x), fabsf(De01.y)), fmaxf(fabsf(De23.x), fabsf(De23.y)));
                     };
                     int sl = s0;
                     for (; sl + 1 < s1; sl += 2) {
@@ -1068,15 +1066,13 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                 // predictor's impulse has no energy channel)
                 constexpr int NCH = PRED ? 3 : 4;
                 long long ps[4] = {0, 0, 0, 0};
-                // every chunk sum of a channel is at most the chunk's length
-                // times the largest |impulse channel| of the pass's grains (the
-                // weights lie in [0, 1]); below 2^31 (with a margin for the
-                // sums' rounding) the 32-bit rounding instruction gives the same
-                // integer as the 64-bit one, at a fraction of its cost on this
-                // GPU.  Decided for the whole warp, so that its lanes never run
-                // both forms.
-                const int mlen = __reduce_max_sync(FULL, own ? zb - za : 0);
-                const bool narrow = dmaxw * (float)mlen < 2147000000.f;
+                // every chunk sum of a channel is at most the sum of the grains'
+                // |impulse| in it (the weights lie in [0, 1]); below 2^31 (with a
+                // margin for the sums' rounding) the 32-bit rounding instruction
+                // gives the same integer as the 64-bit one, at a fraction of its
+                // cost on this GPU.  Decided for the whole warp, so that its
+                // lanes never run both forms.
+                const bool narrow = __all_sync(FULL, !own || Sabs < 2147000000.f);
                 auto quantise = [&](auto round_piece, auto add_piece) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
@@ -1118,12 +1114,8 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
                             }
 #pragma unroll
                         for (int ch = 0; ch < 4; ++ch) ps[ch] = ps32[ch];
-                    } else if (narrow) {
-                        quantise([](float v) { return (long long)__float2int_rn(v); },
-                                 [&](int ch, int lin, long long v) {
-                                     shared_add_i64_always(&sdep[ch * bvol + lin], v);
-                                 });
                     } else {
+                        // wide chunk sums, or a tile too dense for the split box
                         quantise([&](float v) {
                             big |= !(fabsf(v) < 4.5e15f);
                             return rround(v);
