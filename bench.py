@@ -384,8 +384,8 @@ def run_ours(args):
         ctx, te_async = run_e2e(1)
         ctx.close()
         ctx, te_sync = run_e2e(0)
-        h2d = ngr * (3 * 8 + 3 * 4) + w.ncell * 4 * 8
-        d2h = ngr * (3 * 8 + 3 * 4 + 8) + w.ncell * 4 * 8
+        h2d, d2h = e2e_bytes_per_step(ngr, w.ncell, v32=True)
+        h2d64, d2h64 = e2e_bytes_per_step(ngr, w.ncell, v32=False)
         e2e = {"value": weak_value(world, ngr * ke, te_async), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ke,
                "host_io": "asynchronous (dust_options.host_io_async = 1), pinned buffers; "
@@ -395,8 +395,7 @@ def run_ours(args):
                                      "ms_per_step": te_sync / ke * 1e3},
                "float64_velocities": {"value": weak_value(world, ngr * ke, te_f64),
                                       "ms_per_step": te_f64 / ke * 1e3,
-                                      "h2d_bytes_per_step": ngr * 6 * 8 + w.ncell * 4 * 8,
-                                      "d2h_bytes_per_step": ngr * (6 * 8 + 8) + w.ncell * 4 * 8},
+                                      "h2d_bytes_per_step": h2d64, "d2h_bytes_per_step": d2h64},
                "ms_per_step": te_async / ke * 1e3,
                "breakdown": e2e_breakdown(ctx, D, torch, dev, w, hq, hv32, hrho, hg, outs[0][0][:3],
                                           outs[0][3], outs[0][1], outs[0][2])}
@@ -518,6 +517,18 @@ def run_batch(args, D, torch, dev, stream):
             "workload": "64 2-D (x,z) orbital-advection shearing boxes, 32^2..512^2 zones, "
                         "1-16 grains/zone, St 0.01/0.1/1, dust/gas 0.01/0.02/0.1, TSC, "
                         "feedback on, mixed precision"}
+
+
+def e2e_bytes_per_step(ngrains, ncell, v32=True):
+    """Host-link bytes of one end-to-end step: in, the grains' coordinates
+    (float64) and velocities (float32 with v32, else float64) and the gas
+    (density and three velocity components, float64); out, the grains'
+    coordinates, velocities and int64 ids and the int64 deposit (four
+    channels per zone)."""
+    vb = 4 if v32 else 8
+    h2d = ngrains * (3 * 8 + 3 * vb) + ncell * 4 * 8
+    d2h = ngrains * (3 * 8 + 3 * vb + 8) + ncell * 4 * 8
+    return h2d, d2h
 
 
 def e2e_breakdown(ctx, D, torch, dev, w, hq, hv, hrho, hg, oq, ov, oid, odep):
