@@ -196,23 +196,27 @@ __device__ __forceinline__ void segments_block(const SA &A, int64_t vb, int32_t 
         return;
     }
     const unsigned FULL = 0xffffffffu;
-    // all loads first, then the shared stores: the loads' round trips overlap
-    int32_t rid[kSegStage / 32], rsrc[kSegStage / 32];
+    // all loads of a half first, then its shared stores: the loads' round
+    // trips overlap
+    constexpr int kHalf = kSegStage / 64;
 #pragma unroll
-    for (int r = 0; r < kSegStage / 32; ++r) {
-        const int32_t u = W0 + lane + 32 * r;
-        if (u < W1) {
-            rid[r] = A.pair_id[u];
-            rsrc[r] = A.pair_src[u];
+    for (int h = 0; h < 2; ++h) {
+        int32_t rid[kHalf], rsrc[kHalf];
+#pragma unroll
+        for (int r = 0; r < kHalf; ++r) {
+            const int32_t u = W0 + lane + 32 * (r + h * kHalf);
+            if (u < W1) {
+                rid[r] = A.pair_id[u];
+                rsrc[r] = A.pair_src[u];
+            }
         }
-    }
-    __syncwarp(FULL);
 #pragma unroll
-    for (int r = 0; r < kSegStage / 32; ++r) {
-        const int32_t u = W0 + lane + 32 * r;
-        if (u < W1) {
-            sid[warp][u - W0] = rid[r];
-            ssrc[warp][u - W0] = rsrc[r];
+        for (int r = 0; r < kHalf; ++r) {
+            const int32_t u = W0 + lane + 32 * (r + h * kHalf);
+            if (u < W1) {
+                sid[warp][u - W0] = rid[r];
+                ssrc[warp][u - W0] = rsrc[r];
+            }
         }
     }
     __syncwarp(FULL);
