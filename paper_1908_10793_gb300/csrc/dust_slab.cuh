@@ -57,7 +57,7 @@ __device__ __forceinline__ void prefetch_l2(const T *p)
 }
 
 // The grain columns a push reads at store position src, prefetched into L2
-// one push iteration (or one zone group) before they are read.
+// one push iteration (or one pass) before they are read.
 template <typename Store>
 __device__ __forceinline__ void prefetch_grain(const Store &S, int src)
 {
@@ -275,7 +275,7 @@ __device__ __noinline__ int32_t slab_predict_key(const GridDev &g, const PhysDev
 // persistent kernel): the tile ends with a block barrier and invalidates its
 // copy barrier, so that the shared memory can be reused.
 // TX > 0: the copy compiled for a TX x TY x TZ tile with TSC weights.  PRED: the gas
-// predictor instead of the step: the same groups, chunks and deposit into
+// predictor instead of the step: the same passes, chunks and deposit into
 // TA.s.dep, from the grains' drag impulse at x^n (nothing is moved).
 // Returns false when the wait for the gas box ran out (DUST_FLAG_TIMEOUT).
 template <int GEOM, int FLAT, int MODE, int TX = 0, int TY = 0, int TZ = 0, bool PRED = false>
@@ -309,7 +309,7 @@ __device__ __forceinline__ bool slab_tile(const TiledArgs<float> &TA, const int 
     const StoreDev<float> &S = A.s;
     const StoreDev<float> &O = TA.perm ? TA.dst : A.s;
     if (!PRED && (TA.emit_keys || TA.perm)) {
-        // grains removed before the last sort sit after every zone's group:
+        // grains removed before the last sort sit after every zone's segment:
         // they keep the removed-grain key and are moved as they are
         const int D0 = TA.key_off[g.nkeys], D1 = (int)A.s.n;
         for (int gi = D0 + tile * blockDim.x + threadIdx.x; gi < D1; gi += ntile * blockDim.x) {
