@@ -12,6 +12,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "host", "host_logic_check.cpp")
 WORKLIST = os.path.join(ROOT, "tests", "host", "worklist_check.cpp")
+SMEM = os.path.join(ROOT, "tests", "host", "smem_budget_check.cu")
 
 
 def _cuda_include():
@@ -45,3 +46,20 @@ def test_persistent_batch_work_list(tmp_path):
     earlier in the list, and the kernel's item decode finds every item
     once."""
     _run_check(tmp_path, WORKLIST, "worklist_check")
+
+
+def test_slab_shared_memory_allows_two_blocks_per_sm(tmp_path):
+    """The slab tile function's shared-memory layout (gas and deposit boxes,
+    zone tables, zone offsets, the per-warp slot table and record buffers)
+    for the tile shapes with compiled copies leaves room for two blocks per
+    SM; one block more of layout would halve the resident warps.  Compiled
+    with nvcc as host code (the layout function sits in a CUDA header)."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "smem_budget_check")
+    subprocess.check_call([nvcc, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"),
+                           "-I", os.path.join(ROOT, "paper_1908_10793_gb300", "csrc"),
+                           "-gencode", "arch=compute_103a,code=sm_103a", SMEM, "-o", exe])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
